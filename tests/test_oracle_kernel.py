@@ -1,0 +1,41 @@
+"""Pins of the Wendland kernel (paper Sec. 5.2) against closed forms."""
+import numpy as np
+from scipy import integrate
+
+from oracle import kernel
+
+
+def test_unit_integral():
+    # a smoothing kernel has unit integral: 4 pi int_0^2 w(q) q^2 dq = 1
+    val, err = integrate.quad(lambda q: 4 * np.pi * kernel.w(q) * q * q, 0.0, 2.0, epsabs=1e-14)
+    assert abs(val - 1.0) < 1e-12
+
+
+def test_unit_integral_scaled():
+    # W(r, h) = w(r/h)/h^3 integrates to one for any h
+    for h in (0.013, 0.5, 2.0):
+        val, _ = integrate.quad(lambda r: 4 * np.pi * kernel.W(r, h) * r * r, 0.0, 2 * h, epsabs=1e-14)
+        assert abs(val - 1.0) < 1e-10
+
+
+def test_f_is_derivative_over_q():
+    # F = (1/r) dW/dr  <=>  f(q) = w'(q) / q; central differences
+    q = np.linspace(0.05, 1.95, 39)
+    e = 1e-6
+    dw = (kernel.w(q + e) - kernel.w(q - e)) / (2 * e)
+    np.testing.assert_allclose(kernel.f(q), dw / q, rtol=1e-7, atol=1e-10)
+
+
+def test_support_edges_and_sign():
+    assert kernel.w(2.0) == 0.0 and kernel.f(2.0) == 0.0
+    assert kernel.w(2.5) == 0.0 and kernel.f(2.5) == 0.0
+    q = np.linspace(0, 1.999, 200)
+    assert np.all(kernel.f(q) < 0.0) and np.all(kernel.w(q) > 0.0)
+
+
+def test_second_moment_of_F():
+    # integration by parts: int r.grad W dV = -3 int W dV = -3, and r.grad W = r^2 F;
+    # this pins the h^5 scaling of F against the h^3 scaling of W
+    for h in (0.013, 1.0):
+        val, _ = integrate.quad(lambda r: 4 * np.pi * kernel.F(r, h) * r ** 4, 0.0, 2 * h, epsabs=1e-14)
+        assert abs(val + 3.0) < 1e-9
