@@ -1,0 +1,238 @@
+/*
+ * sphvisc: the semi-implicit viscous solve of SPH on one GB300 (sm_103a).
+ *
+ * C ABI of the library.  It implements the hot path of Bilotta et al.,
+ * "A numerically robust, parallel-friendly variant of BiCGSTAB for the
+ * semi-implicit integration of the viscous term in Smoothed Particle
+ * Hydrodynamics" (arXiv 2206.14780):
+ *
+ *   A(dt) V = B(dt)            Sec. 3.2, "Shared formulation"
+ *
+ * one sparse N x N matrix shared by the d = 3 velocity components, applied
+ * matrix-free over cell-list neighbours and solved with the restructured
+ * BiCGSTAB of Sec. 4.2.
+ *
+ * Conventions for every entry point:
+ *  - Pointers marked (device) are CUDA device pointers owned by the caller;
+ *    pointers marked (host) are host memory owned by the caller.  The library
+ *    never frees caller memory.
+ *  - Arrays are in the caller's particle order.  The library keeps its own
+ *    cell-sorted copy inside an opaque sph_neighbors handle.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it; entry points that return host-visible
+ *    results (reports, counts) synchronise that stream before returning.
+ *  - Every call returns an sph_status and never aborts.  On error the
+ *    thread-local message sph_last_error() says what failed.  Output buffers
+ *    are unspecified after an error.
+ *  - Device workspace is allocated by sph_build_neighbors / sph_visc_setup /
+ *    the first solve on a handle, and reused afterwards; it is released by
+ *    sph_neighbors_destroy.
+ */
+#ifndef SPHVISC_H
+#define SPHVISC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPH_OK = 0,
+  SPH_ERR_INVALID = 1,     /* bad argument (null pointer, size, box, option)      */
+  SPH_ERR_CUDA = 2,        /* a CUDA runtime call failed                           */
+  SPH_ERR_CAPACITY = 3,    /* a particle has more neighbours than max_neighbors    */
+  SPH_ERR_NONFINITE = 4,   /* NaN or Inf in an input or in the solver's scalars    */
+  SPH_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                   */
+  SPH_NOT_CONVERGED = 6,   /* maxit reached, or the true residual stayed above rtol */
+  SPH_ERR_NOMEM = 7        /* device allocation failed                             */
+} sph_status;
+
+/* particle types (the set F of fluid particles and W of boundary particles) */
+enum { SPH_FLUID = 0, SPH_WALL = 1 };
+/* boundary model: dummy (Adami; Eq. implicit-system-dummy-full) or dynamic
+   (Eq. implicit-system-dyn-full) */
+enum { SPH_BC_DUMMY = 0, SPH_BC_DYNAMIC = 1 };
+/* average viscosity mubar_ab (Sec. 2.3): harmonic 2 mu_a mu_b/(mu_a+mu_b) or
+   arithmetic (mu_a+mu_b)/2 */
+enum { SPH_MEAN_HARMONIC = 0, SPH_MEAN_ARITHMETIC = 1 };
+/* per-component solver states (Sec. 4.2, "Stopping criterion") */
+enum { SPH_CONVERGED = 0, SPH_STALLED = 1, SPH_PROGRESSING = 2 };
+/* solve precision */
+enum {
+  SPH_PREC_MIXED = 0,   /* FP32 operator/vectors, FP64 dots+scalars, FP64 refinement */
+  SPH_PREC_FP64 = 1     /* every vector and coefficient in FP64                      */
+};
+
+/* One particle set.  All arrays have n entries, caller order, (device). */
+typedef struct {
+  int64_t n;               /* number of particles (fluid + wall), >= 1          */
+  const float* pos;        /* [n][4]: x, y, z (m) and mass m (kg)               */
+  const float* rho;        /* [n]: density rho (kg/m^3), > 0                    */
+  const float* mu;         /* [n]: dynamic viscosity mu (Pa s), > 0; App. A
+                              advises storing mu rather than nu*rho             */
+  const uint8_t* ptype;    /* [n]: SPH_FLUID or SPH_WALL                        */
+  double lo[3], hi[3];     /* box; on a periodic axis hi-lo is the period and
+                              hi-lo >= 3 * 2h; particles on open axes may lie
+                              outside [lo, hi) (they are clamped into the edge
+                              cells, which keeps the search exact)              */
+  int32_t periodic[3];     /* 1 = periodic axis (minimum image)                 */
+  float h;                 /* smoothing length; Wendland support radius 2h      */
+} sph_scene;
+
+/* Opaque neighbour structure: cell-sorted particle copy, permutation and the
+   sliced-ELL neighbour lists (Sec. 5.2: a particle sees about 80 neighbours at
+   h = 1.3 dp; App. A: relative positions evaluated as one difference). */
+typedef struct sph_neighbors sph_neighbors;
+
+/* Build (or rebuild in place, if *handle is non-NULL) the neighbour lists.
+ * alpha is a neighbour of beta iff alpha != beta and |r_ab|^2 < (2h)^2, with
+ * r_ab the minimum image on periodic axes, decided exactly as in float64 on
+ * the float32 positions (a float32 test with a safety band, then a float64
+ * recheck inside the band).
+ * max_neighbors: capacity per particle, 1..1024; a larger count returns
+ *   SPH_ERR_CAPACITY.
+ * Copies pos/rho/mu/ptype into the handle: the scene arrays may be freed after
+ * the call returns. */
+sph_status sph_build_neighbors(const sph_scene* scene, int32_t max_neighbors,
+                               sph_neighbors** handle, void* stream);
+
+/* Host query: number of particles, total neighbour pairs, largest row. */
+sph_status sph_neighbors_info(const sph_neighbors* handle, int64_t* n, int64_t* nnz,
+                              int32_t* max_count);
+
+/* Export the lists as CSR in caller order with each row ascending.
+ * offsets (device) [n+1] int64; idx (device) [nnz] int32.  Synchronises. */
+sph_status sph_neighbors_export(const sph_neighbors* handle, int64_t* offsets, int32_t* idx,
+                                void* stream);
+
+/* Replace the per-particle viscosity (caller order, device [n]) without
+ * rebuilding the lists (the lagged viscosity of Sec. 3.3). */
+sph_status sph_set_viscosity(sph_neighbors* handle, const float* mu, void* stream);
+
+sph_status sph_neighbors_destroy(sph_neighbors* handle);
+
+/* Parameters of the viscous matrix A(dt) (Sec. 3.2). */
+typedef struct {
+  double dt;               /* time step of the implicit system, > 0              */
+  int32_t boundary;        /* SPH_BC_DUMMY or SPH_BC_DYNAMIC                      */
+  int32_t mean;            /* SPH_MEAN_HARMONIC or SPH_MEAN_ARITHMETIC            */
+} sph_visc_params;
+
+/* Compute and cache the matrix coefficients of A(dt) on the handle:
+ *   fluid row b:  A_bb = 1 + dt sum_a c_ab,  A_ba = -dt c_ab,
+ *                 c_ab = 2 mubar_ab m_a |F_ab| / (rho_a rho_b)   (Eq. kab;
+ *                 |F| reading: the printed signs make the rows anti-diffusive)
+ *                 a wall neighbour uses mubar = mu_b (the row's own mu)
+ *   dummy wall:   A_bb = 1, A_ba = W_ba / sum_{a' fluid} W_ba' over fluid a
+ *                 (Eq. implicit-system-dummy-full); an empty sum gives an
+ *                 identity row
+ *   dynamic wall: identity row (Eq. implicit-system-dyn-full)
+ * and the Jacobi diagonal (App. B).  Coefficients are computed in float64 and
+ * stored as a float32 pair (hi + lo).  Called implicitly by apply/solve when
+ * the parameters change. */
+sph_status sph_visc_setup(sph_neighbors* handle, const sph_visc_params* params, void* stream);
+
+/* y = A(dt) v in float32 (the operator of the inner iterations), with the
+ * fluid rows in the difference form v_b + dt sum_a c_ab (v_b - v_a).
+ * v, y: (device) [n][4] float (xyz, w ignored / written 0), caller order;
+ * v and y must not overlap. */
+sph_status sph_visc_apply(sph_neighbors* handle, const sph_visc_params* params, const float* v,
+                          float* y, void* stream);
+
+/* r = b - A(dt) x in float64 with the float64 coefficients (the true residual).
+ * x, b, r: (device) [n][3] double, caller order. */
+sph_status sph_visc_residual(sph_neighbors* handle, const sph_visc_params* params,
+                             const double* x, const double* b, double* r, void* stream);
+
+typedef struct {
+  double rtol;             /* accept when ||b - A x||_2 / ||b||_2 <= rtol (all
+                              three components jointly, float64 true residual);
+                              default 1e-6                                       */
+  double eps_inner;        /* relative tolerance of each inner BiCGSTAB pass on
+                              the Jacobi-scaled recursive residual; the paper's
+                              tau^2 = max(eps^2 b.b, FLT_MIN) (Sec. 4.1)          */
+  int32_t maxit;           /* cap on inner iterations summed over passes          */
+  int32_t max_refine;      /* cap on refinement passes                            */
+  int32_t precision;       /* SPH_PREC_MIXED or SPH_PREC_FP64                     */
+  int32_t merged_reductions; /* 0: three reductions per iteration, gamma and |r|^2
+                              from direct dots as the paper does; 1: two, with
+                              gamma' = r0^.r* - w r0^.Ar*, |r|^2 = |r*|^2 - 2w
+                              r*.Ar* + w^2 |Ar*|^2                               */
+  int32_t chunk;           /* iterations launched between host checks (>= 1)      */
+  int32_t jacobi;          /* 1: left Jacobi scaling (App. B); 0: none            */
+} sph_solve_opts;
+
+typedef struct {
+  int32_t status;          /* same value the call returns                        */
+  int32_t iters;           /* inner BiCGSTAB iterations, all passes              */
+  int32_t refinements;     /* inner passes run (true-residual recomputations - 1)*/
+  int8_t state[3];         /* last inner pass, per component (SPH_CONVERGED ...) */
+  int8_t stalled_any[3];   /* 1 if the component stalled in any pass             */
+  double true_rel_res;     /* ||b - A x||_2 / ||b||_2, float64, all components   */
+  double true_rel_res_c[3];/* per component (absolute residual if b_c = 0)       */
+} sph_solve_report;
+
+/* Solve A(dt) X = B with the restructured BiCGSTAB (Sec. 4.2): per iteration
+ *   p = r + beta p - alpha' A p;  delta = r0^.A p;  alpha = gamma/delta;
+ *   r* = r - alpha A p;  x += alpha p;  omega = (r*.Ar*)/(Ar*.Ar*);
+ *   r = r* - omega A r*;  x += omega r*;  gamma' = r0^.r;  alpha' = gamma'/delta;
+ *   beta = alpha'/omega
+ * with the paper's safeguards (delta = 0 sets alpha = alpha' = beta = 0 and the
+ * component is stalled; the iteration completes and there is one exit point)
+ * and the three per-component states.  In SPH_PREC_MIXED the iterations run in
+ * float32 with float64 dots and scalars inside iterative refinement on the
+ * float64 true residual.
+ * b: (device) [n][3] double, the right-hand side B (Sec. 3.2: u^n + dt(f_P+g)
+ *    for fluid rows, 2 u_w for dummy walls, u_w for dynamic walls).
+ * x: (device) [n][3] double; in: initial guess, out: solution.
+ * report: (host), filled before return.  Synchronises the stream.
+ * Returns SPH_OK, or SPH_NOT_CONVERGED (x holds the best iterate; the report
+ * says which components stalled). */
+sph_status sph_visc_solve(sph_neighbors* handle, const sph_visc_params* params,
+                          const sph_solve_opts* opts, const double* b, double* x,
+                          sph_solve_report* report, void* stream);
+
+/* Papanastasiou viscosity from the previous velocities (Sec. 2.4, Eq. papa):
+ *   grad u_b = sum_a V_a |F_ab| r_ab (x) u_ab;  gdot = sym(grad u);
+ *   D = sqrt(2 gdot:gdot);  mu_b = tau0 Ybar(D) + mu0,
+ * Ybar(D) = m T(m D) for m D < 0.5 (T: the paper's 8-term Horner series of
+ * (1 - e^-x)/x) and (1 - e^{-m D})/D above.  Wall neighbours contribute their
+ * wall velocity.  vel, wall_vel: (device) [n][4] float, caller order;
+ * mu_out: (device) [n] float, caller order (fluid rows; wall rows get mu0).
+ * Also stores the result as the handle's viscosity when set_handle != 0. */
+sph_status sph_mu_papanastasiou(sph_neighbors* handle, const float* vel, const float* wall_vel,
+                                double tau0, double mu0, double m, float* mu_out,
+                                int32_t set_handle, void* stream);
+
+/* Instrumentation (tracing): launch counts and the device time of the operator
+ * apply inside solves, measured with CUDA events recorded on the solve's own
+ * stream around every apply launch.  Off by default; enabling it adds two event
+ * records per apply. */
+typedef struct {
+  int64_t launches;        /* kernels this library launched (all handles, all calls) */
+  int64_t apply_launches;  /* operator applies timed on this handle                  */
+  double apply_ms;         /* summed device time of those applies (ms)               */
+  int64_t apply_bytes;     /* algorithmic bytes of one apply: 8 per stored
+                              coefficient (index + value) plus, per row, 16 read of
+                              v, 16 write of the result, 16 read of r0^ for the dot
+                              and 9 of row data (count, kind, 1/D)                  */
+  int64_t op_nnz;          /* stored coefficients of A(dt)                          */
+} sph_profile_counters;
+
+sph_status sph_profile_enable(sph_neighbors* handle, int32_t on);
+/* Reads the counters (synchronises the handle's last stream); reset != 0
+ * clears the per-handle timing after reading. */
+sph_status sph_profile_read(sph_neighbors* handle, sph_profile_counters* out, int32_t reset);
+
+/* Thread-local description of the last error (empty string if none). */
+const char* sph_last_error(void);
+
+/* Library version string. */
+const char* sph_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPHVISC_H */

@@ -1,0 +1,253 @@
+"""Thin ctypes binding of include/sphvisc.h (argument marshalling only).
+
+Every computation runs in libsphvisc.so; this module only converts torch
+tensors to device pointers and C structs, and raises on a non-OK status.
+There is no CPU fallback: if the library is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsphvisc.so")
+
+SPH_OK = 0
+STATUS = {0: "SPH_OK", 1: "SPH_ERR_INVALID", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_CAPACITY", 4: "SPH_ERR_NONFINITE",
+          5: "SPH_ERR_TIMEOUT", 6: "SPH_NOT_CONVERGED", 7: "SPH_ERR_NOMEM"}
+SPH_BC_DUMMY, SPH_BC_DYNAMIC = 0, 1
+SPH_MEAN_HARMONIC, SPH_MEAN_ARITHMETIC = 0, 1
+SPH_PREC_MIXED, SPH_PREC_FP64 = 0, 1
+SPH_CONVERGED, SPH_STALLED, SPH_PROGRESSING = 0, 1, 2
+
+# every symbol include/sphvisc.h declares
+EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", "sph_set_viscosity",
+           "sph_neighbors_destroy", "sph_visc_setup", "sph_visc_apply", "sph_visc_residual", "sph_visc_solve",
+           "sph_mu_papanastasiou", "sph_profile_enable", "sph_profile_read", "sph_last_error", "sph_version"]
+
+
+class sph_scene(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("pos", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("mu", ctypes.c_void_p),
+                ("ptype", ctypes.c_void_p), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("periodic", ctypes.c_int32 * 3), ("h", ctypes.c_float)]
+
+
+class sph_visc_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("boundary", ctypes.c_int32), ("mean", ctypes.c_int32)]
+
+
+class sph_solve_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("eps_inner", ctypes.c_double), ("maxit", ctypes.c_int32),
+                ("max_refine", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("merged_reductions", ctypes.c_int32), ("chunk", ctypes.c_int32), ("jacobi", ctypes.c_int32)]
+
+
+class sph_solve_report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("refinements", ctypes.c_int32),
+                ("state", ctypes.c_int8 * 3), ("stalled_any", ctypes.c_int8 * 3),
+                ("true_rel_res", ctypes.c_double), ("true_rel_res_c", ctypes.c_double * 3)]
+
+
+class sph_profile_counters(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("apply_launches", ctypes.c_int64), ("apply_ms", ctypes.c_double),
+                ("apply_bytes", ctypes.c_int64), ("op_nnz", ctypes.c_int64)]
+
+
+class SphError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsphvisc.so (built by paper_2206_14780_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2206_14780_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "sph_build_neighbors": [ctypes.POINTER(sph_scene), i32, ctypes.POINTER(vp), vp],
+        "sph_neighbors_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)],
+        "sph_neighbors_export": [vp, vp, vp, vp],
+        "sph_set_viscosity": [vp, vp, vp],
+        "sph_neighbors_destroy": [vp],
+        "sph_visc_setup": [vp, ctypes.POINTER(sph_visc_params), vp],
+        "sph_visc_apply": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp],
+        "sph_visc_residual": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp, vp],
+        "sph_visc_solve": [vp, ctypes.POINTER(sph_visc_params), ctypes.POINTER(sph_solve_opts), vp, vp,
+                           ctypes.POINTER(sph_solve_report), vp],
+        "sph_mu_papanastasiou": [vp, vp, vp, dbl, dbl, dbl, vp, i32, vp],
+        "sph_profile_enable": [vp, i32],
+        "sph_profile_read": [vp, ctypes.POINTER(sph_profile_counters), i32],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.sph_last_error.restype = ctypes.c_char_p
+    lib.sph_last_error.argtypes = []
+    lib.sph_version.restype = ctypes.c_char_p
+    lib.sph_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != SPH_OK:
+        raise SphError(status, _lib.sph_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def launch_count():
+    """Kernels launched by the library so far (process-wide)."""
+    load()
+    c = sph_profile_counters()
+    _check(_lib.sph_profile_read(None, ctypes.byref(c), 0))
+    return c.launches
+
+
+def visc_params(dt, boundary=SPH_BC_DUMMY, mean=SPH_MEAN_HARMONIC):
+    return sph_visc_params(float(dt), int(boundary), int(mean))
+
+
+def solve_opts(rtol=1e-6, eps_inner=1e-4, maxit=20000, max_refine=30, precision=SPH_PREC_MIXED,
+               merged_reductions=1, chunk=8, jacobi=1):
+    return sph_solve_opts(rtol, eps_inner, maxit, max_refine, precision, merged_reductions, chunk, jacobi)
+
+
+def scene_tensors(scene, device="cuda"):
+    """Copy a scene's particle arrays to the device (float32 pos[n,4], rho, mu, uint8 type)."""
+    import torch
+
+    return dict(pos=torch.from_numpy(np.ascontiguousarray(scene.pos, np.float32)).to(device),
+                rho=torch.from_numpy(np.ascontiguousarray(scene.rho, np.float32)).to(device),
+                mu=torch.from_numpy(np.ascontiguousarray(scene.mu, np.float32)).to(device),
+                ptype=torch.from_numpy(np.ascontiguousarray(scene.ptype, np.uint8)).to(device))
+
+
+class Neighbors:
+    """Owner of one sph_neighbors handle (sph_build_neighbors ... sph_neighbors_destroy)."""
+
+    def __init__(self, handle, n, keep):
+        self.handle = handle
+        self.n = n
+        self._keep = keep
+
+    def rebuild(self, pos, rho, mu, ptype, lo, hi, periodic, h, max_neighbors=128, stream=None):
+        """sph_build_neighbors on this handle (rebuild in place, keeps the workspace)."""
+        sc = _scene_struct(pos, rho, mu, ptype, lo, hi, periodic, h)
+        handle = ctypes.c_void_p(self.handle.value if isinstance(self.handle, ctypes.c_void_p) else self.handle)
+        _check(_lib.sph_build_neighbors(ctypes.byref(sc), int(max_neighbors), ctypes.byref(handle), _stream(stream)))
+        self.handle = handle
+        self.n = sc.n
+        self._keep = (pos, rho, mu, ptype)
+
+    def info(self):
+        n, nnz, mc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(_lib.sph_neighbors_info(self.handle, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(mc)))
+        return n.value, nnz.value, mc.value
+
+    def export(self, stream=None):
+        import torch
+
+        n, nnz, _ = self.info()
+        off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        idx = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+        _check(_lib.sph_neighbors_export(self.handle, _ptr(off), _ptr(idx), _stream(stream)))
+        return off, idx[:nnz]
+
+    def set_viscosity(self, mu, stream=None):
+        _check(_lib.sph_set_viscosity(self.handle, _ptr(mu), _stream(stream)))
+
+    def setup(self, params, stream=None):
+        _check(_lib.sph_visc_setup(self.handle, ctypes.byref(params), _stream(stream)))
+
+    def apply(self, params, v, y, stream=None):
+        _check(_lib.sph_visc_apply(self.handle, ctypes.byref(params), _ptr(v), _ptr(y), _stream(stream)))
+
+    def residual(self, params, x, b, r, stream=None):
+        _check(_lib.sph_visc_residual(self.handle, ctypes.byref(params), _ptr(x), _ptr(b), _ptr(r),
+                                      _stream(stream)))
+
+    def solve(self, params, opts, b, x, stream=None, raise_on_nonconvergence=False):
+        rep = sph_solve_report()
+        st = _lib.sph_visc_solve(self.handle, ctypes.byref(params), ctypes.byref(opts), _ptr(b), _ptr(x),
+                                 ctypes.byref(rep), _stream(stream))
+        if st not in (SPH_OK, 6) or (st == 6 and raise_on_nonconvergence):
+            _check(st)
+        return dict(status=st, iters=rep.iters, refinements=rep.refinements, state=list(rep.state),
+                    stalled_any=list(rep.stalled_any), true_rel_res=rep.true_rel_res,
+                    true_rel_res_c=list(rep.true_rel_res_c))
+
+    def mu_papanastasiou(self, vel, wall_vel, tau0, mu0, m, mu_out, set_handle=True, stream=None):
+        _check(_lib.sph_mu_papanastasiou(self.handle, _ptr(vel), _ptr(wall_vel), float(tau0), float(mu0), float(m),
+                                         _ptr(mu_out), int(bool(set_handle)), _stream(stream)))
+
+    def profile(self, on=True):
+        _check(_lib.sph_profile_enable(self.handle, int(bool(on))))
+
+    def profile_read(self, reset=False):
+        c = sph_profile_counters()
+        _check(_lib.sph_profile_read(self.handle, ctypes.byref(c), int(bool(reset))))
+        return dict(launches=c.launches, apply_launches=c.apply_launches, apply_ms=c.apply_ms,
+                    apply_bytes=c.apply_bytes, op_nnz=c.op_nnz)
+
+    def close(self):
+        if self.handle:
+            _lib.sph_neighbors_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _scene_struct(pos, rho, mu, ptype, lo, hi, periodic, h):
+    sc = sph_scene()
+    sc.n = int(pos.shape[0])
+    sc.pos, sc.rho, sc.mu, sc.ptype = _ptr(pos), _ptr(rho), _ptr(mu), _ptr(ptype)
+    for ax in range(3):
+        sc.lo[ax] = float(lo[ax])
+        sc.hi[ax] = float(hi[ax])
+        sc.periodic[ax] = int(periodic[ax])
+    sc.h = float(h)
+    return sc
+
+
+def build_neighbors(pos, rho, mu, ptype, lo, hi, periodic, h, max_neighbors=128, stream=None):
+    """sph_build_neighbors on device tensors; returns a Neighbors owner."""
+    load()
+    sc = _scene_struct(pos, rho, mu, ptype, lo, hi, periodic, h)
+    handle = ctypes.c_void_p()
+    _check(_lib.sph_build_neighbors(ctypes.byref(sc), int(max_neighbors), ctypes.byref(handle), _stream(stream)))
+    return Neighbors(handle, sc.n, keep=(pos, rho, mu, ptype))
+
+
+def build_for_scene(scene, max_neighbors=128, device="cuda", stream=None):
+    t = scene_tensors(scene, device)
+    return build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], scene.lo, scene.hi, scene.periodic, scene.h,
+                           max_neighbors, stream), t

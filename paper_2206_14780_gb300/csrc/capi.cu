@@ -1,0 +1,238 @@
+// extern "C" entry points of include/sphvisc.h: argument checks, dispatch and
+// the thread-local error message.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+static thread_local char g_err[512] = {0};
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void prof_begin(sph_neighbors* H, cudaStream_t st) {
+  if (!H->prof_on || H->prof_used + 2 > 256) return;
+  cudaEventRecord(H->prof_ev[H->prof_used], st);
+}
+void prof_end(sph_neighbors* H, cudaStream_t st) {
+  if (!H->prof_on || H->prof_used + 2 > 256) return;
+  cudaEventRecord(H->prof_ev[H->prof_used + 1], st);
+  H->prof_used += 2;
+}
+void prof_flush(sph_neighbors* H, int valid_pairs) {
+  if (!H->prof_on) return;
+  const int pairs = H->prof_used / 2;
+  for (int k = 0; k < pairs && k < valid_pairs; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, H->prof_ev[2 * k], H->prof_ev[2 * k + 1]) == cudaSuccess) {
+      H->prof_ms += ms;
+      H->prof_n += 1;
+    }
+  }
+  H->prof_used = 0;
+}
+
+sph_status set_viscosity_impl(sph_neighbors* H, const float* mu, cudaStream_t st);
+sph_status mu_papanastasiou(sph_neighbors* H, const float* vel, const float* wall_vel, double tau0, double mu0,
+                            double m, float* mu_out, int set_handle, cudaStream_t st);
+
+}  // namespace sph
+
+using namespace sph;
+
+static inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+const char* sph_last_error(void) { return g_err; }
+
+const char* sph_version(void) { return "sphvisc 0.1 (sm_103a)"; }
+
+sph_status sph_build_neighbors(const sph_scene* scene, int32_t max_neighbors, sph_neighbors** handle,
+                               void* stream) {
+  clear_error();
+  return build_neighbors(scene, max_neighbors, handle, as_stream(stream));
+}
+
+sph_status sph_neighbors_info(const sph_neighbors* h, int64_t* n, int64_t* nnz, int32_t* max_count) {
+  clear_error();
+  if (!h) {
+    set_error("sph_neighbors_info: null handle");
+    return SPH_ERR_INVALID;
+  }
+  if (n) *n = h->n;
+  if (nnz) *nnz = h->nnz;
+  if (max_count) *max_count = h->max_cnt;
+  return SPH_OK;
+}
+
+sph_status sph_neighbors_export(const sph_neighbors* h, int64_t* offsets, int32_t* idx, void* stream) {
+  clear_error();
+  return export_neighbors(h, offsets, idx, as_stream(stream));
+}
+
+sph_status sph_set_viscosity(sph_neighbors* h, const float* mu, void* stream) {
+  clear_error();
+  if (!h || !mu) {
+    set_error("sph_set_viscosity: null argument");
+    return SPH_ERR_INVALID;
+  }
+  return set_viscosity_impl(h, mu, as_stream(stream));
+}
+
+sph_status sph_neighbors_destroy(sph_neighbors* h) {
+  clear_error();
+  if (!h) return SPH_OK;
+  h->pos_s.release();
+  h->rho_s.release();
+  h->mu_s.release();
+  h->type_s.release();
+  h->perm.release();
+  h->iperm.release();
+  h->key_s.release();
+  h->cell_start.release();
+  h->cnt.release();
+  h->slice_off.release();
+  h->nbr.release();
+  h->op_cnt.release();
+  h->op_off.release();
+  h->op_idx.release();
+  h->op_hi.release();
+  h->op_lo.release();
+  h->op_kind.release();
+  h->invD.release();
+  h->D64.release();
+  h->tmp_i32a.release();
+  h->tmp_i32b.release();
+  h->tmp_i64.release();
+  h->flags.release();
+  h->v_r.release();
+  h->v_rh.release();
+  h->v_p.release();
+  h->v_Ap.release();
+  h->v_rs.release();
+  h->v_As.release();
+  h->v_d.release();
+  h->v_tmp.release();
+  h->x64.release();
+  h->b64.release();
+  h->r64.release();
+  h->partials.release();
+  h->counters.release();
+  h->scal.release();
+  for (auto& w : h->w64) w.release();
+  for (auto& e : h->prof_ev)
+    if (e) cudaEventDestroy(e);
+  if (h->host_scal) cudaFreeHost(h->host_scal);
+  if (h->host_flags) cudaFreeHost(h->host_flags);
+  delete h;
+  return SPH_OK;
+}
+
+sph_status sph_visc_setup(sph_neighbors* h, const sph_visc_params* params, void* stream) {
+  clear_error();
+  if (!h) {
+    set_error("sph_visc_setup: null handle");
+    return SPH_ERR_INVALID;
+  }
+  return ensure_operator(h, params, as_stream(stream));
+}
+
+sph_status sph_visc_apply(sph_neighbors* h, const sph_visc_params* params, const float* v, float* y,
+                          void* stream) {
+  clear_error();
+  if (v == y && v) {
+    set_error("sph_visc_apply: v and y must not overlap");
+    return SPH_ERR_INVALID;
+  }
+  return visc_apply(h, params, v, y, as_stream(stream));
+}
+
+sph_status sph_visc_residual(sph_neighbors* h, const sph_visc_params* params, const double* x, const double* b,
+                             double* r, void* stream) {
+  clear_error();
+  return visc_residual(h, params, x, b, r, as_stream(stream));
+}
+
+sph_status sph_visc_solve(sph_neighbors* h, const sph_visc_params* params, const sph_solve_opts* opts,
+                          const double* b, double* x, sph_solve_report* report, void* stream) {
+  clear_error();
+  if (!h || !params || !opts || !b || !x || !report) {
+    set_error("sph_visc_solve: null argument");
+    return SPH_ERR_INVALID;
+  }
+  if (opts->rtol < 0.0 || opts->eps_inner < 0.0 || opts->eps_inner >= 1.0 || opts->maxit < 0 ||
+      opts->max_refine < 0 || opts->chunk < 0) {
+    set_error("sph_visc_solve: invalid options (rtol >= 0, 0 <= eps_inner < 1, maxit/max_refine/chunk >= 0)");
+    return SPH_ERR_INVALID;
+  }
+  if (opts->precision == SPH_PREC_MIXED) return solve_mixed(h, params, opts, b, x, report, as_stream(stream));
+  if (opts->precision == SPH_PREC_FP64) return solve_fp64(h, params, opts, b, x, report, as_stream(stream));
+  set_error("sph_visc_solve: unknown precision %d", opts->precision);
+  return SPH_ERR_INVALID;
+}
+
+sph_status sph_mu_papanastasiou(sph_neighbors* h, const float* vel, const float* wall_vel, double tau0, double mu0,
+                                double m, float* mu_out, int32_t set_handle, void* stream) {
+  clear_error();
+  if (!h || !vel || !wall_vel || !mu_out) {
+    set_error("sph_mu_papanastasiou: null argument");
+    return SPH_ERR_INVALID;
+  }
+  if (!(tau0 >= 0.0) || !(mu0 > 0.0) || !(m > 0.0)) {
+    set_error("sph_mu_papanastasiou: need tau0 >= 0, mu0 > 0, m > 0");
+    return SPH_ERR_INVALID;
+  }
+  return mu_papanastasiou(h, vel, wall_vel, tau0, mu0, m, mu_out, set_handle, as_stream(stream));
+}
+
+sph_status sph_profile_enable(sph_neighbors* h, int32_t on) {
+  clear_error();
+  if (!h) {
+    set_error("sph_profile_enable: null handle");
+    return SPH_ERR_INVALID;
+  }
+  if (on) {
+    for (auto& e : h->prof_ev)
+      if (!e) SPH_TRY_CUDA(cudaEventCreate(&e));
+  }
+  h->prof_on = on != 0;
+  h->prof_used = 0;
+  return SPH_OK;
+}
+
+sph_status sph_profile_read(sph_neighbors* h, sph_profile_counters* out, int32_t reset) {
+  clear_error();
+  if (!out) {
+    set_error("sph_profile_read: null output");
+    return SPH_ERR_INVALID;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->launches = g_launches.load();
+  if (h) {
+    out->apply_launches = h->prof_n;
+    out->apply_ms = h->prof_ms;
+    out->op_nnz = h->op_nnz;
+    out->apply_bytes = 8 * h->op_nnz + (16 + 16 + 16 + 9) * h->n;
+    if (reset) {
+      h->prof_n = 0;
+      h->prof_ms = 0.0;
+    }
+  }
+  return SPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,371 @@
+// The viscous matrix A(dt) (paper Sec. 3.2), its float32 apply and its float64
+// true residual.
+//
+// Row kinds (stored per row):
+//   0 fluid    (A v)_b = v_b + sum_a a_ba (v_b - v_a),  a_ba = dt c_ab,
+//              c_ab = 2 mubar_ab m_a |F_ab| / (rho_a rho_b)      (Eqs. kab, diag, offdiag)
+//   1 Shepard  (A v)_b = v_b + sum_{a fluid} a_ba v_a,  a_ba = W_ba / S_b
+//              (dummy wall, Eq. implicit-system-dummy-full)
+//   2 identity (A v)_b = v_b  (dynamic wall; dummy wall with S_b = 0)
+// The fluid rows use the difference form: its float32 rounding stays relative
+// to the result even when dt sum c is in the thousands.
+//
+// Coefficients are evaluated once per (dt, boundary, mean, mu) in float64 and
+// kept as a float32 pair a = hi + lo: the float32 apply reads hi only, the
+// float64 residual reads hi + lo (relative error 2^-48).
+#include <cmath>
+
+#include "reduce.cuh"
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+enum : uint8_t { KIND_FLUID = 0, KIND_SHEPARD = 1, KIND_IDENTITY = 2 };
+
+struct OpGeom {
+  double L[3];
+  int periodic[3];
+  double h;
+  double inv_h;
+};
+
+// float64 relative position r_a - r_b with the minimum image (Sec. 2.2 / App. A)
+__device__ __forceinline__ double pair_r(float4 pa, float4 pb, const OpGeom& g) {
+  double d[3] = {(double)pa.x - (double)pb.x, (double)pa.y - (double)pb.y, (double)pa.z - (double)pb.z};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    if (g.periodic[ax]) d[ax] = d[ax] - g.L[ax] * rint(d[ax] / g.L[ax]);
+  }
+  return sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+}
+
+// Wendland psi_{3,1} (Sec. 5.2): w(q) = 21/(16 pi) (1 - q/2)^4 (2q + 1);
+// |f(q)| = 105/(128 pi) (2 - q)^3; both vanish for q >= 2.
+__device__ __forceinline__ double wendland_w(double q) {
+  if (q >= 2.0) return 0.0;
+  const double t = 1.0 - 0.5 * q;
+  const double t2 = t * t;
+  return (21.0 / (16.0 * M_PI)) * (t2 * t2) * (2.0 * q + 1.0);
+}
+__device__ __forceinline__ double wendland_absf(double q) {
+  if (q >= 2.0) return 0.0;
+  const double t = 2.0 - q;
+  return (105.0 / (128.0 * M_PI)) * (t * t * t);
+}
+
+__device__ __forceinline__ double mean_mu(double ma, double mb, int mean) {
+  return mean == SPH_MEAN_ARITHMETIC ? 0.5 * (ma + mb) : 2.0 * ma * mb / (ma + mb);
+}
+
+__global__ void k_op_count(const float4* __restrict__ pos, const uint8_t* __restrict__ type,
+                           const int32_t* __restrict__ cnt, const int64_t* __restrict__ slice_off,
+                           const int32_t* __restrict__ nbr, int64_t n, int64_t n_pad, OpGeom g, int boundary,
+                           int32_t* __restrict__ op_cnt, uint8_t* __restrict__ kind) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    if (s >= n) {
+      op_cnt[s] = 0;
+      kind[s] = KIND_IDENTITY;
+      continue;
+    }
+    const int c = cnt[s];
+    if (type[s] == SPH_FLUID) {
+      op_cnt[s] = c;
+      kind[s] = KIND_FLUID;
+      continue;
+    }
+    if (boundary != SPH_BC_DUMMY) {
+      op_cnt[s] = 0;
+      kind[s] = KIND_IDENTITY;
+      continue;
+    }
+    const float4 pb = pos[s];
+    const int64_t base = slice_off[s / kSlice] + (s % kSlice);
+    double S = 0.0;
+    int nf = 0;
+    for (int j = 0; j < c; ++j) {
+      const int32_t t = nbr[base + (int64_t)j * kSlice];
+      if (type[t] != SPH_FLUID) continue;
+      S += wendland_w(pair_r(pos[t], pb, g) * g.inv_h);
+      ++nf;
+    }
+    if (S > 0.0) {
+      op_cnt[s] = nf;
+      kind[s] = KIND_SHEPARD;
+    } else {
+      op_cnt[s] = 0;
+      kind[s] = KIND_IDENTITY;
+    }
+  }
+}
+
+__global__ void k_op_fill(const float4* __restrict__ pos, const float* __restrict__ rho, const float* __restrict__ mu,
+                          const uint8_t* __restrict__ type, const int32_t* __restrict__ cnt,
+                          const int64_t* __restrict__ slice_off, const int32_t* __restrict__ nbr,
+                          const uint8_t* __restrict__ kind, const int64_t* __restrict__ op_off, int64_t n,
+                          int64_t n_pad, OpGeom g, double dt, int mean, int32_t* __restrict__ op_idx,
+                          float* __restrict__ op_hi, float* __restrict__ op_lo, float* __restrict__ invD,
+                          double* __restrict__ D64) {
+  // 2 |f(q)| / h^5 folds into one float64 constant per scene
+  const double inv_h5 = g.inv_h * g.inv_h * g.inv_h * g.inv_h * g.inv_h;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    if (s >= n || kind[s] == KIND_IDENTITY) {
+      invD[s] = 1.f;
+      D64[s] = 1.0;
+      continue;
+    }
+    const float4 pb = pos[s];
+    const int c = cnt[s];
+    const int64_t base = slice_off[s / kSlice] + (s % kSlice);
+    const int64_t obase = op_off[s / kSlice] + (s % kSlice);
+    int o = 0;
+    if (kind[s] == KIND_FLUID) {
+      const double mub_self = (double)mu[s];
+      const double rho_b = (double)rho[s];
+      double sum = 0.0;
+      for (int j = 0; j < c; ++j) {
+        const int32_t t = nbr[base + (int64_t)j * kSlice];
+        const float4 pa = pos[t];
+        const double q = pair_r(pa, pb, g) * g.inv_h;
+        const double absF = wendland_absf(q) * inv_h5;
+        const double mub = (type[t] == SPH_FLUID) ? mean_mu((double)mu[t], mub_self, mean) : mub_self;
+        const double cab = 2.0 * mub * (double)pa.w * absF / ((double)rho[t] * rho_b);
+        const double a = dt * cab;
+        const float hi = __double2float_rn(a);
+        const float lo = __double2float_rn(a - (double)hi);
+        const int64_t e = obase + (int64_t)o * kSlice;
+        op_idx[e] = t;
+        op_hi[e] = hi;
+        op_lo[e] = lo;
+        sum += a;
+        ++o;
+      }
+      const double D = 1.0 + sum;
+      D64[s] = D;
+      invD[s] = __double2float_rn(1.0 / D);
+    } else {  // Shepard wall row: W_ba / S_b over fluid neighbours
+      double S = 0.0;
+      for (int j = 0; j < c; ++j) {
+        const int32_t t = nbr[base + (int64_t)j * kSlice];
+        if (type[t] != SPH_FLUID) continue;
+        S += wendland_w(pair_r(pos[t], pb, g) * g.inv_h);
+      }
+      const double invS = 1.0 / S;
+      for (int j = 0; j < c; ++j) {
+        const int32_t t = nbr[base + (int64_t)j * kSlice];
+        if (type[t] != SPH_FLUID) continue;
+        const double a = wendland_w(pair_r(pos[t], pb, g) * g.inv_h) * invS;
+        const float hi = __double2float_rn(a);
+        const float lo = __double2float_rn(a - (double)hi);
+        const int64_t e = obase + (int64_t)o * kSlice;
+        op_idx[e] = t;
+        op_hi[e] = hi;
+        op_lo[e] = lo;
+        ++o;
+      }
+      invD[s] = 1.f;
+      D64[s] = 1.0;
+    }
+  }
+}
+
+// y = A v (or D^-1 A v) in float32, one warp per 32-row slice, one row per lane.
+template <bool JACOBI>
+__global__ void __launch_bounds__(kBlock) k_apply_f32(const int64_t* __restrict__ op_off,
+                                                      const int32_t* __restrict__ op_cnt,
+                                                      const int32_t* __restrict__ op_idx,
+                                                      const float* __restrict__ op_hi,
+                                                      const uint8_t* __restrict__ kind,
+                                                      const float* __restrict__ invD, const float4* __restrict__ v,
+                                                      float4* __restrict__ y, int64_t nslices) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nwarps) {
+    const int64_t s = sl * kSlice + lane;
+    const int c = op_cnt[s];
+    const uint8_t k = kind[s];
+    const float4 vb = v[s];
+    const float kap = (k == KIND_FLUID) ? 1.f : 0.f;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    const int64_t base = op_off[sl] + lane;
+    for (int j = 0; j < c; ++j) {
+      const int64_t e = base + (int64_t)j * kSlice;
+      const int32_t t = op_idx[e];
+      const float a = op_hi[e];
+      const float4 va = v[t];
+      ax = fmaf(a, fmaf(kap, vb.x, -va.x), ax);
+      ay = fmaf(a, fmaf(kap, vb.y, -va.y), ay);
+      az = fmaf(a, fmaf(kap, vb.z, -va.z), az);
+    }
+    float4 out;
+    if (k == KIND_FLUID) {
+      const float sc = JACOBI ? invD[s] : 1.f;
+      out = make_float4((vb.x + ax) * sc, (vb.y + ay) * sc, (vb.z + az) * sc, 0.f);
+    } else if (k == KIND_SHEPARD) {
+      out = make_float4(vb.x - ax, vb.y - ay, vb.z - az, 0.f);
+    } else {
+      out = make_float4(vb.x, vb.y, vb.z, 0.f);
+    }
+    y[s] = out;
+  }
+}
+
+__global__ void k_gather_f4(const float* __restrict__ v_caller, const int32_t* __restrict__ perm, int64_t n,
+                            int64_t n_pad, float4* __restrict__ v_s) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    if (s < n) {
+      const float4 t = reinterpret_cast<const float4*>(v_caller)[perm[s]];
+      v_s[s] = make_float4(t.x, t.y, t.z, 0.f);
+    } else {
+      v_s[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+__global__ void k_scatter_f4(const float4* __restrict__ y_s, const int32_t* __restrict__ perm, int64_t n,
+                             float* __restrict__ y_caller) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+    reinterpret_cast<float4*>(y_caller)[perm[s]] = y_s[s];
+}
+
+}  // namespace
+
+// float64 residual r = b - A x on sorted [n_pad][3] arrays; partial sums of
+// r_c^2 (K = 3) go through the grid reduction into res_out[0..3) when given.
+__global__ void __launch_bounds__(kBlock) k_residual_f64(const int64_t* __restrict__ op_off,
+                                                         const int32_t* __restrict__ op_cnt,
+                                                         const int32_t* __restrict__ op_idx,
+                                                         const float* __restrict__ op_hi,
+                                                         const float* __restrict__ op_lo,
+                                                         const uint8_t* __restrict__ kind,
+                                                         const double* __restrict__ x, const double* __restrict__ b,
+                                                         double* __restrict__ r, int64_t n, int64_t nslices,
+                                                         double* __restrict__ partials, unsigned int* counter,
+                                                         double* __restrict__ res_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double acc2[3] = {0.0, 0.0, 0.0};
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nwarps) {
+    const int64_t s = sl * kSlice + lane;
+    const int c = op_cnt[s];
+    const uint8_t k = kind[s];
+    const double xb0 = x[3 * s], xb1 = x[3 * s + 1], xb2 = x[3 * s + 2];
+    const double kap = (k == KIND_FLUID) ? 1.0 : 0.0;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    const int64_t base = op_off[sl] + lane;
+    for (int j = 0; j < c; ++j) {
+      const int64_t e = base + (int64_t)j * kSlice;
+      const int32_t t = op_idx[e];
+      const double a = (double)op_hi[e] + (double)op_lo[e];
+      a0 += a * (kap * xb0 - x[3 * t]);
+      a1 += a * (kap * xb1 - x[3 * t + 1]);
+      a2 += a * (kap * xb2 - x[3 * t + 2]);
+    }
+    double y0 = xb0, y1 = xb1, y2 = xb2;
+    if (k == KIND_FLUID) {
+      y0 += a0; y1 += a1; y2 += a2;
+    } else if (k == KIND_SHEPARD) {
+      y0 -= a0; y1 -= a1; y2 -= a2;
+    }
+    double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+    if (s < n) {
+      r0 = b[3 * s] - y0;
+      r1 = b[3 * s + 1] - y1;
+      r2 = b[3 * s + 2] - y2;
+    }
+    r[3 * s] = r0;
+    r[3 * s + 1] = r1;
+    r[3 * s + 2] = r2;
+    acc2[0] += r0 * r0;
+    acc2[1] += r1 * r1;
+    acc2[2] += r2 * r2;
+  }
+  if (partials == nullptr) return;
+  block_partials_f64<3>(acc2, partials + (size_t)blockIdx.x * kMaxDots);
+  if (arrive_last(counter)) {
+    __shared__ double res[3];
+    final_sum<3>(partials, counter, res);
+    if (threadIdx.x < 3) res_out[threadIdx.x] = res[threadIdx.x];
+  }
+}
+
+sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStream_t st) {
+  if (!P || !(P->dt > 0.0) || !std::isfinite(P->dt) || (P->boundary != SPH_BC_DUMMY && P->boundary != SPH_BC_DYNAMIC) ||
+      (P->mean != SPH_MEAN_HARMONIC && P->mean != SPH_MEAN_ARITHMETIC)) {
+    set_error("viscous parameters: dt must be positive and finite, boundary/mean one of the enums");
+    return SPH_ERR_INVALID;
+  }
+  if (H->op_valid && H->op_params.dt == P->dt && H->op_params.boundary == P->boundary &&
+      H->op_params.mean == P->mean && H->op_mu_version == H->mu_version)
+    return SPH_OK;
+  OpGeom g{};
+  for (int ax = 0; ax < 3; ++ax) {
+    g.L[ax] = H->grid.L[ax];
+    g.periodic[ax] = H->grid.periodic[ax];
+  }
+  g.h = (double)H->h;
+  g.inv_h = 1.0 / g.h;
+  SPH_TRY(H->op_cnt.alloc(H->n_pad));
+  SPH_TRY(H->op_kind.alloc(H->n_pad));
+  SPH_TRY(H->op_off.alloc(H->nslices + 1));
+  SPH_TRY(H->invD.alloc(H->n_pad));
+  SPH_TRY(H->D64.alloc(H->n_pad));
+  const int grid = grid_for(H, H->n_pad);
+  SPH_LAUNCH(k_op_count, grid, kBlock, 0, st)(H->pos_s.p, H->type_s.p, H->cnt.p, H->slice_off.p, H->nbr.p, H->n, H->n_pad, g,
+                                      P->boundary, H->op_cnt.p, H->op_kind.p);
+  SPH_TRY_CUDA(cudaGetLastError());
+  int64_t total_pad = 0, total = 0;
+  int32_t maxc = 0;
+  SPH_TRY(build_slices(H, H->op_cnt.p, H->op_off.p, &total_pad, &total, &maxc, st));
+  SPH_TRY(H->op_idx.alloc(total_pad > 0 ? total_pad : 1));
+  SPH_TRY(H->op_hi.alloc(total_pad > 0 ? total_pad : 1));
+  SPH_TRY(H->op_lo.alloc(total_pad > 0 ? total_pad : 1));
+  H->op_nnz_pad = total_pad;
+  H->op_nnz = total;
+  SPH_LAUNCH(k_op_fill, grid, kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->type_s.p, H->cnt.p, H->slice_off.p,
+                                     H->nbr.p, H->op_kind.p, H->op_off.p, H->n, H->n_pad, g, P->dt, P->mean,
+                                     H->op_idx.p, H->op_hi.p, H->op_lo.p, H->invD.p, H->D64.p);
+  SPH_TRY_CUDA(cudaGetLastError());
+  H->op_valid = true;
+  H->op_params = *P;
+  H->op_mu_version = H->mu_version;
+  return SPH_OK;
+}
+
+void launch_residual_f64(const sph_neighbors* H, int grid, const double* x, const double* b, double* r,
+                         double* partials, unsigned int* counter, double* res_out, cudaStream_t st) {
+  SPH_LAUNCH(k_residual_f64, grid, kBlock, 0, st)(H->op_off.p, H->op_cnt.p, H->op_idx.p, H->op_hi.p, H->op_lo.p,
+                                          H->op_kind.p, x, b, r, H->n, H->nslices, partials, counter, res_out);
+}
+
+void launch_apply_f32(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st) {
+  const int grid = grid_for(H, H->nslices * 32);
+  if (jacobi)
+    SPH_LAUNCH(k_apply_f32<true>, grid, kBlock, 0, st)(H->op_off.p, H->op_cnt.p, H->op_idx.p, H->op_hi.p, H->op_kind.p,
+                                               H->invD.p, v, y, H->nslices);
+  else
+    SPH_LAUNCH(k_apply_f32<false>, grid, kBlock, 0, st)(H->op_off.p, H->op_cnt.p, H->op_idx.p, H->op_hi.p, H->op_kind.p,
+                                                H->invD.p, v, y, H->nslices);
+}
+
+sph_status visc_apply(sph_neighbors* H, const sph_visc_params* P, const float* v, float* y, cudaStream_t st) {
+  if (!H || !v || !y) {
+    set_error("sph_visc_apply: null argument");
+    return SPH_ERR_INVALID;
+  }
+  SPH_TRY(ensure_operator(H, P, st));
+  SPH_TRY(H->v_tmp.alloc(2 * H->n_pad));
+  float4* vs = H->v_tmp.p;
+  float4* ys = H->v_tmp.p + H->n_pad;
+  const int grid = grid_for(H, H->n_pad);
+  SPH_LAUNCH(k_gather_f4, grid, kBlock, 0, st)(v, H->perm.p, H->n, H->n_pad, vs);
+  SPH_TRY_CUDA(cudaGetLastError());
+  launch_apply_f32(H, vs, ys, false, st);
+  SPH_TRY_CUDA(cudaGetLastError());
+  SPH_LAUNCH(k_scatter_f4, grid, kBlock, 0, st)(ys, H->perm.p, H->n, y);
+  SPH_TRY_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+}  // namespace sph

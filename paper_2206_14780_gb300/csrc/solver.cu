@@ -1,0 +1,609 @@
+// Restructured BiCGSTAB (paper Sec. 4.2) with the per-component stopping logic,
+// run as float32 passes inside float64 iterative refinement.
+//
+// One inner pass solves (D^-1 A) d = D^-1 r64 for the three components at once.
+// Iteration i (restructured listing of Sec. 4.2):
+//   p     = r + beta p - alpha' A p           (a zero coefficient skips its vector)
+//   delta = r0^ . A p ;  alpha = gamma / delta
+//   r*    = r - alpha A p ;  d += alpha p
+//   omega = (r* . A r*) / (A r* . A r*)
+//   r     = r* - omega A r* ;  d += omega r*
+//   gamma' = r0^ . r ;  alpha' = gamma' / delta ;  beta = alpha' / omega
+// delta = 0 (or non-finite) sets alpha = alpha' = beta = 0 and marks the
+// component stalled; the iteration still completes; the pass stops when no
+// component is progressing (converged: r.r < tau^2; stalled) -- one exit point.
+// A component that is no longer progressing is frozen (alpha = omega = 0).
+//
+// Kernels of one iteration (each grid-wide dot goes through the last-block
+// reduction of reduce.cuh, so no extra launch and no host round trip):
+//   paper-exact (merged_reductions = 0):
+//     k_p_update, k_apply_dot<DELTA>, k_rstar, k_apply_dot<OMEGA>, k_xr_update(+gamma', r.r)
+//   merged (= 1): gamma' and r.r from the omega reduction, and the p update of
+//     the next iteration fused into the x/r update:
+//     k_apply_dot<DELTA>, k_rstar, k_apply_dot<OMEGA_MERGED>, k_xrp_update
+//
+// Outer loop: r64 = b - A x in float64 (hi + lo coefficients), stop when
+// ||r64|| / ||b|| <= rtol, else run a pass on D^-1 r64 and add d to x (float64).
+#include <cmath>
+#include <cstring>
+
+#include "reduce.cuh"
+#include "sph_internal.cuh"
+
+namespace sph {
+
+
+namespace {
+
+constexpr double kFltMin = 1.17549435082228750797e-38;  // 2^-126
+
+enum Phase : int { PH_DELTA = 0, PH_OMEGA = 1, PH_OMEGA_MERGED = 2 };
+
+struct Vecs {
+  float4* r;
+  float4* rh;
+  float4* p;
+  float4* Ap;
+  float4* rs;
+  float4* As;
+  float4* d;
+};
+
+struct OpView {
+  const int64_t* off;
+  const int32_t* cnt;
+  const int32_t* idx;
+  const float* hi;
+  const uint8_t* kind;
+  const float* invD;
+  int64_t nslices;
+  int64_t n_pad;
+};
+
+
+// ---- scalar updates (thread 0 of the last block) -------------------------
+
+__device__ void scal_after_delta(SolverScalars* S, const double* dots) {
+  for (int c = 0; c < 3; ++c) {
+    if (S->state[c] != SPH_PROGRESSING) {
+      S->alpha[c] = 0.0;
+      S->stall_now[c] = 0;
+      continue;
+    }
+    const double d = dots[c];
+    S->delta[c] = d;
+    double a = 0.0;
+    int stall = 0;
+    if (d == 0.0 || !isfinite(d)) {
+      stall = 1;
+    } else {
+      a = S->gamma[c] / d;
+      if (!isfinite(a)) {
+        a = 0.0;
+        stall = 1;
+      }
+    }
+    S->alpha[c] = a;
+    S->stall_now[c] = stall;
+  }
+}
+
+__device__ void scal_after_omega(SolverScalars* S, const double* dots) {
+  for (int c = 0; c < 3; ++c) {
+    if (S->state[c] != SPH_PROGRESSING) {
+      S->omega[c] = 0.0;
+      continue;
+    }
+    const double sA = dots[c], AA = dots[3 + c];
+    double om = (AA > 0.0 && isfinite(AA)) ? sA / AA : 0.0;
+    if (!isfinite(om)) om = 0.0;
+    S->omega[c] = om;
+  }
+}
+
+// gamma' and r.r known: alpha', beta, states, iteration count, stop flag.
+__device__ void scal_after_update(SolverScalars* S, const double* gam_new, const double* rr) {
+  int progressing = 0;
+  for (int c = 0; c < 3; ++c) {
+    if (S->state[c] != SPH_PROGRESSING) {
+      S->alpha_p[c] = 0.0;
+      S->beta[c] = 0.0;
+      continue;
+    }
+    const double om = S->omega[c];
+    const bool ok = !S->stall_now[c] && om != 0.0;
+    double ap = ok ? gam_new[c] / S->delta[c] : 0.0;
+    double be = ok ? ap / om : 0.0;
+    if (!isfinite(ap) || !isfinite(be)) {
+      ap = 0.0;
+      be = 0.0;
+    }
+    if (!isfinite(gam_new[c]) || !isfinite(rr[c])) S->nonfinite = 1;
+    S->alpha_p[c] = ap;
+    S->beta[c] = be;
+    S->gamma[c] = gam_new[c];
+    S->rr[c] = rr[c];
+    int st;
+    if (rr[c] < S->tau2[c]) st = SPH_CONVERGED;
+    else if (S->stall_now[c] || om == 0.0 || !isfinite(rr[c])) st = SPH_STALLED;
+    else st = SPH_PROGRESSING;
+    if (st == SPH_STALLED) S->stalled_any[c] = 1;
+    S->state[c] = st;
+    progressing += (st == SPH_PROGRESSING);
+  }
+  S->iter += 1;
+  S->done = (progressing == 0 || S->iter >= S->maxit) ? 1 : 0;
+}
+
+// ---- kernels ----------------------------------------------------------------
+
+// r = rh = float32(r64 / D) (Jacobi) and d = 0; then gamma = tau^2 base = r.r
+__global__ void __launch_bounds__(kBlock) k_pass_init(const double* __restrict__ r64, const double* __restrict__ D64,
+                                                      int jacobi, int64_t n_pad, Vecs V, double eps2, int maxit,
+                                                      SolverScalars* S, double* partials, unsigned int* counter) {
+  double accd[3] = {0.0, 0.0, 0.0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    const double sc = jacobi ? 1.0 / D64[s] : 1.0;
+    const float4 r = make_float4((float)(r64[3 * s] * sc), (float)(r64[3 * s + 1] * sc), (float)(r64[3 * s + 2] * sc),
+                                 0.f);
+    V.r[s] = r;
+    V.rh[s] = r;
+    V.d[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    accd[0] += (double)r.x * r.x;
+    accd[1] += (double)r.y * r.y;
+    accd[2] += (double)r.z * r.z;
+  }
+  block_partials_f64<3>(accd, partials + (size_t)blockIdx.x * kMaxDots);
+  if (arrive_last(counter)) {
+    __shared__ double res[3];
+    final_sum<3>(partials, counter, res);
+    if (threadIdx.x == 0) {
+      int progressing = 0;
+      for (int c = 0; c < 3; ++c) {
+        const double g = res[c];
+        S->gamma[c] = g;
+        S->rr[c] = g;
+        S->tau2[c] = fmax(eps2 * g, kFltMin);
+        S->alpha[c] = S->alpha_p[c] = S->beta[c] = S->omega[c] = S->delta[c] = 0.0;
+        S->stall_now[c] = 0;
+        S->stalled_any[c] = 0;
+        const int st = (g == 0.0 || g < S->tau2[c]) ? SPH_CONVERGED : SPH_PROGRESSING;
+        S->state[c] = st;
+        progressing += (st == SPH_PROGRESSING);
+      }
+      S->iter = 0;
+      S->maxit = maxit;
+      S->nonfinite = 0;
+      S->done = progressing == 0 ? 1 : 0;
+      S->pad = S->done;   // "skip" flag of the fused completion kernel
+    }
+  }
+}
+
+// p = r + beta p - alpha' Ap
+__global__ void __launch_bounds__(kBlock) k_p_update(int64_t n_pad, Vecs V, const SolverScalars* __restrict__ S) {
+  if (S->done) return;
+  const float b0 = (float)S->beta[0], b1 = (float)S->beta[1], b2 = (float)S->beta[2];
+  const float a0 = (float)S->alpha_p[0], a1 = (float)S->alpha_p[1], a2 = (float)S->alpha_p[2];
+  const bool useP = (b0 != 0.f) || (b1 != 0.f) || (b2 != 0.f);
+  const bool useA = (a0 != 0.f) || (a1 != 0.f) || (a2 != 0.f);
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    float4 p = V.r[s];
+    if (useP) {
+      const float4 q = V.p[s];
+      p.x = fmaf(b0, q.x, p.x);
+      p.y = fmaf(b1, q.y, p.y);
+      p.z = fmaf(b2, q.z, p.z);
+    }
+    if (useA) {
+      const float4 q = V.Ap[s];
+      p.x = fmaf(-a0, q.x, p.x);
+      p.y = fmaf(-a1, q.y, p.y);
+      p.z = fmaf(-a2, q.z, p.z);
+    }
+    p.w = 0.f;
+    V.p[s] = p;
+  }
+}
+
+// y = D^-1 A v with the dots of the phase.
+//   PH_DELTA:        v = p,  y = Ap; dots r0^.Ap                       (K = 3)
+//   PH_OMEGA:        v = r*, y = Ar*; dots r*.Ar*, Ar*.Ar*             (K = 6)
+//   PH_OMEGA_MERGED: + r0^.r*, r0^.Ar*, r*.r*                          (K = 15)
+template <int PH>
+__global__ void __launch_bounds__(kBlock) k_apply_dot(OpView op, const float4* __restrict__ v, float4* __restrict__ y,
+                                                      const float4* __restrict__ rh, SolverScalars* S,
+                                                      double* partials, unsigned int* counter) {
+  constexpr int K = PH == PH_DELTA ? 3 : (PH == PH_OMEGA ? 6 : 15);
+  if (S->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.f;
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
+    const int64_t s = sl * kSlice + lane;
+    const int c = op.cnt[s];
+    const uint8_t kd = op.kind[s];
+    const float4 vb = v[s];
+    const float kap = (kd == 0) ? 1.f : 0.f;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    const int64_t base = op.off[sl] + lane;
+    for (int j = 0; j < c; ++j) {
+      const int64_t e = base + (int64_t)j * kSlice;
+      const int32_t t = op.idx[e];
+      const float a = op.hi[e];
+      const float4 va = v[t];
+      ax = fmaf(a, fmaf(kap, vb.x, -va.x), ax);
+      ay = fmaf(a, fmaf(kap, vb.y, -va.y), ay);
+      az = fmaf(a, fmaf(kap, vb.z, -va.z), az);
+    }
+    float4 o;
+    if (kd == 0) {
+      const float sc = op.invD[s];
+      o = make_float4((vb.x + ax) * sc, (vb.y + ay) * sc, (vb.z + az) * sc, 0.f);
+    } else if (kd == 1) {
+      o = make_float4(vb.x - ax, vb.y - ay, vb.z - az, 0.f);
+    } else {
+      o = make_float4(vb.x, vb.y, vb.z, 0.f);
+    }
+    y[s] = o;
+    const float4 h = rh[s];
+    if (PH == PH_DELTA) {
+      acc[0] = fmaf(h.x, o.x, acc[0]);
+      acc[1] = fmaf(h.y, o.y, acc[1]);
+      acc[2] = fmaf(h.z, o.z, acc[2]);
+    } else {
+      acc[0] = fmaf(vb.x, o.x, acc[0]);
+      acc[1] = fmaf(vb.y, o.y, acc[1]);
+      acc[2] = fmaf(vb.z, o.z, acc[2]);
+      acc[3] = fmaf(o.x, o.x, acc[3]);
+      acc[4] = fmaf(o.y, o.y, acc[4]);
+      acc[5] = fmaf(o.z, o.z, acc[5]);
+      if (PH == PH_OMEGA_MERGED) {
+        acc[6] = fmaf(h.x, vb.x, acc[6]);
+        acc[7] = fmaf(h.y, vb.y, acc[7]);
+        acc[8] = fmaf(h.z, vb.z, acc[8]);
+        acc[9] = fmaf(h.x, o.x, acc[9]);
+        acc[10] = fmaf(h.y, o.y, acc[10]);
+        acc[11] = fmaf(h.z, o.z, acc[11]);
+        acc[12] = fmaf(vb.x, vb.x, acc[12]);
+        acc[13] = fmaf(vb.y, vb.y, acc[13]);
+        acc[14] = fmaf(vb.z, vb.z, acc[14]);
+      }
+    }
+  }
+  block_partials<K>(acc, partials + (size_t)blockIdx.x * kMaxDots);
+  if (arrive_last(counter)) {
+    __shared__ double res[K];
+    final_sum<K>(partials, counter, res);
+    if (threadIdx.x == 0) {
+      if (PH == PH_DELTA) {
+        scal_after_delta(S, res);
+      } else {
+        scal_after_omega(S, res);
+        if (PH == PH_OMEGA_MERGED) {
+          double gn[3], rr[3];
+          for (int c = 0; c < 3; ++c) {
+            const double om = S->omega[c];
+            gn[c] = res[6 + c] - om * res[9 + c];
+            rr[c] = res[12 + c] - 2.0 * om * res[c] + om * om * res[3 + c];
+          }
+          scal_after_update(S, gn, rr);
+        }
+      }
+    }
+  }
+}
+
+// r* = r - alpha Ap ; d += alpha p
+__global__ void __launch_bounds__(kBlock) k_rstar(int64_t n_pad, Vecs V, const SolverScalars* __restrict__ S) {
+  if (S->done) return;
+  const float a0 = (float)S->alpha[0], a1 = (float)S->alpha[1], a2 = (float)S->alpha[2];
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    const float4 r = V.r[s], ap = V.Ap[s], p = V.p[s];
+    float4 d = V.d[s];
+    V.rs[s] = make_float4(fmaf(-a0, ap.x, r.x), fmaf(-a1, ap.y, r.y), fmaf(-a2, ap.z, r.z), 0.f);
+    d.x = fmaf(a0, p.x, d.x);
+    d.y = fmaf(a1, p.y, d.y);
+    d.z = fmaf(a2, p.z, d.z);
+    V.d[s] = d;
+  }
+}
+
+// r = r* - omega Ar* ; d += omega r* ; dots r0^.r, r.r (paper-exact gamma')
+__global__ void __launch_bounds__(kBlock) k_xr_update(int64_t n_pad, Vecs V, SolverScalars* S, double* partials,
+                                                      unsigned int* counter) {
+  if (S->done) return;
+  const float w0 = (float)S->omega[0], w1 = (float)S->omega[1], w2 = (float)S->omega[2];
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    const float4 rs = V.rs[s], as = V.As[s], h = V.rh[s];
+    float4 d = V.d[s];
+    const float4 r = make_float4(fmaf(-w0, as.x, rs.x), fmaf(-w1, as.y, rs.y), fmaf(-w2, as.z, rs.z), 0.f);
+    d.x = fmaf(w0, rs.x, d.x);
+    d.y = fmaf(w1, rs.y, d.y);
+    d.z = fmaf(w2, rs.z, d.z);
+    V.r[s] = r;
+    V.d[s] = d;
+    acc[0] = fmaf(h.x, r.x, acc[0]);
+    acc[1] = fmaf(h.y, r.y, acc[1]);
+    acc[2] = fmaf(h.z, r.z, acc[2]);
+    acc[3] = fmaf(r.x, r.x, acc[3]);
+    acc[4] = fmaf(r.y, r.y, acc[4]);
+    acc[5] = fmaf(r.z, r.z, acc[5]);
+  }
+  block_partials<6>(acc, partials + (size_t)blockIdx.x * kMaxDots);
+  if (arrive_last(counter)) {
+    __shared__ double res[6];
+    final_sum<6>(partials, counter, res);
+    if (threadIdx.x == 0) scal_after_update(S, res, res + 3);
+  }
+}
+
+// merged form: r = r* - omega Ar* ; d += omega r* ; p = r + beta p - alpha' Ap.
+// Runs for the iteration whose omega kernel set the stop flag too (the
+// iteration completes); `pad` carries "skip" and is re-armed by the last block.
+__global__ void __launch_bounds__(kBlock) k_xrp_update(int64_t n_pad, Vecs V, SolverScalars* S,
+                                                       unsigned int* counter) {
+  if (S->pad) return;
+  const float w0 = (float)S->omega[0], w1 = (float)S->omega[1], w2 = (float)S->omega[2];
+  const float b0 = (float)S->beta[0], b1 = (float)S->beta[1], b2 = (float)S->beta[2];
+  const float a0 = (float)S->alpha_p[0], a1 = (float)S->alpha_p[1], a2 = (float)S->alpha_p[2];
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    const float4 rs = V.rs[s], as = V.As[s], p = V.p[s], ap = V.Ap[s];
+    float4 d = V.d[s];
+    const float4 r = make_float4(fmaf(-w0, as.x, rs.x), fmaf(-w1, as.y, rs.y), fmaf(-w2, as.z, rs.z), 0.f);
+    d.x = fmaf(w0, rs.x, d.x);
+    d.y = fmaf(w1, rs.y, d.y);
+    d.z = fmaf(w2, rs.z, d.z);
+    V.r[s] = r;
+    V.d[s] = d;
+    V.p[s] = make_float4(fmaf(-a0, ap.x, fmaf(b0, p.x, r.x)), fmaf(-a1, ap.y, fmaf(b1, p.y, r.y)),
+                         fmaf(-a2, ap.z, fmaf(b2, p.z, r.z)), 0.f);
+  }
+  if (arrive_last(counter)) {
+    if (threadIdx.x == 0) {
+      S->pad = S->done;
+      *counter = 0u;
+    }
+  }
+}
+
+// x64 += d
+__global__ void k_add_correction(int64_t n_pad, const float4* __restrict__ d, double* __restrict__ x) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = d[s];
+    x[3 * s] += (double)v.x;
+    x[3 * s + 1] += (double)v.y;
+    x[3 * s + 2] += (double)v.z;
+  }
+}
+
+__global__ void k_gather_d3(const double* __restrict__ src, const int32_t* __restrict__ perm, int64_t n, int64_t n_pad,
+                            double* __restrict__ dst) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    if (s < n) {
+      const int64_t i = perm[s];
+      dst[3 * s] = src[3 * i];
+      dst[3 * s + 1] = src[3 * i + 1];
+      dst[3 * s + 2] = src[3 * i + 2];
+    } else {
+      dst[3 * s] = dst[3 * s + 1] = dst[3 * s + 2] = 0.0;
+    }
+  }
+}
+
+__global__ void k_scatter_d3(const double* __restrict__ src, const int32_t* __restrict__ perm, int64_t n,
+                             double* __restrict__ dst) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = perm[s];
+    dst[3 * i] = src[3 * s];
+    dst[3 * i + 1] = src[3 * s + 1];
+    dst[3 * i + 2] = src[3 * s + 2];
+  }
+}
+
+// squares per component of an [n_pad][3] float64 array, grid-reduced into out[3]
+__global__ void __launch_bounds__(kBlock) k_norm2_d3(const double* __restrict__ a, int64_t n_pad, double* partials,
+                                                     unsigned int* counter, double* out) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    acc[0] += a[3 * s] * a[3 * s];
+    acc[1] += a[3 * s + 1] * a[3 * s + 1];
+    acc[2] += a[3 * s + 2] * a[3 * s + 2];
+  }
+  block_partials_f64<3>(acc, partials + (size_t)blockIdx.x * kMaxDots);
+  if (arrive_last(counter)) {
+    __shared__ double res[3];
+    final_sum<3>(partials, counter, res);
+    if (threadIdx.x < 3) out[threadIdx.x] = res[threadIdx.x];
+  }
+}
+
+}  // namespace
+
+// Counters: one per reduction site, so consecutive kernels never share one.
+enum { CNT_INIT = 0, CNT_DELTA, CNT_OMEGA, CNT_XR, CNT_XRP, CNT_RES, CNT_NORM, CNT_COUNT };
+
+sph_status ensure_workspace(sph_neighbors* H) {
+  const int64_t np = H->n_pad;
+  SPH_TRY(H->v_r.alloc(np));
+  SPH_TRY(H->v_rh.alloc(np));
+  SPH_TRY(H->v_p.alloc(np));
+  SPH_TRY(H->v_Ap.alloc(np));
+  SPH_TRY(H->v_rs.alloc(np));
+  SPH_TRY(H->v_As.alloc(np));
+  SPH_TRY(H->v_d.alloc(np));
+  SPH_TRY(H->x64.alloc(3 * np));
+  SPH_TRY(H->b64.alloc(3 * np));
+  SPH_TRY(H->r64.alloc(3 * np));
+  if (H->red_grid == 0) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply_dot<PH_OMEGA_MERGED>, kBlock, 0);
+    if (occ < 1) occ = 1;
+    H->red_grid = H->num_sms * occ;
+  }
+  SPH_TRY(H->partials.alloc((size_t)H->red_grid * kMaxDots));
+  if (!H->counters.p) {
+    SPH_TRY(H->counters.alloc(CNT_COUNT));
+    SPH_TRY_CUDA(cudaMemset(H->counters.p, 0, CNT_COUNT * sizeof(unsigned int)));
+  }
+  SPH_TRY(H->scal.alloc(1));
+  if (!H->host_scal) SPH_TRY_CUDA(cudaMallocHost(reinterpret_cast<void**>(&H->host_scal), sizeof(SolverScalars)));
+  if (!H->host_flags) SPH_TRY_CUDA(cudaMallocHost(reinterpret_cast<void**>(&H->host_flags), 64));
+  return SPH_OK;
+}
+
+static int red_grid_for(const sph_neighbors* H, int64_t items) {
+  int64_t want = (items + kBlock - 1) / kBlock;
+  if (want > H->red_grid) want = H->red_grid;
+  return want < 1 ? 1 : (int)want;
+}
+
+// r64 = b64 - A x64 and rr[3] into H->host_flags area (synchronises)
+static sph_status true_residual(sph_neighbors* H, cudaStream_t st, double rr[3]) {
+  const int grid = red_grid_for(H, H->n_pad);
+  double* dev_out = reinterpret_cast<double*>(H->scal.p) + offsetof(SolverScalars, dots) / sizeof(double);
+  launch_residual_f64(H, grid, H->x64.p, H->b64.p, H->r64.p, H->partials.p, H->counters.p + CNT_RES, dev_out, st);
+  SPH_TRY_CUDA(cudaGetLastError());
+  SPH_TRY_CUDA(cudaMemcpyAsync(rr, dev_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SPH_TRY_CUDA(cudaStreamSynchronize(st));
+  return SPH_OK;
+}
+
+sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_solve_opts* O, const double* b,
+                       double* x, sph_solve_report* R, cudaStream_t st) {
+  SPH_TRY(ensure_operator(H, P, st));
+  SPH_TRY(ensure_workspace(H));
+  const int64_t np = H->n_pad;
+  const int grid_rows = red_grid_for(H, np);
+  const int grid_slices = red_grid_for(H, H->nslices * 32);
+  Vecs V{H->v_r.p, H->v_rh.p, H->v_p.p, H->v_Ap.p, H->v_rs.p, H->v_As.p, H->v_d.p};
+  OpView op{H->op_off.p, H->op_cnt.p, H->op_idx.p, H->op_hi.p, H->op_kind.p, H->invD.p, H->nslices, np};
+  SolverScalars* S = H->scal.p;
+  unsigned int* C = H->counters.p;
+
+  SPH_LAUNCH(k_gather_d3, grid_for(H, np), kBlock, 0, st)(b, H->perm.p, H->n, np, H->b64.p);
+  SPH_LAUNCH(k_gather_d3, grid_for(H, np), kBlock, 0, st)(x, H->perm.p, H->n, np, H->x64.p);
+  SPH_TRY_CUDA(cudaGetLastError());
+  double* dev_dots = reinterpret_cast<double*>(S) + offsetof(SolverScalars, dots) / sizeof(double);
+  SPH_LAUNCH(k_norm2_d3, grid_rows, kBlock, 0, st)(H->b64.p, np, H->partials.p, C + CNT_NORM, dev_dots);
+  SPH_TRY_CUDA(cudaGetLastError());
+  double bb[3];
+  SPH_TRY_CUDA(cudaMemcpyAsync(bb, dev_dots, sizeof(bb), cudaMemcpyDeviceToHost, st));
+  SPH_TRY_CUDA(cudaStreamSynchronize(st));
+  const double bnorm = std::sqrt(bb[0] + bb[1] + bb[2]);
+
+  const double rtol = O->rtol > 0.0 ? O->rtol : 1e-6;
+  const double eps = O->eps_inner > 0.0 ? O->eps_inner : 1e-4;
+  const int maxit = O->maxit > 0 ? O->maxit : 10000;
+  const int max_ref = O->max_refine > 0 ? O->max_refine : 20;
+  const int chunk0 = O->chunk > 0 ? O->chunk : 8;
+  const bool merged = O->merged_reductions != 0;
+  const int jacobi = O->jacobi ? 1 : 0;
+
+  std::memset(R, 0, sizeof(*R));
+  int total_iters = 0, passes = 0;
+  double rr[3] = {0, 0, 0};
+  sph_status status = SPH_NOT_CONVERGED;
+  for (int ref = 0;; ++ref) {
+    SPH_TRY(true_residual(H, st, rr));
+    if (!std::isfinite(rr[0]) || !std::isfinite(rr[1]) || !std::isfinite(rr[2])) {
+      set_error("sph_visc_solve: the true residual is not finite");
+      status = SPH_ERR_NONFINITE;
+      break;
+    }
+    const double rnorm = std::sqrt(rr[0] + rr[1] + rr[2]);
+    if (rnorm <= rtol * bnorm) {
+      status = SPH_OK;
+      break;
+    }
+    if (ref >= max_ref || total_iters >= maxit) break;
+    // inner pass
+    SPH_LAUNCH(k_pass_init, grid_rows, kBlock, 0, st)(H->r64.p, H->D64.p, jacobi, np, V, eps * eps, maxit - total_iters, S,
+                                              H->partials.p, C + CNT_INIT);
+    SPH_TRY_CUDA(cudaGetLastError());
+    if (merged) SPH_LAUNCH(k_p_update, grid_rows, kBlock, 0, st)(np, V, S);
+    int chunk = chunk0;
+    int iter_seen = 0;
+    for (;;) {
+      for (int it = 0; it < chunk; ++it) {
+        if (!merged) SPH_LAUNCH(k_p_update, grid_rows, kBlock, 0, st)(np, V, S);
+        prof_begin(H, st);
+        SPH_LAUNCH(k_apply_dot<PH_DELTA>, grid_slices, kBlock, 0, st)(op, V.p, V.Ap, V.rh, S, H->partials.p, C + CNT_DELTA);
+        prof_end(H, st);
+        SPH_LAUNCH(k_rstar, grid_rows, kBlock, 0, st)(np, V, S);
+        if (merged) {
+          prof_begin(H, st);
+          SPH_LAUNCH(k_apply_dot<PH_OMEGA_MERGED>, grid_slices, kBlock, 0, st)(op, V.rs, V.As, V.rh, S, H->partials.p,
+                                                                        C + CNT_OMEGA);
+          prof_end(H, st);
+          SPH_LAUNCH(k_xrp_update, grid_rows, kBlock, 0, st)(np, V, S, C + CNT_XRP);
+        } else {
+          prof_begin(H, st);
+          SPH_LAUNCH(k_apply_dot<PH_OMEGA>, grid_slices, kBlock, 0, st)(op, V.rs, V.As, V.rh, S, H->partials.p,
+                                                                 C + CNT_OMEGA);
+          prof_end(H, st);
+          SPH_LAUNCH(k_xr_update, grid_rows, kBlock, 0, st)(np, V, S, H->partials.p, C + CNT_XR);
+        }
+      }
+      SPH_TRY_CUDA(cudaGetLastError());
+      SPH_TRY_CUDA(cudaMemcpyAsync(H->host_scal, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
+      SPH_TRY_CUDA(cudaStreamSynchronize(st));
+      prof_flush(H, 2 * (H->host_scal->iter - iter_seen));
+      iter_seen = H->host_scal->iter;
+      if (H->host_scal->done) break;
+      chunk = chunk < 64 ? chunk * 2 : chunk;
+    }
+    const SolverScalars& hs = *H->host_scal;
+    total_iters += hs.iter;
+    passes++;
+    for (int c = 0; c < 3; ++c) {
+      R->state[c] = (int8_t)hs.state[c];
+      R->stalled_any[c] |= (int8_t)hs.stalled_any[c];
+    }
+    SPH_LAUNCH(k_add_correction, grid_for(H, np), kBlock, 0, st)(np, V.d, H->x64.p);
+    SPH_TRY_CUDA(cudaGetLastError());
+    if (hs.iter == 0) {  // nothing progressed: a further pass would repeat it
+      SPH_TRY(true_residual(H, st, rr));
+      const double rnorm2 = std::sqrt(rr[0] + rr[1] + rr[2]);
+      status = rnorm2 <= rtol * bnorm ? SPH_OK : SPH_NOT_CONVERGED;
+      break;
+    }
+  }
+  SPH_LAUNCH(k_scatter_d3, grid_for(H, H->n), kBlock, 0, st)(H->x64.p, H->perm.p, H->n, x);
+  SPH_TRY_CUDA(cudaGetLastError());
+  SPH_TRY_CUDA(cudaStreamSynchronize(st));
+  R->iters = total_iters;
+  R->refinements = passes;
+  R->true_rel_res = bnorm > 0.0 ? std::sqrt(rr[0] + rr[1] + rr[2]) / bnorm : std::sqrt(rr[0] + rr[1] + rr[2]);
+  for (int c = 0; c < 3; ++c)
+    R->true_rel_res_c[c] = bb[c] > 0.0 ? std::sqrt(rr[c] / bb[c]) : std::sqrt(rr[c]);
+  R->status = status;
+  if (status == SPH_NOT_CONVERGED)
+    set_error("sph_visc_solve: true residual %.3e above rtol %.1e after %d iterations / %d passes",
+              R->true_rel_res, rtol, total_iters, passes);
+  return status;
+}
+
+sph_status visc_residual(sph_neighbors* H, const sph_visc_params* P, const double* x, const double* b, double* r,
+                         cudaStream_t st) {
+  if (!H || !x || !b || !r) {
+    set_error("sph_visc_residual: null argument");
+    return SPH_ERR_INVALID;
+  }
+  SPH_TRY(ensure_operator(H, P, st));
+  SPH_TRY(ensure_workspace(H));
+  const int64_t np = H->n_pad;
+  SPH_LAUNCH(k_gather_d3, grid_for(H, np), kBlock, 0, st)(b, H->perm.p, H->n, np, H->b64.p);
+  SPH_LAUNCH(k_gather_d3, grid_for(H, np), kBlock, 0, st)(x, H->perm.p, H->n, np, H->x64.p);
+  SPH_TRY_CUDA(cudaGetLastError());
+  double rr[3];
+  SPH_TRY(true_residual(H, st, rr));
+  SPH_LAUNCH(k_scatter_d3, grid_for(H, H->n), kBlock, 0, st)(H->r64.p, H->perm.p, H->n, r);
+  SPH_TRY_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+}  // namespace sph

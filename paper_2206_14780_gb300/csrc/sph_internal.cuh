@@ -1,0 +1,207 @@
+// Internal declarations of the sphvisc library (not part of the C ABI).
+//
+// Data layout in HBM (all in the cell-sorted particle order "s"):
+//   pos_s   float4[n_pad]   x, y, z, m
+//   rho_s, mu_s float[n_pad]; type_s uint8[n_pad]
+//   perm    int32[n]        sorted -> caller index;  iperm: caller -> sorted
+//   neighbour lists: sliced ELL with slices of 32 rows (SELL-32): row s of
+//   slice k = s / 32 keeps its j-th entry at slice_off[k] + 32 j + (s % 32),
+//   so a warp reading entry j of its 32 rows touches 128 consecutive bytes.
+//   The operator keeps its own SELL-32 (only the entries with a coefficient).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/sphvisc.h"
+
+namespace sph {
+
+constexpr int kSlice = 32;        // rows per SELL slice (one warp)
+constexpr int kBlock = 256;       // threads per block of the row kernels
+constexpr int kMaxDots = 15;      // float64 partial sums one reduction may carry
+
+void set_error(const char* fmt, ...);
+void clear_error();
+void note_launch();        // counts kernel launches (sph_profile_read)
+
+// every kernel launch of the library goes through this macro so it is counted
+#define SPH_LAUNCH(kernel, ...) ::sph::note_launch(), kernel<<<__VA_ARGS__>>>
+
+#define SPH_TRY_CUDA(call)                                                               \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      ::sph::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return (e_ == cudaErrorMemoryAllocation) ? SPH_ERR_NOMEM : SPH_ERR_CUDA;             \
+    }                                                                                    \
+  } while (0)
+
+#define SPH_TRY(expr)                         \
+  do {                                        \
+    sph_status s_ = (expr);                   \
+    if (s_ != SPH_OK) return s_;              \
+  } while (0)
+
+// A device allocation owned by the handle.
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  sph_status alloc(size_t count) {
+    if (count <= n && p) return SPH_OK;
+    release();
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      n = 0;
+      set_error("cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+      return SPH_ERR_NOMEM;
+    }
+    n = count;
+    return SPH_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// Scalars of one inner BiCGSTAB pass, float64, in device memory.
+struct SolverScalars {
+  double gamma[3];     // r0^ . r
+  double delta[3];     // r0^ . A p
+  double alpha[3];     // gamma / delta
+  double alpha_p[3];   // alpha' = gamma_{i+1} / delta_i
+  double beta[3];      // alpha' / omega
+  double omega[3];     // (r*.Ar*) / (Ar*.Ar*)
+  double rr[3];        // r . r after the update
+  double tau2[3];      // max(eps^2 b.b, FLT_MIN)
+  double dots[kMaxDots];  // last raw reduction result (debug / outer norms)
+  int32_t state[3];    // SPH_CONVERGED / SPH_STALLED / SPH_PROGRESSING
+  int32_t stall_now[3];
+  int32_t stalled_any[3];
+  int32_t iter;        // iterations of this pass
+  int32_t maxit;       // cap for this pass
+  int32_t done;        // 1: no component progressing or cap reached
+  int32_t nonfinite;   // a scalar went NaN/Inf
+  int32_t pad;
+};
+
+struct Grid {
+  int ncell[3];
+  double cell[3];     // cell side per axis (>= 2h)
+  double lo[3];
+  double L[3];        // hi - lo
+  int periodic[3];
+  int64_t ncells;
+};
+
+}  // namespace sph
+
+// The opaque handle of the C ABI.
+struct sph_neighbors {
+  int64_t n = 0;
+  int64_t n_pad = 0;        // n rounded up to a whole number of slices
+  int64_t nslices = 0;
+  sph::Grid grid{};
+  float h = 0.f;
+  int device = 0;
+  int num_sms = 0;
+
+  // cell-sorted particle copy
+  sph::DBuf<float4> pos_s;
+  sph::DBuf<float> rho_s, mu_s;
+  sph::DBuf<uint8_t> type_s;
+  sph::DBuf<int32_t> perm, iperm, key_s;
+  sph::DBuf<int32_t> cell_start;   // [ncells + 1]
+
+  // neighbour SELL-32
+  sph::DBuf<int32_t> cnt;          // [n_pad]
+  sph::DBuf<int64_t> slice_off;    // [nslices + 1]
+  sph::DBuf<int32_t> nbr;          // [nnz_pad] sorted neighbour index
+  int64_t nnz = 0, nnz_pad = 0;
+  int32_t max_cnt = 0;
+
+  // operator (coefficients of A(dt)) SELL-32
+  bool op_valid = false;
+  sph_visc_params op_params{};
+  uint64_t mu_version = 0, op_mu_version = ~0ull;
+  sph::DBuf<int32_t> op_cnt;       // [n_pad]
+  sph::DBuf<int64_t> op_off;       // [nslices + 1]
+  sph::DBuf<int32_t> op_idx;       // [op_nnz_pad]
+  sph::DBuf<float> op_hi, op_lo;   // coefficient split: a = hi + lo (float64 accuracy)
+  sph::DBuf<uint8_t> op_kind;      // 0 fluid (difference form), 1 Shepard wall, 2 identity
+  sph::DBuf<float> invD;           // float32 1/D (Jacobi), 1 for wall rows
+  sph::DBuf<double> D64;           // float64 D
+  int64_t op_nnz_pad = 0;
+
+  // scratch used by builds and solves
+  sph::DBuf<int32_t> tmp_i32a, tmp_i32b;
+  sph::DBuf<int64_t> tmp_i64;
+  sph::DBuf<int32_t> flags;        // device error flags [8]
+
+  // solver workspace
+  sph::DBuf<float4> v_r, v_rh, v_p, v_Ap, v_rs, v_As, v_d, v_tmp;
+  sph::DBuf<double> x64, b64, r64;   // [n_pad][3]
+  sph::DBuf<double> partials;        // [grid][kMaxDots]
+  sph::DBuf<unsigned int> counters;  // last-block counters
+  sph::DBuf<sph::SolverScalars> scal;
+  int32_t* host_flags = nullptr;     // pinned [4]
+  sph::SolverScalars* host_scal = nullptr;  // pinned
+  int red_grid = 0;                  // blocks of the reducing kernels
+
+  // instrumentation (sph_profile_*)
+  bool prof_on = false;
+  cudaEvent_t prof_ev[256] = {};
+  int prof_used = 0;
+  double prof_ms = 0.0;
+  int64_t prof_n = 0;
+  int64_t op_nnz = 0;
+
+  // FP64-precision solve workspace
+  sph::DBuf<double> w64[7];
+};
+
+namespace sph {
+
+// neighbors.cu
+sph_status scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t m, cudaStream_t st);
+sph_status slice_offsets(const int32_t* cnt, int64_t nslices, int64_t* off, int32_t* width_tmp,
+                         cudaStream_t st);
+
+sph_status build_slices(sph_neighbors* H, const int32_t* cnt, int64_t* off, int64_t* total_pad, int64_t* total,
+                        int32_t* maxc, cudaStream_t st);
+sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** out, cudaStream_t st);
+sph_status export_neighbors(const sph_neighbors* H, int64_t* offsets, int32_t* idx, cudaStream_t st);
+
+// operator.cu
+void launch_residual_f64(const sph_neighbors* H, int grid, const double* x, const double* b, double* r,
+                         double* partials, unsigned int* counter, double* res_out, cudaStream_t st);
+sph_status visc_apply(sph_neighbors* H, const sph_visc_params* P, const float* v, float* y, cudaStream_t st);
+sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStream_t st);
+void launch_apply_f32(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st);
+
+// solver.cu
+sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_solve_opts* O,
+                       const double* b, double* x, sph_solve_report* R, cudaStream_t st);
+sph_status visc_residual(sph_neighbors* H, const sph_visc_params* P, const double* x, const double* b, double* r,
+                         cudaStream_t st);
+sph_status ensure_workspace(sph_neighbors* H);
+sph_status solve_fp64(sph_neighbors* H, const sph_visc_params* P, const sph_solve_opts* O,
+                      const double* b, double* x, sph_solve_report* R, cudaStream_t st);
+
+int grid_for(const sph_neighbors* H, int64_t work_items, int block = kBlock);
+
+// event pair around one apply launch when profiling is on; prof_flush folds
+// the recorded pairs into prof_ms (call only after a stream synchronisation)
+void prof_begin(sph_neighbors* H, cudaStream_t st);
+void prof_end(sph_neighbors* H, cudaStream_t st);
+void prof_flush(sph_neighbors* H, int valid_pairs);
+
+}  // namespace sph

@@ -230,27 +230,30 @@ def lava_box(seed: int = 0, n: int = 100, dx: float = 0.005, rho0: float = 1000.
 
 def slope(seed: int = 0, nx: int = 200, ny: int = 100, nz: int = 200, dx: float = 0.005,
           rho0: float = 1000.0, tau0: float = 100.0, mu0: float = 1e3, m_reg: float = 1000.0,
-          dt: float = 5e-4, U: float = 0.01, noise: float = 0.05, jitter: float = 0.1,
-          theta_deg: float = 10.0, layers: int = 3, boundary: int = BC_DUMMY) -> Scene:
+          dt: float = 5e-4, U: float = 0.1, plug: float = 1.0 / 3.0, noise: float = 1e-5,
+          jitter: float = 0.1, theta_deg: float = 10.0, layers: int = 3, boundary: int = BC_DUMMY) -> Scene:
     """Slope flow of a Papanastasiou (regularised Bingham) fluid on an inclined floor.
 
-    The incline is represented by a flat floor normal to y, periodic in x and z,
-    with gravity rotated by theta (x downslope).  The seeded shear field is
-    u_x = U (1 - (1 - y/H)^2) times (1 + noise * N(0,1)), so |du/dy| runs from
-    2U/H at the floor to 0 at the free surface and the Papanastasiou viscosity
-    spans [mu(2U/H), m tau0 + mu0].  ``mu`` is left at the plateau value; the
-    mu pass fills it from ``vel``.
+    The incline is a flat floor normal to y, periodic in x and z, with gravity
+    rotated by theta (x downslope).  The seeded velocity is a Bingham-like
+    profile: a sheared layer u_x = U (1 - (1 - y/y0)^2) below y0 = (1 - plug) H
+    and a rigid plug u_x = U above it, times (1 + noise N(0,1)), plus transverse
+    components noise U N(0,1).  |du/dy| runs from 2U/y0 at the floor to 0 in the
+    plug, so the viscosity spans [mu(2U/y0), m tau0 + mu0] (about 1e3 to 1e5 Pa s
+    with the defaults).  ``mu`` is left at the plateau value; the mu pass fills
+    it from ``vel``.
     """
     H = ny * dx
+    y0 = (1.0 - plug) * H
     rng = rng_for(CFG_SLOPE, seed)
     fluid = _lattice(nx, ny, nz, dx)
     fluid = fluid + rng.uniform(-jitter * dx, jitter * dx, size=fluid.shape)
     floor = _lattice(nx, layers, nz, dx, origin=(0.0, -layers * dx, 0.0))
-    yy = np.clip(fluid[:, 1], 0.0, H)
+    yy = np.clip(fluid[:, 1], 0.0, y0)
     v = np.zeros_like(fluid)
-    v[:, 0] = U * (1.0 - (1.0 - yy / H) ** 2) * (1.0 + noise * rng.standard_normal(fluid.shape[0]))
-    v[:, 1] = noise * U * 0.1 * rng.standard_normal(fluid.shape[0])
-    v[:, 2] = noise * U * 0.1 * rng.standard_normal(fluid.shape[0])
+    v[:, 0] = U * (1.0 - (1.0 - yy / y0) ** 2) * (1.0 + noise * rng.standard_normal(fluid.shape[0]))
+    v[:, 1] = noise * U * rng.standard_normal(fluid.shape[0])
+    v[:, 2] = noise * U * rng.standard_normal(fluid.shape[0])
     th = math.radians(theta_deg)
     g = (9.81 * math.sin(th), -9.81 * math.cos(th), 0.0)
     lo = (0.0, -layers * dx, 0.0)
@@ -258,7 +261,7 @@ def slope(seed: int = 0, nx: int = 200, ny: int = 100, nz: int = 200, dx: float 
     mu_plateau = m_reg * tau0 + mu0
     return _assemble("slope", fluid, floor, np.zeros((floor.shape[0], 3)), dx, rho0, mu_plateau, dt,
                      lo, hi, (1, 0, 1), v, g=g, boundary=boundary, rheology=(tau0, mu0, m_reg),
-                     meta=dict(seed=seed, U=U, H=H))
+                     meta=dict(seed=seed, U=U, H=H, y0=y0))
 
 
 def slope_subset(seed: int = 0, **kw) -> Scene:

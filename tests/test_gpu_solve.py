@@ -1,0 +1,77 @@
+"""GPU solves reach the float64 true residual and match the oracle's solution."""
+import numpy as np
+import pytest
+
+import scenes
+from oracle import neighbors as onb, operator as oop, solvers as osv
+from sph_testutil import SCENES_SMALL, gpu_solve, lib_build, oracle_system, rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+RTOL_RES = 1e-6      # true relative residual ||b - A x|| / ||b|| (oracle's float64 A)
+RTOL_SOL = 1e-5      # relative L2 distance to the oracle's solution
+
+
+@pytest.mark.parametrize("name", sorted(SCENES_SMALL))
+@pytest.mark.parametrize("merged", [0, 1])
+def test_solution_matches_oracle(name, merged):
+    from paper_2206_14780_gb300 import binding
+
+    s = SCENES_SMALL[name]()
+    nb, _ = lib_build(s)
+    off, idx, A = oracle_system(s)
+    x_ref = osv.reference_solution(A, s.b, s.x0)
+    x, rep = gpu_solve(nb, s, binding.solve_opts(merged_reductions=merged))
+    assert rep["status"] == 0, rep
+    res, _ = oop.true_residual(A, x, s.b)
+    assert res <= RTOL_RES, (res, rep)
+    assert abs(rep["true_rel_res"] - res) <= 1e-3 * RTOL_RES + 1e-2 * res
+    assert rel_l2(x, x_ref) <= RTOL_SOL
+
+
+def test_stiff_box_several_tiles():
+    # c2-like stiffness (nu = 10, dt = 5e-4: dt sum c ~ 670) on a 20^3 box
+    s = scenes.lava_box(5, n=20)
+    nb, _ = lib_build(s)
+    off, idx, A = oracle_system(s)
+    x_ref = osv.reference_solution(A, s.b, s.x0)
+    x, rep = gpu_solve(nb, s)
+    res, per = oop.true_residual(A, x, s.b)
+    assert rep["status"] == 0 and res <= RTOL_RES, (res, rep)
+    assert rel_l2(x, x_ref) <= RTOL_SOL
+
+
+def test_zero_rhs_component_and_exact_guess():
+    s = SCENES_SMALL["random_box_mu_mass"]()
+    nb, _ = lib_build(s)
+    off, idx, A = oracle_system(s)
+    b = s.b.copy()
+    b[:, 1] = 0.0
+    x0 = s.x0.copy()
+    x0[:, 1] = 0.0
+    x, rep = gpu_solve(nb, s, b=b, x0=x0)
+    assert rep["status"] == 0
+    np.testing.assert_array_equal(x[:, 1], 0.0)
+    # exact initial guess: no iteration at all
+    x_ref = osv.reference_solution(A, s.b, s.x0, rtol=1e-14)
+    x2, rep2 = gpu_solve(nb, s, x0=x_ref)
+    assert rep2["iters"] == 0 and rep2["status"] == 0
+
+
+def test_all_zero_rhs():
+    s = SCENES_SMALL["couette_dummy"]()
+    nb, _ = lib_build(s)
+    z = np.zeros_like(s.b)
+    x, rep = gpu_solve(nb, s, b=z, x0=z)
+    assert rep["status"] == 0 and rep["iters"] == 0
+    np.testing.assert_array_equal(x, 0.0)
+
+
+def test_iteration_cap_reports_not_converged():
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.lava_box(5, n=14)
+    nb, _ = lib_build(s)
+    x, rep = gpu_solve(nb, s, binding.solve_opts(maxit=3, max_refine=1))
+    assert rep["status"] == 6 and rep["iters"] <= 3
+    assert np.all(np.isfinite(x))
