@@ -150,9 +150,11 @@ typedef struct {
   double rtol;             /* accept when ||b - A x||_2 / ||b||_2 <= rtol (all
                               three components jointly, float64 true residual);
                               default 1e-6                                       */
-  double eps_inner;        /* relative tolerance of each inner BiCGSTAB pass on
-                              the Jacobi-scaled recursive residual; the paper's
-                              tau^2 = max(eps^2 b.b, FLT_MIN) (Sec. 4.1)          */
+  double eps_inner;        /* floor of the relative tolerance of one inner
+                              BiCGSTAB pass on its Jacobi-scaled recursive
+                              residual (the paper's tau^2 = max(eps^2 b.b,
+                              FLT_MIN), Sec. 4.1); each pass asks for
+                              max(eps_inner, rtol ||b|| / (4 ||r64||)); 0 = 1e-5 */
   int32_t maxit;           /* cap on inner iterations summed over passes          */
   int32_t max_refine;      /* cap on refinement passes                            */
   int32_t precision;       /* SPH_PREC_MIXED or SPH_PREC_FP64                     */

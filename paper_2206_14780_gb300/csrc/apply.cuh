@@ -1,0 +1,70 @@
+// One row of y = A v (or D^-1 A v) over the operator's SELL-32 storage.
+//
+// Storage: entry j of row s sits at off[s/32] + 32 j + s%32 as an int2
+// (x = neighbour row, y = the float32 coefficient's bits), so a warp reading
+// entry j of its 32 rows loads 256 consecutive bytes with one instruction.
+// The stream is read once per apply: it is loaded with the evict-first hint
+// (ld.global.cs) so L1/L2 keep the gathered neighbour vectors instead.
+//
+// The loop runs to the slice width (uniform across the warp) in groups of U
+// entries: U coefficient loads, then U neighbour gathers, then the FMAs, so a
+// warp keeps U independent memory requests in flight instead of walking one
+// dependent load chain per neighbour.  Entries past a row's own count read the
+// row itself with a zero coefficient.
+#pragma once
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+enum : uint8_t { KIND_FLUID = 0, KIND_SHEPARD = 1, KIND_IDENTITY = 2 };
+
+struct OpView {
+  const int64_t* off;    // [nslices + 1]
+  const int32_t* cnt;    // [n_pad]
+  const int2* ih;        // [op_nnz_pad] (row, coefficient bits)
+  const uint8_t* kind;   // [n_pad]
+  const float* invD;     // [n_pad]
+  int64_t nslices;
+  int64_t n_pad;
+};
+
+// Fluid rows: v_b + sum a (v_b - v_a) [times 1/D with Jacobi]; Shepard rows:
+// v_b + sum a v_a; identity rows: v_b.
+template <int U, bool JACOBI>
+__device__ __forceinline__ float4 apply_row(const OpView& op, const float4* __restrict__ v, int64_t sl, int lane,
+                                            float4& vb_out) {
+  const int64_t s = sl * kSlice + lane;
+  const int c = op.cnt[s];
+  const uint8_t kd = op.kind[s];
+  const float4 vb = v[s];
+  vb_out = vb;
+  const float kap = (kd == KIND_FLUID) ? 1.f : 0.f;
+  const int64_t o0 = op.off[sl];
+  const int w = (int)((op.off[sl + 1] - o0) / kSlice);
+  const int2* __restrict__ p = op.ih + o0 + lane;
+  float ax = 0.f, ay = 0.f, az = 0.f;
+  for (int j0 = 0; j0 < w; j0 += U) {
+    int2 e[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) e[u] = (j0 + u < c) ? __ldcs(p + (int64_t)(j0 + u) * kSlice) : make_int2((int)s, 0);
+    float4 va[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) va[u] = __ldg(v + e[u].x);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float a = __int_as_float(e[u].y);
+      ax = fmaf(a, fmaf(kap, vb.x, -va[u].x), ax);
+      ay = fmaf(a, fmaf(kap, vb.y, -va[u].y), ay);
+      az = fmaf(a, fmaf(kap, vb.z, -va[u].z), az);
+    }
+  }
+  if (kd == KIND_FLUID) {
+    const float sc = JACOBI ? op.invD[s] : 1.f;
+    return make_float4((vb.x + ax) * sc, (vb.y + ay) * sc, (vb.z + az) * sc, 0.f);
+  }
+  if (kd == KIND_SHEPARD) return make_float4(vb.x - ax, vb.y - ay, vb.z - az, 0.f);
+  return make_float4(vb.x, vb.y, vb.z, 0.f);
+}
+
+}  // namespace sph

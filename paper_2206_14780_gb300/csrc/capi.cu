@@ -109,8 +109,7 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
   h->nbr.release();
   h->op_cnt.release();
   h->op_off.release();
-  h->op_idx.release();
-  h->op_hi.release();
+  h->op_ih.release();
   h->op_lo.release();
   h->op_kind.release();
   h->invD.release();

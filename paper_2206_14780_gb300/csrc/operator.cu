@@ -15,14 +15,13 @@
 // float64 residual reads hi + lo (relative error 2^-48).
 #include <cmath>
 
+#include "apply.cuh"
 #include "reduce.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
 
 namespace {
-
-enum : uint8_t { KIND_FLUID = 0, KIND_SHEPARD = 1, KIND_IDENTITY = 2 };
 
 struct OpGeom {
   double L[3];
@@ -104,9 +103,8 @@ __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restric
                           const uint8_t* __restrict__ type, const int32_t* __restrict__ cnt,
                           const int64_t* __restrict__ slice_off, const int32_t* __restrict__ nbr,
                           const uint8_t* __restrict__ kind, const int64_t* __restrict__ op_off, int64_t n,
-                          int64_t n_pad, OpGeom g, double dt, int mean, int32_t* __restrict__ op_idx,
-                          float* __restrict__ op_hi, float* __restrict__ op_lo, float* __restrict__ invD,
-                          double* __restrict__ D64) {
+                          int64_t n_pad, OpGeom g, double dt, int mean, int2* __restrict__ op_ih,
+                          float* __restrict__ op_lo, float* __restrict__ invD, double* __restrict__ D64) {
   // 2 |f(q)| / h^5 folds into one float64 constant per scene
   const double inv_h5 = g.inv_h * g.inv_h * g.inv_h * g.inv_h * g.inv_h;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
@@ -135,8 +133,7 @@ __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restric
         const float hi = __double2float_rn(a);
         const float lo = __double2float_rn(a - (double)hi);
         const int64_t e = obase + (int64_t)o * kSlice;
-        op_idx[e] = t;
-        op_hi[e] = hi;
+        op_ih[e] = make_int2(t, __float_as_int(hi));
         op_lo[e] = lo;
         sum += a;
         ++o;
@@ -159,8 +156,7 @@ __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restric
         const float hi = __double2float_rn(a);
         const float lo = __double2float_rn(a - (double)hi);
         const int64_t e = obase + (int64_t)o * kSlice;
-        op_idx[e] = t;
-        op_hi[e] = hi;
+        op_ih[e] = make_int2(t, __float_as_int(hi));
         op_lo[e] = lo;
         ++o;
       }
@@ -171,43 +167,13 @@ __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restric
 }
 
 // y = A v (or D^-1 A v) in float32, one warp per 32-row slice, one row per lane.
-template <bool JACOBI>
-__global__ void __launch_bounds__(kBlock) k_apply_f32(const int64_t* __restrict__ op_off,
-                                                      const int32_t* __restrict__ op_cnt,
-                                                      const int32_t* __restrict__ op_idx,
-                                                      const float* __restrict__ op_hi,
-                                                      const uint8_t* __restrict__ kind,
-                                                      const float* __restrict__ invD, const float4* __restrict__ v,
-                                                      float4* __restrict__ y, int64_t nslices) {
+template <int U, bool JACOBI>
+__global__ void __launch_bounds__(kBlock) k_apply_f32(OpView op, const float4* __restrict__ v, float4* __restrict__ y) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nwarps) {
-    const int64_t s = sl * kSlice + lane;
-    const int c = op_cnt[s];
-    const uint8_t k = kind[s];
-    const float4 vb = v[s];
-    const float kap = (k == KIND_FLUID) ? 1.f : 0.f;
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    const int64_t base = op_off[sl] + lane;
-    for (int j = 0; j < c; ++j) {
-      const int64_t e = base + (int64_t)j * kSlice;
-      const int32_t t = op_idx[e];
-      const float a = op_hi[e];
-      const float4 va = v[t];
-      ax = fmaf(a, fmaf(kap, vb.x, -va.x), ax);
-      ay = fmaf(a, fmaf(kap, vb.y, -va.y), ay);
-      az = fmaf(a, fmaf(kap, vb.z, -va.z), az);
-    }
-    float4 out;
-    if (k == KIND_FLUID) {
-      const float sc = JACOBI ? invD[s] : 1.f;
-      out = make_float4((vb.x + ax) * sc, (vb.y + ay) * sc, (vb.z + az) * sc, 0.f);
-    } else if (k == KIND_SHEPARD) {
-      out = make_float4(vb.x - ax, vb.y - ay, vb.z - az, 0.f);
-    } else {
-      out = make_float4(vb.x, vb.y, vb.z, 0.f);
-    }
-    y[s] = out;
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
+    float4 vb;
+    y[sl * kSlice + lane] = apply_row<U, JACOBI>(op, v, sl, lane, vb);
   }
 }
 
@@ -235,8 +201,7 @@ __global__ void k_scatter_f4(const float4* __restrict__ y_s, const int32_t* __re
 // r_c^2 (K = 3) go through the grid reduction into res_out[0..3) when given.
 __global__ void __launch_bounds__(kBlock) k_residual_f64(const int64_t* __restrict__ op_off,
                                                          const int32_t* __restrict__ op_cnt,
-                                                         const int32_t* __restrict__ op_idx,
-                                                         const float* __restrict__ op_hi,
+                                                         const int2* __restrict__ op_ih,
                                                          const float* __restrict__ op_lo,
                                                          const uint8_t* __restrict__ kind,
                                                          const double* __restrict__ x, const double* __restrict__ b,
@@ -256,8 +221,9 @@ __global__ void __launch_bounds__(kBlock) k_residual_f64(const int64_t* __restri
     const int64_t base = op_off[sl] + lane;
     for (int j = 0; j < c; ++j) {
       const int64_t e = base + (int64_t)j * kSlice;
-      const int32_t t = op_idx[e];
-      const double a = (double)op_hi[e] + (double)op_lo[e];
+      const int2 ih = op_ih[e];
+      const int32_t t = ih.x;
+      const double a = (double)__int_as_float(ih.y) + (double)op_lo[e];
       a0 += a * (kap * xb0 - x[3 * t]);
       a1 += a * (kap * xb1 - x[3 * t + 1]);
       a2 += a * (kap * xb2 - x[3 * t + 2]);
@@ -318,14 +284,13 @@ sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStrea
   int64_t total_pad = 0, total = 0;
   int32_t maxc = 0;
   SPH_TRY(build_slices(H, H->op_cnt.p, H->op_off.p, &total_pad, &total, &maxc, st));
-  SPH_TRY(H->op_idx.alloc(total_pad > 0 ? total_pad : 1));
-  SPH_TRY(H->op_hi.alloc(total_pad > 0 ? total_pad : 1));
+  SPH_TRY(H->op_ih.alloc(total_pad > 0 ? total_pad : 1));
   SPH_TRY(H->op_lo.alloc(total_pad > 0 ? total_pad : 1));
   H->op_nnz_pad = total_pad;
   H->op_nnz = total;
   SPH_LAUNCH(k_op_fill, grid, kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->type_s.p, H->cnt.p, H->slice_off.p,
                                      H->nbr.p, H->op_kind.p, H->op_off.p, H->n, H->n_pad, g, P->dt, P->mean,
-                                     H->op_idx.p, H->op_hi.p, H->op_lo.p, H->invD.p, H->D64.p);
+                                     H->op_ih.p, H->op_lo.p, H->invD.p, H->D64.p);
   SPH_TRY_CUDA(cudaGetLastError());
   H->op_valid = true;
   H->op_params = *P;
@@ -335,18 +300,20 @@ sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStrea
 
 void launch_residual_f64(const sph_neighbors* H, int grid, const double* x, const double* b, double* r,
                          double* partials, unsigned int* counter, double* res_out, cudaStream_t st) {
-  SPH_LAUNCH(k_residual_f64, grid, kBlock, 0, st)(H->op_off.p, H->op_cnt.p, H->op_idx.p, H->op_hi.p, H->op_lo.p,
+  SPH_LAUNCH(k_residual_f64, grid, kBlock, 0, st)(H->op_off.p, H->op_cnt.p, H->op_ih.p, H->op_lo.p,
                                           H->op_kind.p, x, b, r, H->n, H->nslices, partials, counter, res_out);
+}
+
+OpView op_view(const sph_neighbors* H) {
+  return OpView{H->op_off.p, H->op_cnt.p, H->op_ih.p, H->op_kind.p, H->invD.p, H->nslices, H->n_pad};
 }
 
 void launch_apply_f32(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st) {
   const int grid = grid_for(H, H->nslices * 32);
-  if (jacobi)
-    SPH_LAUNCH(k_apply_f32<true>, grid, kBlock, 0, st)(H->op_off.p, H->op_cnt.p, H->op_idx.p, H->op_hi.p, H->op_kind.p,
-                                               H->invD.p, v, y, H->nslices);
-  else
-    SPH_LAUNCH(k_apply_f32<false>, grid, kBlock, 0, st)(H->op_off.p, H->op_cnt.p, H->op_idx.p, H->op_hi.p, H->op_kind.p,
-                                                H->invD.p, v, y, H->nslices);
+  const OpView op = op_view(H);
+  auto kern = (H->unroll == 4) ? (jacobi ? k_apply_f32<4, true> : k_apply_f32<4, false>)
+                                : (jacobi ? k_apply_f32<8, true> : k_apply_f32<8, false>);
+  SPH_LAUNCH(kern, grid, kBlock, 0, st)(op, v, y);
 }
 
 sph_status visc_apply(sph_neighbors* H, const sph_visc_params* P, const float* v, float* y, cudaStream_t st) {

@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "apply.cuh"
 #include "reduce.cuh"
 #include "sph_internal.cuh"
 
@@ -48,18 +49,6 @@ struct Vecs {
   float4* As;
   float4* d;
 };
-
-struct OpView {
-  const int64_t* off;
-  const int32_t* cnt;
-  const int32_t* idx;
-  const float* hi;
-  const uint8_t* kind;
-  const float* invD;
-  int64_t nslices;
-  int64_t n_pad;
-};
-
 
 // ---- scalar updates (thread 0 of the last block) -------------------------
 
@@ -210,7 +199,7 @@ __global__ void __launch_bounds__(kBlock) k_p_update(int64_t n_pad, Vecs V, cons
 //   PH_DELTA:        v = p,  y = Ap; dots r0^.Ap                       (K = 3)
 //   PH_OMEGA:        v = r*, y = Ar*; dots r*.Ar*, Ar*.Ar*             (K = 6)
 //   PH_OMEGA_MERGED: + r0^.r*, r0^.Ar*, r*.r*                          (K = 15)
-template <int PH>
+template <int PH, int U>
 __global__ void __launch_bounds__(kBlock) k_apply_dot(OpView op, const float4* __restrict__ v, float4* __restrict__ y,
                                                       const float4* __restrict__ rh, SolverScalars* S,
                                                       double* partials, unsigned int* counter) {
@@ -223,30 +212,8 @@ __global__ void __launch_bounds__(kBlock) k_apply_dot(OpView op, const float4* _
   for (int k = 0; k < K; ++k) acc[k] = 0.f;
   for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
     const int64_t s = sl * kSlice + lane;
-    const int c = op.cnt[s];
-    const uint8_t kd = op.kind[s];
-    const float4 vb = v[s];
-    const float kap = (kd == 0) ? 1.f : 0.f;
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    const int64_t base = op.off[sl] + lane;
-    for (int j = 0; j < c; ++j) {
-      const int64_t e = base + (int64_t)j * kSlice;
-      const int32_t t = op.idx[e];
-      const float a = op.hi[e];
-      const float4 va = v[t];
-      ax = fmaf(a, fmaf(kap, vb.x, -va.x), ax);
-      ay = fmaf(a, fmaf(kap, vb.y, -va.y), ay);
-      az = fmaf(a, fmaf(kap, vb.z, -va.z), az);
-    }
-    float4 o;
-    if (kd == 0) {
-      const float sc = op.invD[s];
-      o = make_float4((vb.x + ax) * sc, (vb.y + ay) * sc, (vb.z + az) * sc, 0.f);
-    } else if (kd == 1) {
-      o = make_float4(vb.x - ax, vb.y - ay, vb.z - az, 0.f);
-    } else {
-      o = make_float4(vb.x, vb.y, vb.z, 0.f);
-    }
+    float4 vb;
+    const float4 o = apply_row<U, true>(op, v, sl, lane, vb);
     y[s] = o;
     const float4 h = rh[s];
     if (PH == PH_DELTA) {
@@ -440,7 +407,7 @@ sph_status ensure_workspace(sph_neighbors* H) {
   SPH_TRY(H->r64.alloc(3 * np));
   if (H->red_grid == 0) {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply_dot<PH_OMEGA_MERGED>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply_dot<PH_OMEGA_MERGED, 8>, kBlock, 0);
     if (occ < 1) occ = 1;
     H->red_grid = H->num_sms * occ;
   }
@@ -472,6 +439,15 @@ static sph_status true_residual(sph_neighbors* H, cudaStream_t st, double rr[3])
   return SPH_OK;
 }
 
+template <int PH>
+static void launch_apply_dot(sph_neighbors* H, int grid, const OpView& op, const float4* v, float4* y,
+                             const float4* rh, SolverScalars* S, unsigned int* counter, cudaStream_t st) {
+  auto kern = (H->unroll == 4) ? k_apply_dot<PH, 4> : k_apply_dot<PH, 8>;
+  prof_begin(H, st);
+  SPH_LAUNCH(kern, grid, kBlock, 0, st)(op, v, y, rh, S, H->partials.p, counter);
+  prof_end(H, st);
+}
+
 sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_solve_opts* O, const double* b,
                        double* x, sph_solve_report* R, cudaStream_t st) {
   SPH_TRY(ensure_operator(H, P, st));
@@ -480,7 +456,7 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
   const int grid_rows = red_grid_for(H, np);
   const int grid_slices = red_grid_for(H, H->nslices * 32);
   Vecs V{H->v_r.p, H->v_rh.p, H->v_p.p, H->v_Ap.p, H->v_rs.p, H->v_As.p, H->v_d.p};
-  OpView op{H->op_off.p, H->op_cnt.p, H->op_idx.p, H->op_hi.p, H->op_kind.p, H->invD.p, H->nslices, np};
+  const OpView op = op_view(H);
   SolverScalars* S = H->scal.p;
   unsigned int* C = H->counters.p;
 
@@ -496,7 +472,7 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
   const double bnorm = std::sqrt(bb[0] + bb[1] + bb[2]);
 
   const double rtol = O->rtol > 0.0 ? O->rtol : 1e-6;
-  const double eps = O->eps_inner > 0.0 ? O->eps_inner : 1e-4;
+  const double eps_floor = O->eps_inner > 0.0 ? O->eps_inner : 1e-5;
   const int maxit = O->maxit > 0 ? O->maxit : 10000;
   const int max_ref = O->max_refine > 0 ? O->max_refine : 20;
   const int chunk0 = O->chunk > 0 ? O->chunk : 8;
@@ -520,7 +496,9 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
       break;
     }
     if (ref >= max_ref || total_iters >= maxit) break;
-    // inner pass
+    // inner pass: ask it for what the outer loop still needs (with a 4x margin),
+    // but never for more than eps_floor (float32 recursions stall below that)
+    const double eps = std::fmax(eps_floor, 0.25 * rtol * bnorm / rnorm);
     SPH_LAUNCH(k_pass_init, grid_rows, kBlock, 0, st)(H->r64.p, H->D64.p, jacobi, np, V, eps * eps, maxit - total_iters, S,
                                               H->partials.p, C + CNT_INIT);
     SPH_TRY_CUDA(cudaGetLastError());
@@ -530,21 +508,13 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
     for (;;) {
       for (int it = 0; it < chunk; ++it) {
         if (!merged) SPH_LAUNCH(k_p_update, grid_rows, kBlock, 0, st)(np, V, S);
-        prof_begin(H, st);
-        SPH_LAUNCH(k_apply_dot<PH_DELTA>, grid_slices, kBlock, 0, st)(op, V.p, V.Ap, V.rh, S, H->partials.p, C + CNT_DELTA);
-        prof_end(H, st);
+        launch_apply_dot<PH_DELTA>(H, grid_slices, op, V.p, V.Ap, V.rh, S, C + CNT_DELTA, st);
         SPH_LAUNCH(k_rstar, grid_rows, kBlock, 0, st)(np, V, S);
         if (merged) {
-          prof_begin(H, st);
-          SPH_LAUNCH(k_apply_dot<PH_OMEGA_MERGED>, grid_slices, kBlock, 0, st)(op, V.rs, V.As, V.rh, S, H->partials.p,
-                                                                        C + CNT_OMEGA);
-          prof_end(H, st);
+          launch_apply_dot<PH_OMEGA_MERGED>(H, grid_slices, op, V.rs, V.As, V.rh, S, C + CNT_OMEGA, st);
           SPH_LAUNCH(k_xrp_update, grid_rows, kBlock, 0, st)(np, V, S, C + CNT_XRP);
         } else {
-          prof_begin(H, st);
-          SPH_LAUNCH(k_apply_dot<PH_OMEGA>, grid_slices, kBlock, 0, st)(op, V.rs, V.As, V.rh, S, H->partials.p,
-                                                                 C + CNT_OMEGA);
-          prof_end(H, st);
+          launch_apply_dot<PH_OMEGA>(H, grid_slices, op, V.rs, V.As, V.rh, S, C + CNT_OMEGA, st);
           SPH_LAUNCH(k_xr_update, grid_rows, kBlock, 0, st)(np, V, S, H->partials.p, C + CNT_XR);
         }
       }

@@ -134,8 +134,8 @@ struct sph_neighbors {
   uint64_t mu_version = 0, op_mu_version = ~0ull;
   sph::DBuf<int32_t> op_cnt;       // [n_pad]
   sph::DBuf<int64_t> op_off;       // [nslices + 1]
-  sph::DBuf<int32_t> op_idx;       // [op_nnz_pad]
-  sph::DBuf<float> op_hi, op_lo;   // coefficient split: a = hi + lo (float64 accuracy)
+  sph::DBuf<int2> op_ih;           // [op_nnz_pad] (row, bits of float32 hi)
+  sph::DBuf<float> op_lo;          // a = hi + lo reproduces the float64 coefficient
   sph::DBuf<uint8_t> op_kind;      // 0 fluid (difference form), 1 Shepard wall, 2 identity
   sph::DBuf<float> invD;           // float32 1/D (Jacobi), 1 for wall rows
   sph::DBuf<double> D64;           // float64 D
@@ -155,6 +155,7 @@ struct sph_neighbors {
   int32_t* host_flags = nullptr;     // pinned [4]
   sph::SolverScalars* host_scal = nullptr;  // pinned
   int red_grid = 0;                  // blocks of the reducing kernels
+  int unroll = 8;                    // neighbour entries in flight per lane (4 or 8)
 
   // instrumentation (sph_profile_*)
   bool prof_on = false;
@@ -186,6 +187,8 @@ void launch_residual_f64(const sph_neighbors* H, int grid, const double* x, cons
 sph_status visc_apply(sph_neighbors* H, const sph_visc_params* P, const float* v, float* y, cudaStream_t st);
 sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStream_t st);
 void launch_apply_f32(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st);
+struct OpView;
+OpView op_view(const sph_neighbors* H);
 
 // solver.cu
 sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_solve_opts* O,
