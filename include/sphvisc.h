@@ -141,6 +141,33 @@ sph_status sph_visc_setup(sph_neighbors* handle, const sph_visc_params* params, 
 sph_status sph_visc_apply(sph_neighbors* handle, const sph_visc_params* params, const float* v,
                           float* y, void* stream);
 
+/* Largest particle count sph_visc_apply_noalloc accepts (after rounding n up
+ * to a multiple of 32). */
+#define SPH_NOALLOC_MAX_ROWS 262144
+
+/* Same result as sph_visc_apply, for callers that must not allocate device
+ * memory at the time of the call: e.g. a plugin whose host framework owns all
+ * device memory through its own pool (a cudaMalloc would fail or fragment that
+ * pool), or a time-step loop that forbids allocation calls.  The paper has no
+ * counterpart; this is an interface convenience.
+ *  - Allocates nothing: no cudaMalloc/cudaFree and no allocating library call.
+ *    Its scratch (the cell-sorted copies of v and y, 32 bytes per row) is a
+ *    file-scope device array of 2 * SPH_NOALLOC_MAX_ROWS float4 (8 MiB) that
+ *    every GPU loading this library keeps until the process exits.
+ *  - The coefficients for `params` must already be on the handle
+ *    (sph_visc_setup, or an apply/solve with the same params; those calls may
+ *    allocate); otherwise SPH_ERR_INVALID.
+ *  - n rounded up to 32 above SPH_NOALLOC_MAX_ROWS: SPH_ERR_INVALID.
+ *  - The first call on a device looks up the array's device address there
+ *    (cudaGetSymbolAddress, once per device, with that device current); make
+ *    that first call before any stream capture.
+ *  - All calls share the one array: calls whose work overlaps on the GPU (other
+ *    streams, other host threads) race on it.  Every row it reads is written
+ *    by the same call first, so stale contents from a previous call are never
+ *    used. */
+sph_status sph_visc_apply_noalloc(sph_neighbors* handle, const sph_visc_params* params,
+                                  const float* v, float* y, void* stream);
+
 /* r = b - A(dt) x in float64 with the float64 coefficients (the true residual).
  * x, b, r: (device) [n][3] double, caller order. */
 sph_status sph_visc_residual(sph_neighbors* handle, const sph_visc_params* params,

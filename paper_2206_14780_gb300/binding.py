@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsphvisc.so")
 
 SPH_OK = 0
+SPH_NOALLOC_MAX_ROWS = 262144
 STATUS = {0: "SPH_OK", 1: "SPH_ERR_INVALID", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_CAPACITY", 4: "SPH_ERR_NONFINITE",
           5: "SPH_ERR_TIMEOUT", 6: "SPH_NOT_CONVERGED", 7: "SPH_ERR_NOMEM"}
 SPH_BC_DUMMY, SPH_BC_DYNAMIC = 0, 1
@@ -24,7 +25,7 @@ SPH_CONVERGED, SPH_STALLED, SPH_PROGRESSING = 0, 1, 2
 
 # every symbol include/sphvisc.h declares
 EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", "sph_set_viscosity",
-           "sph_neighbors_destroy", "sph_visc_setup", "sph_visc_apply", "sph_visc_residual", "sph_visc_solve",
+           "sph_neighbors_destroy", "sph_visc_setup", "sph_visc_apply", "sph_visc_apply_noalloc", "sph_visc_residual", "sph_visc_solve",
            "sph_mu_papanastasiou", "sph_profile_enable", "sph_profile_read", "sph_last_error", "sph_version"]
 
 
@@ -81,6 +82,7 @@ def load(path: str = LIB_PATH):
         "sph_neighbors_destroy": [vp],
         "sph_visc_setup": [vp, ctypes.POINTER(sph_visc_params), vp],
         "sph_visc_apply": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp],
+        "sph_visc_apply_noalloc": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp],
         "sph_visc_residual": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp, vp],
         "sph_visc_solve": [vp, ctypes.POINTER(sph_visc_params), ctypes.POINTER(sph_solve_opts), vp, vp,
                            ctypes.POINTER(sph_solve_report), vp],
@@ -186,6 +188,10 @@ class Neighbors:
 
     def apply(self, params, v, y, stream=None):
         _check(_lib.sph_visc_apply(self.handle, ctypes.byref(params), _ptr(v), _ptr(y), _stream(stream)))
+
+    def apply_noalloc(self, params, v, y, stream=None):
+        """sph_visc_apply_noalloc: y = A v with no device allocation (needs setup first)."""
+        _check(_lib.sph_visc_apply_noalloc(self.handle, ctypes.byref(params), _ptr(v), _ptr(y), _stream(stream)))
 
     def residual(self, params, x, b, r, stream=None):
         _check(_lib.sph_visc_residual(self.handle, ctypes.byref(params), _ptr(x), _ptr(b), _ptr(r),

@@ -160,6 +160,12 @@ sph_status sph_visc_apply(sph_neighbors* h, const sph_visc_params* params, const
   return visc_apply(h, params, v, y, as_stream(stream));
 }
 
+sph_status sph_visc_apply_noalloc(sph_neighbors* h, const sph_visc_params* params, const float* v, float* y,
+                                  void* stream) {
+  clear_error();
+  return visc_apply_noalloc(h, params, v, y, as_stream(stream));
+}
+
 sph_status sph_visc_residual(sph_neighbors* h, const sph_visc_params* params, const double* x, const double* b,
                              double* r, void* stream) {
   clear_error();

@@ -185,6 +185,8 @@ sph_status export_neighbors(const sph_neighbors* H, int64_t* offsets, int32_t* i
 void launch_residual_f64(const sph_neighbors* H, int grid, const double* x, const double* b, double* r,
                          double* partials, unsigned int* counter, double* res_out, cudaStream_t st);
 sph_status visc_apply(sph_neighbors* H, const sph_visc_params* P, const float* v, float* y, cudaStream_t st);
+sph_status visc_apply_noalloc(sph_neighbors* H, const sph_visc_params* P, const float* v, float* y,
+                              cudaStream_t st);
 sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStream_t st);
 void launch_apply_f32(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st);
 struct OpView;
