@@ -46,7 +46,7 @@ def parse(argv=None):
     ap.add_argument("--cpu-n", type=int, default=40, help="fluid lattice side of the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--merged", type=int, default=1)
+    ap.add_argument("--merged", type=int, default=0)
     ap.add_argument("--eps-inner", type=float, default=1e-5)
     ap.add_argument("--cpu-oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args(argv)

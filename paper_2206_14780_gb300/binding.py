@@ -135,7 +135,7 @@ def visc_params(dt, boundary=SPH_BC_DUMMY, mean=SPH_MEAN_HARMONIC):
 
 
 def solve_opts(rtol=1e-6, eps_inner=1e-5, maxit=20000, max_refine=30, precision=SPH_PREC_MIXED,
-               merged_reductions=1, chunk=8, jacobi=1):
+               merged_reductions=0, chunk=8, jacobi=1):
     return sph_solve_opts(rtol, eps_inner, maxit, max_refine, precision, merged_reductions, chunk, jacobi)
 
 

@@ -1,0 +1,109 @@
+// Scalar side of the restructured BiCGSTAB (paper Sec. 4.2): run by thread 0 of
+// the last block after each grid reduction, shared by the float32 and float64
+// solves.  States per component follow the "Stopping criterion" paragraph:
+// converged (r.r < tau^2), stalled (delta = 0, or a coefficient that zeroes out)
+// or progressing; a component that is not progressing is frozen (alpha = omega
+// = 0) and the pass stops when none progresses.
+#pragma once
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+constexpr double kFltMin = 1.17549435082228750797e-38;  // 2^-126: the tau^2 floor (Sec. 4.1)
+
+__device__ inline void scal_after_delta(SolverScalars* S, const double* dots) {
+  for (int c = 0; c < 3; ++c) {
+    if (S->state[c] != SPH_PROGRESSING) {
+      S->alpha[c] = 0.0;
+      S->stall_now[c] = 0;
+      continue;
+    }
+    const double d = dots[c];
+    S->delta[c] = d;
+    double a = 0.0;
+    int stall = 0;
+    if (d == 0.0 || !isfinite(d)) {
+      stall = 1;
+    } else {
+      a = S->gamma[c] / d;
+      if (!isfinite(a)) {
+        a = 0.0;
+        stall = 1;
+      }
+    }
+    S->alpha[c] = a;
+    S->stall_now[c] = stall;
+  }
+}
+
+__device__ inline void scal_after_omega(SolverScalars* S, const double* dots) {
+  for (int c = 0; c < 3; ++c) {
+    if (S->state[c] != SPH_PROGRESSING) {
+      S->omega[c] = 0.0;
+      continue;
+    }
+    const double sA = dots[c], AA = dots[3 + c];
+    double om = (AA > 0.0 && isfinite(AA)) ? sA / AA : 0.0;
+    if (!isfinite(om)) om = 0.0;
+    S->omega[c] = om;
+  }
+}
+
+// gamma' and r.r known: alpha', beta, states, iteration count, stop flag.
+__device__ inline void scal_after_update(SolverScalars* S, const double* gam_new, const double* rr) {
+  int progressing = 0;
+  for (int c = 0; c < 3; ++c) {
+    if (S->state[c] != SPH_PROGRESSING) {
+      S->alpha_p[c] = 0.0;
+      S->beta[c] = 0.0;
+      continue;
+    }
+    const double om = S->omega[c];
+    const bool ok = !S->stall_now[c] && om != 0.0;
+    double ap = ok ? gam_new[c] / S->delta[c] : 0.0;
+    double be = ok ? ap / om : 0.0;
+    if (!isfinite(ap) || !isfinite(be)) {
+      ap = 0.0;
+      be = 0.0;
+    }
+    if (!isfinite(gam_new[c]) || !isfinite(rr[c])) S->nonfinite = 1;
+    S->alpha_p[c] = ap;
+    S->beta[c] = be;
+    S->gamma[c] = gam_new[c];
+    S->rr[c] = rr[c];
+    int st;
+    if (rr[c] < S->tau2[c]) st = SPH_CONVERGED;
+    else if (S->stall_now[c] || om == 0.0 || !isfinite(rr[c])) st = SPH_STALLED;
+    else st = SPH_PROGRESSING;
+    if (st == SPH_STALLED) S->stalled_any[c] = 1;
+    S->state[c] = st;
+    progressing += (st == SPH_PROGRESSING);
+  }
+  S->iter += 1;
+  S->done = (progressing == 0 || S->iter >= S->maxit) ? 1 : 0;
+}
+
+
+// pass initialisation from gamma0 = r0.r0 (= b.b of the inner system)
+__device__ inline void scal_init(SolverScalars* S, const double* g, double eps2, int maxit) {
+  int progressing = 0;
+  for (int c = 0; c < 3; ++c) {
+    S->gamma[c] = g[c];
+    S->rr[c] = g[c];
+    S->tau2[c] = fmax(eps2 * g[c], kFltMin);
+    S->alpha[c] = S->alpha_p[c] = S->beta[c] = S->omega[c] = S->delta[c] = 0.0;
+    S->stall_now[c] = 0;
+    S->stalled_any[c] = 0;
+    const int st = (g[c] == 0.0 || g[c] < S->tau2[c]) ? SPH_CONVERGED : SPH_PROGRESSING;
+    S->state[c] = st;
+    progressing += (st == SPH_PROGRESSING);
+  }
+  S->iter = 0;
+  S->maxit = maxit;
+  S->nonfinite = 0;
+  S->done = progressing == 0 ? 1 : 0;
+  S->pad = S->done;
+}
+
+}  // namespace sph

@@ -114,6 +114,9 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
   h->op_kind.release();
   h->invD.release();
   h->D64.release();
+  h->aux64.release();
+  h->v_xh.release();
+  h->v_xl.release();
   h->tmp_i32a.release();
   h->tmp_i32b.release();
   h->tmp_i64.release();
@@ -131,6 +134,7 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
   h->r64.release();
   h->partials.release();
   h->counters.release();
+  h->counters64.release();
   h->scal.release();
   for (auto& w : h->w64) w.release();
   for (auto& e : h->prof_ev)

@@ -25,19 +25,42 @@ namespace {
 
 struct OpGeom {
   double L[3];
+  double invL[3];
   int periodic[3];
   double h;
   double inv_h;
 };
 
-// float64 relative position r_a - r_b with the minimum image (Sec. 2.2 / App. A)
-__device__ __forceinline__ double pair_r(float4 pa, float4 pb, const OpGeom& g) {
+// float64 sqrt and reciprocal from a float32 seed plus one Newton step: relative
+// error ~1e-14 at a handful of float64 operations (float64 runs at a small
+// fraction of the float32 rate on this GPU; an IEEE sqrt or divide costs ~10x).
+__device__ __forceinline__ double sqrt_newton(double x) {
+  const float sf = sqrtf((float)x);
+  if (sf == 0.f) return 0.0;
+  const double s0 = (double)sf;
+  return fma(fma(-s0, s0, x), (double)(0.5f / sf), s0);
+}
+__device__ __forceinline__ double rcp_newton(double x) {
+  const double y0 = (double)__frcp_rn((float)x);
+  return y0 * fma(-x, y0, 2.0);
+}
+
+// |r_a - r_b| for the coefficients (the neighbour predicate itself is decided
+// elsewhere, bit for bit; here ~1e-14 relative is enough)
+__device__ __forceinline__ double pair_r_fast(float4 pa, float4 pb, const OpGeom& g) {
   double d[3] = {(double)pa.x - (double)pb.x, (double)pa.y - (double)pb.y, (double)pa.z - (double)pb.z};
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    if (g.periodic[ax]) d[ax] = d[ax] - g.L[ax] * rint(d[ax] / g.L[ax]);
+    if (g.periodic[ax]) d[ax] = fma(-g.L[ax], rint(d[ax] * g.invL[ax]), d[ax]);
   }
-  return sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  return sqrt_newton(fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2])));
+}
+
+// per particle: V = m / rho and 1 / mu in float64 (N divisions instead of one per pair)
+__global__ void k_op_aux(const float4* __restrict__ pos, const float* __restrict__ rho, const float* __restrict__ mu,
+                         int64_t n_pad, double2* __restrict__ aux) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x)
+    aux[s] = make_double2((double)pos[s].w / (double)rho[s], 1.0 / (double)mu[s]);
 }
 
 // Wendland psi_{3,1} (Sec. 5.2): w(q) = 21/(16 pi) (1 - q/2)^4 (2q + 1);
@@ -48,16 +71,6 @@ __device__ __forceinline__ double wendland_w(double q) {
   const double t2 = t * t;
   return (21.0 / (16.0 * M_PI)) * (t2 * t2) * (2.0 * q + 1.0);
 }
-__device__ __forceinline__ double wendland_absf(double q) {
-  if (q >= 2.0) return 0.0;
-  const double t = 2.0 - q;
-  return (105.0 / (128.0 * M_PI)) * (t * t * t);
-}
-
-__device__ __forceinline__ double mean_mu(double ma, double mb, int mean) {
-  return mean == SPH_MEAN_ARITHMETIC ? 0.5 * (ma + mb) : 2.0 * ma * mb / (ma + mb);
-}
-
 __global__ void k_op_count(const float4* __restrict__ pos, const uint8_t* __restrict__ type,
                            const int32_t* __restrict__ cnt, const int64_t* __restrict__ slice_off,
                            const int32_t* __restrict__ nbr, int64_t n, int64_t n_pad, OpGeom g, int boundary,
@@ -86,7 +99,7 @@ __global__ void k_op_count(const float4* __restrict__ pos, const uint8_t* __rest
     for (int j = 0; j < c; ++j) {
       const int32_t t = nbr[base + (int64_t)j * kSlice];
       if (type[t] != SPH_FLUID) continue;
-      S += wendland_w(pair_r(pos[t], pb, g) * g.inv_h);
+      S += wendland_w(pair_r_fast(pos[t], pb, g) * g.inv_h);
       ++nf;
     }
     if (S > 0.0) {
@@ -100,13 +113,15 @@ __global__ void k_op_count(const float4* __restrict__ pos, const uint8_t* __rest
 }
 
 __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restrict__ rho, const float* __restrict__ mu,
-                          const uint8_t* __restrict__ type, const int32_t* __restrict__ cnt,
-                          const int64_t* __restrict__ slice_off, const int32_t* __restrict__ nbr,
-                          const uint8_t* __restrict__ kind, const int64_t* __restrict__ op_off, int64_t n,
-                          int64_t n_pad, OpGeom g, double dt, int mean, int2* __restrict__ op_ih,
-                          float* __restrict__ op_lo, float* __restrict__ invD, double* __restrict__ D64) {
-  // 2 |f(q)| / h^5 folds into one float64 constant per scene
+                          const uint8_t* __restrict__ type, const double2* __restrict__ aux,
+                          const int32_t* __restrict__ cnt, const int64_t* __restrict__ slice_off,
+                          const int32_t* __restrict__ nbr, const uint8_t* __restrict__ kind,
+                          const int64_t* __restrict__ op_off, int64_t n, int64_t n_pad, OpGeom g, double dt, int mean,
+                          int2* __restrict__ op_ih, float* __restrict__ op_lo, float* __restrict__ invD,
+                          double* __restrict__ D64) {
+  // a_ba = dt c_ab = [2 dt (105/(128 pi)) / (h^5 rho_b)] * V_a * mubar * (2 - q)^3
   const double inv_h5 = g.inv_h * g.inv_h * g.inv_h * g.inv_h * g.inv_h;
+  const double kf = 2.0 * dt * (105.0 / (128.0 * M_PI)) * inv_h5;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
     if (s >= n || kind[s] == KIND_IDENTITY) {
       invD[s] = 1.f;
@@ -120,16 +135,18 @@ __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restric
     int o = 0;
     if (kind[s] == KIND_FLUID) {
       const double mub_self = (double)mu[s];
-      const double rho_b = (double)rho[s];
+      const double imu_self = aux[s].y;
+      const double Rb = kf / (double)rho[s];
       double sum = 0.0;
       for (int j = 0; j < c; ++j) {
         const int32_t t = nbr[base + (int64_t)j * kSlice];
         const float4 pa = pos[t];
-        const double q = pair_r(pa, pb, g) * g.inv_h;
-        const double absF = wendland_absf(q) * inv_h5;
-        const double mub = (type[t] == SPH_FLUID) ? mean_mu((double)mu[t], mub_self, mean) : mub_self;
-        const double cab = 2.0 * mub * (double)pa.w * absF / ((double)rho[t] * rho_b);
-        const double a = dt * cab;
+        const double2 at = aux[t];
+        const double tq = fmax(2.0 - pair_r_fast(pa, pb, g) * g.inv_h, 0.0);
+        double mub = mub_self;
+        if (type[t] == SPH_FLUID)
+          mub = (mean == SPH_MEAN_ARITHMETIC) ? 0.5 * ((double)mu[t] + mub_self) : 2.0 * rcp_newton(at.y + imu_self);
+        const double a = Rb * at.x * mub * (tq * tq * tq);
         const float hi = __double2float_rn(a);
         const float lo = __double2float_rn(a - (double)hi);
         const int64_t e = obase + (int64_t)o * kSlice;
@@ -141,18 +158,18 @@ __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restric
       const double D = 1.0 + sum;
       D64[s] = D;
       invD[s] = __double2float_rn(1.0 / D);
-    } else {  // Shepard wall row: W_ba / S_b over fluid neighbours
+    } else {  // Shepard wall row: W_ba / S_b over fluid neighbours (the 1/h^3 cancels)
       double S = 0.0;
       for (int j = 0; j < c; ++j) {
         const int32_t t = nbr[base + (int64_t)j * kSlice];
         if (type[t] != SPH_FLUID) continue;
-        S += wendland_w(pair_r(pos[t], pb, g) * g.inv_h);
+        S += wendland_w(pair_r_fast(pos[t], pb, g) * g.inv_h);
       }
       const double invS = 1.0 / S;
       for (int j = 0; j < c; ++j) {
         const int32_t t = nbr[base + (int64_t)j * kSlice];
         if (type[t] != SPH_FLUID) continue;
-        const double a = wendland_w(pair_r(pos[t], pb, g) * g.inv_h) * invS;
+        const double a = wendland_w(pair_r_fast(pos[t], pb, g) * g.inv_h) * invS;
         const float hi = __double2float_rn(a);
         const float lo = __double2float_rn(a - (double)hi);
         const int64_t e = obase + (int64_t)o * kSlice;
@@ -195,50 +212,81 @@ __global__ void k_scatter_f4(const float4* __restrict__ y_s, const int32_t* __re
     reinterpret_cast<float4*>(y_caller)[perm[s]] = y_s[s];
 }
 
-}  // namespace
+// x64 -> float32 hi + lo (x = hi + lo to ~2^-48 relative)
+__global__ void k_split_x(const double* __restrict__ x, int64_t n_pad, float4* __restrict__ xh,
+                          float4* __restrict__ xl) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    const double x0 = x[3 * s], x1 = x[3 * s + 1], x2 = x[3 * s + 2];
+    const float h0 = (float)x0, h1 = (float)x1, h2 = (float)x2;
+    xh[s] = make_float4(h0, h1, h2, 0.f);
+    xl[s] = make_float4((float)(x0 - (double)h0), (float)(x1 - (double)h1), (float)(x2 - (double)h2), 0.f);
+  }
+}
 
-// float64 residual r = b - A x on sorted [n_pad][3] arrays; partial sums of
-// r_c^2 (K = 3) go through the grid reduction into res_out[0..3) when given.
-__global__ void __launch_bounds__(kBlock) k_residual_f64(const int64_t* __restrict__ op_off,
-                                                         const int32_t* __restrict__ op_cnt,
-                                                         const int2* __restrict__ op_ih,
-                                                         const float* __restrict__ op_lo,
-                                                         const uint8_t* __restrict__ kind,
-                                                         const double* __restrict__ x, const double* __restrict__ b,
-                                                         double* __restrict__ r, int64_t n, int64_t nslices,
-                                                         double* __restrict__ partials, unsigned int* counter,
-                                                         double* __restrict__ res_out) {
+// Knuth's TwoSum: s + e == a + b exactly (no branch, any magnitudes)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// sum_a a_ba (kap x_b - x_a) for one component with float32 error-free
+// transformations: the difference of the hi parts exactly (TwoSum), its product
+// with a_hi exactly (Dekker's TwoProd via fma), the running sum exactly
+// (TwoSum), and the terms of order 2^-24 (a_hi * diff error, a_lo * diff,
+// a_hi * lo-part difference) in plain float32.  Error ~2^-47 of sum |terms|.
+struct DFAcc {
+  float sh = 0.f, sl = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float ahi, float alo, float kxbh, float xah, float kxbl, float xal) {
+    float d, de;
+    two_sum(kxbh, -xah, d, de);
+    const float p = ahi * d;
+    const float pe = fmaf(ahi, d, -p);
+    float t, te;
+    two_sum(sh, p, t, te);
+    sh = t;
+    sl += te;
+    c += pe + fmaf(ahi, de, fmaf(alo, d, ahi * (kxbl - xal)));
+  }
+  __device__ __forceinline__ double value() const { return (double)sh + ((double)sl + (double)c); }
+};
+
+// float64-accurate residual r = b - A x on sorted [n_pad][3] arrays, float32
+// arithmetic per pair and float64 per row; partial sums of r_c^2 (K = 3) go
+// through the grid reduction into res_out[0..3) when partials is given.
+__global__ void __launch_bounds__(kBlock) k_residual_df(OpView op, const float* __restrict__ op_lo,
+                                                        const float4* __restrict__ xh, const float4* __restrict__ xl,
+                                                        const double* __restrict__ x, const double* __restrict__ b,
+                                                        double* __restrict__ r, int64_t n, double* __restrict__ partials,
+                                                        unsigned int* counter, double* __restrict__ res_out) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double acc2[3] = {0.0, 0.0, 0.0};
-  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nwarps) {
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
     const int64_t s = sl * kSlice + lane;
-    const int c = op_cnt[s];
-    const uint8_t k = kind[s];
-    const double xb0 = x[3 * s], xb1 = x[3 * s + 1], xb2 = x[3 * s + 2];
-    const double kap = (k == KIND_FLUID) ? 1.0 : 0.0;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    const int64_t base = op_off[sl] + lane;
+    const int c = op.cnt[s];
+    const uint8_t k = op.kind[s];
+    const float kap = (k == KIND_FLUID) ? 1.f : 0.f;
+    const float4 bh = xh[s], bl = xl[s];
+    const float kbh0 = kap * bh.x, kbh1 = kap * bh.y, kbh2 = kap * bh.z;
+    const float kbl0 = kap * bl.x, kbl1 = kap * bl.y, kbl2 = kap * bl.z;
+    DFAcc a0, a1, a2;
+    const int64_t base = op.off[sl] + lane;
     for (int j = 0; j < c; ++j) {
       const int64_t e = base + (int64_t)j * kSlice;
-      const int2 ih = op_ih[e];
-      const int32_t t = ih.x;
-      const double a = (double)__int_as_float(ih.y) + (double)op_lo[e];
-      a0 += a * (kap * xb0 - x[3 * t]);
-      a1 += a * (kap * xb1 - x[3 * t + 1]);
-      a2 += a * (kap * xb2 - x[3 * t + 2]);
+      const int2 ih = op.ih[e];
+      const float ahi = __int_as_float(ih.y), alo = op_lo[e];
+      const float4 ah = xh[ih.x], al = xl[ih.x];
+      a0.add(ahi, alo, kbh0, ah.x, kbl0, al.x);
+      a1.add(ahi, alo, kbh1, ah.y, kbl1, al.y);
+      a2.add(ahi, alo, kbh2, ah.z, kbl2, al.z);
     }
-    double y0 = xb0, y1 = xb1, y2 = xb2;
-    if (k == KIND_FLUID) {
-      y0 += a0; y1 += a1; y2 += a2;
-    } else if (k == KIND_SHEPARD) {
-      y0 -= a0; y1 -= a1; y2 -= a2;
-    }
+    const double sg = (k == KIND_FLUID) ? 1.0 : (k == KIND_SHEPARD ? -1.0 : 0.0);
     double r0 = 0.0, r1 = 0.0, r2 = 0.0;
     if (s < n) {
-      r0 = b[3 * s] - y0;
-      r1 = b[3 * s + 1] - y1;
-      r2 = b[3 * s + 2] - y2;
+      r0 = b[3 * s] - (x[3 * s] + sg * a0.value());
+      r1 = b[3 * s + 1] - (x[3 * s + 1] + sg * a1.value());
+      r2 = b[3 * s + 2] - (x[3 * s + 2] + sg * a2.value());
     }
     r[3 * s] = r0;
     r[3 * s + 1] = r1;
@@ -256,6 +304,8 @@ __global__ void __launch_bounds__(kBlock) k_residual_f64(const int64_t* __restri
   }
 }
 
+}  // namespace
+
 sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStream_t st) {
   if (!P || !(P->dt > 0.0) || !std::isfinite(P->dt) || (P->boundary != SPH_BC_DUMMY && P->boundary != SPH_BC_DYNAMIC) ||
       (P->mean != SPH_MEAN_HARMONIC && P->mean != SPH_MEAN_ARITHMETIC)) {
@@ -268,6 +318,7 @@ sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStrea
   OpGeom g{};
   for (int ax = 0; ax < 3; ++ax) {
     g.L[ax] = H->grid.L[ax];
+    g.invL[ax] = 1.0 / H->grid.L[ax];
     g.periodic[ax] = H->grid.periodic[ax];
   }
   g.h = (double)H->h;
@@ -288,7 +339,10 @@ sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStrea
   SPH_TRY(H->op_lo.alloc(total_pad > 0 ? total_pad : 1));
   H->op_nnz_pad = total_pad;
   H->op_nnz = total;
-  SPH_LAUNCH(k_op_fill, grid, kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->type_s.p, H->cnt.p, H->slice_off.p,
+  SPH_TRY(H->aux64.alloc(H->n_pad));
+  SPH_LAUNCH(k_op_aux, grid, kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->n_pad, H->aux64.p);
+  SPH_LAUNCH(k_op_fill, grid, kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->type_s.p, H->aux64.p, H->cnt.p,
+                                             H->slice_off.p,
                                      H->nbr.p, H->op_kind.p, H->op_off.p, H->n, H->n_pad, g, P->dt, P->mean,
                                      H->op_ih.p, H->op_lo.p, H->invD.p, H->D64.p);
   SPH_TRY_CUDA(cudaGetLastError());
@@ -300,8 +354,9 @@ sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStrea
 
 void launch_residual_f64(const sph_neighbors* H, int grid, const double* x, const double* b, double* r,
                          double* partials, unsigned int* counter, double* res_out, cudaStream_t st) {
-  SPH_LAUNCH(k_residual_f64, grid, kBlock, 0, st)(H->op_off.p, H->op_cnt.p, H->op_ih.p, H->op_lo.p,
-                                          H->op_kind.p, x, b, r, H->n, H->nslices, partials, counter, res_out);
+  SPH_LAUNCH(k_split_x, grid_for(H, H->n_pad), kBlock, 0, st)(x, H->n_pad, H->v_xh.p, H->v_xl.p);
+  SPH_LAUNCH(k_residual_df, grid, kBlock, 0, st)(op_view(H), H->op_lo.p, H->v_xh.p, H->v_xl.p, x, b, r, H->n,
+                                                 partials, counter, res_out);
 }
 
 OpView op_view(const sph_neighbors* H) {

@@ -143,10 +143,4 @@ sph_status mu_papanastasiou(sph_neighbors* H, const float* vel, const float* wal
   return SPH_OK;
 }
 
-sph_status solve_fp64(sph_neighbors*, const sph_visc_params*, const sph_solve_opts*, const double*, double*,
-                      sph_solve_report*, cudaStream_t) {
-  set_error("sph_visc_solve: SPH_PREC_FP64 is not available in this build");
-  return SPH_ERR_INVALID;
-}
-
 }  // namespace sph

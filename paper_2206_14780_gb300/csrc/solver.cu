@@ -5,7 +5,7 @@
 // Iteration i (restructured listing of Sec. 4.2):
 //   p     = r + beta p - alpha' A p           (a zero coefficient skips its vector)
 //   delta = r0^ . A p ;  alpha = gamma / delta
-//   r*    = r - alpha A p ;  d += alpha p
+//   r*    = r - alpha A p ;  d += alpha p   (applied in the x/r update kernel)
 //   omega = (r* . A r*) / (A r* . A r*)
 //   r     = r* - omega A r* ;  d += omega r*
 //   gamma' = r0^ . r ;  alpha' = gamma' / delta ;  beta = alpha' / omega
@@ -28,6 +28,7 @@
 #include <cstring>
 
 #include "apply.cuh"
+#include "bicgstab_scalars.cuh"
 #include "reduce.cuh"
 #include "sph_internal.cuh"
 
@@ -35,8 +36,6 @@ namespace sph {
 
 
 namespace {
-
-constexpr double kFltMin = 1.17549435082228750797e-38;  // 2^-126
 
 enum Phase : int { PH_DELTA = 0, PH_OMEGA = 1, PH_OMEGA_MERGED = 2 };
 
@@ -49,80 +48,6 @@ struct Vecs {
   float4* As;
   float4* d;
 };
-
-// ---- scalar updates (thread 0 of the last block) -------------------------
-
-__device__ void scal_after_delta(SolverScalars* S, const double* dots) {
-  for (int c = 0; c < 3; ++c) {
-    if (S->state[c] != SPH_PROGRESSING) {
-      S->alpha[c] = 0.0;
-      S->stall_now[c] = 0;
-      continue;
-    }
-    const double d = dots[c];
-    S->delta[c] = d;
-    double a = 0.0;
-    int stall = 0;
-    if (d == 0.0 || !isfinite(d)) {
-      stall = 1;
-    } else {
-      a = S->gamma[c] / d;
-      if (!isfinite(a)) {
-        a = 0.0;
-        stall = 1;
-      }
-    }
-    S->alpha[c] = a;
-    S->stall_now[c] = stall;
-  }
-}
-
-__device__ void scal_after_omega(SolverScalars* S, const double* dots) {
-  for (int c = 0; c < 3; ++c) {
-    if (S->state[c] != SPH_PROGRESSING) {
-      S->omega[c] = 0.0;
-      continue;
-    }
-    const double sA = dots[c], AA = dots[3 + c];
-    double om = (AA > 0.0 && isfinite(AA)) ? sA / AA : 0.0;
-    if (!isfinite(om)) om = 0.0;
-    S->omega[c] = om;
-  }
-}
-
-// gamma' and r.r known: alpha', beta, states, iteration count, stop flag.
-__device__ void scal_after_update(SolverScalars* S, const double* gam_new, const double* rr) {
-  int progressing = 0;
-  for (int c = 0; c < 3; ++c) {
-    if (S->state[c] != SPH_PROGRESSING) {
-      S->alpha_p[c] = 0.0;
-      S->beta[c] = 0.0;
-      continue;
-    }
-    const double om = S->omega[c];
-    const bool ok = !S->stall_now[c] && om != 0.0;
-    double ap = ok ? gam_new[c] / S->delta[c] : 0.0;
-    double be = ok ? ap / om : 0.0;
-    if (!isfinite(ap) || !isfinite(be)) {
-      ap = 0.0;
-      be = 0.0;
-    }
-    if (!isfinite(gam_new[c]) || !isfinite(rr[c])) S->nonfinite = 1;
-    S->alpha_p[c] = ap;
-    S->beta[c] = be;
-    S->gamma[c] = gam_new[c];
-    S->rr[c] = rr[c];
-    int st;
-    if (rr[c] < S->tau2[c]) st = SPH_CONVERGED;
-    else if (S->stall_now[c] || om == 0.0 || !isfinite(rr[c])) st = SPH_STALLED;
-    else st = SPH_PROGRESSING;
-    if (st == SPH_STALLED) S->stalled_any[c] = 1;
-    S->state[c] = st;
-    progressing += (st == SPH_PROGRESSING);
-  }
-  S->iter += 1;
-  S->done = (progressing == 0 || S->iter >= S->maxit) ? 1 : 0;
-}
 
 // ---- kernels ----------------------------------------------------------------
 
@@ -146,26 +71,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_init(const double* __restrict__
   if (arrive_last(counter)) {
     __shared__ double res[3];
     final_sum<3>(partials, counter, res);
-    if (threadIdx.x == 0) {
-      int progressing = 0;
-      for (int c = 0; c < 3; ++c) {
-        const double g = res[c];
-        S->gamma[c] = g;
-        S->rr[c] = g;
-        S->tau2[c] = fmax(eps2 * g, kFltMin);
-        S->alpha[c] = S->alpha_p[c] = S->beta[c] = S->omega[c] = S->delta[c] = 0.0;
-        S->stall_now[c] = 0;
-        S->stalled_any[c] = 0;
-        const int st = (g == 0.0 || g < S->tau2[c]) ? SPH_CONVERGED : SPH_PROGRESSING;
-        S->state[c] = st;
-        progressing += (st == SPH_PROGRESSING);
-      }
-      S->iter = 0;
-      S->maxit = maxit;
-      S->nonfinite = 0;
-      S->done = progressing == 0 ? 1 : 0;
-      S->pad = S->done;   // "skip" flag of the fused completion kernel
-    }
+    if (threadIdx.x == 0) scal_init(S, res, eps2, maxit);
   }
 }
 
@@ -263,34 +169,30 @@ __global__ void __launch_bounds__(kBlock) k_apply_dot(OpView op, const float4* _
   }
 }
 
-// r* = r - alpha Ap ; d += alpha p
+// r* = r - alpha Ap (the matching d += alpha p is folded into the x/r update)
 __global__ void __launch_bounds__(kBlock) k_rstar(int64_t n_pad, Vecs V, const SolverScalars* __restrict__ S) {
   if (S->done) return;
   const float a0 = (float)S->alpha[0], a1 = (float)S->alpha[1], a2 = (float)S->alpha[2];
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
-    const float4 r = V.r[s], ap = V.Ap[s], p = V.p[s];
-    float4 d = V.d[s];
+    const float4 r = V.r[s], ap = V.Ap[s];
     V.rs[s] = make_float4(fmaf(-a0, ap.x, r.x), fmaf(-a1, ap.y, r.y), fmaf(-a2, ap.z, r.z), 0.f);
-    d.x = fmaf(a0, p.x, d.x);
-    d.y = fmaf(a1, p.y, d.y);
-    d.z = fmaf(a2, p.z, d.z);
-    V.d[s] = d;
   }
 }
 
-// r = r* - omega Ar* ; d += omega r* ; dots r0^.r, r.r (paper-exact gamma')
+// r = r* - omega Ar* ; d += alpha p + omega r* ; dots r0^.r, r.r (paper-exact gamma')
 __global__ void __launch_bounds__(kBlock) k_xr_update(int64_t n_pad, Vecs V, SolverScalars* S, double* partials,
                                                       unsigned int* counter) {
   if (S->done) return;
   const float w0 = (float)S->omega[0], w1 = (float)S->omega[1], w2 = (float)S->omega[2];
+  const float al0 = (float)S->alpha[0], al1 = (float)S->alpha[1], al2 = (float)S->alpha[2];
   float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
-    const float4 rs = V.rs[s], as = V.As[s], h = V.rh[s];
+    const float4 rs = V.rs[s], as = V.As[s], h = V.rh[s], p = V.p[s];
     float4 d = V.d[s];
     const float4 r = make_float4(fmaf(-w0, as.x, rs.x), fmaf(-w1, as.y, rs.y), fmaf(-w2, as.z, rs.z), 0.f);
-    d.x = fmaf(w0, rs.x, d.x);
-    d.y = fmaf(w1, rs.y, d.y);
-    d.z = fmaf(w2, rs.z, d.z);
+    d.x = fmaf(w0, rs.x, fmaf(al0, p.x, d.x));
+    d.y = fmaf(w1, rs.y, fmaf(al1, p.y, d.y));
+    d.z = fmaf(w2, rs.z, fmaf(al2, p.z, d.z));
     V.r[s] = r;
     V.d[s] = d;
     acc[0] = fmaf(h.x, r.x, acc[0]);
@@ -308,7 +210,7 @@ __global__ void __launch_bounds__(kBlock) k_xr_update(int64_t n_pad, Vecs V, Sol
   }
 }
 
-// merged form: r = r* - omega Ar* ; d += omega r* ; p = r + beta p - alpha' Ap.
+// merged form: r = r* - omega Ar* ; d += alpha p + omega r* ; p = r + beta p - alpha' Ap.
 // Runs for the iteration whose omega kernel set the stop flag too (the
 // iteration completes); `pad` carries "skip" and is re-armed by the last block.
 __global__ void __launch_bounds__(kBlock) k_xrp_update(int64_t n_pad, Vecs V, SolverScalars* S,
@@ -317,13 +219,14 @@ __global__ void __launch_bounds__(kBlock) k_xrp_update(int64_t n_pad, Vecs V, So
   const float w0 = (float)S->omega[0], w1 = (float)S->omega[1], w2 = (float)S->omega[2];
   const float b0 = (float)S->beta[0], b1 = (float)S->beta[1], b2 = (float)S->beta[2];
   const float a0 = (float)S->alpha_p[0], a1 = (float)S->alpha_p[1], a2 = (float)S->alpha_p[2];
+  const float al0 = (float)S->alpha[0], al1 = (float)S->alpha[1], al2 = (float)S->alpha[2];
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
     const float4 rs = V.rs[s], as = V.As[s], p = V.p[s], ap = V.Ap[s];
     float4 d = V.d[s];
     const float4 r = make_float4(fmaf(-w0, as.x, rs.x), fmaf(-w1, as.y, rs.y), fmaf(-w2, as.z, rs.z), 0.f);
-    d.x = fmaf(w0, rs.x, d.x);
-    d.y = fmaf(w1, rs.y, d.y);
-    d.z = fmaf(w2, rs.z, d.z);
+    d.x = fmaf(w0, rs.x, fmaf(al0, p.x, d.x));
+    d.y = fmaf(w1, rs.y, fmaf(al1, p.y, d.y));
+    d.z = fmaf(w2, rs.z, fmaf(al2, p.z, d.z));
     V.r[s] = r;
     V.d[s] = d;
     V.p[s] = make_float4(fmaf(-a0, ap.x, fmaf(b0, p.x, r.x)), fmaf(-a1, ap.y, fmaf(b1, p.y, r.y)),
@@ -405,6 +308,8 @@ sph_status ensure_workspace(sph_neighbors* H) {
   SPH_TRY(H->x64.alloc(3 * np));
   SPH_TRY(H->b64.alloc(3 * np));
   SPH_TRY(H->r64.alloc(3 * np));
+  SPH_TRY(H->v_xh.alloc(np));
+  SPH_TRY(H->v_xl.alloc(np));
   if (H->red_grid == 0) {
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply_dot<PH_OMEGA_MERGED, 8>, kBlock, 0);

@@ -139,6 +139,7 @@ struct sph_neighbors {
   sph::DBuf<uint8_t> op_kind;      // 0 fluid (difference form), 1 Shepard wall, 2 identity
   sph::DBuf<float> invD;           // float32 1/D (Jacobi), 1 for wall rows
   sph::DBuf<double> D64;           // float64 D
+  sph::DBuf<double2> aux64;        // per particle (m / rho, 1 / mu) in float64
   int64_t op_nnz_pad = 0;
 
   // scratch used by builds and solves
@@ -149,8 +150,10 @@ struct sph_neighbors {
   // solver workspace
   sph::DBuf<float4> v_r, v_rh, v_p, v_Ap, v_rs, v_As, v_d, v_tmp;
   sph::DBuf<double> x64, b64, r64;   // [n_pad][3]
+  sph::DBuf<float4> v_xh, v_xl;      // x64 split into float32 hi + lo (double-float residual)
   sph::DBuf<double> partials;        // [grid][kMaxDots]
   sph::DBuf<unsigned int> counters;  // last-block counters
+  sph::DBuf<unsigned int> counters64;  // last-block counters of the float64 solve
   sph::DBuf<sph::SolverScalars> scal;
   int32_t* host_flags = nullptr;     // pinned [4]
   sph::SolverScalars* host_scal = nullptr;  // pinned
@@ -165,7 +168,7 @@ struct sph_neighbors {
   int64_t prof_n = 0;
   int64_t op_nnz = 0;
 
-  // FP64-precision solve workspace
+  // float64 solve vectors r, r0^, p, Ap, r*, Ar* ([n_pad][3] each)
   sph::DBuf<double> w64[7];
 };
 

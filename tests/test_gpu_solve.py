@@ -75,3 +75,32 @@ def test_iteration_cap_reports_not_converged():
     x, rep = gpu_solve(nb, s, binding.solve_opts(maxit=3, max_refine=1))
     assert rep["status"] == 6 and rep["iters"] <= 3
     assert np.all(np.isfinite(x))
+
+
+@pytest.mark.parametrize("name", ["couette_dummy", "random_box_mu_mass", "lava_box_12", "couette_dynamic"])
+@pytest.mark.parametrize("merged", [0, 1])
+def test_fp64_solve_matches_oracle(name, merged):
+    from paper_2206_14780_gb300 import binding
+
+    s = SCENES_SMALL[name]()
+    nb, _ = lib_build(s)
+    off, idx, A = oracle_system(s)
+    x_ref = osv.reference_solution(A, s.b, s.x0)
+    x, rep = gpu_solve(nb, s, binding.solve_opts(precision=binding.SPH_PREC_FP64, merged_reductions=merged))
+    res, _ = oop.true_residual(A, x, s.b)
+    assert rep["status"] == 0 and res <= RTOL_RES, (res, rep)
+    assert rel_l2(x, x_ref) <= RTOL_SOL
+
+
+def test_fp64_solve_reaches_tight_tolerance():
+    # the float64 mode goes far below what float32 iterations can: 1e-11 true residual
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.lava_box(6, n=14)
+    nb, _ = lib_build(s)
+    off, idx, A = oracle_system(s)
+    x_ref = osv.reference_solution(A, s.b, s.x0, rtol=1e-14)
+    x, rep = gpu_solve(nb, s, binding.solve_opts(rtol=1e-11, precision=binding.SPH_PREC_FP64))
+    res, _ = oop.true_residual(A, x, s.b)
+    assert rep["status"] == 0 and res <= 1e-11, (res, rep)
+    assert rel_l2(x, x_ref) <= 1e-9
