@@ -47,7 +47,8 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--merged", type=int, default=0)
-    ap.add_argument("--eps-inner", type=float, default=1e-5)
+    ap.add_argument("--eps-inner", type=float, default=1e-2)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cpu-oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -209,7 +210,8 @@ def run_sphvisc(args):
     binding.load()
     s = scenes.lava_box(rank, n=args.n)
     params = binding.visc_params(s.dt, s.boundary, s.mean)
-    opts = binding.solve_opts(merged_reductions=args.merged, eps_inner=args.eps_inner)
+    opts = binding.solve_opts(merged_reductions=args.merged, eps_inner=args.eps_inner,
+                              precision=binding.SPH_PREC_FP64 if args.precision == "fp64" else binding.SPH_PREC_MIXED)
     t = binding.scene_tensors(s, dev)
     b = torch.from_numpy(s.b).to(dev)
     x0 = torch.from_numpy(s.x0).to(dev)
@@ -297,6 +299,9 @@ def run_sphvisc(args):
                     frac=(achieved / hbm) if achieved else None, traffic=None,
                     kernel="k_apply_dot (operator apply + fused dots)", peak_source=peak_kind,
                     apply_launches=prof["apply_launches"], apply_avg_us=avg_apply_ms * 1e3,
+                    apply_avg_us_Ap=1e3 * prof["phase_ms"][0] / max(1, prof["phase_launches"][0]),
+                    apply_avg_us_Ars=1e3 * prof["phase_ms"][1] / max(1, prof["phase_launches"][1]),
+                    apply_variant=prof["apply_variant"], autotune_us=prof["tune_us"][:2],
                     algorithmic_bytes_per_launch=prof["apply_bytes"])
     cpu = None
     if not args.no_cpu_baseline and world == 1:

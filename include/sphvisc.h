@@ -181,7 +181,12 @@ typedef struct {
                               BiCGSTAB pass on its Jacobi-scaled recursive
                               residual (the paper's tau^2 = max(eps^2 b.b,
                               FLT_MIN), Sec. 4.1); each pass asks for
-                              max(eps_inner, rtol ||b|| / (4 ||r64||)); 0 = 1e-5 */
+                              max(eps_inner, rtol ||b|| / (4 ||r64||)); 0 = 1e-2.
+                              Each pass restarts BiCGSTAB from the float64 true
+                              residual with a fresh shadow vector r0^, which on
+                              stiff systems takes fewer iterations in total than
+                              one long float32 recursion near its accuracy
+                              limit (~kappa * 2^-24)                             */
   int32_t maxit;           /* cap on inner iterations summed over passes          */
   int32_t max_refine;      /* cap on refinement passes                            */
   int32_t precision;       /* SPH_PREC_MIXED or SPH_PREC_FP64                     */
@@ -248,6 +253,12 @@ typedef struct {
                               v, 16 write of the result, 16 read of r0^ for the dot
                               and 9 of row data (count, kind, 1/D)                  */
   int64_t op_nnz;          /* stored coefficients of A(dt)                          */
+  int64_t phase_launches[2]; /* apply_launches split: [0] A p (delta), [1] A r* (omega) */
+  double phase_ms[2];        /* apply_ms split the same way                           */
+  int32_t apply_variant[2];  /* row-loop form the autotuner chose per phase: 0..3 =
+                                (8 entries, plain), (4, plain), (8, prefetch), (4, prefetch) */
+  float tune_us[3][4];       /* autotuner timings (us) per phase (A p, A r*, A r* with
+                                merged dots) and form; 0 where not measured          */
 } sph_profile_counters;
 
 sph_status sph_profile_enable(sph_neighbors* handle, int32_t on);

@@ -53,7 +53,9 @@ class sph_solve_report(ctypes.Structure):
 
 class sph_profile_counters(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("apply_launches", ctypes.c_int64), ("apply_ms", ctypes.c_double),
-                ("apply_bytes", ctypes.c_int64), ("op_nnz", ctypes.c_int64)]
+                ("apply_bytes", ctypes.c_int64), ("op_nnz", ctypes.c_int64),
+                ("phase_launches", ctypes.c_int64 * 2), ("phase_ms", ctypes.c_double * 2),
+                ("apply_variant", ctypes.c_int32 * 2), ("tune_us", (ctypes.c_float * 4) * 3)]
 
 
 class SphError(RuntimeError):
@@ -134,7 +136,7 @@ def visc_params(dt, boundary=SPH_BC_DUMMY, mean=SPH_MEAN_HARMONIC):
     return sph_visc_params(float(dt), int(boundary), int(mean))
 
 
-def solve_opts(rtol=1e-6, eps_inner=1e-5, maxit=20000, max_refine=30, precision=SPH_PREC_MIXED,
+def solve_opts(rtol=1e-6, eps_inner=1e-2, maxit=20000, max_refine=30, precision=SPH_PREC_MIXED,
                merged_reductions=0, chunk=8, jacobi=1):
     return sph_solve_opts(rtol, eps_inner, maxit, max_refine, precision, merged_reductions, chunk, jacobi)
 
@@ -218,7 +220,9 @@ class Neighbors:
         c = sph_profile_counters()
         _check(_lib.sph_profile_read(self.handle, ctypes.byref(c), int(bool(reset))))
         return dict(launches=c.launches, apply_launches=c.apply_launches, apply_ms=c.apply_ms,
-                    apply_bytes=c.apply_bytes, op_nnz=c.op_nnz)
+                    apply_bytes=c.apply_bytes, op_nnz=c.op_nnz, phase_launches=list(c.phase_launches),
+                    phase_ms=list(c.phase_ms), apply_variant=list(c.apply_variant),
+                    tune_us=[list(r) for r in c.tune_us])
 
     def close(self):
         if self.handle:

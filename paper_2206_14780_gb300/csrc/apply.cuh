@@ -31,7 +31,13 @@ struct OpView {
 
 // Fluid rows: v_b + sum a (v_b - v_a) [times 1/D with Jacobi]; Shepard rows:
 // v_b + sum a v_a; identity rows: v_b.
-template <int U, bool JACOBI>
+//
+// PF = false: each group of U entries issues its U coefficient loads, then its U
+// gathers, then the FMAs.  PF = true: the coefficient loads of the next group
+// are issued before the current group's FMAs (software pipelining).  Which of
+// the four (U, PF) forms runs fastest depends on the registers the surrounding
+// kernel needs, so the solver times them on the actual operator (autotune.cu).
+template <int U, bool PF, bool JACOBI>
 __device__ __forceinline__ float4 apply_row(const OpView& op, const float4* __restrict__ v, int64_t sl, int lane,
                                             float4& vb_out) {
   const int64_t s = sl * kSlice + lane;
@@ -44,19 +50,45 @@ __device__ __forceinline__ float4 apply_row(const OpView& op, const float4* __re
   const int w = (int)((op.off[sl + 1] - o0) / kSlice);
   const int2* __restrict__ p = op.ih + o0 + lane;
   float ax = 0.f, ay = 0.f, az = 0.f;
-  for (int j0 = 0; j0 < w; j0 += U) {
+  if (!PF) {
+    for (int j0 = 0; j0 < w; j0 += U) {
+      int2 e[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) e[u] = (j0 + u < c) ? __ldcs(p + (int64_t)(j0 + u) * kSlice) : make_int2((int)s, 0);
+      float4 va[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) va[u] = __ldg(v + e[u].x);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float a = __int_as_float(e[u].y);
+        ax = fmaf(a, fmaf(kap, vb.x, -va[u].x), ax);
+        ay = fmaf(a, fmaf(kap, vb.y, -va[u].y), ay);
+        az = fmaf(a, fmaf(kap, vb.z, -va[u].z), az);
+      }
+    }
+  } else {
     int2 e[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) e[u] = (j0 + u < c) ? __ldcs(p + (int64_t)(j0 + u) * kSlice) : make_int2((int)s, 0);
-    float4 va[U];
+    for (int u = 0; u < U; ++u) e[u] = (u < c) ? __ldcs(p + (int64_t)u * kSlice) : make_int2((int)s, 0);
+    for (int j0 = 0; j0 < w; j0 += U) {
+      float4 va[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) va[u] = __ldg(v + e[u].x);
+      for (int u = 0; u < U; ++u) va[u] = __ldg(v + e[u].x);
+      int2 en[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const float a = __int_as_float(e[u].y);
-      ax = fmaf(a, fmaf(kap, vb.x, -va[u].x), ax);
-      ay = fmaf(a, fmaf(kap, vb.y, -va[u].y), ay);
-      az = fmaf(a, fmaf(kap, vb.z, -va[u].z), az);
+      for (int u = 0; u < U; ++u) {
+        const int j = j0 + U + u;
+        en[u] = (j < c) ? __ldcs(p + (int64_t)j * kSlice) : make_int2((int)s, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float a = __int_as_float(e[u].y);
+        ax = fmaf(a, fmaf(kap, vb.x, -va[u].x), ax);
+        ay = fmaf(a, fmaf(kap, vb.y, -va[u].y), ay);
+        az = fmaf(a, fmaf(kap, vb.z, -va[u].z), az);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) e[u] = en[u];
     }
   }
   if (kd == KIND_FLUID) {
@@ -66,5 +98,8 @@ __device__ __forceinline__ float4 apply_row(const OpView& op, const float4* __re
   if (kd == KIND_SHEPARD) return make_float4(vb.x - ax, vb.y - ay, vb.z - az, 0.f);
   return make_float4(vb.x, vb.y, vb.z, 0.f);
 }
+
+// the four row-loop forms, indexed 0..3 = (U, PF) in {(8,0), (4,0), (8,1), (4,1)}
+constexpr int kApplyVariants = 4;
 
 }  // namespace sph

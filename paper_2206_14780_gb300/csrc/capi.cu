@@ -23,8 +23,9 @@ void clear_error() { g_err[0] = 0; }
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-void prof_begin(sph_neighbors* H, cudaStream_t st) {
+void prof_begin(sph_neighbors* H, cudaStream_t st, int phase) {
   if (!H->prof_on || H->prof_used + 2 > 256) return;
+  H->prof_phase[H->prof_used / 2] = phase;
   cudaEventRecord(H->prof_ev[H->prof_used], st);
 }
 void prof_end(sph_neighbors* H, cudaStream_t st) {
@@ -40,6 +41,9 @@ void prof_flush(sph_neighbors* H, int valid_pairs) {
     if (cudaEventElapsedTime(&ms, H->prof_ev[2 * k], H->prof_ev[2 * k + 1]) == cudaSuccess) {
       H->prof_ms += ms;
       H->prof_n += 1;
+      const int ph = H->prof_phase[k] ? 1 : 0;
+      H->prof_ms_ph[ph] += ms;
+      H->prof_n_ph[ph] += 1;
     }
   }
   H->prof_used = 0;
@@ -136,6 +140,7 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
   h->counters.release();
   h->counters64.release();
   h->scal.release();
+  h->scal_tune.release();
   for (auto& w : h->w64) w.release();
   for (auto& e : h->prof_ev)
     if (e) cudaEventDestroy(e);
@@ -236,9 +241,19 @@ sph_status sph_profile_read(sph_neighbors* h, sph_profile_counters* out, int32_t
     out->apply_ms = h->prof_ms;
     out->op_nnz = h->op_nnz;
     out->apply_bytes = 8 * h->op_nnz + (16 + 16 + 16 + 9) * h->n;
+    for (int k = 0; k < 2; ++k) {
+      out->phase_launches[k] = h->prof_n_ph[k];
+      out->phase_ms[k] = h->prof_ms_ph[k];
+    }
+    out->apply_variant[0] = h->apply_var[0];
+    out->apply_variant[1] = h->apply_var[1] > h->apply_var[2] ? h->apply_var[1] : h->apply_var[2];
+    for (int ph = 0; ph < 3; ++ph)
+      for (int v = 0; v < 4; ++v) out->tune_us[ph][v] = h->tune_us[ph][v];
     if (reset) {
       h->prof_n = 0;
       h->prof_ms = 0.0;
+      h->prof_n_ph[0] = h->prof_n_ph[1] = 0;
+      h->prof_ms_ph[0] = h->prof_ms_ph[1] = 0.0;
     }
   }
   return SPH_OK;

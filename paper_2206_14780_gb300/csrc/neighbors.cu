@@ -412,8 +412,6 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
   } while (0)
 
   TRYF_CUDA(cudaGetDevice(&H->device));
-  // neighbour entries kept in flight per lane by the apply (tuning knob)
-  if (const char* e = std::getenv("SPH_APPLY_UNROLL")) H->unroll = (std::atoi(e) == 4) ? 4 : 8;
   TRYF_CUDA(cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, H->device));
   const int64_t n = sc->n;
   H->n = n;

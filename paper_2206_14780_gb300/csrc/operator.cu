@@ -184,13 +184,13 @@ __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restric
 }
 
 // y = A v (or D^-1 A v) in float32, one warp per 32-row slice, one row per lane.
-template <int U, bool JACOBI>
+template <bool JACOBI>
 __global__ void __launch_bounds__(kBlock) k_apply_f32(OpView op, const float4* __restrict__ v, float4* __restrict__ y) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
     float4 vb;
-    y[sl * kSlice + lane] = apply_row<U, JACOBI>(op, v, sl, lane, vb);
+    y[sl * kSlice + lane] = apply_row<8, false, JACOBI>(op, v, sl, lane, vb);
   }
 }
 
@@ -366,8 +366,7 @@ OpView op_view(const sph_neighbors* H) {
 void launch_apply_f32(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st) {
   const int grid = grid_for(H, H->nslices * 32);
   const OpView op = op_view(H);
-  auto kern = (H->unroll == 4) ? (jacobi ? k_apply_f32<4, true> : k_apply_f32<4, false>)
-                                : (jacobi ? k_apply_f32<8, true> : k_apply_f32<8, false>);
+  auto kern = jacobi ? k_apply_f32<true> : k_apply_f32<false>;
   SPH_LAUNCH(kern, grid, kBlock, 0, st)(op, v, y);
 }
 

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kBlock) k_p_update(int64_t n_pad, Vecs V, cons
 //   PH_DELTA:        v = p,  y = Ap; dots r0^.Ap                       (K = 3)
 //   PH_OMEGA:        v = r*, y = Ar*; dots r*.Ar*, Ar*.Ar*             (K = 6)
 //   PH_OMEGA_MERGED: + r0^.r*, r0^.Ar*, r*.r*                          (K = 15)
-template <int PH, int U>
+template <int PH, int U, bool PF>
 __global__ void __launch_bounds__(kBlock) k_apply_dot(OpView op, const float4* __restrict__ v, float4* __restrict__ y,
                                                       const float4* __restrict__ rh, SolverScalars* S,
                                                       double* partials, unsigned int* counter) {
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_dot(OpView op, const float4* _
   for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
     const int64_t s = sl * kSlice + lane;
     float4 vb;
-    const float4 o = apply_row<U, true>(op, v, sl, lane, vb);
+    const float4 o = apply_row<U, PF, true>(op, v, sl, lane, vb);
     y[s] = o;
     const float4 h = rh[s];
     if (PH == PH_DELTA) {
@@ -168,6 +168,22 @@ __global__ void __launch_bounds__(kBlock) k_apply_dot(OpView op, const float4* _
     }
   }
 }
+
+}  // namespace
+
+// [phase][variant] with variants (U, PF) = (8,0), (4,0), (8,1), (4,1) as in apply.cuh
+ApplyDotFn apply_kernel(int phase, int variant) {
+  static const ApplyDotFn table[3][kApplyVariants] = {
+      {k_apply_dot<PH_DELTA, 8, false>, k_apply_dot<PH_DELTA, 4, false>, k_apply_dot<PH_DELTA, 8, true>,
+       k_apply_dot<PH_DELTA, 4, true>},
+      {k_apply_dot<PH_OMEGA, 8, false>, k_apply_dot<PH_OMEGA, 4, false>, k_apply_dot<PH_OMEGA, 8, true>,
+       k_apply_dot<PH_OMEGA, 4, true>},
+      {k_apply_dot<PH_OMEGA_MERGED, 8, false>, k_apply_dot<PH_OMEGA_MERGED, 4, false>,
+       k_apply_dot<PH_OMEGA_MERGED, 8, true>, k_apply_dot<PH_OMEGA_MERGED, 4, true>}};
+  return table[phase < 0 ? 0 : (phase > 2 ? 2 : phase)][variant < 0 || variant >= kApplyVariants ? 0 : variant];
+}
+
+namespace {
 
 // r* = r - alpha Ap (the matching d += alpha p is folded into the x/r update)
 __global__ void __launch_bounds__(kBlock) k_rstar(int64_t n_pad, Vecs V, const SolverScalars* __restrict__ S) {
@@ -294,7 +310,7 @@ __global__ void __launch_bounds__(kBlock) k_norm2_d3(const double* __restrict__ 
 }  // namespace
 
 // Counters: one per reduction site, so consecutive kernels never share one.
-enum { CNT_INIT = 0, CNT_DELTA, CNT_OMEGA, CNT_XR, CNT_XRP, CNT_RES, CNT_NORM, CNT_COUNT };
+enum { CNT_INIT = 0, CNT_DELTA, CNT_OMEGA, CNT_XR, CNT_XRP, CNT_RES, CNT_NORM, CNT_TUNE, CNT_COUNT };
 
 sph_status ensure_workspace(sph_neighbors* H) {
   const int64_t np = H->n_pad;
@@ -312,9 +328,14 @@ sph_status ensure_workspace(sph_neighbors* H) {
   SPH_TRY(H->v_xl.alloc(np));
   if (H->red_grid == 0) {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply_dot<PH_OMEGA_MERGED, 8>, kBlock, 0);
-    if (occ < 1) occ = 1;
-    H->red_grid = H->num_sms * occ;
+    // the largest grid any apply variant runs with (partials are sized for it)
+    int best = 1;
+    for (int ph = 0; ph < 3; ++ph)
+      for (int v = 0; v < kApplyVariants; ++v) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)apply_kernel(ph, v), kBlock, 0);
+        best = occ > best ? occ : best;
+      }
+    H->red_grid = H->num_sms * best;
   }
   SPH_TRY(H->partials.alloc((size_t)H->red_grid * kMaxDots));
   if (!H->counters.p) {
@@ -347,9 +368,11 @@ static sph_status true_residual(sph_neighbors* H, cudaStream_t st, double rr[3])
 template <int PH>
 static void launch_apply_dot(sph_neighbors* H, int grid, const OpView& op, const float4* v, float4* y,
                              const float4* rh, SolverScalars* S, unsigned int* counter, cudaStream_t st) {
-  auto kern = (H->unroll == 4) ? k_apply_dot<PH, 4> : k_apply_dot<PH, 8>;
-  prof_begin(H, st);
-  SPH_LAUNCH(kern, grid, kBlock, 0, st)(op, v, y, rh, S, H->partials.p, counter);
+  const int var = H->apply_var[PH];
+  const int g = H->apply_grid[PH] > 0 && H->apply_grid[PH] < grid ? H->apply_grid[PH] : grid;
+  const ApplyDotFn kern = apply_kernel(PH, var);
+  prof_begin(H, st, PH == PH_DELTA ? 0 : 1);
+  SPH_LAUNCH(kern, g, kBlock, 0, st)(op, v, y, rh, S, H->partials.p, counter);
   prof_end(H, st);
 }
 
@@ -357,6 +380,7 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
                        double* x, sph_solve_report* R, cudaStream_t st) {
   SPH_TRY(ensure_operator(H, P, st));
   SPH_TRY(ensure_workspace(H));
+  SPH_TRY(autotune_apply(H, O->merged_reductions != 0, H->counters.p + CNT_TUNE, st));
   const int64_t np = H->n_pad;
   const int grid_rows = red_grid_for(H, np);
   const int grid_slices = red_grid_for(H, H->nslices * 32);
@@ -377,7 +401,7 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
   const double bnorm = std::sqrt(bb[0] + bb[1] + bb[2]);
 
   const double rtol = O->rtol > 0.0 ? O->rtol : 1e-6;
-  const double eps_floor = O->eps_inner > 0.0 ? O->eps_inner : 1e-5;
+  const double eps_floor = O->eps_inner > 0.0 ? O->eps_inner : 1e-2;
   const int maxit = O->maxit > 0 ? O->maxit : 10000;
   const int max_ref = O->max_refine > 0 ? O->max_refine : 20;
   const int chunk0 = O->chunk > 0 ? O->chunk : 8;

@@ -16,7 +16,7 @@
 #include <cstdio>
 #include <string>
 
-#include "../../include/sphvisc.h"
+#include "sphvisc.h"
 
 namespace sph {
 
@@ -158,7 +158,13 @@ struct sph_neighbors {
   int32_t* host_flags = nullptr;     // pinned [4]
   sph::SolverScalars* host_scal = nullptr;  // pinned
   int red_grid = 0;                  // blocks of the reducing kernels
-  int unroll = 8;                    // neighbour entries in flight per lane (4 or 8)
+  // apply autotuner (autotune.cu): chosen row-loop form and grid per phase
+  int apply_var[3] = {0, 0, 0};
+  int apply_grid[3] = {0, 0, 0};
+  float tune_us[3][4] = {};
+  bool tuned = false;
+  int64_t tuned_n_pad = 0;
+  sph::DBuf<sph::SolverScalars> scal_tune;
 
   // instrumentation (sph_profile_*)
   bool prof_on = false;
@@ -166,6 +172,9 @@ struct sph_neighbors {
   int prof_used = 0;
   double prof_ms = 0.0;
   int64_t prof_n = 0;
+  int prof_phase[128] = {};
+  double prof_ms_ph[2] = {0.0, 0.0};
+  int64_t prof_n_ph[2] = {0, 0};
   int64_t op_nnz = 0;
 
   // float64 solve vectors r, r0^, p, Ap, r*, Ar* ([n_pad][3] each)
@@ -194,6 +203,9 @@ sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStrea
 void launch_apply_f32(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st);
 struct OpView;
 OpView op_view(const sph_neighbors* H);
+using ApplyDotFn = void (*)(OpView, const float4*, float4*, const float4*, SolverScalars*, double*, unsigned int*);
+ApplyDotFn apply_kernel(int phase, int variant);
+sph_status autotune_apply(sph_neighbors* H, bool merged, unsigned int* counter, cudaStream_t st);
 
 // solver.cu
 sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_solve_opts* O,
@@ -208,7 +220,7 @@ int grid_for(const sph_neighbors* H, int64_t work_items, int block = kBlock);
 
 // event pair around one apply launch when profiling is on; prof_flush folds
 // the recorded pairs into prof_ms (call only after a stream synchronisation)
-void prof_begin(sph_neighbors* H, cudaStream_t st);
+void prof_begin(sph_neighbors* H, cudaStream_t st, int phase = 0);
 void prof_end(sph_neighbors* H, cudaStream_t st);
 void prof_flush(sph_neighbors* H, int valid_pairs);
 
