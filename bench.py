@@ -46,6 +46,8 @@ def parse(argv=None):
     ap.add_argument("--cpu-n", type=int, default=40, help="fluid lattice side of the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-only", action="store_true")
     ap.add_argument("--merged", type=int, default=0)
     ap.add_argument("--eps-inner", type=float, default=1e-2)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -313,6 +315,11 @@ def run_sphvisc(args):
                            f"restarted to a 1e-6 true residual) on the same box workload at {args.cpu_n}^3 fluid "
                            f"(N={rows[0]['n']}), {sec:.1f} s, scaled linearly by particle count to N={s.n}; "
                            f"BiCGSTAB iteration counts depend on dt*nu/dx^2, not on N"))
+    ensemble = None
+    if not args.no_ensemble and world == 1:
+        nb.close()
+        torch.cuda.empty_cache()
+        ensemble = run_ensemble(0, dev)
     its = [r["iters"] for r in reps]
     out = dict(metric=METRIC, value=ms_max / (args.steps * world), unit=UNIT, n_gpus=world, steps=args.steps,
                warmup=max(3, args.warmup), ms_per_step=ms_max / args.steps, higher_is_better=False,
@@ -324,7 +331,7 @@ def run_sphvisc(args):
                            step="neighbour build + A(dt) coefficients + restructured BiCGSTAB to 1e-6",
                            iters=its, passes=[r["refinements"] for r in reps],
                            true_rel_res=[r["true_rel_res"] for r in reps], parallelism=f"replicas x{world}"),
-               roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
+               roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), ensemble=ensemble,
                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"],
                            samples=clk["samples"]),
                wall_s=wall)
@@ -333,6 +340,74 @@ def run_sphvisc(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- ensemble ------
+
+def run_ensemble(seed=0, dev=None):
+    """64 independent scenes (log-uniform 10k-500k particles, nu in 1-1e3, dt in 1e-4-5e-4):
+    one batched solve (persistent kernel in a CUDA graph) vs 64 sequential plain solves."""
+    import torch
+
+    import scenes
+    from paper_2206_14780_gb300 import binding
+
+    dev = dev or torch.device("cuda", 0)
+    ens = scenes.ensemble(seed)
+    nbs, bs, x0s, params = [], [], [], []
+    for s in ens:
+        t = binding.scene_tensors(s, dev)
+        nbs.append(binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h))
+        bs.append(torch.from_numpy(s.b).to(dev))
+        x0s.append(torch.from_numpy(s.x0).to(dev))
+        params.append(binding.visc_params(s.dt, s.boundary, s.mean))
+    opts = binding.solve_opts()
+    stream = torch.cuda.current_stream(dev)
+    xs = [x.clone() for x in x0s]
+
+    def sequential():
+        reps = []
+        for nb, p, b, x, x0 in zip(nbs, params, bs, xs, x0s):
+            x.copy_(x0)
+            reps.append(nb.solve(p, opts, b, x))
+        return reps
+
+    sequential()                                   # warm-up: coefficients + per-handle autotune
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    seq = sequential()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    seq_ms = e0.elapsed_time(e1)
+    batch = binding.Batch(nbs, params)
+    for x, x0 in zip(xs, x0s):
+        x.copy_(x0)
+    batch.solve(opts, bs, xs)                      # warm-up: autotune + graph capture
+    for x, x0 in zip(xs, x0s):
+        x.copy_(x0)
+    launches0 = binding.launch_count()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    st, bat = batch.solve(opts, bs, xs)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    bat_ms = e0.elapsed_time(e1)
+    info = batch.info()
+    out = dict(workload="64 scenes (channel/box alternating), totals log-uniform 1e4-5e5 particles, "
+                        "nu log-uniform 1-1e3 m^2/s, dt log-uniform 1e-4-5e-4 s",
+               particles=int(sum(s.n for s in ens)), scenes=len(ens),
+               sequential_ms=seq_ms, batched_ms=bat_ms, speedup=seq_ms / bat_ms,
+               sequential_ms_per_solve=seq_ms / len(ens), batched_ms_per_solve=bat_ms / len(ens),
+               sequential_iters=int(sum(r["iters"] for r in seq)), batched_iters=int(sum(r["iters"] for r in bat)),
+               max_true_rel_res_sequential=max(r["true_rel_res"] for r in seq),
+               max_true_rel_res_batched=max(r["true_rel_res"] for r in bat), batched_status=st,
+               batched_launches=binding.launch_count() - launches0, persistent_variant=info["variant"],
+               graph=info["graph"], persistent_grid=info["grid"], autotune_ms=info["tune_ms"])
+    batch.close()
+    for nb in nbs:
+        nb.close()
+    return out
 
 
 # ------------------------------------------------------------ reference arm ---
@@ -372,6 +447,9 @@ def main():
     args = parse()
     if args.cpu_oracle_worker:
         cpu_worker(args)
+        return
+    if args.ensemble_only:
+        print(json.dumps(run_ensemble(0)))
         return
     if args.impl == "reference":
         run_reference(args)

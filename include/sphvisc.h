@@ -228,6 +228,41 @@ sph_status sph_visc_solve(sph_neighbors* handle, const sph_visc_params* params,
                           const sph_solve_opts* opts, const double* b, double* x,
                           sph_solve_report* report, void* stream);
 
+/* ---- Batched ensemble solve -------------------------------------------------
+ * S independent scenes (each its own handle and A(dt)) solved together: every
+ * scene runs the restructured BiCGSTAB of Sec. 4.2 with its own scalars, states
+ * and stopping decision, and the float64 refinement of sph_visc_solve.  One
+ * refinement pass is one CUDA-graph replay of: the float64 residual of every
+ * scene (scenes at rtol drop out on the device), pass set-up, ONE persistent
+ * cooperative kernel running the iterations of all active scenes, and x += d.
+ * Grid barriers inside the persistent kernel wait a bounded time and report
+ * SPH_ERR_TIMEOUT instead of hanging.  The persistent kernel's row-loop form is
+ * autotuned on the first solve. */
+typedef struct sph_batch sph_batch;
+
+/* handles: (host) [nscenes] built handles; params: (host) [nscenes] A(dt)
+ * parameters (set up on each handle here; a handle rebuilt or given new
+ * viscosities afterwards makes sph_batch_solve fail with SPH_ERR_INVALID).
+ * The batch keeps pointers to the handles: destroy it before them. */
+sph_status sph_batch_create(sph_neighbors* const* handles, const sph_visc_params* params,
+                            int32_t nscenes, sph_batch** batch, void* stream);
+
+/* b, x: (host) arrays of nscenes (device) pointers, each [n_s][3] double in that
+ * scene's caller order (x: in guess, out solution); reports: (host) [nscenes].
+ * opts as for sph_visc_solve (SPH_PREC_MIXED only; merged_reductions and chunk
+ * are ignored: the batch always computes gamma' directly).  Synchronises.
+ * Returns SPH_OK when every scene reached rtol. */
+sph_status sph_batch_solve(sph_batch* batch, const sph_solve_opts* opts, const double* const* b,
+                           double* const* x, sph_solve_report* reports, void* stream);
+
+/* The autotuned row-loop form (0..3, as in sph_profile_counters), whether the
+ * pass runs as a captured graph (1) or as direct launches (0), the tuning
+ * times (ms, [4]) and the persistent grid size.  Any pointer may be NULL. */
+sph_status sph_batch_info(const sph_batch* batch, int32_t* variant, int32_t* graph, float* tune_ms,
+                          int32_t* grid);
+
+sph_status sph_batch_destroy(sph_batch* batch);
+
 /* Papanastasiou viscosity from the previous velocities (Sec. 2.4, Eq. papa):
  *   grad u_b = sum_a V_a |F_ab| r_ab (x) u_ab;  gdot = sym(grad u);
  *   D = sqrt(2 gdot:gdot);  mu_b = tau0 Ybar(D) + mu0,

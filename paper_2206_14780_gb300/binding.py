@@ -26,7 +26,8 @@ SPH_CONVERGED, SPH_STALLED, SPH_PROGRESSING = 0, 1, 2
 # every symbol include/sphvisc.h declares
 EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", "sph_set_viscosity",
            "sph_neighbors_destroy", "sph_visc_setup", "sph_visc_apply", "sph_visc_apply_noalloc", "sph_visc_residual", "sph_visc_solve",
-           "sph_mu_papanastasiou", "sph_profile_enable", "sph_profile_read", "sph_last_error", "sph_version"]
+           "sph_mu_papanastasiou", "sph_profile_enable", "sph_profile_read", "sph_last_error", "sph_version",
+           "sph_batch_create", "sph_batch_solve", "sph_batch_info", "sph_batch_destroy"]
 
 
 class sph_scene(ctypes.Structure):
@@ -90,6 +91,12 @@ def load(path: str = LIB_PATH):
                            ctypes.POINTER(sph_solve_report), vp],
         "sph_mu_papanastasiou": [vp, vp, vp, dbl, dbl, dbl, vp, i32, vp],
         "sph_profile_enable": [vp, i32],
+        "sph_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(sph_visc_params), i32, ctypes.POINTER(vp), vp],
+        "sph_batch_solve": [vp, ctypes.POINTER(sph_solve_opts), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                            ctypes.POINTER(sph_solve_report), vp],
+        "sph_batch_info": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
+                           ctypes.POINTER(i32)],
+        "sph_batch_destroy": [vp],
         "sph_profile_read": [vp, ctypes.POINTER(sph_profile_counters), i32],
     }
     for name, args in sig.items():
@@ -246,6 +253,54 @@ def _scene_struct(pos, rho, mu, ptype, lo, hi, periodic, h):
         sc.periodic[ax] = int(periodic[ax])
     sc.h = float(h)
     return sc
+
+
+def _report(rep):
+    return dict(status=rep.status, iters=rep.iters, refinements=rep.refinements, state=list(rep.state),
+                stalled_any=list(rep.stalled_any), true_rel_res=rep.true_rel_res,
+                true_rel_res_c=list(rep.true_rel_res_c))
+
+
+class Batch:
+    """Owner of an sph_batch (sph_batch_create ... sph_batch_destroy) over built Neighbors."""
+
+    def __init__(self, neighbors, params, stream=None):
+        load()
+        self.nbs = list(neighbors)
+        S = len(self.nbs)
+        hs = (ctypes.c_void_p * S)(*[nb.handle.value if isinstance(nb.handle, ctypes.c_void_p) else nb.handle
+                                    for nb in self.nbs])
+        ps = (sph_visc_params * S)(*params)
+        h = ctypes.c_void_p()
+        _check(_lib.sph_batch_create(hs, ps, S, ctypes.byref(h), _stream(stream)))
+        self.handle = h
+
+    def solve(self, opts, bs, xs, stream=None):
+        S = len(self.nbs)
+        bp = (ctypes.c_void_p * S)(*[b.data_ptr() for b in bs])
+        xp = (ctypes.c_void_p * S)(*[x.data_ptr() for x in xs])
+        reps = (sph_solve_report * S)()
+        st = _lib.sph_batch_solve(self.handle, ctypes.byref(opts), bp, xp, reps, _stream(stream))
+        if st not in (SPH_OK, 6):
+            _check(st)
+        return st, [_report(r) for r in reps]
+
+    def info(self):
+        v, g, grid = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        t = (ctypes.c_float * 4)()
+        _check(_lib.sph_batch_info(self.handle, ctypes.byref(v), ctypes.byref(g), t, ctypes.byref(grid)))
+        return dict(variant=v.value, graph=bool(g.value), tune_ms=list(t), grid=grid.value)
+
+    def close(self):
+        if self.handle:
+            _lib.sph_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def build_neighbors(pos, rho, mu, ptype, lo, hi, periodic, h, max_neighbors=128, stream=None):

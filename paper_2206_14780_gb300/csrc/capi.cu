@@ -22,6 +22,7 @@ void clear_error() { g_err[0] = 0; }
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 void prof_begin(sph_neighbors* H, cudaStream_t st, int phase) {
   if (!H->prof_on || H->prof_used + 2 > 256) return;

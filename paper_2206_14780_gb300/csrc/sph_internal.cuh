@@ -27,6 +27,7 @@ constexpr int kMaxDots = 15;      // float64 partial sums one reduction may carr
 void set_error(const char* fmt, ...);
 void clear_error();
 void note_launch();        // counts kernel launches (sph_profile_read)
+void note_launches(int k); // graph replays: the kernels each replay runs
 
 // every kernel launch of the library goes through this macro so it is counted
 #define SPH_LAUNCH(kernel, ...) ::sph::note_launch(), kernel<<<__VA_ARGS__>>>

@@ -328,10 +328,25 @@ def random_box(seed: int = 0, nf: int = 200, nw_layers: int = 2, dx: float = 0.0
     return s
 
 
+def _couette_count(ny, layers=3):
+    nx = nz = 2 * ny
+    return nx * ny * nz + 2 * layers * nx * nz
+
+
+def _box_count(n, layers=3):
+    m = n + 2 * layers
+    return n ** 3 + m * m * layers + 2 * layers * m * n + 2 * layers * n * n
+
+
 def ensemble(seed: int = 0, S: int = 64, n_lo: float = 1e4, n_hi: float = 5e5, dx: float = 0.005,
              nu_lo: float = 1.0, nu_hi: float = 1e3, dt_lo: float = 1e-4, dt_hi: float = 5e-4,
              rho0: float = 1000.0):
-    """Independent scenes of log-uniform particle counts, nu and dt (channel / box alternating)."""
+    """Independent scenes of log-uniform particle counts, nu and dt (channel / box alternating).
+
+    The drawn count is the scene's total (fluid + wall particles): the lattice
+    size whose total is closest to it is used, so the ensemble totals about
+    S * (n_hi - n_lo) / ln(n_hi / n_lo) particles (8.0M for the defaults).
+    """
     rng = rng_for(CFG_ENSEMBLE, seed)
     scenes = []
     for s in range(S):
@@ -340,14 +355,12 @@ def ensemble(seed: int = 0, S: int = 64, n_lo: float = 1e4, n_hi: float = 5e5, d
         dt = math.exp(rng.uniform(math.log(dt_lo), math.log(dt_hi)))
         sub = int(rng.integers(0, 2**31 - 1))
         if s % 2 == 0:
-            # channel: ny = nx/2 = nz/2 plus 6 wall layers
-            ny = max(6, int(round((target / 4.0) ** (1.0 / 3.0))))
-            nx = nz = 2 * ny
-            sc = couette(sub, nx=nx, ny=ny, nz=nz, dx=dx, rho0=rho0, nu=nu, dt=dt, U=1.0, noise=0.01)
+            ny = min(range(6, 200), key=lambda k: abs(_couette_count(k) - target))
+            sc = couette(sub, nx=2 * ny, ny=ny, nz=2 * ny, dx=dx, rho0=rho0, nu=nu, dt=dt, U=1.0, noise=0.01)
         else:
-            n = max(8, int(round(target ** (1.0 / 3.0))))
+            n = min(range(8, 400), key=lambda k: abs(_box_count(k) - target))
             sc = lava_box(sub, n=n, dx=dx, rho0=rho0, nu=nu, dt=dt)
         sc.name = f"ensemble[{s}]:{sc.name}"
-        sc.meta.update(nu=nu, dt=dt)
+        sc.meta.update(nu=nu, dt=dt, target=target)
         scenes.append(sc)
     return scenes
