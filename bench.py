@@ -48,6 +48,8 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-only", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--precision-only", action="store_true")
     ap.add_argument("--merged", type=int, default=0)
     ap.add_argument("--eps-inner", type=float, default=1e-2)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -320,6 +322,10 @@ def run_sphvisc(args):
         nb.close()
         torch.cuda.empty_cache()
         ensemble = run_ensemble(0, dev)
+    precision = None
+    if not args.no_precision and world == 1:
+        torch.cuda.empty_cache()
+        precision = run_precision(dev)
     its = [r["iters"] for r in reps]
     out = dict(metric=METRIC, value=ms_max / (args.steps * world), unit=UNIT, n_gpus=world, steps=args.steps,
                warmup=max(3, args.warmup), ms_per_step=ms_max / args.steps, higher_is_better=False,
@@ -332,6 +338,7 @@ def run_sphvisc(args):
                            iters=its, passes=[r["refinements"] for r in reps],
                            true_rel_res=[r["true_rel_res"] for r in reps], parallelism=f"replicas x{world}"),
                roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), ensemble=ensemble,
+               precision_study=precision,
                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"],
                            samples=clk["samples"]),
                wall_s=wall)
@@ -410,6 +417,63 @@ def run_ensemble(seed=0, dev=None):
     return out
 
 
+# ----------------------------------------------------- precision study ------
+
+def run_precision(dev=None, full=True):
+    """Papanastasiou slope (200x100x200 jittered fluid on a 3-layer floor, 4.12M particles): the mu
+    pass, then the mixed (float32 operator, float64 dots and refinement) and all-float64 solves."""
+    import torch
+
+    import scenes
+    from paper_2206_14780_gb300 import binding
+
+    dev = dev or torch.device("cuda", 0)
+    s = scenes.slope(0) if full else scenes.slope_subset(0)
+    t = binding.scene_tensors(s, dev)
+    nb = binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
+    vel, wv = torch.from_numpy(s.vel).to(dev), torch.from_numpy(s.wall_vel).to(dev)
+    mu = torch.empty(s.n, dtype=torch.float32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    nb.mu_papanastasiou(vel, wv, *s.rheology, mu, set_handle=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    nb.mu_papanastasiou(vel, wv, *s.rheology, mu, set_handle=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    mu_ms = e0.elapsed_time(e1)
+    fl = torch.from_numpy(s.ptype == scenes.FLUID).to(dev)
+    mu_f = mu[fl]
+    p = binding.visc_params(s.dt, s.boundary, s.mean)
+    b = torch.from_numpy(s.b).to(dev)
+    x0 = torch.from_numpy(s.x0).to(dev)
+    res = {}
+    xs = {}
+    for name, prec, rtol in (("mixed", binding.SPH_PREC_MIXED, 1e-6), ("fp64", binding.SPH_PREC_FP64, 1e-6),
+                             ("fp64_tight", binding.SPH_PREC_FP64, 1e-10)):
+        x = x0.clone()
+        o = binding.solve_opts(rtol=rtol, precision=prec)
+        if prec == binding.SPH_PREC_MIXED:
+            nb.solve(p, o, b, x)                  # warm-up (coefficients, autotune)
+            x = x0.clone()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        rep = nb.solve(p, o, b, x)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        res[name] = dict(ms=e0.elapsed_time(e1), iters=rep["iters"], passes=rep["refinements"],
+                         true_rel_res=rep["true_rel_res"], status=rep["status"])
+        xs[name] = x
+    ref = xs["fp64_tight"]
+    for name in ("mixed", "fp64"):
+        res[name]["rel_l2_vs_fp64_tight"] = float(torch.linalg.norm(xs[name] - ref) / torch.linalg.norm(ref))
+    nb.close()
+    return dict(workload=("slope: %dx%dx%d jittered fluid on a 3-layer floor, periodic x/z, Papanastasiou "
+                          "tau0=100 Pa, mu0=1e3 Pa s, m=1000 s, dt=5e-4 s" % (200, 100, 200) if full else
+                          "slope subset 50x20x50"),
+                particles=s.n, mu_pass_ms=mu_ms, mu_min=float(mu_f.min()), mu_max=float(mu_f.max()), **res)
+
+
 # ------------------------------------------------------------ reference arm ---
 
 def run_reference(args):
@@ -450,6 +514,9 @@ def main():
         return
     if args.ensemble_only:
         print(json.dumps(run_ensemble(0)))
+        return
+    if args.precision_only:
+        print(json.dumps(run_precision()))
         return
     if args.impl == "reference":
         run_reference(args)
