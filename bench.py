@@ -49,6 +49,8 @@ def parse(argv=None):
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-only", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-sequence", action="store_true")
+    ap.add_argument("--sequence-steps", type=int, default=200)
     ap.add_argument("--precision-only", action="store_true")
     ap.add_argument("--merged", type=int, default=0)
     ap.add_argument("--eps-inner", type=float, default=1e-2)
@@ -317,6 +319,9 @@ def run_sphvisc(args):
                            f"restarted to a 1e-6 true residual) on the same box workload at {args.cpu_n}^3 fluid "
                            f"(N={rows[0]['n']}), {sec:.1f} s, scaled linearly by particle count to N={s.n}; "
                            f"BiCGSTAB iteration counts depend on dt*nu/dx^2, not on N"))
+    sequence = None
+    if not args.no_sequence and world == 1:
+        sequence = run_sequence(nb, s, b, x0, args.sequence_steps, dev)
     ensemble = None
     if not args.no_ensemble and world == 1:
         nb.close()
@@ -338,7 +343,7 @@ def run_sphvisc(args):
                            iters=its, passes=[r["refinements"] for r in reps],
                            true_rel_res=[r["true_rel_res"] for r in reps], parallelism=f"replicas x{world}"),
                roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), ensemble=ensemble,
-               precision_study=precision,
+               precision_study=precision, sequence=sequence,
                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"],
                            samples=clk["samples"]),
                wall_s=wall)
@@ -415,6 +420,42 @@ def run_ensemble(seed=0, dev=None):
     for nb in nbs:
         nb.close()
     return out
+
+
+# ----------------------------------------------------- 200-step sequence ----
+
+def run_sequence(nb, s, b, x0, steps, dev):
+    """Warm-started sequence on the same A(dt) (positions frozen): step k solves with
+    b = v^k + dt g on fluid rows (g a fixed smooth stirring force) and x0 = the previous
+    solution v^k, so the field settles to a steady stirred state."""
+    import torch
+
+    import scenes
+    from paper_2206_14780_gb300 import binding
+
+    p = binding.visc_params(s.dt, s.boundary, s.mean)
+    o = binding.solve_opts()
+    fl = torch.from_numpy(s.ptype == 0).to(dev)
+    dtg = torch.from_numpy(s.dt * scenes.stirring_force(s)).to(dev)
+    bk = b.clone() + dtg
+    x = x0.clone()
+    its = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for k in range(steps):
+        rep = nb.solve(p, o, bk, x)
+        its.append(rep["iters"])
+        bk[fl] = x[fl] + dtg[fl]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    return dict(steps=steps, total_ms=ms, ms_per_solve=ms / steps, iters_first=its[0], iters_last=its[-1],
+                iters_mean=sum(its) / len(its), last_true_rel_res=rep["true_rel_res"], last_status=rep["status"],
+                rms_velocity_last=float(x[fl].pow(2).mean().sqrt()),
+                note="same A(dt) every step (positions frozen), b = previous solution + dt g on fluid rows "
+                     "(g: fixed stirring force, 160 m/s^2 sine modes), x0 = previous solution")
 
 
 # ----------------------------------------------------- precision study ------

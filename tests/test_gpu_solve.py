@@ -4,7 +4,7 @@ import pytest
 
 import scenes
 from oracle import neighbors as onb, operator as oop, solvers as osv
-from sph_testutil import SCENES_SMALL, gpu_solve, lib_build, oracle_system, rel_l2, torch_cuda
+from sph_testutil import SCENES_SMALL, gpu_solve, lib_build, oracle_system, params_for, rel_l2, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -104,3 +104,29 @@ def test_fp64_solve_reaches_tight_tolerance():
     res, _ = oop.true_residual(A, x, s.b)
     assert rep["status"] == 0 and res <= 1e-11, (res, rep)
     assert rel_l2(x, x_ref) <= 1e-9
+
+
+def test_warm_started_sequence_matches_oracle_sequence():
+    # the 200-step sequence in miniature: b = v^n (fluid rows) and x0 = the
+    # previous solution, the same A(dt) every step (positions frozen); each
+    # step's GPU solution against the oracle's solve of the same right-hand side
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.lava_box(9, n=12)
+    nb, _ = lib_build(s)
+    off, idx, A = oracle_system(s)
+    fl = s.ptype == scenes.FLUID
+    xg = torch.from_numpy(s.x0).cuda()
+    b_np = s.b.copy()
+    iters = []
+    for step in range(6):
+        rep = nb.solve(params_for(s), binding.solve_opts(), torch.from_numpy(b_np).cuda(), xg)
+        assert rep["status"] == 0
+        iters.append(rep["iters"])
+        xk = xg.cpu().numpy()
+        x_ref = osv.reference_solution(A, b_np, xk)
+        assert rel_l2(xk, x_ref) <= 1e-5
+        b_np = b_np.copy()
+        b_np[fl] = xk[fl]
+    assert iters[-1] <= iters[0]      # the field smooths: later steps need no more work
