@@ -263,6 +263,60 @@ sph_status sph_batch_info(const sph_batch* batch, int32_t* variant, int32_t* gra
 
 sph_status sph_batch_destroy(sph_batch* batch);
 
+/* ---- Learned warm start ---------------------------------------------------
+ * The paper names a better initial guess as future work (Sec. 8).  A
+ * per-particle MLP, 16 -> 64 -> 64 -> 64 -> 3 with SiLU (9,603 parameters),
+ * predicts delta = (x* - v^n) / U from 16 local features; the solve then starts
+ * from x0 = v^n + U delta on fluid rows (walls start at b), and the unchanged
+ * BiCGSTAB with its float64 true residual stays the judge of the result.
+ * Inference and training run on BF16 tensor cores with FP32 accumulation.
+ * Parameters are exchanged as 9,603 float32 values, row-major [out][in]:
+ * W1 64x16, b1 64, W2 64x64, b2 64, W3 64x64, b3 64, W4 3x64, b4 3. */
+typedef struct sph_mlp sph_mlp;
+
+/* params: (host) [9603] float32, or NULL for zeros. */
+sph_status sph_mlp_create(const float* params, sph_mlp** mlp);
+sph_status sph_mlp_set_params(sph_mlp* mlp, const float* params);   /* (host); resets Adam */
+sph_status sph_mlp_get_params(const sph_mlp* mlp, float* params);   /* (host) [9603] */
+sph_status sph_mlp_destroy(sph_mlp* mlp);
+
+/* Features (device, [n][16] bf16 bits, caller order) of the particles of
+ * `handle` for velocities vel (device, [n][4] float): v/U, the Jacobi-scaled
+ * explicit viscous increment D^-1 (v - A v) / U and its second application,
+ * log10(mu)/5, log10(1 + dt sum c)/4, nearest wall neighbour / 2h, the Shepard
+ * sum of W V, neighbour count / 80, |v| relative to the neighbourhood RMS, and
+ * the wall flag.  scale_out (host, may be NULL): U = RMS |v| over the fluid. */
+sph_status sph_mlp_features(sph_neighbors* handle, const sph_visc_params* params, const float* vel,
+                            uint16_t* feats, double* scale_out, void* stream);
+
+/* Training targets (x* - v) / U (device [n][4] float) and the fluid mask
+ * (device [n] u8) from a solution x_star (device [n][3] double); uses the U of
+ * the last sph_mlp_features call on the handle. */
+sph_status sph_mlp_targets(sph_neighbors* handle, const float* vel, const double* x_star,
+                           const uint8_t* ptype, float* targets, uint8_t* mask, void* stream);
+
+/* out (device [m][4] float) = network(feats (device [m][16] bf16)). */
+sph_status sph_mlp_forward(const sph_mlp* mlp, const uint16_t* feats, int64_t m, float* out, void* stream);
+
+/* Mean squared error over the masked rows (mask may be NULL = all rows;
+ * count = the number of masked rows) and its gradient: grad_out (device
+ * [9603] float), loss_out (device [1] float); either may be NULL. */
+sph_status sph_mlp_grad(sph_mlp* mlp, const uint16_t* feats, const float* targets, const uint8_t* mask,
+                        int64_t m, int64_t count, float* grad_out, float* loss_out, void* stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on that loss; loss_host (may be
+ * NULL) receives the loss before the step (synchronises when given). */
+sph_status sph_mlp_train_step(sph_mlp* mlp, const uint16_t* feats, const float* targets,
+                              const uint8_t* mask, int64_t m, int64_t count, float lr, float* loss_host,
+                              void* stream);
+
+/* x0 (device [n][3] double, caller order) = v + U network(features) on fluid
+ * rows, b on wall rows; vel (device [n][4] float), ptype (device [n] u8), b
+ * (device [n][3] double) in caller order. */
+sph_status sph_warm_start(sph_neighbors* handle, const sph_visc_params* params, const sph_mlp* mlp,
+                          const float* vel, const uint8_t* ptype, const double* b, double* x0,
+                          void* stream);
+
 /* Papanastasiou viscosity from the previous velocities (Sec. 2.4, Eq. papa):
  *   grad u_b = sum_a V_a |F_ab| r_ab (x) u_ab;  gdot = sym(grad u);
  *   D = sqrt(2 gdot:gdot);  mu_b = tau0 Ybar(D) + mu0,

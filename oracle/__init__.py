@@ -20,6 +20,9 @@ Everything here is plain, slow and in float64, written from the paper:
                  dense LU and a hand-written Gaussian elimination
 * ``rheology``   velocity gradient, strain rate, second invariant and the
                  Papanastasiou viscosity with the truncated series (Sec. 2.4)
+* ``mlp``        the warm-start network (forward, loss, backward) in float64,
+                 optionally with the bf16 rounding points of the GPU kernels
+* ``features``   the sixteen per-particle inputs of that network
 
 Readings of the paper where it is garbled or silent (all listed in the design doc):
 X1 the kernel gradient factor F enters K_ab as a magnitude, so the fluid rows are
@@ -34,4 +37,4 @@ against closed forms, invariants, brute force or library routines.  Iteration
 counts of the paper's experiments are NOT pinned (different stiffness regime):
 parity unpinned for iteration counts only.
 """
-from . import kernel, neighbors, operator, solvers, rheology  # noqa: F401
+from . import kernel, neighbors, operator, solvers, rheology, mlp, features  # noqa: F401

@@ -27,7 +27,10 @@ SPH_CONVERGED, SPH_STALLED, SPH_PROGRESSING = 0, 1, 2
 EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", "sph_set_viscosity",
            "sph_neighbors_destroy", "sph_visc_setup", "sph_visc_apply", "sph_visc_apply_noalloc", "sph_visc_residual", "sph_visc_solve",
            "sph_mu_papanastasiou", "sph_profile_enable", "sph_profile_read", "sph_last_error", "sph_version",
-           "sph_batch_create", "sph_batch_solve", "sph_batch_info", "sph_batch_destroy"]
+           "sph_batch_create", "sph_batch_solve", "sph_batch_info", "sph_batch_destroy",
+           "sph_mlp_create", "sph_mlp_set_params", "sph_mlp_get_params", "sph_mlp_destroy", "sph_mlp_features",
+           "sph_mlp_targets", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train_step", "sph_warm_start"]
+MLP_NPARAMS = 9603
 
 
 class sph_scene(ctypes.Structure):
@@ -97,6 +100,16 @@ def load(path: str = LIB_PATH):
         "sph_batch_info": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
                            ctypes.POINTER(i32)],
         "sph_batch_destroy": [vp],
+        "sph_mlp_create": [vp, ctypes.POINTER(vp)],
+        "sph_mlp_set_params": [vp, vp],
+        "sph_mlp_get_params": [vp, vp],
+        "sph_mlp_destroy": [vp],
+        "sph_mlp_features": [vp, ctypes.POINTER(sph_visc_params), vp, vp, ctypes.POINTER(dbl), vp],
+        "sph_mlp_targets": [vp, vp, vp, vp, vp, vp, vp],
+        "sph_mlp_forward": [vp, vp, i64, vp, vp],
+        "sph_mlp_grad": [vp, vp, vp, vp, i64, i64, vp, vp, vp],
+        "sph_mlp_train_step": [vp, vp, vp, vp, i64, i64, ctypes.c_float, ctypes.POINTER(ctypes.c_float), vp],
+        "sph_warm_start": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp, vp, vp, vp],
         "sph_profile_read": [vp, ctypes.POINTER(sph_profile_counters), i32],
     }
     for name, args in sig.items():
@@ -301,6 +314,73 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Mlp:
+    """Owner of an sph_mlp (the learned warm-start network)."""
+
+    def __init__(self, params=None):
+        load()
+        h = ctypes.c_void_p()
+        if params is None:
+            _check(_lib.sph_mlp_create(None, ctypes.byref(h)))
+        else:
+            p = np.ascontiguousarray(params, np.float32)
+            assert p.size == MLP_NPARAMS
+            _check(_lib.sph_mlp_create(p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+        self.handle = h
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == MLP_NPARAMS
+        _check(_lib.sph_mlp_set_params(self.handle, p.ctypes.data_as(ctypes.c_void_p)))
+
+    def params(self):
+        p = np.empty(MLP_NPARAMS, np.float32)
+        _check(_lib.sph_mlp_get_params(self.handle, p.ctypes.data_as(ctypes.c_void_p)))
+        return p
+
+    def forward(self, feats, out, stream=None):
+        _check(_lib.sph_mlp_forward(self.handle, _ptr(feats), int(feats.shape[0]), _ptr(out), _stream(stream)))
+
+    def grad(self, feats, targets, mask, count, grad_out, loss_out, stream=None):
+        _check(_lib.sph_mlp_grad(self.handle, _ptr(feats), _ptr(targets), _ptr(mask), int(feats.shape[0]),
+                                 int(count), _ptr(grad_out), _ptr(loss_out), _stream(stream)))
+
+    def train_step(self, feats, targets, mask, count, lr, stream=None):
+        loss = ctypes.c_float()
+        _check(_lib.sph_mlp_train_step(self.handle, _ptr(feats), _ptr(targets), _ptr(mask), int(feats.shape[0]),
+                                       int(count), float(lr), ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def close(self):
+        if self.handle:
+            _lib.sph_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mlp_features(nb, params, vel, feats, stream=None):
+    """sph_mlp_features: feats (device int16 [n,16] holding bf16 bits); returns U."""
+    U = ctypes.c_double()
+    _check(_lib.sph_mlp_features(nb.handle, ctypes.byref(params), _ptr(vel), _ptr(feats), ctypes.byref(U),
+                                 _stream(stream)))
+    return U.value
+
+
+def mlp_targets(nb, vel, x_star, ptype, targets, mask, stream=None):
+    _check(_lib.sph_mlp_targets(nb.handle, _ptr(vel), _ptr(x_star), _ptr(ptype), _ptr(targets), _ptr(mask),
+                                _stream(stream)))
+
+
+def warm_start(nb, params, mlp, vel, ptype, b, x0, stream=None):
+    _check(_lib.sph_warm_start(nb.handle, ctypes.byref(params), mlp.handle, _ptr(vel), _ptr(ptype), _ptr(b),
+                               _ptr(x0), _stream(stream)))
 
 
 def build_neighbors(pos, rho, mu, ptype, lo, hi, periodic, h, max_neighbors=128, stream=None):

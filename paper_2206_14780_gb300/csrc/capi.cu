@@ -120,6 +120,10 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
   h->invD.release();
   h->D64.release();
   h->aux64.release();
+  h->feat_tmp.release();
+  h->feat_scale.release();
+  h->feat_out.release();
+  h->feat_delta.release();
   h->v_xh.release();
   h->v_xl.release();
   h->tmp_i32a.release();

@@ -1,0 +1,283 @@
+// Per-particle features of the learned warm start and the warm-start x0.
+//
+// Sixteen features per particle (bf16, caller order), velocities scaled by
+// U = RMS of |v^n| over the fluid:
+//   0-2   v / U
+//   3-5   e1 / U,  e1 = D^-1 (v - A v)         explicit viscous increment
+//                                               dt L v, Jacobi-scaled (fluid rows)
+//   6-8   e2 / U,  e2 = D^-1 (e1 - A e1)       the next (second Neumann) term
+//   9     log10(mu) / 5
+//   10    log10(D) / 4, D = 1 + dt sum c        local stiffness
+//   11    distance to the nearest wall neighbour / (2h), 1 without one
+//   12    Shepard sum over fluid neighbours and self of W V
+//   13    neighbour count / 80
+//   14    |v_b| / (|v_b| + RMS of |v_a| over the neighbours)
+//   15    1 for wall particles
+// Wall rows get zeros in 3-8 (their operator rows are not the viscous term).
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "reduce.cuh"
+#include "sph_internal.cuh"
+
+struct sph_mlp;
+
+namespace sph {
+
+void mlp_forward_launch(const sph_mlp* M, const __nv_bfloat16* feats, int64_t m, float4* out, int num_sms,
+                        cudaStream_t st);
+
+namespace {
+
+__global__ void k_feat_gather(const float4* __restrict__ v, const int32_t* __restrict__ perm, int64_t n, int64_t n_pad,
+                              float4* __restrict__ vs) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    if (s < n) {
+      const float4 t = v[perm[s]];
+      vs[s] = make_float4(t.x, t.y, t.z, 0.f);
+    } else {
+      vs[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// e = D^-1 (v - y) on fluid rows, 0 elsewhere
+__global__ void k_feat_incr(const float4* __restrict__ v, const float4* __restrict__ y, const float* __restrict__ invD,
+                            const uint8_t* __restrict__ type, int64_t n, int64_t n_pad, float4* __restrict__ e) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    if (s < n && type[s] == SPH_FLUID) {
+      const float4 a = v[s], b = y[s];
+      const float d = invD[s];
+      e[s] = make_float4((a.x - b.x) * d, (a.y - b.y) * d, (a.z - b.z) * d, 0.f);
+    } else {
+      e[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// sum over fluid rows of |v|^2 and their count -> out[0], out[1]
+__global__ void __launch_bounds__(kBlock) k_feat_scale(const float4* __restrict__ v, const uint8_t* __restrict__ type,
+                                                       int64_t n, double* partials, unsigned int* counter,
+                                                       double* out) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    if (type[s] == SPH_FLUID) {
+      const float4 a = v[s];
+      acc[0] += (double)a.x * a.x + (double)a.y * a.y + (double)a.z * a.z;
+      acc[1] += 1.0;
+    }
+  }
+  block_partials_f64<2>(acc, partials + (size_t)blockIdx.x * kMaxDots);
+  if (arrive_last(counter)) {
+    __shared__ double res[2];
+    final_sum<2>(partials, counter, res);
+    if (threadIdx.x < 2) out[threadIdx.x] = res[threadIdx.x];
+  }
+}
+
+struct FeatGeom {
+  float L[3], invL[3];
+  int periodic[3];
+  float inv_h, inv_2h, w_scale;  // w_scale = 21/(16 pi) / h^3
+};
+
+__global__ void __launch_bounds__(kBlock) k_features(const float4* __restrict__ pos, const float* __restrict__ rho,
+                                                     const float* __restrict__ mu, const uint8_t* __restrict__ type,
+                                                     const double* __restrict__ D64,
+                                                     const int32_t* __restrict__ cnt,
+                                                     const int64_t* __restrict__ slice_off,
+                                                     const int32_t* __restrict__ nbr, const int32_t* __restrict__ perm,
+                                                     const float4* __restrict__ v, const float4* __restrict__ e1,
+                                                     const float4* __restrict__ e2, int64_t n, FeatGeom g,
+                                                     const double* __restrict__ scale,
+                                                     __nv_bfloat16* __restrict__ feats) {
+  const float U = (float)sqrt(scale[0] / fmax(scale[1], 1.0));
+  const float iU = U > 0.f ? 1.f / U : 0.f;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const float4 pb = pos[s];
+    const float4 vb = v[s];
+    const int c = cnt[s];
+    const int64_t base = slice_off[s / kSlice] + (s % kSlice);
+    float dmin = 1.f, shep = g.w_scale * (pb.w / rho[s]), v2 = 0.f;
+    for (int j = 0; j < c; ++j) {
+      const int32_t t = nbr[base + (int64_t)j * kSlice];
+      const float4 pa = pos[t];
+      float d[3] = {pa.x - pb.x, pa.y - pb.y, pa.z - pb.z};
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax)
+        if (g.periodic[ax]) d[ax] -= g.L[ax] * rintf(d[ax] * g.invL[ax]);
+      const float r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      if (type[t] == SPH_FLUID) {
+        const float q = r * g.inv_h;
+        const float tq = fmaxf(1.f - 0.5f * q, 0.f);
+        const float t2 = tq * tq;
+        shep += g.w_scale * t2 * t2 * (2.f * q + 1.f) * (pa.w / rho[t]);
+      } else {
+        dmin = fminf(dmin, r * g.inv_2h);
+      }
+      const float4 va = v[t];
+      v2 += va.x * va.x + va.y * va.y + va.z * va.z;
+    }
+    const bool fluid = type[s] == SPH_FLUID;
+    const float vn = sqrtf(vb.x * vb.x + vb.y * vb.y + vb.z * vb.z);
+    const float rms = c > 0 ? sqrtf(v2 / (float)c) : 0.f;
+    float f[16];
+    f[0] = vb.x * iU;
+    f[1] = vb.y * iU;
+    f[2] = vb.z * iU;
+    const float4 a = e1[s], b = e2[s];
+    f[3] = fluid ? a.x * iU : 0.f;
+    f[4] = fluid ? a.y * iU : 0.f;
+    f[5] = fluid ? a.z * iU : 0.f;
+    f[6] = fluid ? b.x * iU : 0.f;
+    f[7] = fluid ? b.y * iU : 0.f;
+    f[8] = fluid ? b.z * iU : 0.f;
+    f[9] = log10f(mu[s]) * 0.2f;
+    f[10] = (float)(log10(D64[s]) * 0.25);
+    f[11] = dmin;
+    f[12] = shep;
+    f[13] = (float)c * (1.f / 80.f);
+    f[14] = (vn + rms) > 0.f ? vn / (vn + rms) : 0.f;
+    f[15] = fluid ? 0.f : 1.f;
+    __nv_bfloat16* out = feats + (int64_t)perm[s] * 16;
+#pragma unroll
+    for (int k = 0; k < 16; k += 2)
+      *reinterpret_cast<__nv_bfloat162*>(out + k) = __floats2bfloat162_rn(f[k], f[k + 1]);
+  }
+}
+
+// x0 = v + U delta on fluid rows, b on walls (caller order)
+__global__ void k_warm_x0(const float4* __restrict__ vel, const float4* __restrict__ delta,
+                          const uint8_t* __restrict__ ptype, const double* __restrict__ b, int64_t n,
+                          const double* __restrict__ scale, double* __restrict__ x0) {
+  const double U = sqrt(scale[0] / fmax(scale[1], 1.0));
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (ptype[i] == SPH_FLUID) {
+      const float4 v = vel[i], d = delta[i];
+      x0[3 * i] = (double)v.x + U * (double)d.x;
+      x0[3 * i + 1] = (double)v.y + U * (double)d.y;
+      x0[3 * i + 2] = (double)v.z + U * (double)d.z;
+    } else {
+      x0[3 * i] = b[3 * i];
+      x0[3 * i + 1] = b[3 * i + 1];
+      x0[3 * i + 2] = b[3 * i + 2];
+    }
+  }
+}
+
+// training targets (x* - v) / U and the fluid mask (caller order)
+__global__ void k_targets(const float4* __restrict__ vel, const double* __restrict__ xs,
+                          const uint8_t* __restrict__ ptype, int64_t n, const double* __restrict__ scale,
+                          float4* __restrict__ tgt, uint8_t* __restrict__ mask) {
+  const double U = sqrt(scale[0] / fmax(scale[1], 1.0));
+  const double iU = U > 0.0 ? 1.0 / U : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = vel[i];
+    const bool fl = ptype[i] == SPH_FLUID;
+    tgt[i] = fl ? make_float4((float)((xs[3 * i] - v.x) * iU), (float)((xs[3 * i + 1] - v.y) * iU),
+                              (float)((xs[3 * i + 2] - v.z) * iU), 0.f)
+                : make_float4(0.f, 0.f, 0.f, 0.f);
+    mask[i] = fl ? 1 : 0;
+  }
+}
+
+}  // namespace
+
+// features of the particle set on handle H for velocities vel (caller order);
+// leaves the scale sums (|v|^2, count) in H->feat_scale (device)
+sph_status features_impl(sph_neighbors* H, const sph_visc_params* P, const float* vel, __nv_bfloat16* feats,
+                         cudaStream_t st) {
+  SPH_TRY(ensure_operator(H, P, st));
+  SPH_TRY(ensure_workspace(H));
+  SPH_TRY(H->feat_tmp.alloc(4 * H->n_pad));
+  SPH_TRY(H->feat_scale.alloc(2));
+  const int64_t np = H->n_pad;
+  float4* vs = H->feat_tmp.p;
+  float4* y = vs + np;
+  float4* e1 = vs + 2 * np;
+  float4* e2 = vs + 3 * np;
+  const int grid = grid_for(H, np);
+  SPH_LAUNCH(k_feat_gather, grid, kBlock, 0, st)(reinterpret_cast<const float4*>(vel), H->perm.p, H->n, np, vs);
+  launch_apply_f32(H, vs, y, false, st);
+  SPH_LAUNCH(k_feat_incr, grid, kBlock, 0, st)(vs, y, H->invD.p, H->type_s.p, H->n, np, e1);
+  launch_apply_f32(H, e1, y, false, st);
+  SPH_LAUNCH(k_feat_incr, grid, kBlock, 0, st)(e1, y, H->invD.p, H->type_s.p, H->n, np, e2);
+  int rg = grid < H->red_grid ? grid : H->red_grid;
+  SPH_LAUNCH(k_feat_scale, rg, kBlock, 0, st)(vs, H->type_s.p, H->n, H->partials.p, H->counters.p + 7,
+                                              H->feat_scale.p);
+  FeatGeom g{};
+  for (int ax = 0; ax < 3; ++ax) {
+    g.L[ax] = (float)H->grid.L[ax];
+    g.invL[ax] = (float)(1.0 / H->grid.L[ax]);
+    g.periodic[ax] = H->grid.periodic[ax];
+  }
+  const double h = (double)H->h;
+  g.inv_h = (float)(1.0 / h);
+  g.inv_2h = (float)(0.5 / h);
+  g.w_scale = (float)(21.0 / (16.0 * M_PI) / (h * h * h));
+  SPH_LAUNCH(k_features, grid_for(H, H->n), kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->type_s.p, H->D64.p,
+                                                           H->cnt.p, H->slice_off.p, H->nbr.p, H->perm.p, vs, e1, e2,
+                                                           H->n, g, H->feat_scale.p, feats);
+  SPH_TRY_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+}  // namespace sph
+
+using namespace sph;
+
+extern "C" {
+
+sph_status sph_mlp_features(sph_neighbors* h, const sph_visc_params* params, const float* vel, uint16_t* feats,
+                            double* scale_out, void* stream) {
+  clear_error();
+  if (!h || !params || !vel || !feats) {
+    set_error("sph_mlp_features: null argument");
+    return SPH_ERR_INVALID;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  SPH_TRY(features_impl(h, params, vel, reinterpret_cast<__nv_bfloat16*>(feats), st));
+  if (scale_out) {
+    double sc[2];
+    SPH_TRY_CUDA(cudaMemcpyAsync(sc, h->feat_scale.p, sizeof(sc), cudaMemcpyDeviceToHost, st));
+    SPH_TRY_CUDA(cudaStreamSynchronize(st));
+    *scale_out = std::sqrt(sc[0] / (sc[1] > 1.0 ? sc[1] : 1.0));
+  }
+  return SPH_OK;
+}
+
+sph_status sph_mlp_targets(sph_neighbors* h, const float* vel, const double* x_star, const uint8_t* ptype,
+                           float* targets, uint8_t* mask, void* stream) {
+  clear_error();
+  if (!h || !vel || !x_star || !ptype || !targets || !mask || !h->feat_scale.p) {
+    set_error("sph_mlp_targets: null argument (call sph_mlp_features first)");
+    return SPH_ERR_INVALID;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  SPH_LAUNCH(k_targets, grid_for(h, h->n), kBlock, 0, st)(reinterpret_cast<const float4*>(vel), x_star, ptype, h->n,
+                                                          h->feat_scale.p, reinterpret_cast<float4*>(targets), mask);
+  SPH_TRY_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+sph_status sph_warm_start(sph_neighbors* h, const sph_visc_params* params, const sph_mlp* mlp, const float* vel,
+                          const uint8_t* ptype, const double* b, double* x0, void* stream) {
+  clear_error();
+  if (!h || !params || !mlp || !vel || !ptype || !b || !x0) {
+    set_error("sph_warm_start: null argument");
+    return SPH_ERR_INVALID;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  SPH_TRY(h->feat_out.alloc(h->n * 8));      // bf16 features [n][16]
+  SPH_TRY(h->feat_delta.alloc(h->n));        // float4 network outputs
+  __nv_bfloat16* f = reinterpret_cast<__nv_bfloat16*>(h->feat_out.p);
+  SPH_TRY(features_impl(h, params, vel, f, st));
+  mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st);
+  SPH_LAUNCH(k_warm_x0, grid_for(h, h->n), kBlock, 0, st)(reinterpret_cast<const float4*>(vel), h->feat_delta.p, ptype,
+                                                          b, h->n, h->feat_scale.p, x0);
+  SPH_TRY_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+}  // extern "C"

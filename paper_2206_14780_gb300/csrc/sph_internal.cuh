@@ -178,6 +178,12 @@ struct sph_neighbors {
   int64_t prof_n_ph[2] = {0, 0};
   int64_t op_nnz = 0;
 
+  // learned warm start (features.cu)
+  sph::DBuf<float4> feat_tmp;        // sorted v, A v, e1, e2
+  sph::DBuf<double> feat_scale;      // sum |v|^2 and count over the fluid
+  sph::DBuf<uint32_t> feat_out;      // bf16 features [n][16]
+  sph::DBuf<float4> feat_delta;      // network output [n]
+
   // float64 solve vectors r, r0^, p, Ap, r*, Ar* ([n_pad][3] each)
   sph::DBuf<double> w64[7];
 };
