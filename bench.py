@@ -52,6 +52,9 @@ def parse(argv=None):
     ap.add_argument("--no-sequence", action="store_true")
     ap.add_argument("--sequence-steps", type=int, default=200)
     ap.add_argument("--precision-only", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-only", action="store_true")
+    ap.add_argument("--weights", default=None, help="warm-start network (.npz); default: the committed weights")
     ap.add_argument("--merged", type=int, default=0)
     ap.add_argument("--eps-inner", type=float, default=1e-2)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -331,6 +334,10 @@ def run_sphvisc(args):
     if not args.no_precision and world == 1:
         torch.cuda.empty_cache()
         precision = run_precision(dev)
+    learned = None
+    if not args.no_learned and world == 1:
+        torch.cuda.empty_cache()
+        learned = run_learned(args.weights, dev)
     its = [r["iters"] for r in reps]
     out = dict(metric=METRIC, value=ms_max / (args.steps * world), unit=UNIT, n_gpus=world, steps=args.steps,
                warmup=max(3, args.warmup), ms_per_step=ms_max / args.steps, higher_is_better=False,
@@ -343,7 +350,7 @@ def run_sphvisc(args):
                            iters=its, passes=[r["refinements"] for r in reps],
                            true_rel_res=[r["true_rel_res"] for r in reps], parallelism=f"replicas x{world}"),
                roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), ensemble=ensemble,
-               precision_study=precision, sequence=sequence,
+               precision_study=precision, sequence=sequence, learned=learned,
                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"],
                            samples=clk["samples"]),
                wall_s=wall)
@@ -419,6 +426,135 @@ def run_ensemble(seed=0, dev=None):
     batch.close()
     for nb in nbs:
         nb.close()
+    return out
+
+
+# ------------------------------------------------------ learned warm start ----
+
+def _starts(nb, p, net, t, b, x0_vn, fl):
+    """The four initial guesses: name -> callable filling x (device) and returning nothing."""
+    from paper_2206_14780_gb300 import binding
+
+    def zero(x):
+        x.copy_(b)
+        x[fl] = 0.0
+
+    def vn(x):
+        x.copy_(x0_vn)
+
+    def vn_walls(x):
+        binding.warm_start(nb, p, None, t["vel"], t["ptype"], b, x)
+
+    def learned(x):
+        binding.warm_start(nb, p, net, t["vel"], t["ptype"], b, x)
+
+    return dict(zero=zero, vn=vn, vn_walls=vn_walls, learned=learned)
+
+
+def run_learned(weights=None, dev=None, reps=3):
+    """Learned warm start against x0 = 0, x0 = v^n (walls b) and v^n with the
+    dummy-wall closure, on scenes the network never saw: the 1.16M-particle
+    lava box (seed 1) with single solves, and the 64-scene ensemble (seed 1,
+    about 9M particles) through the batched solver.  Per start: iterations,
+    true residual and ms, the warm start's own kernels included."""
+    import numpy as np
+    import torch
+
+    import scenes
+    from paper_2206_14780_gb300 import binding
+    from paper_2206_14780_gb300.train_warmstart import DEFAULT_WEIGHTS
+
+    dev = dev or torch.device("cuda", 0)
+    path = weights or DEFAULT_WEIGHTS
+    if not os.path.exists(path):
+        return dict(unavailable=f"no trained weights at {os.path.relpath(path, ROOT)}")
+    z = np.load(path)
+    net = binding.Mlp(z["params"])
+    meta = json.loads(str(z["meta"])) if "meta" in z else {}
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    opts = binding.solve_opts()
+    out = dict(weights=os.path.relpath(path, ROOT), training=meta.get("train"),
+               note="ms = warm start + solve, CUDA events; x0 = 0 and v^n cost a copy")
+
+    # single 1.16M-particle box
+    s = scenes.lava_box(1, n=100)
+    t = binding.scene_tensors(s, dev)
+    t["vel"] = torch.from_numpy(s.vel).to(dev)
+    p = binding.visc_params(s.dt, s.boundary, s.mean)
+    nb = binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
+    b = torch.from_numpy(s.b).to(dev)
+    fl = torch.from_numpy(np.flatnonzero(s.ptype == scenes.FLUID)).to(dev)
+    x0_vn = torch.from_numpy(s.x0).to(dev)
+    x = torch.empty_like(b)
+    res = {}
+    for name, fill in _starts(nb, p, net, t, b, x0_vn, fl).items():
+        fill(x)
+        nb.solve(p, opts, b, x)                        # warm-up (coefficients, autotune)
+        st_ms, so_ms, its, rr = [], [], [], []
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            ev[0].record(stream)
+            fill(x)
+            ev[1].record(stream)
+            rep = nb.solve(p, opts, b, x)
+            ev[2].record(stream)
+            torch.cuda.synchronize(dev)
+            st_ms.append(ev[0].elapsed_time(ev[1]))
+            so_ms.append(ev[1].elapsed_time(ev[2]))
+            its.append(rep["iters"])
+            rr.append(rep["true_rel_res"])
+        r = torch.empty_like(b)
+        fill(x)
+        nb.residual(p, x, b, r)
+        res[name] = dict(iters=int(np.median(its)), start_ms=float(np.median(st_ms)),
+                         solve_ms=float(np.median(so_ms)), ms=float(np.median(st_ms) + np.median(so_ms)),
+                         true_rel_res=max(rr), r0_rel=float(r.norm() / b.norm()))
+    out["box_1157k"] = dict(workload=f"lava box 100^3 fluid, seed 1 (N={s.n}), nu=10, dt=5e-4, v~N(0,0.1^2)",
+                            **res)
+    nb.close()
+    del t, b, x, x0_vn
+    torch.cuda.empty_cache()
+
+    # 64-scene ensemble through the batched solver
+    ens = scenes.ensemble(1)
+    nbs, ts, bs, x0s, ps, fls = [], [], [], [], [], []
+    for sc in ens:
+        tt = binding.scene_tensors(sc, dev)
+        tt["vel"] = torch.from_numpy(sc.vel).to(dev)
+        ts.append(tt)
+        nbs.append(binding.build_neighbors(tt["pos"], tt["rho"], tt["mu"], tt["ptype"], sc.lo, sc.hi, sc.periodic,
+                                           sc.h))
+        bs.append(torch.from_numpy(sc.b).to(dev))
+        x0s.append(torch.from_numpy(sc.x0).to(dev))
+        ps.append(binding.visc_params(sc.dt, sc.boundary, sc.mean))
+        fls.append(torch.from_numpy(np.flatnonzero(sc.ptype == scenes.FLUID)).to(dev))
+    xs = [torch.empty_like(bb) for bb in bs]
+    batch = binding.Batch(nbs, ps)
+    starts = [_starts(nbs[k], ps[k], net, ts[k], bs[k], x0s[k], fls[k]) for k in range(len(ens))]
+    eres = {}
+    for name in ("zero", "vn", "vn_walls", "learned"):
+        for k in range(len(ens)):
+            starts[k][name](xs[k])
+        batch.solve(opts, bs, xs)                      # warm-up
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for k in range(len(ens)):
+            starts[k][name](xs[k])
+        ev[1].record(stream)
+        st, reps_ = batch.solve(opts, bs, xs)
+        ev[2].record(stream)
+        torch.cuda.synchronize(dev)
+        eres[name] = dict(iters_sum=int(sum(r["iters"] for r in reps_)),
+                          iters_max=int(max(r["iters"] for r in reps_)),
+                          start_ms=ev[0].elapsed_time(ev[1]), solve_ms=ev[1].elapsed_time(ev[2]),
+                          ms=ev[0].elapsed_time(ev[2]), max_true_rel_res=max(r["true_rel_res"] for r in reps_),
+                          status=st)
+    out["ensemble_64"] = dict(workload=f"64 scenes, seed 1, {sum(sc.n for sc in ens)} particles, batched solve",
+                              **eres)
+    batch.close()
+    for nb_ in nbs:
+        nb_.close()
     return out
 
 
@@ -558,6 +694,9 @@ def main():
         return
     if args.precision_only:
         print(json.dumps(run_precision()))
+        return
+    if args.learned_only:
+        print(json.dumps(run_learned(args.weights)))
         return
     if args.impl == "reference":
         run_reference(args)

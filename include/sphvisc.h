@@ -310,9 +310,36 @@ sph_status sph_mlp_train_step(sph_mlp* mlp, const uint16_t* feats, const float* 
                               const uint8_t* mask, int64_t m, int64_t count, float lr, float* loss_host,
                               void* stream);
 
+/* Loss options of sph_mlp_residual_targets (bit flags). */
+#define SPH_RLOSS_JACOBI 1 /* weight the residual by D^-1 (default: unweighted)      */
+#define SPH_RLOSS_LOG 2    /* per-problem log loss log(sum w^2|r|^2 / sum |b|^2)    */
+
+/* Targets for training the warm start on the solver's own starting residual.
+ * x0 = v + U net(features) on fluid rows with the dummy-wall closure of
+ * sph_warm_start on wall rows; r = b - A x0; w = D^-1 with SPH_RLOSS_JACOBI,
+ * else 1.  Loss (fluid rows): L = sum w^2 |r|^2 / (U^2 count), or with
+ * SPH_RLOSS_LOG L = log(sum w^2 |r|^2 / sum |b|^2), whose scale does not depend
+ * on how stiff or how far from converged a problem is.  dL/dy =
+ * -(2 U / (U^2 count)) A^T (w^2 r) (resp. -(2 U / sum w^2|r|^2) A^T (w^2 r)),
+ * holding the wall closure fixed.  The fluid block of A is symmetric when all
+ * particles have one mass, so A^T z = A z there, and the targets
+ * t = y + g A (w^2 r) with g = 1 / U (resp. count U / sum w^2 |r|^2)
+ * (device [n][4] float; mask = fluid, device [n] u8) make the mean-squared-error
+ * gradient of sph_mlp_grad / sph_mlp_train_step with count = the fluid count
+ * equal to dL/dparameters.  feats (device [n][16] bf16) receives the features;
+ * loss_host (may be NULL; synchronises) the loss L.  Unknown flags:
+ * SPH_ERR_INVALID. */
+sph_status sph_mlp_residual_targets(sph_neighbors* handle, const sph_visc_params* params,
+                                    const sph_mlp* mlp, const float* vel, const uint8_t* ptype,
+                                    const double* b, int flags, uint16_t* feats, float* targets,
+                                    uint8_t* mask, double* loss_host, void* stream);
+
 /* x0 (device [n][3] double, caller order) = v + U network(features) on fluid
- * rows, b on wall rows; vel (device [n][4] float), ptype (device [n] u8), b
- * (device [n][3] double) in caller order. */
+ * rows (v alone when mlp is NULL: the previous-step start of Sec. 4); on dummy
+ * wall rows x0 = b - sum over fluid neighbours of (W / S) x0, which makes the
+ * wall rows of b - A x0 vanish (Eq. dummyvel), and x0 = b on dynamic wall rows.
+ * vel (device [n][4] float), ptype (device [n] u8), b (device [n][3] double)
+ * in caller order. */
 sph_status sph_warm_start(sph_neighbors* handle, const sph_visc_params* params, const sph_mlp* mlp,
                           const float* vel, const uint8_t* ptype, const double* b, double* x0,
                           void* stream);

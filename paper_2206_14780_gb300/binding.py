@@ -29,7 +29,8 @@ EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", 
            "sph_mu_papanastasiou", "sph_profile_enable", "sph_profile_read", "sph_last_error", "sph_version",
            "sph_batch_create", "sph_batch_solve", "sph_batch_info", "sph_batch_destroy",
            "sph_mlp_create", "sph_mlp_set_params", "sph_mlp_get_params", "sph_mlp_destroy", "sph_mlp_features",
-           "sph_mlp_targets", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train_step", "sph_warm_start"]
+           "sph_mlp_targets", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train_step", "sph_warm_start",
+           "sph_mlp_residual_targets"]
 MLP_NPARAMS = 9603
 
 
@@ -110,6 +111,8 @@ def load(path: str = LIB_PATH):
         "sph_mlp_grad": [vp, vp, vp, vp, i64, i64, vp, vp, vp],
         "sph_mlp_train_step": [vp, vp, vp, vp, i64, i64, ctypes.c_float, ctypes.POINTER(ctypes.c_float), vp],
         "sph_warm_start": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp, vp, vp, vp],
+        "sph_mlp_residual_targets": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp, vp, ctypes.c_int, vp, vp,
+                                     vp, ctypes.POINTER(dbl), vp],
         "sph_profile_read": [vp, ctypes.POINTER(sph_profile_counters), i32],
     }
     for name, args in sig.items():
@@ -378,9 +381,23 @@ def mlp_targets(nb, vel, x_star, ptype, targets, mask, stream=None):
                                 _stream(stream)))
 
 
+RLOSS_JACOBI = 1
+RLOSS_LOG = 2
+
+
+def mlp_residual_targets(nb, params, mlp, vel, ptype, b, feats, targets, mask, flags=RLOSS_LOG, stream=None):
+    """sph_mlp_residual_targets; returns the residual loss L."""
+    L = ctypes.c_double()
+    _check(_lib.sph_mlp_residual_targets(nb.handle, ctypes.byref(params), mlp.handle, _ptr(vel), _ptr(ptype), _ptr(b),
+                                         int(flags), _ptr(feats), _ptr(targets), _ptr(mask), ctypes.byref(L),
+                                         _stream(stream)))
+    return L.value
+
+
 def warm_start(nb, params, mlp, vel, ptype, b, x0, stream=None):
-    _check(_lib.sph_warm_start(nb.handle, ctypes.byref(params), mlp.handle, _ptr(vel), _ptr(ptype), _ptr(b),
-                               _ptr(x0), _stream(stream)))
+    """sph_warm_start; mlp=None gives v^n with the dummy-wall closure."""
+    _check(_lib.sph_warm_start(nb.handle, ctypes.byref(params), mlp.handle if mlp is not None else None, _ptr(vel),
+                               _ptr(ptype), _ptr(b), _ptr(x0), _stream(stream)))
 
 
 def build_neighbors(pos, rho, mu, ptype, lo, hi, periodic, h, max_neighbors=128, stream=None):

@@ -147,14 +147,14 @@ __global__ void __launch_bounds__(kBlock) k_features(const float4* __restrict__ 
   }
 }
 
-// x0 = v + U delta on fluid rows, b on walls (caller order)
+// x0 = v + U delta on fluid rows (v alone when delta is null), b on walls (caller order)
 __global__ void k_warm_x0(const float4* __restrict__ vel, const float4* __restrict__ delta,
                           const uint8_t* __restrict__ ptype, const double* __restrict__ b, int64_t n,
                           const double* __restrict__ scale, double* __restrict__ x0) {
-  const double U = sqrt(scale[0] / fmax(scale[1], 1.0));
+  const double U = delta ? sqrt(scale[0] / fmax(scale[1], 1.0)) : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     if (ptype[i] == SPH_FLUID) {
-      const float4 v = vel[i], d = delta[i];
+      const float4 v = vel[i], d = delta ? delta[i] : make_float4(0.f, 0.f, 0.f, 0.f);
       x0[3 * i] = (double)v.x + U * (double)d.x;
       x0[3 * i + 1] = (double)v.y + U * (double)d.y;
       x0[3 * i + 2] = (double)v.z + U * (double)d.z;
@@ -178,6 +178,88 @@ __global__ void k_targets(const float4* __restrict__ vel, const double* __restri
     tgt[i] = fl ? make_float4((float)((xs[3 * i] - v.x) * iU), (float)((xs[3 * i + 1] - v.y) * iU),
                               (float)((xs[3 * i + 2] - v.z) * iU), 0.f)
                 : make_float4(0.f, 0.f, 0.f, 0.f);
+    mask[i] = fl ? 1 : 0;
+  }
+}
+
+// x0 (caller, double) -> sorted float4; wall rows zeroed when fluid_only
+__global__ void k_x0_sorted(const double* __restrict__ x0, const int32_t* __restrict__ perm,
+                            const uint8_t* __restrict__ type, int fluid_only, int64_t n, int64_t n_pad,
+                            float4* __restrict__ xs) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    if (s < n && (!fluid_only || type[s] == SPH_FLUID)) {
+      const int64_t i = perm[s];
+      xs[s] = make_float4((float)x0[3 * i], (float)x0[3 * i + 1], (float)x0[3 * i + 2], 0.f);
+    } else {
+      xs[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// dummy-wall closure (Eq. dummyvel): x0_wall = b_wall - (A x~)_wall, where x~ is
+// x0 with its wall rows zeroed, so A x~ on a wall row is the Shepard average of
+// the fluid x0 (dynamic walls: identity rows, x0_wall = b)
+__global__ void k_wall_close(const float4* __restrict__ Ax, const double* __restrict__ b,
+                             const int32_t* __restrict__ perm, const uint8_t* __restrict__ type, int64_t n,
+                             double* __restrict__ x0) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    if (type[s] != SPH_FLUID) {
+      const int64_t i = perm[s];
+      const float4 a = Ax[s];
+      x0[3 * i] = b[3 * i] - (double)a.x;
+      x0[3 * i + 1] = b[3 * i + 1] - (double)a.y;
+      x0[3 * i + 2] = b[3 * i + 2] - (double)a.z;
+    }
+  }
+}
+
+// r = b - A x0 on fluid rows (sorted), weight w = 1/D (jacobi) or 1: z = w^2 r and
+// out[0] = sum w^2 |r|^2, out[1] = sum |b|^2 over the fluid rows
+__global__ void __launch_bounds__(kBlock) k_resid_z(const float4* __restrict__ Ax, const double* __restrict__ b,
+                                                    const int32_t* __restrict__ perm,
+                                                    const uint8_t* __restrict__ type, const float* __restrict__ invD,
+                                                    int jacobi, int64_t n, int64_t n_pad, float4* __restrict__ z,
+                                                    double* partials, unsigned int* counter, double* out) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s < n && type[s] == SPH_FLUID) {
+      const int64_t i = perm[s];
+      const float d = jacobi ? invD[s] : 1.f;
+      const float4 a = Ax[s];
+      const float rx = (float)b[3 * i] - a.x, ry = (float)b[3 * i + 1] - a.y, rz = (float)b[3 * i + 2] - a.z;
+      acc[0] += (double)(rx * d) * (rx * d) + (double)(ry * d) * (ry * d) + (double)(rz * d) * (rz * d);
+      acc[1] += b[3 * i] * b[3 * i] + b[3 * i + 1] * b[3 * i + 1] + b[3 * i + 2] * b[3 * i + 2];
+      o = make_float4(rx * d * d, ry * d * d, rz * d * d, 0.f);
+    }
+    z[s] = o;
+  }
+  block_partials_f64<2>(acc, partials + (size_t)blockIdx.x * kMaxDots);
+  if (arrive_last(counter)) {
+    __shared__ double res[2];
+    final_sum<2>(partials, counter, res);
+    if (threadIdx.x < 2) out[threadIdx.x] = res[threadIdx.x];
+  }
+}
+
+// pseudo-targets t = y + g (A z) on fluid rows (caller order), mask = fluid, with
+// g = 1 / U for the plain loss and g = count U / sum w^2 |r|^2 for the log loss
+__global__ void k_resid_targets(const float4* __restrict__ y, const float4* __restrict__ Az,
+                                const int32_t* __restrict__ perm, const uint8_t* __restrict__ type, int64_t n,
+                                const double* __restrict__ scale, const double* __restrict__ sums, int log_loss,
+                                float4* __restrict__ tgt, uint8_t* __restrict__ mask) {
+  const double U = sqrt(scale[0] / fmax(scale[1], 1.0));
+  double g = 0.0;
+  if (log_loss)
+    g = sums[0] > 0.0 ? scale[1] * U / sums[0] : 0.0;
+  else
+    g = U > 0.0 ? 1.0 / U : 0.0;
+  const float gf = (float)g;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = perm[s];
+    const bool fl = type[s] == SPH_FLUID;
+    const float4 a = y[i], q = Az[s];
+    tgt[i] = fl ? make_float4(a.x + q.x * gf, a.y + q.y * gf, a.z + q.z * gf, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
     mask[i] = fl ? 1 : 0;
   }
 }
@@ -223,6 +305,17 @@ sph_status features_impl(sph_neighbors* H, const sph_visc_params* P, const float
   return SPH_OK;
 }
 
+// x0 (caller order, device double [n][3]) gets its dummy-wall rows from Eq.
+// dummyvel given its fluid rows; uses feat_tmp slots 0 and 1
+static void wall_closure(sph_neighbors* H, double* x0, const double* b, cudaStream_t st) {
+  const int64_t np = H->n_pad;
+  float4* xs = H->feat_tmp.p;
+  float4* ax = xs + np;
+  SPH_LAUNCH(k_x0_sorted, grid_for(H, np), kBlock, 0, st)(x0, H->perm.p, H->type_s.p, 1, H->n, np, xs);
+  launch_apply_f32(H, xs, ax, false, st);
+  SPH_LAUNCH(k_wall_close, grid_for(H, H->n), kBlock, 0, st)(ax, b, H->perm.p, H->type_s.p, H->n, x0);
+}
+
 }  // namespace sph
 
 using namespace sph;
@@ -264,19 +357,86 @@ sph_status sph_mlp_targets(sph_neighbors* h, const float* vel, const double* x_s
 sph_status sph_warm_start(sph_neighbors* h, const sph_visc_params* params, const sph_mlp* mlp, const float* vel,
                           const uint8_t* ptype, const double* b, double* x0, void* stream) {
   clear_error();
-  if (!h || !params || !mlp || !vel || !ptype || !b || !x0) {
+  if (!h || !params || !vel || !ptype || !b || !x0) {
     set_error("sph_warm_start: null argument");
     return SPH_ERR_INVALID;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  SPH_TRY(h->feat_out.alloc(h->n * 8));      // bf16 features [n][16]
-  SPH_TRY(h->feat_delta.alloc(h->n));        // float4 network outputs
-  __nv_bfloat16* f = reinterpret_cast<__nv_bfloat16*>(h->feat_out.p);
+  const float4* delta = nullptr;
+  if (mlp) {
+    SPH_TRY(h->feat_out.alloc(h->n * 8));      // bf16 features [n][16]
+    SPH_TRY(h->feat_delta.alloc(h->n));        // float4 network outputs
+    __nv_bfloat16* f = reinterpret_cast<__nv_bfloat16*>(h->feat_out.p);
+    SPH_TRY(features_impl(h, params, vel, f, st));
+    mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st);
+    delta = h->feat_delta.p;
+  } else {
+    SPH_TRY(ensure_operator(h, params, st));
+    SPH_TRY(ensure_workspace(h));
+    SPH_TRY(h->feat_tmp.alloc(4 * h->n_pad));
+  }
+  SPH_LAUNCH(k_warm_x0, grid_for(h, h->n), kBlock, 0, st)(reinterpret_cast<const float4*>(vel), delta, ptype, b, h->n,
+                                                          h->feat_scale.p, x0);
+  wall_closure(h, x0, b, st);
+  SPH_TRY_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+/* Residual-loss training targets (the declaration states the loss and the
+   identity behind them).  Buffers: x64 holds x0 in caller order, feat_tmp slots
+   0-3 the sorted x0, A x0, z and A z, r64[0..1] the two sums. */
+sph_status sph_mlp_residual_targets(sph_neighbors* h, const sph_visc_params* params, const sph_mlp* mlp,
+                                    const float* vel, const uint8_t* ptype, const double* b, int flags,
+                                    uint16_t* feats, float* targets, uint8_t* mask, double* loss_host,
+                                    void* stream) {
+  clear_error();
+  if (!h || !params || !mlp || !vel || !ptype || !b || !feats || !targets || !mask) {
+    set_error("sph_mlp_residual_targets: null argument");
+    return SPH_ERR_INVALID;
+  }
+  if (flags & ~(SPH_RLOSS_JACOBI | SPH_RLOSS_LOG)) {
+    set_error("sph_mlp_residual_targets: unknown flags %d", flags);
+    return SPH_ERR_INVALID;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  __nv_bfloat16* f = reinterpret_cast<__nv_bfloat16*>(feats);
   SPH_TRY(features_impl(h, params, vel, f, st));
+  SPH_TRY(h->feat_delta.alloc(h->n));
+  SPH_TRY(h->x64.alloc(3 * h->n_pad));
+  SPH_TRY(h->r64.alloc(3 * h->n_pad));
   mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st);
+  double* x0 = h->x64.p;
   SPH_LAUNCH(k_warm_x0, grid_for(h, h->n), kBlock, 0, st)(reinterpret_cast<const float4*>(vel), h->feat_delta.p, ptype,
                                                           b, h->n, h->feat_scale.p, x0);
+  wall_closure(h, x0, b, st);
+  const int64_t np = h->n_pad;
+  float4* xs = h->feat_tmp.p;
+  float4* ax = xs + np;
+  float4* z = xs + 2 * np;
+  float4* az = xs + 3 * np;
+  SPH_LAUNCH(k_x0_sorted, grid_for(h, np), kBlock, 0, st)(x0, h->perm.p, h->type_s.p, 0, h->n, np, xs);
+  launch_apply_f32(h, xs, ax, false, st);
+  const int rg = grid_for(h, np) < h->red_grid ? grid_for(h, np) : h->red_grid;
+  double* sums = h->r64.p;
+  SPH_LAUNCH(k_resid_z, rg, kBlock, 0, st)(ax, b, h->perm.p, h->type_s.p, h->invD.p, (flags & SPH_RLOSS_JACOBI) ? 1 : 0,
+                                           h->n, np, z, h->partials.p, h->counters.p + 7, sums);
+  launch_apply_f32(h, z, az, false, st);
+  SPH_LAUNCH(k_resid_targets, grid_for(h, h->n), kBlock, 0, st)(h->feat_delta.p, az, h->perm.p, h->type_s.p, h->n,
+                                                                h->feat_scale.p, sums, (flags & SPH_RLOSS_LOG) ? 1 : 0,
+                                                                reinterpret_cast<float4*>(targets), mask);
   SPH_TRY_CUDA(cudaGetLastError());
+  if (loss_host) {
+    double v[4];
+    SPH_TRY_CUDA(cudaMemcpyAsync(v, sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SPH_TRY_CUDA(cudaMemcpyAsync(v + 2, h->feat_scale.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SPH_TRY_CUDA(cudaStreamSynchronize(st));
+    if (flags & SPH_RLOSS_LOG) {
+      *loss_host = (v[0] > 0.0 && v[1] > 0.0) ? std::log(v[0] / v[1]) : 0.0;
+    } else {
+      const double U2 = v[2] / (v[3] > 1.0 ? v[3] : 1.0);
+      *loss_host = (U2 > 0.0 && v[3] > 0.0) ? v[0] / (U2 * v[3]) : 0.0;
+    }
+  }
   return SPH_OK;
 }
 
