@@ -5,11 +5,12 @@
 
 One step is the whole hot path on one particle set already resident in HBM:
 neighbour build (cell sort + lists), coefficients of A(dt) with the Jacobi
-diagonal, and the mixed-precision restructured BiCGSTAB with float64
-refinement until ||b - A x|| / ||b|| <= 1e-6.  The workload is the lava-like
-box: a 100^3 jittered fluid lattice (dx = 5 mm) on a 3-layer dummy floor and
-walls (1,157,308 particles), nu = 10 m^2/s, dt = 5e-4 s, v ~ N(0, 0.1^2),
-b = x0 = v.  Its matrix (1.5 GB of coefficients) is far larger than L2, so no
+diagonal, the start x0 (v^n on fluid rows, dummy-wall rows from Eq. dummyvel)
+and the mixed-precision restructured BiCGSTAB with float64 refinement until
+||b - A x|| / ||b|| <= 1e-6.  The workload is the lava-like box: a 100^3
+jittered fluid lattice (dx = 5 mm) on a 3-layer dummy floor and walls
+(1,157,308 particles), nu = 10 m^2/s, dt = 5e-4 s, v ~ N(0, 0.1^2), b = v.
+Its matrix (1.5 GB of coefficients) is far larger than L2, so no
 flush is needed between steps.
 
 Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank solves its own
@@ -64,7 +65,7 @@ def parse(argv=None):
 
 def workload_name(n):
     return (f"lava box: {n}^3 jittered fluid lattice dx=5mm on 3-layer dummy floor+walls, Wendland h=1.3dx, "
-            f"nu=10 m^2/s, dt=5e-4 s, v~N(0,0.1^2), b=x0=v")
+            f"nu=10 m^2/s, dt=5e-4 s, v~N(0,0.1^2), b=v, x0=v with dummy-wall closure")
 
 
 # ---------------------------------------------------------------- CPU oracle --
@@ -74,13 +75,14 @@ def oracle_solve_seconds(n, seed=0):
     import numpy as np
 
     import scenes
-    from oracle import neighbors as onb, operator as oop, solvers as osv
+    from oracle import neighbors as onb, operator as oop, solvers as osv, warmstart as ows
 
     s = scenes.lava_box(seed, n=n)
     t0 = time.perf_counter()
     off, idx = onb.build(s.pos, s.lo, s.hi, s.periodic, s.h)
     A = oop.assemble(s, off, idx)
-    x = osv.reference_solution(A, s.b, s.x0, rtol=1e-6)
+    x0 = ows.start(A, s.b, s.vel, None, s.ptype, 1.0)
+    x = osv.reference_solution(A, s.b, x0, rtol=1e-6)
     t1 = time.perf_counter()
     res, _ = oop.true_residual(A, x, s.b)
     return t1 - t0, s.n, float(res)
@@ -114,6 +116,28 @@ def read_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def apply_traffic(alg_bytes):
+    """DRAM bytes per apply launch: the ncu-measured ratio of DRAM traffic to algorithmic
+    bytes (profiles/apply_traffic.txt) times this launch's algorithmic bytes, or None when
+    the kernel sources changed since the counters were taken."""
+    import hashlib
+
+    try:
+        kv = {}
+        for line in open(os.path.join(ROOT, "profiles", "apply_traffic.txt")):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.strip().split("=", 1)
+                kv[k] = v
+        src = b"".join(open(os.path.join(ROOT, "paper_2206_14780_gb300", "csrc", f), "rb").read()
+                       for f in ("apply.cuh", "solver.cu"))
+        if hashlib.sha256(src).hexdigest()[:16] != kv["sources_sha256_16"]:
+            return None, "kernel changed since the ncu capture"
+        return float(kv["dram_bytes_per_algorithmic_byte"]) * alg_bytes, \
+            "ncu dram bytes per algorithmic byte at 274k particles, scaled to this launch"
+    except Exception as e:
+        return None, f"unavailable ({type(e).__name__})"
 
 
 class ClockSampler:
@@ -222,6 +246,7 @@ def run_sphvisc(args):
     opts = binding.solve_opts(merged_reductions=args.merged, eps_inner=args.eps_inner,
                               precision=binding.SPH_PREC_FP64 if args.precision == "fp64" else binding.SPH_PREC_MIXED)
     t = binding.scene_tensors(s, dev)
+    t["vel"] = torch.from_numpy(s.vel).to(dev)
     b = torch.from_numpy(s.b).to(dev)
     x0 = torch.from_numpy(s.x0).to(dev)
     x = torch.empty_like(x0)
@@ -230,8 +255,9 @@ def run_sphvisc(args):
     stream = torch.cuda.current_stream(dev)
 
     def step():
+        # x0 = v^n on fluid rows, dummy-wall rows from Eq. dummyvel (sph_warm_start, no network)
         nb.rebuild(t["pos"], t["rho"], t["mu"], t["ptype"], *geo)
-        x.copy_(x0)
+        binding.warm_start(nb, params, None, t["vel"], t["ptype"], b, x)
         return nb.solve(params, opts, b, x)
 
     for _ in range(max(3, args.warmup)):
@@ -261,14 +287,14 @@ def run_sphvisc(args):
     ms_max = max_over_ranks(ms, world, dev)
     barrier(world, dev)
 
-    # end to end through host buffers: H2D of the particle set and b, x0; D2H of x
+    # end to end through host buffers: H2D of the particle set (with v^n) and b; D2H of x
     e2e = None
     if not args.no_e2e:
         host = {k: v.cpu().pin_memory() for k, v in t.items()}
-        hb, hx0 = b.cpu().pin_memory(), x0.cpu().pin_memory()
-        hx = torch.empty_like(hx0).pin_memory()
+        hb = b.cpu().pin_memory()
+        hx = torch.empty_like(hb).pin_memory()
         dt_ = {k: torch.empty_like(v) for k, v in t.items()}
-        h2d = sum(v.numel() * v.element_size() for v in host.values()) + hb.numel() * 8 + hx0.numel() * 8
+        h2d = sum(v.numel() * v.element_size() for v in host.values()) + hb.numel() * 8
         d2h = hx.numel() * 8
         bb = torch.empty_like(b)
 
@@ -276,8 +302,8 @@ def run_sphvisc(args):
             for k in host:
                 dt_[k].copy_(host[k], non_blocking=True)
             bb.copy_(hb, non_blocking=True)
-            x.copy_(hx0, non_blocking=True)
             nb.rebuild(dt_["pos"], dt_["rho"], dt_["mu"], dt_["ptype"], *geo)
+            binding.warm_start(nb, params, None, dt_["vel"], dt_["ptype"], bb, x)
             nb.solve(params, opts, bb, x)
             hx.copy_(x, non_blocking=True)
             torch.cuda.current_stream(dev).synchronize()
@@ -304,8 +330,9 @@ def run_sphvisc(args):
     hbm, peak_kind = read_peaks()
     avg_apply_ms = prof["apply_ms"] / max(1, prof["apply_launches"])
     achieved = prof["apply_bytes"] / (avg_apply_ms * 1e-3) / 1e9 if prof["apply_launches"] else None
+    traffic, traffic_src = apply_traffic(prof["apply_bytes"])
     roofline = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s",
-                    frac=(achieved / hbm) if achieved else None, traffic=None,
+                    frac=(achieved / hbm) if achieved else None, traffic=traffic, traffic_source=traffic_src,
                     kernel="k_apply_dot (operator apply + fused dots)", peak_source=peak_kind,
                     apply_launches=prof["apply_launches"], apply_avg_us=avg_apply_ms * 1e3,
                     apply_avg_us_Ap=1e3 * prof["phase_ms"][0] / max(1, prof["phase_launches"][0]),
@@ -324,7 +351,7 @@ def run_sphvisc(args):
                            f"BiCGSTAB iteration counts depend on dt*nu/dx^2, not on N"))
     sequence = None
     if not args.no_sequence and world == 1:
-        sequence = run_sequence(nb, s, b, x0, args.sequence_steps, dev)
+        sequence = run_sequence(nb, s, b, t, args.sequence_steps, dev)
     ensemble = None
     if not args.no_ensemble and world == 1:
         nb.close()
@@ -346,7 +373,8 @@ def run_sphvisc(args):
                            precision="f32 operator+vectors, f64 dots/scalars, f64 true-residual refinement",
                            merged_reductions=args.merged, eps_inner=args.eps_inner,
                            l2="inputs larger than L2 (A(dt) coefficients ~1.5 GB)",
-                           step="neighbour build + A(dt) coefficients + restructured BiCGSTAB to 1e-6",
+                           step="neighbour build + A(dt) coefficients + x0 (v^n, dummy-wall closure) + "
+                                "restructured BiCGSTAB to 1e-6",
                            iters=its, passes=[r["refinements"] for r in reps],
                            true_rel_res=[r["true_rel_res"] for r in reps], parallelism=f"replicas x{world}"),
                roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), ensemble=ensemble,
@@ -373,21 +401,27 @@ def run_ensemble(seed=0, dev=None):
 
     dev = dev or torch.device("cuda", 0)
     ens = scenes.ensemble(seed)
-    nbs, bs, x0s, params = [], [], [], []
+    nbs, bs, ts, params = [], [], [], []
     for s in ens:
         t = binding.scene_tensors(s, dev)
+        t["vel"] = torch.from_numpy(s.vel).to(dev)
+        ts.append(t)
         nbs.append(binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h))
         bs.append(torch.from_numpy(s.b).to(dev))
-        x0s.append(torch.from_numpy(s.x0).to(dev))
         params.append(binding.visc_params(s.dt, s.boundary, s.mean))
     opts = binding.solve_opts()
     stream = torch.cuda.current_stream(dev)
-    xs = [x.clone() for x in x0s]
+    xs = [torch.empty_like(b) for b in bs]
+
+    def starts():
+        # x0 = v^n with the dummy-wall rows from Eq. dummyvel, per scene
+        for nb, p, t, b, x in zip(nbs, params, ts, bs, xs):
+            binding.warm_start(nb, p, None, t["vel"], t["ptype"], b, x)
 
     def sequential():
         reps = []
-        for nb, p, b, x, x0 in zip(nbs, params, bs, xs, x0s):
-            x.copy_(x0)
+        for nb, p, t, b, x in zip(nbs, params, ts, bs, xs):
+            binding.warm_start(nb, p, None, t["vel"], t["ptype"], b, x)
             reps.append(nb.solve(p, opts, b, x))
         return reps
 
@@ -400,21 +434,20 @@ def run_ensemble(seed=0, dev=None):
     torch.cuda.synchronize(dev)
     seq_ms = e0.elapsed_time(e1)
     batch = binding.Batch(nbs, params)
-    for x, x0 in zip(xs, x0s):
-        x.copy_(x0)
+    starts()
     batch.solve(opts, bs, xs)                      # warm-up: autotune + graph capture
-    for x, x0 in zip(xs, x0s):
-        x.copy_(x0)
     launches0 = binding.launch_count()
     torch.cuda.synchronize(dev)
     e0.record(stream)
+    starts()
     st, bat = batch.solve(opts, bs, xs)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     bat_ms = e0.elapsed_time(e1)
     info = batch.info()
     out = dict(workload="64 scenes (channel/box alternating), totals log-uniform 1e4-5e5 particles, "
-                        "nu log-uniform 1-1e3 m^2/s, dt log-uniform 1e-4-5e-4 s",
+                        "nu log-uniform 1-1e3 m^2/s, dt log-uniform 1e-4-5e-4 s; x0 = v^n with the dummy-wall "
+                        "closure, inside the timed region of both forms",
                particles=int(sum(s.n for s in ens)), scenes=len(ens),
                sequential_ms=seq_ms, batched_ms=bat_ms, speedup=seq_ms / bat_ms,
                sequential_ms_per_solve=seq_ms / len(ens), batched_ms_per_solve=bat_ms / len(ens),
@@ -560,10 +593,11 @@ def run_learned(weights=None, dev=None, reps=3):
 
 # ----------------------------------------------------- 200-step sequence ----
 
-def run_sequence(nb, s, b, x0, steps, dev):
+def run_sequence(nb, s, b, t, steps, dev):
     """Warm-started sequence on the same A(dt) (positions frozen): step k solves with
     b = v^k + dt g on fluid rows (g a fixed smooth stirring force) and x0 = the previous
-    solution v^k, so the field settles to a steady stirred state."""
+    solution v^k (the first from v^0 with the dummy-wall closure), so the field settles
+    to a steady stirred state."""
     import torch
 
     import scenes
@@ -574,7 +608,8 @@ def run_sequence(nb, s, b, x0, steps, dev):
     fl = torch.from_numpy(s.ptype == 0).to(dev)
     dtg = torch.from_numpy(s.dt * scenes.stirring_force(s)).to(dev)
     bk = b.clone() + dtg
-    x = x0.clone()
+    x = torch.empty_like(b)
+    binding.warm_start(nb, p, None, t["vel"], t["ptype"], bk, x)
     its = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream(dev)
