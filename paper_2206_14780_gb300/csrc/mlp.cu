@@ -3,7 +3,8 @@
 //
 // The paper names a better initial guess as future work (Sec. 8); the network
 // predicts delta = (x* - v^n) / U from local features and the solve starts
-// from x0 = v^n + U delta on fluid rows (walls start at their right-hand side).
+// from x0 = v^n + U delta on fluid rows, the dummy-wall rows of x0 following
+// from the fluid ones by Eq. dummyvel (features.cu).
 //
 // Tensor cores: mma.sync.m16n8k16 (bf16 x bf16 -> f32).  One warp owns 16
 // particles.  The accumulator fragment of two adjacent 8-column tiles is, lane
