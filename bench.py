@@ -363,6 +363,9 @@ def run_sphvisc(args):
                            f"restarted to a 1e-6 true residual) on the same box workload at {args.cpu_n}^3 fluid "
                            f"(N={rows[0]['n']}), {sec:.1f} s, scaled linearly by particle count to N={s.n}; "
                            f"BiCGSTAB iteration counts depend on dt*nu/dx^2, not on N"))
+    apply_forms = None
+    if world == 1:
+        apply_forms = run_apply_forms(nb, params, s.n, dev)
     sequence = None
     if not args.no_sequence and world == 1:
         sequence = run_sequence(nb, s, b, t, args.sequence_steps, dev)
@@ -394,7 +397,7 @@ def run_sphvisc(args):
                            ms_per_step_median=statistics.median(per_step),
                            ms_per_step_min=min(per_step), ms_per_step_max=max(per_step)),
                roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), ensemble=ensemble,
-               precision_study=precision, sequence=sequence, learned=learned,
+               precision_study=precision, sequence=sequence, learned=learned, apply_forms=apply_forms,
                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"],
                            samples=clk["samples"]),
                wall_s=wall)
@@ -403,6 +406,38 @@ def run_sphvisc(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------- apply forms ------
+
+def run_apply_forms(nb, params, n, dev, reps=20):
+    """The two apply forms on the same operator: stored coefficients (the solver's) and
+    coefficients recomputed per pair (the paper's GPU form); device time of the apply
+    kernel alone (CUDA events around each launch), algorithmic bytes and GB/s."""
+    import torch
+
+    v = torch.randn((n, 4), dtype=torch.float32, device=dev)
+    y = torch.empty_like(v)
+    nb.apply(params, v, y)
+    nb.apply_otf(params, v, y)                     # packs the per-particle geometry
+    torch.cuda.synchronize(dev)
+    nb.profile(True)
+    nb.profile_read(reset=True)
+    for _ in range(reps):
+        nb.apply(params, v, y)
+    for _ in range(reps):
+        nb.apply_otf(params, v, y)
+    torch.cuda.synchronize(dev)
+    c = nb.profile_read(reset=True)
+    nb.profile(False)
+    out = {}
+    for k, (name, nbytes) in enumerate((("stored", c["apply_bytes"] - 16 * n), ("on_the_fly", c["otf_bytes"]))):
+        us = 1e3 * c["standalone_ms"][k] / max(1, c["standalone_launches"][k])
+        out[name] = dict(us_per_apply=us, algorithmic_bytes=int(nbytes), gbs=nbytes / (us * 1e-6) / 1e9,
+                         launches=c["standalone_launches"][k])
+    out["note"] = ("y = A v alone (no fused dots); stored: 8 B per coefficient + 41 B per row; on the fly: "
+                   "4 B per neighbour-list entry + 61 B per row, coefficients recomputed in float32")
+    return out
 
 
 # ------------------------------------------------------------- ensemble ------

@@ -141,6 +141,18 @@ sph_status sph_visc_setup(sph_neighbors* handle, const sph_visc_params* params, 
 sph_status sph_visc_apply(sph_neighbors* handle, const sph_visc_params* params, const float* v,
                           float* y, void* stream);
 
+/* The same y = A v as sph_visc_apply, with every coefficient recomputed from the
+ * particle data inside the apply (the paper's own GPU form, App. A and App. B):
+ * c_ab = 2 mubar m_a |F_ab| / (rho_a rho_b) of Eq. kab per neighbour pair in
+ * float32, dummy-wall rows by the Shepard sums of Eq. dummyvel, row kinds as in
+ * sph_visc_setup.  It streams the 4-byte neighbour list instead of the stored
+ * 8-byte (index, coefficient) entries and gathers each neighbour's position,
+ * volume and viscosity besides its velocity.  Arguments, layout and errors as
+ * sph_visc_apply; the first call after a rebuild or new viscosities packs the
+ * per-particle geometry (device memory owned by the handle). */
+sph_status sph_visc_apply_otf(sph_neighbors* handle, const sph_visc_params* params, const float* v,
+                              float* y, void* stream);
+
 /* Largest particle count sph_visc_apply_noalloc accepts (after rounding n up
  * to a multiple of 32). */
 #define SPH_NOALLOC_MAX_ROWS 262144
@@ -375,6 +387,14 @@ typedef struct {
                                 (8 entries, plain), (4, plain), (8, prefetch), (4, prefetch) */
   float tune_us[3][4];       /* autotuner timings (us) per phase (A p, A r*, A r* with
                                 merged dots) and form; 0 where not measured          */
+  int64_t standalone_launches[2]; /* sph_visc_apply [0] and sph_visc_apply_otf [1] calls
+                                     timed (their apply kernel only; profiling makes
+                                     each such call synchronise)                      */
+  double standalone_ms[2];        /* summed device time of those apply kernels (ms)    */
+  int64_t otf_bytes;         /* algorithmic bytes of one on-the-fly apply: 4 per
+                                neighbour-list entry plus, per row, 16 read of v, 16
+                                write, 16 of packed geometry, 4 of 1/mu, 4 of R_b, 4
+                                of the count and 1 of the kind                        */
 } sph_profile_counters;
 
 sph_status sph_profile_enable(sph_neighbors* handle, int32_t on);

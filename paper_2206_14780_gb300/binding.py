@@ -25,7 +25,7 @@ SPH_CONVERGED, SPH_STALLED, SPH_PROGRESSING = 0, 1, 2
 
 # every symbol include/sphvisc.h declares
 EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", "sph_set_viscosity",
-           "sph_neighbors_destroy", "sph_visc_setup", "sph_visc_apply", "sph_visc_apply_noalloc", "sph_visc_residual", "sph_visc_solve",
+           "sph_neighbors_destroy", "sph_visc_setup", "sph_visc_apply", "sph_visc_apply_otf", "sph_visc_apply_noalloc", "sph_visc_residual", "sph_visc_solve",
            "sph_mu_papanastasiou", "sph_profile_enable", "sph_profile_read", "sph_last_error", "sph_version",
            "sph_batch_create", "sph_batch_solve", "sph_batch_info", "sph_batch_destroy",
            "sph_mlp_create", "sph_mlp_set_params", "sph_mlp_get_params", "sph_mlp_destroy", "sph_mlp_features",
@@ -60,7 +60,9 @@ class sph_profile_counters(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("apply_launches", ctypes.c_int64), ("apply_ms", ctypes.c_double),
                 ("apply_bytes", ctypes.c_int64), ("op_nnz", ctypes.c_int64),
                 ("phase_launches", ctypes.c_int64 * 2), ("phase_ms", ctypes.c_double * 2),
-                ("apply_variant", ctypes.c_int32 * 2), ("tune_us", (ctypes.c_float * 4) * 3)]
+                ("apply_variant", ctypes.c_int32 * 2), ("tune_us", (ctypes.c_float * 4) * 3),
+                ("standalone_launches", ctypes.c_int64 * 2), ("standalone_ms", ctypes.c_double * 2),
+                ("otf_bytes", ctypes.c_int64)]
 
 
 class SphError(RuntimeError):
@@ -89,6 +91,7 @@ def load(path: str = LIB_PATH):
         "sph_neighbors_destroy": [vp],
         "sph_visc_setup": [vp, ctypes.POINTER(sph_visc_params), vp],
         "sph_visc_apply": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp],
+        "sph_visc_apply_otf": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp],
         "sph_visc_apply_noalloc": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp],
         "sph_visc_residual": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp, vp],
         "sph_visc_solve": [vp, ctypes.POINTER(sph_visc_params), ctypes.POINTER(sph_solve_opts), vp, vp,
@@ -214,6 +217,10 @@ class Neighbors:
     def apply(self, params, v, y, stream=None):
         _check(_lib.sph_visc_apply(self.handle, ctypes.byref(params), _ptr(v), _ptr(y), _stream(stream)))
 
+    def apply_otf(self, params, v, y, stream=None):
+        """sph_visc_apply_otf: y = A v with the coefficients recomputed per pair."""
+        _check(_lib.sph_visc_apply_otf(self.handle, ctypes.byref(params), _ptr(v), _ptr(y), _stream(stream)))
+
     def apply_noalloc(self, params, v, y, stream=None):
         """sph_visc_apply_noalloc: y = A v with no device allocation (needs setup first)."""
         _check(_lib.sph_visc_apply_noalloc(self.handle, ctypes.byref(params), _ptr(v), _ptr(y), _stream(stream)))
@@ -245,7 +252,8 @@ class Neighbors:
         return dict(launches=c.launches, apply_launches=c.apply_launches, apply_ms=c.apply_ms,
                     apply_bytes=c.apply_bytes, op_nnz=c.op_nnz, phase_launches=list(c.phase_launches),
                     phase_ms=list(c.phase_ms), apply_variant=list(c.apply_variant),
-                    tune_us=[list(r) for r in c.tune_us])
+                    tune_us=[list(r) for r in c.tune_us], standalone_launches=list(c.standalone_launches),
+                    standalone_ms=list(c.standalone_ms), otf_bytes=c.otf_bytes)
 
     def close(self):
         if self.handle:

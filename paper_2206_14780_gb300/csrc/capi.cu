@@ -34,6 +34,19 @@ void prof_end(sph_neighbors* H, cudaStream_t st) {
   cudaEventRecord(H->prof_ev[H->prof_used + 1], st);
   H->prof_used += 2;
 }
+void standalone_begin(sph_neighbors* H, cudaStream_t st) {
+  if (H->prof_on && H->sa_ev[0]) cudaEventRecord(H->sa_ev[0], st);
+}
+sph_status standalone_end(sph_neighbors* H, cudaStream_t st, int form) {
+  if (!H->prof_on || !H->sa_ev[0]) return SPH_OK;
+  SPH_TRY_CUDA(cudaEventRecord(H->sa_ev[1], st));
+  SPH_TRY_CUDA(cudaEventSynchronize(H->sa_ev[1]));
+  float ms = 0.f;
+  SPH_TRY_CUDA(cudaEventElapsedTime(&ms, H->sa_ev[0], H->sa_ev[1]));
+  H->sa_ms[form] += ms;
+  H->sa_n[form] += 1;
+  return SPH_OK;
+}
 void prof_flush(sph_neighbors* H, int valid_pairs) {
   if (!H->prof_on) return;
   const int pairs = H->prof_used / 2;
@@ -147,7 +160,12 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
   h->scal.release();
   h->scal_tune.release();
   for (auto& w : h->w64) w.release();
+  h->otf_g.release();
+  h->otf_im.release();
+  h->otf_rb.release();
   for (auto& e : h->prof_ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : h->sa_ev)
     if (e) cudaEventDestroy(e);
   if (h->host_scal) cudaFreeHost(h->host_scal);
   if (h->host_flags) cudaFreeHost(h->host_flags);
@@ -172,6 +190,16 @@ sph_status sph_visc_apply(sph_neighbors* h, const sph_visc_params* params, const
     return SPH_ERR_INVALID;
   }
   return visc_apply(h, params, v, y, as_stream(stream));
+}
+
+sph_status sph_visc_apply_otf(sph_neighbors* h, const sph_visc_params* params, const float* v, float* y,
+                              void* stream) {
+  clear_error();
+  if (v == y && v) {
+    set_error("sph_visc_apply_otf: v and y must not overlap");
+    return SPH_ERR_INVALID;
+  }
+  return visc_apply_otf(h, params, v, y, as_stream(stream));
 }
 
 sph_status sph_visc_apply_noalloc(sph_neighbors* h, const sph_visc_params* params, const float* v, float* y,
@@ -227,6 +255,8 @@ sph_status sph_profile_enable(sph_neighbors* h, int32_t on) {
   if (on) {
     for (auto& e : h->prof_ev)
       if (!e) SPH_TRY_CUDA(cudaEventCreate(&e));
+    for (auto& e : h->sa_ev)
+      if (!e) SPH_TRY_CUDA(cudaEventCreate(&e));
   }
   h->prof_on = on != 0;
   h->prof_used = 0;
@@ -254,11 +284,18 @@ sph_status sph_profile_read(sph_neighbors* h, sph_profile_counters* out, int32_t
     out->apply_variant[1] = h->apply_var[1] > h->apply_var[2] ? h->apply_var[1] : h->apply_var[2];
     for (int ph = 0; ph < 3; ++ph)
       for (int v = 0; v < 4; ++v) out->tune_us[ph][v] = h->tune_us[ph][v];
+    for (int f = 0; f < 2; ++f) {
+      out->standalone_launches[f] = h->sa_n[f];
+      out->standalone_ms[f] = h->sa_ms[f];
+    }
+    out->otf_bytes = 4 * h->nnz + (16 + 16 + 16 + 4 + 4 + 4 + 1) * h->n;
     if (reset) {
       h->prof_n = 0;
       h->prof_ms = 0.0;
       h->prof_n_ph[0] = h->prof_n_ph[1] = 0;
       h->prof_ms_ph[0] = h->prof_ms_ph[1] = 0.0;
+      h->sa_n[0] = h->sa_n[1] = 0;
+      h->sa_ms[0] = h->sa_ms[1] = 0.0;
     }
   }
   return SPH_OK;

@@ -322,6 +322,7 @@ sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStrea
   H->op_valid = true;
   H->op_params = *P;
   H->op_mu_version = H->mu_version;
+  ++H->op_version;
   return SPH_OK;
 }
 
@@ -355,7 +356,9 @@ sph_status visc_apply(sph_neighbors* H, const sph_visc_params* P, const float* v
   const int grid = grid_for(H, H->n_pad);
   SPH_LAUNCH(k_gather_f4, grid, kBlock, 0, st)(v, H->perm.p, H->n, H->n_pad, vs);
   SPH_TRY_CUDA(cudaGetLastError());
+  standalone_begin(H, st);
   launch_apply_f32(H, vs, ys, false, st);
+  SPH_TRY(standalone_end(H, st, 0));
   SPH_TRY_CUDA(cudaGetLastError());
   SPH_LAUNCH(k_scatter_f4, grid, kBlock, 0, st)(ys, H->perm.p, H->n, y);
   SPH_TRY_CUDA(cudaGetLastError());

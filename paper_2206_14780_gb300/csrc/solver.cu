@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kBlock) k_p_update(int64_t n_pad, Vecs V, cons
 //   PH_OMEGA:        v = r*, y = Ar*; dots r*.Ar*, Ar*.Ar*             (K = 6)
 //   PH_OMEGA_MERGED: + r0^.r*, r0^.Ar*, r*.r*                          (K = 15)
 template <int PH, int U, bool PF>
-__global__ void __launch_bounds__(kBlock) k_apply_dot(OpView op, const float4* __restrict__ v, float4* __restrict__ y,
+__global__ void __launch_bounds__(kBlock, 4) k_apply_dot(OpView op, const float4* __restrict__ v, float4* __restrict__ y,
                                                       const float4* __restrict__ rh, SolverScalars* S,
                                                       double* partials, unsigned int* counter) {
   constexpr int K = PH == PH_DELTA ? 3 : (PH == PH_OMEGA ? 6 : 15);

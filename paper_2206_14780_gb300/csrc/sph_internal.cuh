@@ -142,6 +142,13 @@ struct sph_neighbors {
   sph::DBuf<double> D64;           // float64 D
   sph::DBuf<double2> aux64;        // per particle (m / rho, 1 / mu) in float64
   int64_t op_nnz_pad = 0;
+  uint64_t op_version = 0;         // bumped whenever the operator is rebuilt
+
+  // on-the-fly apply (apply_otf.cu): packed geometry for the operator of op_version
+  bool otf_valid = false;
+  uint64_t otf_op_version = 0;
+  sph::DBuf<float4> otf_g;         // (x, y, z, +-V), V = m / rho, negative for walls
+  sph::DBuf<float> otf_im, otf_rb; // 1/mu (or mu), R_b = 2 dt 105/(128 pi) / (h^5 rho_b)
 
   // scratch used by builds and solves
   sph::DBuf<int32_t> tmp_i32a, tmp_i32b;
@@ -177,6 +184,10 @@ struct sph_neighbors {
   double prof_ms_ph[2] = {0.0, 0.0};
   int64_t prof_n_ph[2] = {0, 0};
   int64_t op_nnz = 0;
+  // stand-alone applies (sph_visc_apply, sph_visc_apply_otf): [0] stored, [1] on the fly
+  cudaEvent_t sa_ev[2] = {};
+  double sa_ms[2] = {0.0, 0.0};
+  int64_t sa_n[2] = {0, 0};
 
   // learned warm start (features.cu)
   sph::DBuf<float4> feat_tmp;        // sorted v, A v, e1, e2
@@ -208,6 +219,12 @@ sph_status visc_apply_noalloc(sph_neighbors* H, const sph_visc_params* P, const 
                               cudaStream_t st);
 sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStream_t st);
 void launch_apply_f32(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st);
+// apply_otf.cu: y = A v with the coefficients recomputed per pair
+void launch_apply_otf(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st);
+sph_status visc_apply_otf(sph_neighbors* H, const sph_visc_params* P, const float* v, float* y, cudaStream_t st);
+// CUDA-event timing of one stand-alone apply launch when profiling is on (synchronises)
+void standalone_begin(sph_neighbors* H, cudaStream_t st);
+sph_status standalone_end(sph_neighbors* H, cudaStream_t st, int form);
 struct OpView;
 OpView op_view(const sph_neighbors* H);
 using ApplyDotFn = void (*)(OpView, const float4*, float4*, const float4*, SolverScalars*, double*, unsigned int*);
