@@ -47,7 +47,8 @@ class sph_visc_params(ctypes.Structure):
 class sph_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("eps_inner", ctypes.c_double), ("maxit", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("merged_reductions", ctypes.c_int32), ("chunk", ctypes.c_int32), ("jacobi", ctypes.c_int32)]
+                ("merged_reductions", ctypes.c_int32), ("chunk", ctypes.c_int32), ("jacobi", ctypes.c_int32),
+                ("apply_form", ctypes.c_int32)]
 
 
 class sph_solve_report(ctypes.Structure):
@@ -60,7 +61,7 @@ class sph_profile_counters(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("apply_launches", ctypes.c_int64), ("apply_ms", ctypes.c_double),
                 ("apply_bytes", ctypes.c_int64), ("op_nnz", ctypes.c_int64),
                 ("phase_launches", ctypes.c_int64 * 2), ("phase_ms", ctypes.c_double * 2),
-                ("apply_variant", ctypes.c_int32 * 2), ("tune_us", (ctypes.c_float * 4) * 3),
+                ("apply_variant", ctypes.c_int32 * 2), ("tune_us", (ctypes.c_float * 5) * 3),
                 ("standalone_launches", ctypes.c_int64 * 2), ("standalone_ms", ctypes.c_double * 2),
                 ("otf_bytes", ctypes.c_int64)]
 
@@ -163,8 +164,9 @@ def visc_params(dt, boundary=SPH_BC_DUMMY, mean=SPH_MEAN_HARMONIC):
 
 
 def solve_opts(rtol=1e-6, eps_inner=1e-2, maxit=20000, max_refine=30, precision=SPH_PREC_MIXED,
-               merged_reductions=0, chunk=8, jacobi=1):
-    return sph_solve_opts(rtol, eps_inner, maxit, max_refine, precision, merged_reductions, chunk, jacobi)
+               merged_reductions=0, chunk=8, jacobi=1, apply_form=0):
+    return sph_solve_opts(rtol, eps_inner, maxit, max_refine, precision, merged_reductions, chunk, jacobi,
+                          apply_form)
 
 
 def scene_tensors(scene, device="cuda"):

@@ -99,7 +99,10 @@ __device__ __forceinline__ float4 apply_row(const OpView& op, const float4* __re
   return make_float4(vb.x, vb.y, vb.z, 0.f);
 }
 
-// the four row-loop forms, indexed 0..3 = (U, PF) in {(8,0), (4,0), (8,1), (4,1)}
-constexpr int kApplyVariants = 4;
+// the row-loop forms of the solver's apply: 0..3 = (U, PF) in {(8,0), (4,0),
+// (8,1), (4,1)} above, 4 = the coefficient stream staged through shared memory
+// by bulk copies (solver.cu); the batched solver uses forms 0..3
+constexpr int kApplyVariants = 5;
+constexpr int kApplyVariantsRegister = 4;
 
 }  // namespace sph

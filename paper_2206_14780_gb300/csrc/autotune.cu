@@ -1,8 +1,9 @@
 // Autotuner of the operator apply: for each apply phase of the BiCGSTAB
-// iteration (A p with the delta dot; A r* with the omega dots) it times the four
-// row-loop forms of apply.cuh -- (U, PF) = (8, plain), (4, plain), (8, prefetch),
-// (4, prefetch), each at its own full-occupancy grid -- on the handle's operator,
-// and keeps the fastest.  The compiler schedules the unrolled gathers differently
+// iteration (A p with the delta dot; A r* with the omega dots) it times the five
+// row-loop forms -- the register forms of apply.cuh, (U, PF) = (8, plain),
+// (4, plain), (8, prefetch), (4, prefetch), and the form with the coefficient
+// stream staged in shared memory by bulk copies (solver.cu), each at its own
+// full-occupancy grid -- on the handle's operator, and keeps the fastest.  The compiler schedules the unrolled gathers differently
 // in each kernel (the dot accumulators change the register budget), so the best
 // form differs per phase and is found by measurement, once per handle (again if
 // the particle count changes by more than half).
@@ -68,6 +69,13 @@ sph_status autotune_apply(sph_neighbors* H, bool merged, unsigned int* counter, 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (status != SPH_OK) return status;
+  int32_t fault = 0;
+  SPH_TRY_CUDA(cudaMemcpyAsync(&fault, &H->scal_tune.p->fault, sizeof(fault), cudaMemcpyDeviceToHost, st));
+  SPH_TRY_CUDA(cudaStreamSynchronize(st));
+  if (fault) {
+    set_error("apply autotuner: a staged apply gave up waiting for its coefficients");
+    return SPH_ERR_TIMEOUT;
+  }
   H->tuned = true;
   H->tuned_n_pad = H->n_pad;
   return SPH_OK;

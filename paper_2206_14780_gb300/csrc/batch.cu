@@ -26,6 +26,7 @@
 #include "bicgstab_scalars.cuh"
 #include "dfloat.cuh"
 #include "reduce.cuh"
+#include "residual_row.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -183,21 +184,10 @@ __global__ void __launch_bounds__(kBlock) kb_residual(BatchView B) {
       const OpView& op = d.op;
       const float4* xh = B.V.xh + d.row_off;
       const float4* xl = B.V.xl + d.row_off;
-      const int c = op.cnt[s];
       const uint8_t k = op.kind[s];
       const float kap = (k == KIND_FLUID) ? 1.f : 0.f;
-      const float4 bh = xh[s], bl = xl[s];
       DFAcc a0, a1, a2;
-      const int64_t base = op.off[sl] + lane;
-      for (int j = 0; j < c; ++j) {
-        const int64_t e = base + (int64_t)j * kSlice;
-        const int2 ih = op.ih[e];
-        const float ahi = __int_as_float(ih.y), alo = d.op_lo[e];
-        const float4 ah = xh[ih.x], al = xl[ih.x];
-        a0.add(ahi, alo, kap * bh.x, ah.x, kap * bl.x, al.x);
-        a1.add(ahi, alo, kap * bh.y, ah.y, kap * bl.y, al.y);
-        a2.add(ahi, alo, kap * bh.z, ah.z, kap * bl.z, al.z);
-      }
+      residual_row_df(op, d.op_lo, xh, xl, sl, lane, kap, xh[s], xl[s], a0, a1, a2);
       const double sg = (k == KIND_FLUID) ? 1.0 : (k == KIND_SHEPARD ? -1.0 : 0.0);
       const int64_t g = d.row_off + s;
       double r[3] = {0.0, 0.0, 0.0};

@@ -10,14 +10,16 @@
 // The fluid rows use the difference form: its float32 rounding stays relative
 // to the result even when dt sum c is in the thousands.
 //
-// Coefficients are evaluated once per (dt, boundary, mean, mu) in float64 and
-// kept as a float32 pair a = hi + lo: the float32 apply reads hi only, the
-// float64 residual reads hi + lo (relative error 2^-48).
+// Coefficients are evaluated once per (dt, boundary, mean, mu) in double-float
+// arithmetic (dfloat.cuh; float64 only for per-row constants) and kept as a
+// float32 pair a = hi + lo: the float32 apply reads hi only, the float64-accurate
+// residual reads hi + lo (relative error a few 2^-45).
 #include <cmath>
 
 #include "apply.cuh"
 #include "dfloat.cuh"
 #include "reduce.cuh"
+#include "residual_row.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -32,50 +34,53 @@ struct OpGeom {
   double inv_h;
 };
 
-// float64 sqrt and reciprocal from a float32 seed plus one Newton step: relative
-// error ~1e-14 at a handful of float64 operations (float64 runs at a small
-// fraction of the float32 rate on this GPU; an IEEE sqrt or divide costs ~10x).
-__device__ __forceinline__ double sqrt_newton(double x) {
-  const float sf = sqrtf((float)x);
-  if (sf == 0.f) return 0.0;
-  const double s0 = (double)sf;
-  return fma(fma(-s0, s0, x), (double)(0.5f / sf), s0);
-}
-__device__ __forceinline__ double rcp_newton(double x) {
-  const double y0 = (double)__frcp_rn((float)x);
-  return y0 * fma(-x, y0, 2.0);
+// per particle: V = m / rho and 1 / mu, evaluated in float64 once per particle
+// and kept as double-float pairs (V hi, V lo, 1/mu hi, 1/mu lo)
+__global__ void k_op_aux(const float4* __restrict__ pos, const float* __restrict__ rho, const float* __restrict__ mu,
+                         int64_t n_pad, float4* __restrict__ aux) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    const dfl V = df_from_double((double)pos[s].w / (double)rho[s]);
+    const dfl im = df_from_double(1.0 / (double)mu[s]);
+    aux[s] = make_float4(V.hi, V.lo, im.hi, im.lo);
+  }
 }
 
-// |r_a - r_b| for the coefficients (the neighbour predicate itself is decided
-// elsewhere, bit for bit; here ~1e-14 relative is enough)
-__device__ __forceinline__ double pair_r_fast(float4 pa, float4 pb, const OpGeom& g) {
-  double d[3] = {(double)pa.x - (double)pb.x, (double)pa.y - (double)pb.y, (double)pa.z - (double)pb.z};
+// Geometry of the double-float set-up: periods as (hi, lo), 1/h as (hi, lo)
+struct OpGeomDF {
+  dfl L[3];
+  float invL[3];
+  int periodic[3];
+  dfl inv_h;
+};
+
+// |r_a - r_b| in double-float: the coordinate differences of the float32
+// positions exactly (TwoSum), the minimum image by a whole period, the squared
+// norm with exact products, one Newton step on the root
+__device__ __forceinline__ dfl pair_r_df(float4 pa, float4 pb, const OpGeomDF& g) {
+  dfl d[3] = {df_exact_sum(pa.x, -pb.x), df_exact_sum(pa.y, -pb.y), df_exact_sum(pa.z, -pb.z)};
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    if (g.periodic[ax]) d[ax] = fma(-g.L[ax], rint(d[ax] * g.invL[ax]), d[ax]);
+    if (g.periodic[ax]) {
+      const float k = rintf(d[ax].hi * g.invL[ax]);
+      if (k != 0.f) d[ax] = df_add(d[ax], dfl{-k * g.L[ax].hi, -k * g.L[ax].lo});
+    }
   }
-  return sqrt_newton(fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2])));
+  const dfl r2 = df_add(df_add(df_mul(d[0], d[0]), df_mul(d[1], d[1])), df_mul(d[2], d[2]));
+  return df_sqrt(r2);
 }
 
-// per particle: V = m / rho and 1 / mu in float64 (N divisions instead of one per pair)
-__global__ void k_op_aux(const float4* __restrict__ pos, const float* __restrict__ rho, const float* __restrict__ mu,
-                         int64_t n_pad, double2* __restrict__ aux) {
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x)
-    aux[s] = make_double2((double)pos[s].w / (double)rho[s], 1.0 / (double)mu[s]);
+// Wendland psi_{3,1} without its constant factor (it cancels in W / S):
+// (1 - q/2)^4 (2q + 1), zero for q >= 2
+__device__ __forceinline__ dfl wendland_w_df(dfl q) {
+  dfl t = df_add(dfl{1.f, 0.f}, dfl{-0.5f * q.hi, -0.5f * q.lo});
+  if (t.hi <= 0.f) return dfl{0.f, 0.f};
+  const dfl t2 = df_mul(t, t);
+  return df_mul(df_mul(t2, t2), df_add(dfl{1.f, 0.f}, dfl{2.f * q.hi, 2.f * q.lo}));
 }
 
-// Wendland psi_{3,1} (Sec. 5.2): w(q) = 21/(16 pi) (1 - q/2)^4 (2q + 1);
-// |f(q)| = 105/(128 pi) (2 - q)^3; both vanish for q >= 2.
-__device__ __forceinline__ double wendland_w(double q) {
-  if (q >= 2.0) return 0.0;
-  const double t = 1.0 - 0.5 * q;
-  const double t2 = t * t;
-  return (21.0 / (16.0 * M_PI)) * (t2 * t2) * (2.0 * q + 1.0);
-}
-__global__ void k_op_count(const float4* __restrict__ pos, const uint8_t* __restrict__ type,
-                           const int32_t* __restrict__ cnt, const int64_t* __restrict__ slice_off,
-                           const int32_t* __restrict__ nbr, int64_t n, int64_t n_pad, OpGeom g, int boundary,
-                           int32_t* __restrict__ op_cnt, uint8_t* __restrict__ kind) {
+__global__ void k_op_count(const uint8_t* __restrict__ type, const int32_t* __restrict__ cnt,
+                           const int64_t* __restrict__ slice_off, const int32_t* __restrict__ nbr, int64_t n,
+                           int64_t n_pad, int boundary, int32_t* __restrict__ op_cnt, uint8_t* __restrict__ kind) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
     if (s >= n) {
       op_cnt[s] = 0;
@@ -93,35 +98,39 @@ __global__ void k_op_count(const float4* __restrict__ pos, const uint8_t* __rest
       kind[s] = KIND_IDENTITY;
       continue;
     }
-    const float4 pb = pos[s];
+    // every neighbour lies strictly inside 2h, so each fluid neighbour has
+    // W > 0 and the Shepard sum is positive exactly when there is one (a sum
+    // that still rounds to zero is handled by k_op_fill as an identity row)
     const int64_t base = slice_off[s / kSlice] + (s % kSlice);
-    double S = 0.0;
     int nf = 0;
-    for (int j = 0; j < c; ++j) {
-      const int32_t t = nbr[base + (int64_t)j * kSlice];
-      if (type[t] != SPH_FLUID) continue;
-      S += wendland_w(pair_r_fast(pos[t], pb, g) * g.inv_h);
-      ++nf;
-    }
-    if (S > 0.0) {
-      op_cnt[s] = nf;
-      kind[s] = KIND_SHEPARD;
-    } else {
-      op_cnt[s] = 0;
-      kind[s] = KIND_IDENTITY;
-    }
+    for (int j = 0; j < c; ++j) nf += type[nbr[base + (int64_t)j * kSlice]] == SPH_FLUID ? 1 : 0;
+    op_cnt[s] = nf;
+    kind[s] = nf > 0 ? KIND_SHEPARD : KIND_IDENTITY;
   }
 }
 
+// Coefficients of A(dt) (Eq. kab with |F|, Eqs. diag, offdiag and dummyvel) in
+// double-float arithmetic (relative error a few 2^-45), stored as the float32
+// pair (hi, lo) that the float32 apply and the double-float residual read;
+// float64 is used once per row (R_b, D) only.
+//   fluid row b:  a_ba = dt c_ab = R_b V_a mubar (2 - q)^3,
+//                 R_b = 2 dt (105 / (128 pi)) / (h^5 rho_b), D_b = 1 + sum a
+//   dummy wall:   a_ba = W_ba / S_b over fluid neighbours
 __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restrict__ rho, const float* __restrict__ mu,
-                          const uint8_t* __restrict__ type, const double2* __restrict__ aux,
+                          const uint8_t* __restrict__ type, const float4* __restrict__ aux,
                           const int32_t* __restrict__ cnt, const int64_t* __restrict__ slice_off,
                           const int32_t* __restrict__ nbr, const uint8_t* __restrict__ kind,
-                          const int64_t* __restrict__ op_off, int64_t n, int64_t n_pad, OpGeom g, double dt, int mean,
+                          const int64_t* __restrict__ op_off, int64_t n, int64_t n_pad, OpGeom g64, double dt, int mean,
                           int2* __restrict__ op_ih, float* __restrict__ op_lo, float* __restrict__ invD,
                           double* __restrict__ D64) {
-  // a_ba = dt c_ab = [2 dt (105/(128 pi)) / (h^5 rho_b)] * V_a * mubar * (2 - q)^3
-  const double inv_h5 = g.inv_h * g.inv_h * g.inv_h * g.inv_h * g.inv_h;
+  OpGeomDF g;
+  for (int ax = 0; ax < 3; ++ax) {
+    g.L[ax] = df_from_double(g64.L[ax]);
+    g.invL[ax] = (float)g64.invL[ax];
+    g.periodic[ax] = g64.periodic[ax];
+  }
+  g.inv_h = df_from_double(g64.inv_h);
+  const double inv_h5 = g64.inv_h * g64.inv_h * g64.inv_h * g64.inv_h * g64.inv_h;
   const double kf = 2.0 * dt * (105.0 / (128.0 * M_PI)) * inv_h5;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
     if (s >= n || kind[s] == KIND_IDENTITY) {
@@ -135,47 +144,57 @@ __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restric
     const int64_t obase = op_off[s / kSlice] + (s % kSlice);
     int o = 0;
     if (kind[s] == KIND_FLUID) {
-      const double mub_self = (double)mu[s];
-      const double imu_self = aux[s].y;
-      const double Rb = kf / (double)rho[s];
-      double sum = 0.0;
+      const float mu_b = mu[s];
+      const float4 ab = aux[s];
+      const dfl imu_b{ab.z, ab.w};
+      const dfl Rb = df_from_double(kf / (double)rho[s]);
+      dfl sum{0.f, 0.f};
       for (int j = 0; j < c; ++j) {
         const int32_t t = nbr[base + (int64_t)j * kSlice];
         const float4 pa = pos[t];
-        const double2 at = aux[t];
-        const double tq = fmax(2.0 - pair_r_fast(pa, pb, g) * g.inv_h, 0.0);
-        double mub = mub_self;
-        if (type[t] == SPH_FLUID)
-          mub = (mean == SPH_MEAN_ARITHMETIC) ? 0.5 * ((double)mu[t] + mub_self) : 2.0 * rcp_newton(at.y + imu_self);
-        const double a = Rb * at.x * mub * (tq * tq * tq);
-        const float hi = __double2float_rn(a);
-        const float lo = __double2float_rn(a - (double)hi);
+        const float4 at = aux[t];
+        const dfl q = df_mul(pair_r_df(pa, pb, g), g.inv_h);
+        dfl tq = df_add(dfl{2.f, 0.f}, df_neg(q));
+        if (tq.hi <= 0.f) tq = dfl{0.f, 0.f};
+        const dfl tq3 = df_mul(df_mul(tq, tq), tq);
+        dfl mub{mu_b, 0.f};
+        if (type[t] == SPH_FLUID) {
+          if (mean == SPH_MEAN_ARITHMETIC) {
+            const dfl m2 = df_exact_sum(mu[t], mu_b);
+            mub = dfl{0.5f * m2.hi, 0.5f * m2.lo};
+          } else {
+            const dfl h = df_rcp(df_add(dfl{at.z, at.w}, imu_b));
+            mub = dfl{2.f * h.hi, 2.f * h.lo};
+          }
+        }
+        const dfl a = df_mul(df_mul(Rb, dfl{at.x, at.y}), df_mul(mub, tq3));
         const int64_t e = obase + (int64_t)o * kSlice;
-        op_ih[e] = make_int2(t, __float_as_int(hi));
-        op_lo[e] = lo;
-        sum += a;
+        op_ih[e] = make_int2(t, __float_as_int(a.hi));
+        op_lo[e] = a.lo;
+        sum = df_add(sum, a);
         ++o;
       }
-      const double D = 1.0 + sum;
+      const double D = 1.0 + df_to_double(sum);
       D64[s] = D;
       invD[s] = __double2float_rn(1.0 / D);
-    } else {  // Shepard wall row: W_ba / S_b over fluid neighbours (the 1/h^3 cancels)
-      double S = 0.0;
+    } else {  // Shepard wall row: W_ba / S_b over fluid neighbours
+      dfl S{0.f, 0.f};
       for (int j = 0; j < c; ++j) {
         const int32_t t = nbr[base + (int64_t)j * kSlice];
         if (type[t] != SPH_FLUID) continue;
-        S += wendland_w(pair_r_fast(pos[t], pb, g) * g.inv_h);
+        S = df_add(S, wendland_w_df(df_mul(pair_r_df(pos[t], pb, g), g.inv_h)));
       }
-      const double invS = 1.0 / S;
+      // S rounds to zero only if every fluid neighbour sits at q = 2 to within
+      // rounding: zero coefficients then make the row an identity row (as an
+      // empty Shepard sum does)
+      const dfl invS = S.hi > 0.f ? df_rcp(S) : dfl{0.f, 0.f};
       for (int j = 0; j < c; ++j) {
         const int32_t t = nbr[base + (int64_t)j * kSlice];
         if (type[t] != SPH_FLUID) continue;
-        const double a = wendland_w(pair_r_fast(pos[t], pb, g) * g.inv_h) * invS;
-        const float hi = __double2float_rn(a);
-        const float lo = __double2float_rn(a - (double)hi);
+        const dfl a = df_mul(wendland_w_df(df_mul(pair_r_df(pos[t], pb, g), g.inv_h)), invS);
         const int64_t e = obase + (int64_t)o * kSlice;
-        op_ih[e] = make_int2(t, __float_as_int(hi));
-        op_lo[e] = lo;
+        op_ih[e] = make_int2(t, __float_as_int(a.hi));
+        op_lo[e] = a.lo;
         ++o;
       }
       invD[s] = 1.f;
@@ -237,23 +256,10 @@ __global__ void __launch_bounds__(kBlock) k_residual_df(OpView op, const float* 
   double acc2[3] = {0.0, 0.0, 0.0};
   for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
     const int64_t s = sl * kSlice + lane;
-    const int c = op.cnt[s];
     const uint8_t k = op.kind[s];
     const float kap = (k == KIND_FLUID) ? 1.f : 0.f;
-    const float4 bh = xh[s], bl = xl[s];
-    const float kbh0 = kap * bh.x, kbh1 = kap * bh.y, kbh2 = kap * bh.z;
-    const float kbl0 = kap * bl.x, kbl1 = kap * bl.y, kbl2 = kap * bl.z;
     DFAcc a0, a1, a2;
-    const int64_t base = op.off[sl] + lane;
-    for (int j = 0; j < c; ++j) {
-      const int64_t e = base + (int64_t)j * kSlice;
-      const int2 ih = op.ih[e];
-      const float ahi = __int_as_float(ih.y), alo = op_lo[e];
-      const float4 ah = xh[ih.x], al = xl[ih.x];
-      a0.add(ahi, alo, kbh0, ah.x, kbl0, al.x);
-      a1.add(ahi, alo, kbh1, ah.y, kbl1, al.y);
-      a2.add(ahi, alo, kbh2, ah.z, kbl2, al.z);
-    }
+    residual_row_df(op, op_lo, xh, xl, sl, lane, kap, xh[s], xl[s], a0, a1, a2);
     const double sg = (k == KIND_FLUID) ? 1.0 : (k == KIND_SHEPARD ? -1.0 : 0.0);
     double r0 = 0.0, r1 = 0.0, r2 = 0.0;
     if (s < n) {
@@ -302,8 +308,8 @@ sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStrea
   SPH_TRY(H->invD.alloc(H->n_pad));
   SPH_TRY(H->D64.alloc(H->n_pad));
   const int grid = grid_for(H, H->n_pad);
-  SPH_LAUNCH(k_op_count, grid, kBlock, 0, st)(H->pos_s.p, H->type_s.p, H->cnt.p, H->slice_off.p, H->nbr.p, H->n, H->n_pad, g,
-                                      P->boundary, H->op_cnt.p, H->op_kind.p);
+  SPH_LAUNCH(k_op_count, grid, kBlock, 0, st)(H->type_s.p, H->cnt.p, H->slice_off.p, H->nbr.p, H->n, H->n_pad,
+                                              P->boundary, H->op_cnt.p, H->op_kind.p);
   SPH_TRY_CUDA(cudaGetLastError());
   int64_t total_pad = 0, total = 0;
   int32_t maxc = 0;
@@ -312,9 +318,9 @@ sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStrea
   SPH_TRY(H->op_lo.alloc(total_pad > 0 ? total_pad : 1));
   H->op_nnz_pad = total_pad;
   H->op_nnz = total;
-  SPH_TRY(H->aux64.alloc(H->n_pad));
-  SPH_LAUNCH(k_op_aux, grid, kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->n_pad, H->aux64.p);
-  SPH_LAUNCH(k_op_fill, grid, kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->type_s.p, H->aux64.p, H->cnt.p,
+  SPH_TRY(H->aux_df.alloc(H->n_pad));
+  SPH_LAUNCH(k_op_aux, grid, kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->n_pad, H->aux_df.p);
+  SPH_LAUNCH(k_op_fill, grid, kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->type_s.p, H->aux_df.p, H->cnt.p,
                                              H->slice_off.p,
                                      H->nbr.p, H->op_kind.p, H->op_off.p, H->n, H->n_pad, g, P->dt, P->mean,
                                      H->op_ih.p, H->op_lo.p, H->invD.p, H->D64.p);

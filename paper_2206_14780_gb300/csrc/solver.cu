@@ -28,6 +28,7 @@
 #include <cstring>
 
 #include "apply.cuh"
+#include "bulk.cuh"
 #include "bicgstab_scalars.cuh"
 #include "reduce.cuh"
 #include "sph_internal.cuh"
@@ -105,47 +106,45 @@ __global__ void __launch_bounds__(kBlock) k_p_update(int64_t n_pad, Vecs V, cons
 //   PH_DELTA:        v = p,  y = Ap; dots r0^.Ap                       (K = 3)
 //   PH_OMEGA:        v = r*, y = Ar*; dots r*.Ar*, Ar*.Ar*             (K = 6)
 //   PH_OMEGA_MERGED: + r0^.r*, r0^.Ar*, r*.r*                          (K = 15)
-template <int PH, int U, bool PF>
-__global__ void __launch_bounds__(kBlock, 4) k_apply_dot(OpView op, const float4* __restrict__ v, float4* __restrict__ y,
-                                                      const float4* __restrict__ rh, SolverScalars* S,
-                                                      double* partials, unsigned int* counter) {
-  constexpr int K = PH == PH_DELTA ? 3 : (PH == PH_OMEGA ? 6 : 15);
-  if (S->done) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  float acc[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = 0.f;
-  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
-    const int64_t s = sl * kSlice + lane;
-    float4 vb;
-    const float4 o = apply_row<U, PF, true>(op, v, sl, lane, vb);
-    y[s] = o;
+template <int PH>
+struct PhaseDots {
+  static constexpr int K = PH == PH_DELTA ? 3 : (PH == PH_OMEGA ? 6 : 15);
+};
+
+template <int PH>
+__device__ __forceinline__ void dots_row(float* acc, float4 o, float4 vb, const float4* __restrict__ rh, int64_t s) {
+  if (PH == PH_DELTA) {
     const float4 h = rh[s];
-    if (PH == PH_DELTA) {
-      acc[0] = fmaf(h.x, o.x, acc[0]);
-      acc[1] = fmaf(h.y, o.y, acc[1]);
-      acc[2] = fmaf(h.z, o.z, acc[2]);
-    } else {
-      acc[0] = fmaf(vb.x, o.x, acc[0]);
-      acc[1] = fmaf(vb.y, o.y, acc[1]);
-      acc[2] = fmaf(vb.z, o.z, acc[2]);
-      acc[3] = fmaf(o.x, o.x, acc[3]);
-      acc[4] = fmaf(o.y, o.y, acc[4]);
-      acc[5] = fmaf(o.z, o.z, acc[5]);
-      if (PH == PH_OMEGA_MERGED) {
-        acc[6] = fmaf(h.x, vb.x, acc[6]);
-        acc[7] = fmaf(h.y, vb.y, acc[7]);
-        acc[8] = fmaf(h.z, vb.z, acc[8]);
-        acc[9] = fmaf(h.x, o.x, acc[9]);
-        acc[10] = fmaf(h.y, o.y, acc[10]);
-        acc[11] = fmaf(h.z, o.z, acc[11]);
-        acc[12] = fmaf(vb.x, vb.x, acc[12]);
-        acc[13] = fmaf(vb.y, vb.y, acc[13]);
-        acc[14] = fmaf(vb.z, vb.z, acc[14]);
-      }
+    acc[0] = fmaf(h.x, o.x, acc[0]);
+    acc[1] = fmaf(h.y, o.y, acc[1]);
+    acc[2] = fmaf(h.z, o.z, acc[2]);
+  } else {
+    acc[0] = fmaf(vb.x, o.x, acc[0]);
+    acc[1] = fmaf(vb.y, o.y, acc[1]);
+    acc[2] = fmaf(vb.z, o.z, acc[2]);
+    acc[3] = fmaf(o.x, o.x, acc[3]);
+    acc[4] = fmaf(o.y, o.y, acc[4]);
+    acc[5] = fmaf(o.z, o.z, acc[5]);
+    if (PH == PH_OMEGA_MERGED) {
+      const float4 h = rh[s];
+      acc[6] = fmaf(h.x, vb.x, acc[6]);
+      acc[7] = fmaf(h.y, vb.y, acc[7]);
+      acc[8] = fmaf(h.z, vb.z, acc[8]);
+      acc[9] = fmaf(h.x, o.x, acc[9]);
+      acc[10] = fmaf(h.y, o.y, acc[10]);
+      acc[11] = fmaf(h.z, o.z, acc[11]);
+      acc[12] = fmaf(vb.x, vb.x, acc[12]);
+      acc[13] = fmaf(vb.y, vb.y, acc[13]);
+      acc[14] = fmaf(vb.z, vb.z, acc[14]);
     }
   }
+}
+
+// block partials, then the last block sums them and updates the scalars
+template <int PH>
+__device__ __forceinline__ void dots_finish(const float (&acc)[PhaseDots<PH>::K], SolverScalars* S,
+                                            double* partials, unsigned int* counter) {
+  constexpr int K = PhaseDots<PH>::K;
   block_partials<K>(acc, partials + (size_t)blockIdx.x * kMaxDots);
   if (arrive_last(counter)) {
     __shared__ double res[K];
@@ -169,17 +168,169 @@ __global__ void __launch_bounds__(kBlock, 4) k_apply_dot(OpView op, const float4
   }
 }
 
+template <int PH, int U, bool PF>
+__global__ void __launch_bounds__(kBlock, 4) k_apply_dot(OpView op, const float4* __restrict__ v, float4* __restrict__ y,
+                                                      const float4* __restrict__ rh, SolverScalars* S,
+                                                      double* partials, unsigned int* counter) {
+  constexpr int K = PhaseDots<PH>::K;
+  if (S->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.f;
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
+    const int64_t s = sl * kSlice + lane;
+    float4 vb;
+    const float4 o = apply_row<U, PF, true>(op, v, sl, lane, vb);
+    y[s] = o;
+    dots_row<PH>(acc, o, vb, rh, s);
+  }
+  dots_finish<PH>(acc, S, partials, counter);
+}
+
+// Row-loop form 4: the coefficient stream staged through shared memory.  Each
+// warp owns kStageBuf buffers of kStageCh entries x 32 rows (2 KB) and an
+// mbarrier per buffer; lane 0 fills them with bulk asynchronous copies
+// (cp.async.bulk, bulk.cuh), running ahead over the warp's slices in order, so
+// the stream's bytes in flight cost no registers and each warp keeps up to
+// kStageBuf x 2 KB of it in flight.  The lanes read their entry of each staged
+// row from shared memory (conflict-free: 32 consecutive int2) and gather the
+// neighbour vectors kStageU at a time, as the register forms do.  Every issued
+// copy is consumed before the warp leaves its loop.  A wait that does not
+// complete within ~2 s of SM clock sets S->fault, stops the warp issuing,
+// waits (bounded) for its copies still in flight and lets the kernel finish;
+// the host then reports SPH_ERR_TIMEOUT.
+constexpr int kStageCh = 8;
+constexpr int kStageBuf = 2;
+constexpr int kStageU = 4;
+constexpr long long kStageWaitCycles = 4000000000ll;
+
+template <int PH>
+__global__ void __launch_bounds__(kBlock, 4) k_apply_dot_staged(OpView op, const float4* __restrict__ v,
+                                                             float4* __restrict__ y, const float4* __restrict__ rh,
+                                                             SolverScalars* S, double* partials,
+                                                             unsigned int* counter) {
+  constexpr int K = PhaseDots<PH>::K;
+  constexpr int kWarps = kBlock / 32;
+  __shared__ __align__(128) int2 sbuf[kWarps][kStageBuf][kStageCh * kSlice];
+  __shared__ __align__(8) uint64_t sbar[kWarps][kStageBuf];
+  if (S->done) return;
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  if (lane == 0) {
+    for (int b = 0; b < kStageBuf; ++b) mbar_init(&sbar[wid][b], 1);
+    fence_mbarrier_init();
+  }
+  __syncwarp();
+
+  // producer cursor: next chunk (slice psl, chunk pch of pnch) to copy
+  int64_t psl = gw;
+  int pch = 0;
+  int pnch = psl < op.nslices ? (int)(((op.off[psl + 1] - op.off[psl]) / kSlice + kStageCh - 1) / kStageCh) : 0;
+  uint32_t inflight = 0;   // bit b: buffer b has a copy not yet waited for
+  bool stop = false;       // set on a fault: issue nothing more
+  auto produce = [&](int b) {
+    while (psl < op.nslices && pch >= pnch) {
+      psl += nw;
+      pch = 0;
+      pnch = psl < op.nslices ? (int)(((op.off[psl + 1] - op.off[psl]) / kSlice + kStageCh - 1) / kStageCh) : 0;
+    }
+    if (stop || psl >= op.nslices) return;
+    if (lane == 0) {
+      const int w = (int)((op.off[psl + 1] - op.off[psl]) / kSlice);
+      const int ne = min(kStageCh, w - pch * kStageCh);
+      const uint32_t bytes = (uint32_t)ne * kSlice * (uint32_t)sizeof(int2);
+      fence_proxy_async();
+      mbar_expect_tx(&sbar[wid][b], bytes);
+      bulk_g2s(&sbuf[wid][b][0], op.ih + op.off[psl] + (int64_t)pch * kStageCh * kSlice, bytes, &sbar[wid][b]);
+    }
+    inflight |= 1u << b;
+    ++pch;
+  };
+  uint32_t par = 0;        // bit b: parity of the next phase to complete on buffer b
+  for (int b = 0; b < kStageBuf; ++b) produce(b);
+
+  float acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.f;
+  int cb = 0;
+  for (int64_t sl = gw; sl < op.nslices && !stop; sl += nw) {
+    const int64_t s = sl * kSlice + lane;
+    const int c = op.cnt[s];
+    const uint8_t kd = op.kind[s];
+    const float4 vb = v[s];
+    const float kap = (kd == KIND_FLUID) ? 1.f : 0.f;
+    const int w = (int)((op.off[sl + 1] - op.off[sl]) / kSlice);
+    const int nch = (w + kStageCh - 1) / kStageCh;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    for (int ch = 0; ch < nch; ++ch) {
+      const bool ok = mbar_wait(&sbar[wid][cb], (par >> cb) & 1u, kStageWaitCycles);
+      if (__any_sync(0xffffffffu, !ok)) {
+        stop = true;
+        if (lane == 0) atomicExch(&S->fault, 1);
+        break;
+      }
+      par ^= 1u << cb;
+      inflight &= ~(1u << cb);
+      const int2* __restrict__ eb = &sbuf[wid][cb][0];
+#pragma unroll
+      for (int j0 = 0; j0 < kStageCh; j0 += kStageU) {
+        int2 e[kStageU];
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) {
+          const int j = ch * kStageCh + j0 + u;
+          e[u] = (j < c) ? eb[(j0 + u) * kSlice + lane] : make_int2((int)s, 0);
+        }
+        float4 va[kStageU];
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) va[u] = __ldg(v + e[u].x);
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) {
+          const float a = __int_as_float(e[u].y);
+          ax = fmaf(a, fmaf(kap, vb.x, -va[u].x), ax);
+          ay = fmaf(a, fmaf(kap, vb.y, -va[u].y), ay);
+          az = fmaf(a, fmaf(kap, vb.z, -va[u].z), az);
+        }
+      }
+      __syncwarp();
+      produce(cb);
+      cb = cb + 1 == kStageBuf ? 0 : cb + 1;
+    }
+    if (stop) break;
+    float4 o;
+    if (kd == KIND_FLUID) {
+      const float sc = op.invD[s];
+      o = make_float4((vb.x + ax) * sc, (vb.y + ay) * sc, (vb.z + az) * sc, 0.f);
+    } else if (kd == KIND_SHEPARD) {
+      o = make_float4(vb.x - ax, vb.y - ay, vb.z - az, 0.f);
+    } else {
+      o = make_float4(vb.x, vb.y, vb.z, 0.f);
+    }
+    y[s] = o;
+    dots_row<PH>(acc, o, vb, rh, s);
+  }
+  // after a fault: wait (bounded) for the copies this warp still has in flight
+  for (int b = 0; b < kStageBuf; ++b)
+    if (inflight & (1u << b)) mbar_wait(&sbar[wid][b], (par >> b) & 1u, kStageWaitCycles);
+  dots_finish<PH>(acc, S, partials, counter);
+}
+
 }  // namespace
 
 // [phase][variant] with variants (U, PF) = (8,0), (4,0), (8,1), (4,1) as in apply.cuh
+// and 4 = the stream staged through shared memory by bulk copies
 ApplyDotFn apply_kernel(int phase, int variant) {
   static const ApplyDotFn table[3][kApplyVariants] = {
       {k_apply_dot<PH_DELTA, 8, false>, k_apply_dot<PH_DELTA, 4, false>, k_apply_dot<PH_DELTA, 8, true>,
-       k_apply_dot<PH_DELTA, 4, true>},
+       k_apply_dot<PH_DELTA, 4, true>, k_apply_dot_staged<PH_DELTA>},
       {k_apply_dot<PH_OMEGA, 8, false>, k_apply_dot<PH_OMEGA, 4, false>, k_apply_dot<PH_OMEGA, 8, true>,
-       k_apply_dot<PH_OMEGA, 4, true>},
+       k_apply_dot<PH_OMEGA, 4, true>, k_apply_dot_staged<PH_OMEGA>},
       {k_apply_dot<PH_OMEGA_MERGED, 8, false>, k_apply_dot<PH_OMEGA_MERGED, 4, false>,
-       k_apply_dot<PH_OMEGA_MERGED, 8, true>, k_apply_dot<PH_OMEGA_MERGED, 4, true>}};
+       k_apply_dot<PH_OMEGA_MERGED, 8, true>, k_apply_dot<PH_OMEGA_MERGED, 4, true>,
+       k_apply_dot_staged<PH_OMEGA_MERGED>}};
   return table[phase < 0 ? 0 : (phase > 2 ? 2 : phase)][variant < 0 || variant >= kApplyVariants ? 0 : variant];
 }
 
@@ -368,8 +519,10 @@ static sph_status true_residual(sph_neighbors* H, cudaStream_t st, double rr[3])
 template <int PH>
 static void launch_apply_dot(sph_neighbors* H, int grid, const OpView& op, const float4* v, float4* y,
                              const float4* rh, SolverScalars* S, unsigned int* counter, cudaStream_t st) {
-  const int var = H->apply_var[PH];
-  const int g = H->apply_grid[PH] > 0 && H->apply_grid[PH] < grid ? H->apply_grid[PH] : grid;
+  const bool forced = H->force_form >= 0;
+  const int var = forced ? H->force_form : H->apply_var[PH];
+  const int tg = forced ? H->force_grid : H->apply_grid[PH];
+  const int g = tg > 0 && tg < grid ? tg : grid;
   const ApplyDotFn kern = apply_kernel(PH, var);
   prof_begin(H, st, PH == PH_DELTA ? 0 : 1);
   SPH_LAUNCH(kern, g, kBlock, 0, st)(op, v, y, rh, S, H->partials.p, counter);
@@ -384,10 +537,23 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
   const int64_t np = H->n_pad;
   const int grid_rows = red_grid_for(H, np);
   const int grid_slices = red_grid_for(H, H->nslices * 32);
+  H->force_form = -1;
+  if (O->apply_form < 0 || O->apply_form > kApplyVariants) {
+    set_error("sph_visc_solve: apply_form %d outside 0..%d", O->apply_form, kApplyVariants);
+    return SPH_ERR_INVALID;
+  }
+  if (O->apply_form > 0) {
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)apply_kernel(PH_DELTA, O->apply_form - 1), kBlock,
+                                                  0);
+    H->force_form = O->apply_form - 1;
+    H->force_grid = H->num_sms * (occ > 0 ? occ : 1);
+  }
   Vecs V{H->v_r.p, H->v_rh.p, H->v_p.p, H->v_Ap.p, H->v_rs.p, H->v_As.p, H->v_d.p};
   const OpView op = op_view(H);
   SolverScalars* S = H->scal.p;
   unsigned int* C = H->counters.p;
+  SPH_TRY_CUDA(cudaMemsetAsync(&S->fault, 0, sizeof(int32_t), st));
 
   SPH_LAUNCH(k_gather_d3, grid_for(H, np), kBlock, 0, st)(b, H->perm.p, H->n, np, H->b64.p);
   SPH_LAUNCH(k_gather_d3, grid_for(H, np), kBlock, 0, st)(x, H->perm.p, H->n, np, H->x64.p);
@@ -452,6 +618,10 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
       SPH_TRY_CUDA(cudaStreamSynchronize(st));
       prof_flush(H, 2 * (H->host_scal->iter - iter_seen));
       iter_seen = H->host_scal->iter;
+      if (H->host_scal->fault) {
+        set_error("sph_visc_solve: an operator apply gave up waiting for its staged coefficients");
+        return SPH_ERR_TIMEOUT;
+      }
       if (H->host_scal->done) break;
       chunk = chunk < 64 ? chunk * 2 : chunk;
     }

@@ -92,6 +92,8 @@ struct SolverScalars {
   int32_t done;        // 1: no component progressing or cap reached
   int32_t nonfinite;   // a scalar went NaN/Inf
   int32_t pad;
+  int32_t fault;       // an apply kernel gave up a bounded wait (SPH_ERR_TIMEOUT)
+  int32_t pad2;
 };
 
 struct Grid {
@@ -140,7 +142,7 @@ struct sph_neighbors {
   sph::DBuf<uint8_t> op_kind;      // 0 fluid (difference form), 1 Shepard wall, 2 identity
   sph::DBuf<float> invD;           // float32 1/D (Jacobi), 1 for wall rows
   sph::DBuf<double> D64;           // float64 D
-  sph::DBuf<double2> aux64;        // per particle (m / rho, 1 / mu) in float64
+  sph::DBuf<float4> aux_df;        // per particle (m / rho, 1 / mu) as double-float pairs
   int64_t op_nnz_pad = 0;
   uint64_t op_version = 0;         // bumped whenever the operator is rebuilt
 
@@ -169,9 +171,11 @@ struct sph_neighbors {
   // apply autotuner (autotune.cu): chosen row-loop form and grid per phase
   int apply_var[3] = {0, 0, 0};
   int apply_grid[3] = {0, 0, 0};
-  float tune_us[3][4] = {};
+  float tune_us[3][5] = {};
   bool tuned = false;
   int64_t tuned_n_pad = 0;
+  int force_form = -1;               // sph_solve_opts.apply_form - 1 for the current solve
+  int force_grid = 0;
   sph::DBuf<sph::SolverScalars> scal_tune;
 
   // instrumentation (sph_profile_*)

@@ -29,6 +29,49 @@ def test_solution_matches_oracle(name, merged):
     assert rel_l2(x, x_ref) <= RTOL_SOL
 
 
+@pytest.mark.parametrize("form", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("name", ["couette_dummy", "random_box_mu_mass", "lava_box_12"])
+def test_every_apply_form_solves(name, form):
+    """Each row-loop form of the solver's apply (the four register forms and the form
+    with the coefficient stream staged through shared memory by bulk copies), forced
+    instead of autotuned, reaches the true residual and the oracle's solution."""
+    from paper_2206_14780_gb300 import binding
+
+    s = SCENES_SMALL[name]()
+    nb, _ = lib_build(s)
+    off, idx, A = oracle_system(s)
+    x_ref = osv.reference_solution(A, s.b, s.x0)
+    x, rep = gpu_solve(nb, s, binding.solve_opts(apply_form=form))
+    assert rep["status"] == 0, rep
+    res, _ = oop.true_residual(A, x, s.b)
+    assert res <= RTOL_RES, (res, rep)
+    assert rel_l2(x, x_ref) <= RTOL_SOL
+
+
+def test_staged_form_on_a_stiff_box_with_many_slices():
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.lava_box(6, n=24)
+    nb, _ = lib_build(s)
+    off, idx, A = oracle_system(s)
+    x_ref = osv.reference_solution(A, s.b, s.x0)
+    x_auto, rep_a = gpu_solve(nb, s)
+    x, rep = gpu_solve(nb, s, binding.solve_opts(apply_form=5))
+    assert rep["status"] == 0 and rep_a["status"] == 0, (rep, rep_a)
+    res, _ = oop.true_residual(A, x, s.b)
+    assert res <= RTOL_RES
+    assert rel_l2(x, x_ref) <= RTOL_SOL
+
+
+def test_apply_form_out_of_range_is_rejected():
+    from paper_2206_14780_gb300 import binding
+
+    s = SCENES_SMALL["couette_dummy"]()
+    nb, _ = lib_build(s)
+    with pytest.raises(binding.SphError):
+        gpu_solve(nb, s, binding.solve_opts(apply_form=6))
+
+
 def test_stiff_box_several_tiles():
     # c2-like stiffness (nu = 10, dt = 5e-4: dt sum c ~ 670) on a 20^3 box
     s = scenes.lava_box(5, n=20)
