@@ -382,6 +382,7 @@ def run_sphvisc(args):
     if not args.no_learned and world == 1:
         torch.cuda.empty_cache()
         learned = run_learned(args.weights, dev)
+        learned["mlp_forward"] = run_mlp_forward(dev)
     its = [r["iters"] for r in reps]
     out = dict(metric=METRIC, value=whole_job_ms_per_solve(ms_max, args.steps, world), unit=UNIT, n_gpus=world, steps=args.steps,
                warmup=max(3, args.warmup), ms_per_step=ms_max / args.steps, higher_is_better=False,
@@ -406,6 +407,43 @@ def run_sphvisc(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------- network forward ----
+
+def run_mlp_forward(dev, m=1157308, reps=20):
+    """The warm-start network's inference forward (tcgen05 kernel) on m particles of
+    random bf16 features: device time per call, FLOP/s against the measured bf16 peak."""
+    import numpy as np
+    import torch
+
+    from paper_2206_14780_gb300 import binding
+
+    theta = np.random.default_rng(0).normal(scale=0.2, size=binding.MLP_NPARAMS).astype(np.float32)
+    net = binding.Mlp(theta)
+    feats = torch.randn((m, 16), device=dev).to(torch.bfloat16).view(torch.int16).contiguous()
+    out = torch.empty((m, 4), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        net.forward(feats, out)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        net.forward(feats, out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    us = 1e3 * e0.elapsed_time(e1) / reps
+    flop = 2.0 * (16 * 64 + 64 * 64 + 64 * 64 + 64 * 3) * m        # algorithmic (N = 3 in the last layer)
+    peak = None
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        pass
+    tflops = flop / (us * 1e-6) / 1e12
+    return dict(particles=m, us_per_forward=us, tflops=tflops, peak_tflops=peak,
+                frac=(tflops / peak) if peak else None, bytes=48 * m, gbs=48 * m / (us * 1e-6) / 1e9,
+                kernel="k_mlp_forward_tc (tcgen05.mma kind::f16, TMEM accumulators)")
 
 
 # ----------------------------------------------------------- apply forms ------
@@ -782,7 +820,11 @@ def main():
         print(json.dumps(run_precision()))
         return
     if args.learned_only:
-        print(json.dumps(run_learned(args.weights)))
+        import torch
+
+        out = run_learned(args.weights)
+        out["mlp_forward"] = run_mlp_forward(torch.device("cuda", 0))
+        print(json.dumps(out))
         return
     if args.impl == "reference":
         run_reference(args)

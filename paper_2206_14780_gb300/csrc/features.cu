@@ -25,8 +25,8 @@ struct sph_mlp;
 
 namespace sph {
 
-void mlp_forward_launch(const sph_mlp* M, const __nv_bfloat16* feats, int64_t m, float4* out, int num_sms,
-                        cudaStream_t st);
+sph_status mlp_forward_launch(const sph_mlp* M, const __nv_bfloat16* feats, int64_t m, float4* out, int num_sms,
+                              cudaStream_t st);
 
 namespace {
 
@@ -368,7 +368,7 @@ sph_status sph_warm_start(sph_neighbors* h, const sph_visc_params* params, const
     SPH_TRY(h->feat_delta.alloc(h->n));        // float4 network outputs
     __nv_bfloat16* f = reinterpret_cast<__nv_bfloat16*>(h->feat_out.p);
     SPH_TRY(features_impl(h, params, vel, f, st));
-    mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st);
+    SPH_TRY(mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st));
     delta = h->feat_delta.p;
   } else {
     SPH_TRY(ensure_operator(h, params, st));
@@ -404,7 +404,7 @@ sph_status sph_mlp_residual_targets(sph_neighbors* h, const sph_visc_params* par
   SPH_TRY(h->feat_delta.alloc(h->n));
   SPH_TRY(h->x64.alloc(3 * h->n_pad));
   SPH_TRY(h->r64.alloc(3 * h->n_pad));
-  mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st);
+  SPH_TRY(mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st));
   double* x0 = h->x64.p;
   SPH_LAUNCH(k_warm_x0, grid_for(h, h->n), kBlock, 0, st)(reinterpret_cast<const float4*>(vel), h->feat_delta.p, ptype,
                                                           b, h->n, h->feat_scale.p, x0);

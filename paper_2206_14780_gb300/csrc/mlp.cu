@@ -6,11 +6,13 @@
 // from x0 = v^n + U delta on fluid rows, the dummy-wall rows of x0 following
 // from the fluid ones by Eq. dummyvel (features.cu).
 //
-// Tensor cores: mma.sync.m16n8k16 (bf16 x bf16 -> f32).  One warp owns 16
-// particles.  The accumulator fragment of two adjacent 8-column tiles is, lane
-// for lane, the A fragment of the next 16-wide K chunk, so hidden activations
-// stay in registers between layers (bias, SiLU and the bf16 rounding are applied
-// in place).  The backward pass reuses the same trick for the data gradients
+// Inference (sph_mlp_forward, sph_warm_start) runs on the tcgen05 tensor cores
+// (mlp_tc.cu).  Training (sph_mlp_grad, sph_mlp_train_step) runs forward and
+// backward per warp with mma.sync.m16n8k16 (bf16 x bf16 -> f32), keeping every
+// activation and data gradient in registers.  One warp owns 16 particles.  The
+// accumulator fragment of two adjacent 8-column tiles is, lane for lane, the A
+// fragment of the next 16-wide K chunk, so hidden activations stay in registers
+// between layers (bias, SiLU and the bf16 rounding are applied in place).  The backward pass reuses the same trick for the data gradients
 // (delta W with W^T kept in shared memory); the weight gradients
 // dW = delta^T a are products over the warp's 16 rows with operands read from
 // per-warp shared-memory tiles.
@@ -21,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 
 #include "reduce.cuh"
@@ -47,6 +50,7 @@ struct MlpPack {
 struct sph_mlp {
   sph::DBuf<float> theta, m, v, grad, partial, loss;
   sph::DBuf<sph::MlpPack> pack;
+  sph::DBuf<int> fault;          // set when a tensor-core forward gave up a wait
   int64_t step = 0;
   int partial_blocks = 0;
 };
@@ -154,49 +158,6 @@ __device__ __forceinline__ void load_a0(const __nv_bfloat16* __restrict__ f, int
   a[3] = rb < m ? ld32(f + rb * kFeat + 2 * t + 8) : 0u;
 }
 
-// forward only: out[m][4] = (delta_x, delta_y, delta_z, 0)
-__global__ void __launch_bounds__(128) k_mlp_forward(const MlpPack* __restrict__ Pg,
-                                                     const __nv_bfloat16* __restrict__ feats, int64_t m,
-                                                     float4* __restrict__ out) {
-  __shared__ __align__(16) MlpPack P;
-  load_pack(Pg, &P);
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 16 < m; w += warps) {
-    const int64_t r0 = w * 16;
-    uint32_t a0[1][4];
-    load_a0(feats, m, r0, g, t, a0[0]);
-    float c[8][4];
-    uint32_t a[4][4];
-    layer<1>(c, a0, P.W1, 16, P.b1, g, t);
-    act_to_a(c, a);
-    layer<4>(c, a, P.W2, 64, P.b2, g, t);
-    act_to_a(c, a);
-    layer<4>(c, a, P.W3, 64, P.b3, g, t);
-    act_to_a(c, a);
-    float y[4] = {P.b4[2 * t], P.b4[2 * t + 1], P.b4[2 * t], P.b4[2 * t + 1]};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      uint32_t b[2];
-      b[0] = ld32(P.W4 + g * 64 + 16 * k + 2 * t);
-      b[1] = ld32(P.W4 + g * 64 + 16 * k + 2 * t + 8);
-      mma16816(y, a[k], b);
-    }
-    // lanes t = 0, 1 hold output columns 0..3 (3 used) of rows g and g + 8
-    if (t < 2) {
-      const int64_t ra = r0 + g, rb = r0 + g + 8;
-      float* o = reinterpret_cast<float*>(out);
-      if (ra < m) {
-        o[ra * 4 + 2 * t] = y[0];
-        o[ra * 4 + 2 * t + 1] = (2 * t + 1 < 3) ? y[1] : 0.f;
-      }
-      if (rb < m) {
-        o[rb * 4 + 2 * t] = y[2];
-        o[rb * 4 + 2 * t + 1] = (2 * t + 1 < 3) ? y[3] : 0.f;
-      }
-    }
-  }
-}
 
 // per-warp shared scratch of the training kernel
 struct WarpTile {
@@ -453,13 +414,34 @@ int mlp_train_smem() {
   return (int)(sizeof(MlpPack) + ((kNP * 4 + 15) / 16) * 16 + kTrainWarps * sizeof(WarpTile));
 }
 
-void mlp_forward_launch(const sph_mlp* M, const __nv_bfloat16* feats, int64_t m, float4* out, int num_sms,
-                        cudaStream_t st) {
-  int64_t blocks = (m + 16 * 4 - 1) / (16 * 4);
-  const int64_t cap = (int64_t)num_sms * 8;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
-  SPH_LAUNCH(k_mlp_forward, (int)blocks, 128, 0, st)(M->pack.p, feats, m, out);
+const void* mlp_pack_ptr(const sph_mlp* M) { return M->pack.p; }
+
+void mlp_pack_layout(size_t* off_w1, size_t* off_w2, size_t* off_w3, size_t* off_w4, size_t* off_b) {
+  *off_w1 = offsetof(MlpPack, W1);
+  *off_w2 = offsetof(MlpPack, W2);
+  *off_w3 = offsetof(MlpPack, W3);
+  *off_w4 = offsetof(MlpPack, W4);
+  *off_b = offsetof(MlpPack, b1);
+}
+
+sph_status mlp_forward_tc(const sph_mlp* M, const __nv_bfloat16* feats, int64_t m, float4* out, int* err,
+                          int num_sms, cudaStream_t st);
+
+// the inference forward: tcgen05 kernel of mlp_tc.cu
+sph_status mlp_forward_launch(const sph_mlp* M, const __nv_bfloat16* feats, int64_t m, float4* out, int num_sms,
+                              cudaStream_t st) {
+  if (m <= 0) return SPH_OK;
+  return mlp_forward_tc(M, feats, m, out, M->fault.p, num_sms, st);
+}
+
+static sph_status check_fault(const sph_mlp* M) {
+  int f = 0;
+  SPH_TRY_CUDA(cudaMemcpy(&f, M->fault.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (f) {
+    set_error("warm-start network: a tensor-core forward gave up waiting for its MMAs");
+    return SPH_ERR_TIMEOUT;
+  }
+  return SPH_OK;
 }
 
 }  // namespace sph
@@ -481,10 +463,10 @@ sph_status sph_mlp_create(const float* params, sph_mlp** out) {
     return s;
   };
   if (M->theta.alloc(kNP) || M->m.alloc(kNP) || M->v.alloc(kNP) || M->grad.alloc(kNP) || M->loss.alloc(1) ||
-      M->pack.alloc(1))
+      M->pack.alloc(1) || M->fault.alloc(1))
     return fail(SPH_ERR_NOMEM);
   if (cudaMemset(M->m.p, 0, kNP * 4) != cudaSuccess || cudaMemset(M->v.p, 0, kNP * 4) != cudaSuccess ||
-      cudaMemset(M->theta.p, 0, kNP * 4) != cudaSuccess) {
+      cudaMemset(M->theta.p, 0, kNP * 4) != cudaSuccess || cudaMemset(M->fault.p, 0, sizeof(int)) != cudaSuccess) {
     set_error("sph_mlp_create: memset failed");
     return fail(SPH_ERR_CUDA);
   }
@@ -530,7 +512,7 @@ sph_status sph_mlp_get_params(const sph_mlp* M, float* params) {
     return SPH_ERR_INVALID;
   }
   SPH_TRY_CUDA(cudaMemcpy(params, M->theta.p, kNP * 4, cudaMemcpyDeviceToHost));
-  return SPH_OK;
+  return check_fault(M);
 }
 
 sph_status sph_mlp_destroy(sph_mlp* M) {
@@ -542,6 +524,7 @@ sph_status sph_mlp_destroy(sph_mlp* M) {
   M->partial.release();
   M->loss.release();
   M->pack.release();
+  M->fault.release();
   delete M;
   return SPH_OK;
 }
@@ -556,8 +539,8 @@ sph_status sph_mlp_forward(const sph_mlp* M, const uint16_t* feats, int64_t m, f
   int dev = 0, sms = 0;
   SPH_TRY_CUDA(cudaGetDevice(&dev));
   SPH_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  mlp_forward_launch(M, reinterpret_cast<const __nv_bfloat16*>(feats), m, reinterpret_cast<float4*>(out), sms,
-                     reinterpret_cast<cudaStream_t>(stream));
+  SPH_TRY(mlp_forward_launch(M, reinterpret_cast<const __nv_bfloat16*>(feats), m, reinterpret_cast<float4*>(out), sms,
+                             reinterpret_cast<cudaStream_t>(stream)));
   SPH_TRY_CUDA(cudaGetLastError());
   return SPH_OK;
 }
@@ -623,6 +606,7 @@ sph_status sph_mlp_train_step(sph_mlp* M, const uint16_t* feats, const float* ta
   if (loss_host) {
     SPH_TRY_CUDA(cudaMemcpyAsync(loss_host, M->loss.p, 4, cudaMemcpyDeviceToHost, st));
     SPH_TRY_CUDA(cudaStreamSynchronize(st));
+    SPH_TRY(check_fault(M));
   }
   return SPH_OK;
 }
