@@ -16,10 +16,10 @@
 // groups SBO bytes apart (SBO = 16 * K bytes).  An MMA consumes K = 16, i.e. two
 // core matrices along K, so the k-th chunk's descriptor starts 256 k bytes in.
 //
-// Tensor memory: 128 columns per CTA (D of layers 1-3 in columns 0-63, layer 4
-// in 64-79).  The dynamic shared-memory request (60 KB) keeps at most three CTAs
-// on an SM, so their 384 columns never exceed the SM's 512 and tcgen05.alloc
-// never waits.  Waits on the MMA mbarrier are bounded; on a timeout the kernel
+// Tensor memory: 64 columns per CTA (D of every layer in columns 0-63; layer 4
+// uses 0-15 after layer 3's epilogue has read them).  The dynamic shared-memory
+// request (44 KB) keeps at most five CTAs on an SM, so their 320 columns never
+// exceed the SM's 512 and tcgen05.alloc never waits.  Waits on the MMA mbarrier are bounded; on a timeout the kernel
 // sets *err, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
@@ -37,8 +37,8 @@ void mlp_pack_layout(size_t* off_w1, size_t* off_w2, size_t* off_w3, size_t* off
 namespace {
 
 constexpr int kTile = 128;
-constexpr int kTmemCols = 128;
-constexpr int kSmemDyn = 60 * 1024;
+constexpr int kTmemCols = 64;
+constexpr int kSmemDyn = 44 * 1024;
 constexpr long long kMmaWaitCycles = 4000000000ll;
 
 // shared-memory map (bytes from the dynamic base, 1024-aligned pieces)
@@ -209,10 +209,9 @@ __global__ void __launch_bounds__(kTile) k_mlp_forward_tc(const char* __restrict
           tc_mma(tbase, smem_desc(aX, 256), smem_desc(aW1, 256), id64, 0u);
         } else {
           const uint32_t aW = layer == 1 ? aW2 : (layer == 2 ? aW3 : aW4);
-          const uint32_t dcol = layer == 3 ? 64u : 0u;
 #pragma unroll
           for (int k = 0; k < 4; ++k)
-            tc_mma(tbase + dcol, smem_desc(aH + 256 * k, 1024), smem_desc(aW + 256 * k, 1024),
+            tc_mma(tbase, smem_desc(aH + 256 * k, 1024), smem_desc(aW + 256 * k, 1024),
                    layer == 3 ? id16 : id64, k > 0 ? 1u : 0u);
         }
         tc_commit(bar);
@@ -229,7 +228,7 @@ __global__ void __launch_bounds__(kTile) k_mlp_forward_tc(const char* __restrict
         epilogue_hidden(tbase, warp, tid, bias + 64 * layer, smem + SM_H);
       } else {
         float v[4];
-        tc_ld4(tbase + ((uint32_t)(32 * warp) << 16) + 64, v);
+        tc_ld4(tbase + ((uint32_t)(32 * warp) << 16), v);
         if (p < m) out[p] = make_float4(v[0] + bias[192], v[1] + bias[193], v[2] + bias[194], 0.f);
       }
     }
@@ -256,7 +255,7 @@ sph_status mlp_forward_tc(const sph_mlp* M, const __nv_bfloat16* feats, int64_t 
   size_t ow1, ow2, ow3, ow4, ob;
   mlp_pack_layout(&ow1, &ow2, &ow3, &ow4, &ob);
   int64_t blocks = (m + kTile - 1) / kTile;
-  const int64_t cap = (int64_t)num_sms * 3;
+  const int64_t cap = (int64_t)num_sms * 5;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   SPH_LAUNCH(k_mlp_forward_tc, (int)blocks, kTile, kSmemDyn, st)(reinterpret_cast<const char*>(mlp_pack_ptr(M)),
