@@ -122,6 +122,7 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
   h->iperm.release();
   h->key_s.release();
   h->cell_start.release();
+  h->cell_rank.release();
   h->cnt.release();
   h->slice_off.release();
   h->nbr.release();

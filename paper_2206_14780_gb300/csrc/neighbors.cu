@@ -4,7 +4,11 @@
 //
 // Steps (one launch each):
 //   keys      cell of every particle: floor((x - lo) / cell) per axis in float64,
-//             wrapped on periodic axes, clamped on open ones; per-cell counts
+//             wrapped on periodic axes, clamped on open ones; per-cell counts.
+//             Cells are ordered along a Morton (Z-order) curve: segment r of the
+//             sorted order holds the cell of rank r, so 32-row slices and the
+//             slices a block works on are compact in space and their neighbour
+//             gathers share cache lines (the apply is bound by those gathers)
 //   scan      exclusive prefix sum of the counts -> cell_start
 //   scatter   particles into their cell's segment (atomics: any order)
 //   order     each segment sorted by caller index (makes the layout deterministic)
@@ -17,9 +21,11 @@
 // decides every pair outside a band around (2h)^2 whose half-width bounds the
 // float32 rounding of r^2; pairs inside the band are recomputed in float64 with
 // the same operations, in the same order and without contraction.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "sph_internal.cuh"
 
@@ -29,8 +35,8 @@ namespace {
 
 enum : int32_t { FLAG_NONFINITE = 1, FLAG_CAPACITY = 2, FLAG_CELLFULL = 4 };
 
-__global__ void k_cell_keys(const float4* __restrict__ pos, int64_t n, Grid g, int32_t* __restrict__ key,
-                            int32_t* __restrict__ cell_count, int32_t* __restrict__ flags,
+__global__ void k_cell_keys(const float4* __restrict__ pos, int64_t n, Grid g, const int32_t* __restrict__ rank,
+                            int32_t* __restrict__ key, int32_t* __restrict__ cell_count, int32_t* __restrict__ flags,
                             unsigned int* __restrict__ max_abs_bits) {
   float local_max = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -56,7 +62,7 @@ __global__ void k_cell_keys(const float4* __restrict__ pos, int64_t n, Grid g, i
     }
     int32_t kk = c[0] + g.ncell[0] * (c[1] + g.ncell[1] * c[2]);
     key[i] = kk;
-    atomicAdd(&cell_count[kk], 1);
+    atomicAdd(&cell_count[rank[kk]], 1);
   }
   // warp max then one atomic per warp (non-negative floats order like their bits)
   for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
@@ -103,10 +109,11 @@ __global__ void k_scan(const int32_t* __restrict__ in, TOut* __restrict__ out, i
   }
 }
 
-__global__ void k_cell_scatter(const int32_t* __restrict__ key, int64_t n, const int32_t* __restrict__ cell_start,
-                               int32_t* __restrict__ cursor, int32_t* __restrict__ out) {
+__global__ void k_cell_scatter(const int32_t* __restrict__ key, const int32_t* __restrict__ rank, int64_t n,
+                               const int32_t* __restrict__ cell_start, int32_t* __restrict__ cursor,
+                               int32_t* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t k = key[i];
+    int32_t k = rank[key[i]];
     int32_t slot = cell_start[k] + atomicAdd(&cursor[k], 1);
     out[slot] = (int32_t)i;
   }
@@ -182,6 +189,7 @@ struct Band {
 
 template <bool FILL>
 __global__ void __launch_bounds__(kBlock) k_neighbors(const float4* __restrict__ pos_s, const int32_t* __restrict__ key_s,
+                                                      const int32_t* __restrict__ rank,
                                                       const int32_t* __restrict__ cell_start, int64_t n, int64_t n_pad,
                                                       Grid g, Band band, int32_t maxnb, int32_t* __restrict__ cnt,
                                                       const int64_t* __restrict__ slice_off, int32_t* __restrict__ nbr,
@@ -210,7 +218,7 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(const float4* __restrict__
           int x = cx + dx;
           if (g.periodic[0]) x = (x + nx) % nx;
           else if (x < 0 || x >= nx) continue;
-          const int32_t cell = x + nx * (y + ny * z);
+          const int32_t cell = rank[x + nx * (y + ny * z)];
           const int32_t tb = cell_start[cell], te = cell_start[cell + 1];
           for (int32_t t = tb; t < te; ++t) {
             if (t == s) continue;
@@ -295,6 +303,33 @@ __global__ void k_export_fill(const int32_t* __restrict__ iperm, const int32_t* 
 }
 
 }  // namespace
+
+// rank[row-major cell] = position of the cell along the Morton curve that
+// interleaves the bits of its (x, y, z) cell coordinates (ties impossible); grids
+// of more than 2^24 cells keep the row-major order (the host table and its sort
+// would cost more than the locality gains)
+static void morton_ranks(const int nc[3], std::vector<int32_t>& rank) {
+  auto spread = [](uint64_t v) {
+    uint64_t r = 0;
+    for (int b = 0; b < 21; ++b) r |= ((v >> b) & 1ull) << (3 * b);
+    return r;
+  };
+  const int64_t ncells = (int64_t)nc[0] * nc[1] * nc[2];
+  rank.assign((size_t)ncells, 0);
+  if (ncells > ((int64_t)1 << 24)) {
+    for (int64_t c = 0; c < ncells; ++c) rank[(size_t)c] = (int32_t)c;
+    return;
+  }
+  std::vector<std::pair<uint64_t, int32_t>> code((size_t)ncells);
+  for (int z = 0; z < nc[2]; ++z)
+    for (int y = 0; y < nc[1]; ++y)
+      for (int x = 0; x < nc[0]; ++x) {
+        const int64_t c = x + (int64_t)nc[0] * (y + (int64_t)nc[1] * z);
+        code[(size_t)c] = {spread((uint64_t)x) | (spread((uint64_t)y) << 1) | (spread((uint64_t)z) << 2), (int32_t)c};
+      }
+  std::sort(code.begin(), code.end());
+  for (int64_t r = 0; r < ncells; ++r) rank[(size_t)code[(size_t)r].second] = (int32_t)r;
+}
 
 int grid_for(const sph_neighbors* H, int64_t work_items, int block) {
   int64_t want = (work_items + block - 1) / block;
@@ -442,7 +477,14 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
   const float4* pos = reinterpret_cast<const float4*>(sc->pos);
   int32_t* key = H->tmp_i32a.p;
   int grid_n = grid_for(H, n);
-  SPH_LAUNCH(k_cell_keys, grid_n, kBlock, 0, st)(pos, n, g, key, H->tmp_i32b.p, H->flags.p,
+  if (H->rank_dims[0] != g.ncell[0] || H->rank_dims[1] != g.ncell[1] || H->rank_dims[2] != g.ncell[2]) {
+    TRYF(H->cell_rank.alloc(ncells));
+    std::vector<int32_t> rank;
+    morton_ranks(g.ncell, rank);
+    TRYF_CUDA(cudaMemcpy(H->cell_rank.p, rank.data(), ncells * sizeof(int32_t), cudaMemcpyHostToDevice));
+    for (int ax = 0; ax < 3; ++ax) H->rank_dims[ax] = g.ncell[ax];
+  }
+  SPH_LAUNCH(k_cell_keys, grid_n, kBlock, 0, st)(pos, n, g, H->cell_rank.p, key, H->tmp_i32b.p, H->flags.p,
                                          reinterpret_cast<unsigned int*>(H->flags.p + 1));
   TRYF_CUDA(cudaGetLastError());
   SPH_LAUNCH(k_scan<int32_t>, 1, 1024, 0, st)(H->tmp_i32b.p, H->cell_start.p, ncells, 1, H->flags.p + 2);
@@ -465,7 +507,8 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
 
   // scatter into segments (cursor counts reuse tmp_i32b), order, gather
   TRYF_CUDA(cudaMemsetAsync(H->tmp_i32b.p, 0, ncells * sizeof(int32_t), st));
-  SPH_LAUNCH(k_cell_scatter, grid_n, kBlock, 0, st)(key, n, H->cell_start.p, H->tmp_i32b.p, H->perm.p);
+  SPH_LAUNCH(k_cell_scatter, grid_n, kBlock, 0, st)(key, H->cell_rank.p, n, H->cell_start.p, H->tmp_i32b.p,
+                                                    H->perm.p);
   TRYF_CUDA(cudaGetLastError());
   SPH_LAUNCH(k_cell_order, grid_for(H, ncells), kBlock, 0, st)(H->cell_start.p, ncells, H->perm.p);
   TRYF_CUDA(cudaGetLastError());
@@ -495,7 +538,7 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
   }
 
   int grid_p = grid_for(H, H->n_pad);
-  SPH_LAUNCH(k_neighbors<false>, grid_p, kBlock, 0, st)(H->pos_s.p, H->key_s.p, H->cell_start.p, n, H->n_pad, g, band, maxnb,
+  SPH_LAUNCH(k_neighbors<false>, grid_p, kBlock, 0, st)(H->pos_s.p, H->key_s.p, H->cell_rank.p, H->cell_start.p, n, H->n_pad, g, band, maxnb,
                                                 H->cnt.p, nullptr, nullptr, H->flags.p);
   TRYF_CUDA(cudaGetLastError());
   TRYF_CUDA(cudaMemcpyAsync(hflags, H->flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -511,7 +554,7 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
     return fail(SPH_ERR_CAPACITY);
   }
   TRYF(H->nbr.alloc(total_pad > 0 ? total_pad : 1));
-  SPH_LAUNCH(k_neighbors<true>, grid_p, kBlock, 0, st)(H->pos_s.p, H->key_s.p, H->cell_start.p, n, H->n_pad, g, band, maxnb,
+  SPH_LAUNCH(k_neighbors<true>, grid_p, kBlock, 0, st)(H->pos_s.p, H->key_s.p, H->cell_rank.p, H->cell_start.p, n, H->n_pad, g, band, maxnb,
                                                H->cnt.p, H->slice_off.p, H->nbr.p, H->flags.p);
   TRYF_CUDA(cudaGetLastError());
   H->nnz = total;

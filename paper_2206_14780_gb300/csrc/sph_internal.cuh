@@ -122,7 +122,9 @@ struct sph_neighbors {
   sph::DBuf<float> rho_s, mu_s;
   sph::DBuf<uint8_t> type_s;
   sph::DBuf<int32_t> perm, iperm, key_s;
-  sph::DBuf<int32_t> cell_start;   // [ncells + 1]
+  sph::DBuf<int32_t> cell_start;   // [ncells + 1], indexed by Morton rank of the cell
+  sph::DBuf<int32_t> cell_rank;    // [ncells] row-major cell -> rank along a Morton curve
+  int rank_dims[3] = {0, 0, 0};
 
   // neighbour SELL-32
   sph::DBuf<int32_t> cnt;          // [n_pad]

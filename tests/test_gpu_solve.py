@@ -10,6 +10,11 @@ pytestmark = pytest.mark.gpu
 
 RTOL_RES = 1e-6      # true relative residual ||b - A x|| / ||b|| (oracle's float64 A)
 RTOL_SOL = 1e-5      # relative L2 distance to the oracle's solution
+# A residual of 1e-6 bounds the solution error only to ~kappa * 1e-6, and the stiff
+# boxes (dt sum c ~ 670) have kappa in the hundreds: the 1e-5 distance to the oracle's
+# solution is checked on a solve run to a 1e-7 true residual, the residual bound on
+# the 1e-6 solve itself.
+RTOL_FOR_SOL = 1e-7
 
 
 @pytest.mark.parametrize("name", sorted(SCENES_SMALL))
@@ -26,7 +31,9 @@ def test_solution_matches_oracle(name, merged):
     res, _ = oop.true_residual(A, x, s.b)
     assert res <= RTOL_RES, (res, rep)
     assert abs(rep["true_rel_res"] - res) <= 1e-3 * RTOL_RES + 1e-2 * res
-    assert rel_l2(x, x_ref) <= RTOL_SOL
+    x7, rep7 = gpu_solve(nb, s, binding.solve_opts(merged_reductions=merged, rtol=RTOL_FOR_SOL))
+    assert rep7["status"] == 0, rep7
+    assert rel_l2(x7, x_ref) <= RTOL_SOL
 
 
 @pytest.mark.parametrize("form", [1, 2, 3, 4, 5])
@@ -45,7 +52,8 @@ def test_every_apply_form_solves(name, form):
     assert rep["status"] == 0, rep
     res, _ = oop.true_residual(A, x, s.b)
     assert res <= RTOL_RES, (res, rep)
-    assert rel_l2(x, x_ref) <= RTOL_SOL
+    x7, rep7 = gpu_solve(nb, s, binding.solve_opts(apply_form=form, rtol=RTOL_FOR_SOL))
+    assert rep7["status"] == 0 and rel_l2(x7, x_ref) <= RTOL_SOL
 
 
 def test_staged_form_on_a_stiff_box_with_many_slices():
@@ -60,7 +68,8 @@ def test_staged_form_on_a_stiff_box_with_many_slices():
     assert rep["status"] == 0 and rep_a["status"] == 0, (rep, rep_a)
     res, _ = oop.true_residual(A, x, s.b)
     assert res <= RTOL_RES
-    assert rel_l2(x, x_ref) <= RTOL_SOL
+    x7, rep7 = gpu_solve(nb, s, binding.solve_opts(apply_form=5, rtol=RTOL_FOR_SOL))
+    assert rep7["status"] == 0 and rel_l2(x7, x_ref) <= RTOL_SOL
 
 
 def test_apply_form_out_of_range_is_rejected():
@@ -81,7 +90,10 @@ def test_stiff_box_several_tiles():
     x, rep = gpu_solve(nb, s)
     res, per = oop.true_residual(A, x, s.b)
     assert rep["status"] == 0 and res <= RTOL_RES, (res, rep)
-    assert rel_l2(x, x_ref) <= RTOL_SOL
+    from paper_2206_14780_gb300 import binding
+
+    x7, rep7 = gpu_solve(nb, s, binding.solve_opts(rtol=RTOL_FOR_SOL))
+    assert rep7["status"] == 0 and rel_l2(x7, x_ref) <= RTOL_SOL
 
 
 def test_zero_rhs_component_and_exact_guess():
@@ -132,7 +144,9 @@ def test_fp64_solve_matches_oracle(name, merged):
     x, rep = gpu_solve(nb, s, binding.solve_opts(precision=binding.SPH_PREC_FP64, merged_reductions=merged))
     res, _ = oop.true_residual(A, x, s.b)
     assert rep["status"] == 0 and res <= RTOL_RES, (res, rep)
-    assert rel_l2(x, x_ref) <= RTOL_SOL
+    x7, rep7 = gpu_solve(nb, s, binding.solve_opts(precision=binding.SPH_PREC_FP64, merged_reductions=merged,
+                                                   rtol=RTOL_FOR_SOL))
+    assert rep7["status"] == 0 and rel_l2(x7, x_ref) <= RTOL_SOL
 
 
 def test_fp64_solve_reaches_tight_tolerance():
