@@ -209,7 +209,7 @@ typedef struct {
   int32_t chunk;           /* iterations launched between host checks (>= 1)      */
   int32_t jacobi;          /* 1: left Jacobi scaling (App. B); 0: none            */
   int32_t apply_form;      /* 0: the autotuner picks the operator apply's row-loop
-                              form per phase (default); k = 1..5: use form k - 1
+                              form per phase (default); k = 1..6: use form k - 1
                               (sph_profile_counters.apply_variant numbering)     */
 } sph_solve_opts;
 
@@ -389,8 +389,10 @@ typedef struct {
   int32_t apply_variant[2];  /* row-loop form the autotuner chose per phase: 0..3 =
                                 (8 entries, plain), (4, plain), (8, prefetch), (4, prefetch)
                                 in registers; 4 = coefficient stream staged in shared
-                                memory by bulk asynchronous copies                   */
-  float tune_us[3][5];       /* autotuner timings (us) per phase (A p, A r*, A r* with
+                                memory by bulk asynchronous copies; 5 = each 32-row
+                                slice's distinct neighbour vectors gathered once into
+                                shared memory                                        */
+  float tune_us[3][6];       /* autotuner timings (us) per phase (A p, A r*, A r* with
                                 merged dots) and form; 0 where not measured          */
   int64_t standalone_launches[2]; /* sph_visc_apply [0] and sph_visc_apply_otf [1] calls
                                      timed (their apply kernel only; profiling makes

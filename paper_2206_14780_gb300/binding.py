@@ -61,7 +61,7 @@ class sph_profile_counters(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("apply_launches", ctypes.c_int64), ("apply_ms", ctypes.c_double),
                 ("apply_bytes", ctypes.c_int64), ("op_nnz", ctypes.c_int64),
                 ("phase_launches", ctypes.c_int64 * 2), ("phase_ms", ctypes.c_double * 2),
-                ("apply_variant", ctypes.c_int32 * 2), ("tune_us", (ctypes.c_float * 5) * 3),
+                ("apply_variant", ctypes.c_int32 * 2), ("tune_us", (ctypes.c_float * 6) * 3),
                 ("standalone_launches", ctypes.c_int64 * 2), ("standalone_ms", ctypes.c_double * 2),
                 ("otf_bytes", ctypes.c_int64)]
 

@@ -27,6 +27,10 @@ struct OpView {
   const float* invD;     // [n_pad]
   int64_t nslices;
   int64_t n_pad;
+  // per-slice neighbour unions (apply form 5; null until built)
+  const int2* loc;       // [op_nnz_pad] (position in the slice's union, coefficient bits)
+  const int32_t* uni;    // [op_nnz_pad] the slice's distinct neighbour rows at its offset
+  const int32_t* unum;   // [nslices] union size, -1: use ih
 };
 
 // Fluid rows: v_b + sum a (v_b - v_a) [times 1/D with Jacobi]; Shepard rows:
@@ -101,8 +105,12 @@ __device__ __forceinline__ float4 apply_row(const OpView& op, const float4* __re
 
 // the row-loop forms of the solver's apply: 0..3 = (U, PF) in {(8,0), (4,0),
 // (8,1), (4,1)} above, 4 = the coefficient stream staged through shared memory
-// by bulk copies (solver.cu); the batched solver uses forms 0..3
-constexpr int kApplyVariants = 5;
+// by bulk copies, 5 = neighbour vectors staged per slice in shared memory
+// (solver.cu); the batched solver uses forms 0..3
+constexpr int kApplyVariants = 6;
 constexpr int kApplyVariantsRegister = 4;
+// form 5: each slice's neighbour union staged in shared memory (apply_union.cu);
+// unions larger than this keep the global-gather path
+constexpr int kUnionCap = 512;
 
 }  // namespace sph

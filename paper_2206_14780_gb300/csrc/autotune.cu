@@ -1,8 +1,9 @@
 // Autotuner of the operator apply: for each apply phase of the BiCGSTAB
-// iteration (A p with the delta dot; A r* with the omega dots) it times the five
+// iteration (A p with the delta dot; A r* with the omega dots) it times the six
 // row-loop forms -- the register forms of apply.cuh, (U, PF) = (8, plain),
-// (4, plain), (8, prefetch), (4, prefetch), and the form with the coefficient
-// stream staged in shared memory by bulk copies (solver.cu), each at its own
+// (4, plain), (8, prefetch), (4, prefetch), the form with the coefficient
+// stream staged in shared memory by bulk copies, and the form with each slice's
+// neighbour vectors staged in shared memory (solver.cu), each at its own
 // full-occupancy grid -- on the handle's operator, and keeps the fastest.  The compiler schedules the unrolled gathers differently
 // in each kernel (the dot accumulators change the register budget), so the best
 // form differs per phase and is found by measurement, once per handle (again if
@@ -22,6 +23,7 @@ sph_status autotune_apply(sph_neighbors* H, bool merged, unsigned int* counter, 
   SPH_TRY_CUDA(cudaMemsetAsync(H->v_p.p, 0, np * sizeof(float4), st));
   SPH_TRY_CUDA(cudaMemsetAsync(H->v_rh.p, 0, np * sizeof(float4), st));
   SPH_TRY_CUDA(cudaMemsetAsync(H->scal_tune.p, 0, sizeof(SolverScalars), st));
+  SPH_TRY(apply_prepare(H, 5, st));        // the unions form 5 reads
   cudaEvent_t e0, e1;
   SPH_TRY_CUDA(cudaEventCreate(&e0));
   SPH_TRY_CUDA(cudaEventCreate(&e1));
@@ -35,19 +37,19 @@ sph_status autotune_apply(sph_neighbors* H, bool merged, unsigned int* counter, 
     for (int var = 0; var < kApplyVariants; ++var) {
       const ApplyDotFn kern = apply_kernel(ph, var);
       int occ = 1;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)kern, kBlock, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)kern, kBlock, apply_smem(var));
       int64_t g = (int64_t)H->num_sms * (occ > 0 ? occ : 1);
       if (g > want) g = want;
       if (g > H->red_grid) g = H->red_grid;
       if (g < 1) g = 1;
       for (int k = 0; k < 2; ++k)
-        SPH_LAUNCH(kern, (int)g, kBlock, 0, st)(op, H->v_p.p, H->v_As.p, H->v_rh.p, H->scal_tune.p, H->partials.p,
-                                                counter);
+        SPH_LAUNCH(kern, (int)g, kBlock, apply_smem(var), st)(op, H->v_p.p, H->v_As.p, H->v_rh.p, H->scal_tune.p,
+                                                              H->partials.p, counter);
       cudaEventRecord(e0, st);
       const int reps = 5;
       for (int k = 0; k < reps; ++k)
-        SPH_LAUNCH(kern, (int)g, kBlock, 0, st)(op, H->v_p.p, H->v_As.p, H->v_rh.p, H->scal_tune.p, H->partials.p,
-                                                counter);
+        SPH_LAUNCH(kern, (int)g, kBlock, apply_smem(var), st)(op, H->v_p.p, H->v_As.p, H->v_rh.p, H->scal_tune.p,
+                                                              H->partials.p, counter);
       cudaEventRecord(e1, st);
       cudaError_t err = cudaEventSynchronize(e1);
       float ms = 0.f;

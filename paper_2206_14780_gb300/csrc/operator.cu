@@ -340,7 +340,9 @@ void launch_residual_f64(const sph_neighbors* H, int grid, const double* x, cons
 }
 
 OpView op_view(const sph_neighbors* H) {
-  return OpView{H->op_off.p, H->op_cnt.p, H->op_ih.p, H->op_kind.p, H->invD.p, H->nslices, H->n_pad};
+  const bool u = H->union_valid && H->union_op_version == H->op_version;
+  return OpView{H->op_off.p, H->op_cnt.p, H->op_ih.p, H->op_kind.p, H->invD.p, H->nslices, H->n_pad,
+                u ? H->op_loc.p : nullptr, u ? H->uni.p : nullptr, u ? H->unum.p : nullptr};
 }
 
 void launch_apply_f32(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st) {

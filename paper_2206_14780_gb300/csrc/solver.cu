@@ -318,20 +318,135 @@ __global__ void __launch_bounds__(kBlock, 4) k_apply_dot_staged(OpView op, const
   dots_finish<PH>(acc, S, partials, counter);
 }
 
+// Row-loop form 5: each slice's distinct neighbour vectors gathered once into
+// shared memory (the unions of apply_union.cu, ~350 rows for ~2,400 entries on
+// the lava boxes), then every entry of the slice reads its neighbour from there:
+// about seven times fewer global gathers than the register forms.  The entry
+// stream (position in the union, coefficient) is loaded kUnionU entries at a
+// time with the next group in flight.  A slice marked -1 (union above
+// kUnionCap) runs the register form.  Measured slower than the register forms on
+// the lava boxes: its 8 KB of shared memory per warp allow 24 resident warps per
+// SM instead of 32, and the stream, not the gathers, then sets the pace.
+constexpr int kUnionU = 4;
+
+size_t union_smem_bytes() { return (size_t)(kBlock / 32) * kUnionCap * sizeof(float4); }
+
+template <int PH>
+__global__ void __launch_bounds__(kBlock, 3) k_apply_dot_union(OpView op, const float4* __restrict__ v,
+                                                            float4* __restrict__ y, const float4* __restrict__ rh,
+                                                            SolverScalars* S, double* partials,
+                                                            unsigned int* counter) {
+  constexpr int K = PhaseDots<PH>::K;
+  extern __shared__ __align__(16) float4 vsm[];   // [kBlock / 32][kUnionCap]
+  if (S->done) return;
+  const int lane = threadIdx.x & 31;
+  float4* vs = vsm + (threadIdx.x >> 5) * kUnionCap;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.f;
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
+    const int64_t s = sl * kSlice + lane;
+    const int nu = op.unum[sl];
+    float4 o, vb;
+    if (nu < 0) {
+      o = apply_row<4, true, true>(op, v, sl, lane, vb);
+    } else {
+      const int64_t o0 = op.off[sl];
+      const int32_t* __restrict__ U = op.uni + o0;
+      for (int i0 = 0; i0 < nu; i0 += 8 * kSlice) {
+        float4 t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * kSlice + lane;
+          t[u] = i < nu ? __ldg(v + U[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * kSlice + lane;
+          if (i < nu) vs[i] = t[u];
+        }
+      }
+      __syncwarp();
+      const int c = op.cnt[s];
+      const uint8_t kd = op.kind[s];
+      vb = v[s];
+      const float kap = (kd == KIND_FLUID) ? 1.f : 0.f;
+      const int w = (int)((op.off[sl + 1] - o0) / kSlice);
+      const int2* __restrict__ p = op.loc + o0 + lane;
+      float ax = 0.f, ay = 0.f, az = 0.f;
+      int2 e[kUnionU];
+#pragma unroll
+      for (int u = 0; u < kUnionU; ++u) e[u] = (u < c) ? __ldcs(p + (int64_t)u * kSlice) : make_int2(0, 0);
+      for (int j0 = 0; j0 < w; j0 += kUnionU) {
+        int2 en[kUnionU];
+#pragma unroll
+        for (int u = 0; u < kUnionU; ++u) {
+          const int j = j0 + kUnionU + u;
+          en[u] = (j < c) ? __ldcs(p + (int64_t)j * kSlice) : make_int2(0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnionU; ++u) {
+          const float4 va = vs[e[u].x];
+          const float a = __int_as_float(e[u].y);
+          ax = fmaf(a, fmaf(kap, vb.x, -va.x), ax);
+          ay = fmaf(a, fmaf(kap, vb.y, -va.y), ay);
+          az = fmaf(a, fmaf(kap, vb.z, -va.z), az);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnionU; ++u) e[u] = en[u];
+      }
+      __syncwarp();
+      if (kd == KIND_FLUID) {
+        const float sc = op.invD[s];
+        o = make_float4((vb.x + ax) * sc, (vb.y + ay) * sc, (vb.z + az) * sc, 0.f);
+      } else if (kd == KIND_SHEPARD) {
+        o = make_float4(vb.x - ax, vb.y - ay, vb.z - az, 0.f);
+      } else {
+        o = make_float4(vb.x, vb.y, vb.z, 0.f);
+      }
+    }
+    y[s] = o;
+    dots_row<PH>(acc, o, vb, rh, s);
+  }
+  dots_finish<PH>(acc, S, partials, counter);
+}
+
 }  // namespace
 
-// [phase][variant] with variants (U, PF) = (8,0), (4,0), (8,1), (4,1) as in apply.cuh
-// and 4 = the stream staged through shared memory by bulk copies
+// [phase][variant] with variants (U, PF) = (8,0), (4,0), (8,1), (4,1) as in apply.cuh,
+// 4 = the stream staged through shared memory by bulk copies, 5 = per-slice
+// neighbour unions in shared memory
 ApplyDotFn apply_kernel(int phase, int variant) {
   static const ApplyDotFn table[3][kApplyVariants] = {
       {k_apply_dot<PH_DELTA, 8, false>, k_apply_dot<PH_DELTA, 4, false>, k_apply_dot<PH_DELTA, 8, true>,
-       k_apply_dot<PH_DELTA, 4, true>, k_apply_dot_staged<PH_DELTA>},
+       k_apply_dot<PH_DELTA, 4, true>, k_apply_dot_staged<PH_DELTA>, k_apply_dot_union<PH_DELTA>},
       {k_apply_dot<PH_OMEGA, 8, false>, k_apply_dot<PH_OMEGA, 4, false>, k_apply_dot<PH_OMEGA, 8, true>,
-       k_apply_dot<PH_OMEGA, 4, true>, k_apply_dot_staged<PH_OMEGA>},
+       k_apply_dot<PH_OMEGA, 4, true>, k_apply_dot_staged<PH_OMEGA>, k_apply_dot_union<PH_OMEGA>},
       {k_apply_dot<PH_OMEGA_MERGED, 8, false>, k_apply_dot<PH_OMEGA_MERGED, 4, false>,
        k_apply_dot<PH_OMEGA_MERGED, 8, true>, k_apply_dot<PH_OMEGA_MERGED, 4, true>,
-       k_apply_dot_staged<PH_OMEGA_MERGED>}};
+       k_apply_dot_staged<PH_OMEGA_MERGED>, k_apply_dot_union<PH_OMEGA_MERGED>}};
   return table[phase < 0 ? 0 : (phase > 2 ? 2 : phase)][variant < 0 || variant >= kApplyVariants ? 0 : variant];
+}
+
+size_t apply_smem(int variant) { return variant == 5 ? union_smem_bytes() : 0; }
+
+// one-time opt-in of the forms that use more than 48 KB of dynamic shared memory
+static sph_status apply_attrs() {
+  static bool done = false;
+  if (done) return SPH_OK;
+  for (int ph = 0; ph < 3; ++ph)
+    SPH_TRY_CUDA(cudaFuncSetAttribute((const void*)apply_kernel(ph, 5), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)apply_smem(5)));
+  done = true;
+  return SPH_OK;
+}
+
+// what a form needs before it can run on H (form 5: the per-slice unions)
+sph_status apply_prepare(sph_neighbors* H, int variant, cudaStream_t st) {
+  SPH_TRY(apply_attrs());
+  if (variant == 5) SPH_TRY(ensure_union(H, st));
+  return SPH_OK;
 }
 
 namespace {
@@ -483,7 +598,8 @@ sph_status ensure_workspace(sph_neighbors* H) {
     int best = 1;
     for (int ph = 0; ph < 3; ++ph)
       for (int v = 0; v < kApplyVariants; ++v) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)apply_kernel(ph, v), kBlock, 0);
+        if (apply_attrs() != SPH_OK) return SPH_ERR_CUDA;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)apply_kernel(ph, v), kBlock, apply_smem(v));
         best = occ > best ? occ : best;
       }
     H->red_grid = H->num_sms * best;
@@ -525,7 +641,7 @@ static void launch_apply_dot(sph_neighbors* H, int grid, const OpView& op, const
   const int g = tg > 0 && tg < grid ? tg : grid;
   const ApplyDotFn kern = apply_kernel(PH, var);
   prof_begin(H, st, PH == PH_DELTA ? 0 : 1);
-  SPH_LAUNCH(kern, g, kBlock, 0, st)(op, v, y, rh, S, H->partials.p, counter);
+  SPH_LAUNCH(kern, g, kBlock, apply_smem(var), st)(op, v, y, rh, S, H->partials.p, counter);
   prof_end(H, st);
 }
 
@@ -537,15 +653,19 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
   const int64_t np = H->n_pad;
   const int grid_rows = red_grid_for(H, np);
   const int grid_slices = red_grid_for(H, H->nslices * 32);
+  // the chosen forms' prerequisites (the unions of form 5 follow the operator)
+  SPH_TRY(apply_prepare(H, H->apply_var[PH_DELTA], st));
+  SPH_TRY(apply_prepare(H, H->apply_var[O->merged_reductions ? PH_OMEGA_MERGED : PH_OMEGA], st));
   H->force_form = -1;
   if (O->apply_form < 0 || O->apply_form > kApplyVariants) {
     set_error("sph_visc_solve: apply_form %d outside 0..%d", O->apply_form, kApplyVariants);
     return SPH_ERR_INVALID;
   }
   if (O->apply_form > 0) {
+    SPH_TRY(apply_prepare(H, O->apply_form - 1, st));
     int occ = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)apply_kernel(PH_DELTA, O->apply_form - 1), kBlock,
-                                                  0);
+                                                  apply_smem(O->apply_form - 1));
     H->force_form = O->apply_form - 1;
     H->force_grid = H->num_sms * (occ > 0 ? occ : 1);
   }

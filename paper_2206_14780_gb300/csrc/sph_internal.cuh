@@ -148,6 +148,13 @@ struct sph_neighbors {
   int64_t op_nnz_pad = 0;
   uint64_t op_version = 0;         // bumped whenever the operator is rebuilt
 
+  // shared-memory apply form (apply_union.cu): per-slice neighbour unions
+  bool union_valid = false;
+  uint64_t union_op_version = 0;
+  sph::DBuf<int2> op_loc;          // [op_nnz_pad] (position in the slice's union, coefficient bits)
+  sph::DBuf<int32_t> uni;          // [op_nnz_pad] the slice's distinct neighbour rows, at its offset
+  sph::DBuf<int32_t> unum;         // [nslices] union size, -1 above kUnionCap
+
   // on-the-fly apply (apply_otf.cu): packed geometry for the operator of op_version
   bool otf_valid = false;
   uint64_t otf_op_version = 0;
@@ -173,7 +180,7 @@ struct sph_neighbors {
   // apply autotuner (autotune.cu): chosen row-loop form and grid per phase
   int apply_var[3] = {0, 0, 0};
   int apply_grid[3] = {0, 0, 0};
-  float tune_us[3][5] = {};
+  float tune_us[3][6] = {};
   bool tuned = false;
   int64_t tuned_n_pad = 0;
   int force_form = -1;               // sph_solve_opts.apply_form - 1 for the current solve
@@ -227,6 +234,11 @@ sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStrea
 void launch_apply_f32(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st);
 // apply_otf.cu: y = A v with the coefficients recomputed per pair
 void launch_apply_otf(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st);
+// apply_union.cu: per-slice unions for apply form 5 (built once per operator)
+sph_status ensure_union(sph_neighbors* H, cudaStream_t st);
+// dynamic shared memory of an apply form (bytes) and its one-time attribute set-up
+size_t apply_smem(int variant);
+sph_status apply_prepare(sph_neighbors* H, int variant, cudaStream_t st);
 sph_status visc_apply_otf(sph_neighbors* H, const sph_visc_params* P, const float* v, float* y, cudaStream_t st);
 // CUDA-event timing of one stand-alone apply launch when profiling is on (synchronises)
 void standalone_begin(sph_neighbors* H, cudaStream_t st);

@@ -36,12 +36,13 @@ def test_solution_matches_oracle(name, merged):
     assert rel_l2(x7, x_ref) <= RTOL_SOL
 
 
-@pytest.mark.parametrize("form", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("form", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("name", ["couette_dummy", "random_box_mu_mass", "lava_box_12"])
 def test_every_apply_form_solves(name, form):
-    """Each row-loop form of the solver's apply (the four register forms and the form
-    with the coefficient stream staged through shared memory by bulk copies), forced
-    instead of autotuned, reaches the true residual and the oracle's solution."""
+    """Each row-loop form of the solver's apply (the four register forms, the form with
+    the coefficient stream staged through shared memory by bulk copies and the form
+    with per-slice neighbour unions in shared memory), forced instead of autotuned,
+    reaches the true residual and the oracle's solution."""
     from paper_2206_14780_gb300 import binding
 
     s = SCENES_SMALL[name]()
@@ -78,7 +79,7 @@ def test_apply_form_out_of_range_is_rejected():
     s = SCENES_SMALL["couette_dummy"]()
     nb, _ = lib_build(s)
     with pytest.raises(binding.SphError):
-        gpu_solve(nb, s, binding.solve_opts(apply_form=6))
+        gpu_solve(nb, s, binding.solve_opts(apply_form=7))
 
 
 def test_stiff_box_several_tiles():
@@ -187,3 +188,26 @@ def test_warm_started_sequence_matches_oracle_sequence():
         b_np = b_np.copy()
         b_np[fl] = xk[fl]
     assert iters[-1] <= iters[0]      # the field smooths: later steps need no more work
+
+
+def test_union_form_after_operator_rebuild():
+    """Form 5 reads per-slice unions built from the operator; new viscosities and a new
+    dt rebuild the operator, and the next solve must rebuild the unions with it."""
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.lava_box(7, n=14)
+    nb, _ = lib_build(s)
+    off, idx, _ = oracle_system(s)
+    for dt, scale in ((5e-4, 1.0), (2e-4, 3.0)):
+        mu = (np.asarray(s.mu, np.float32) * np.float32(scale)).astype(np.float32)
+        nb.set_viscosity(torch.from_numpy(mu).cuda())
+        A = oop.assemble(s, off, idx, dt=dt, mu=mu)
+        bt = torch.from_numpy(s.b).cuda()
+        xt = torch.from_numpy(s.x0).cuda()
+        rep = nb.solve(params_for(s, dt), binding.solve_opts(apply_form=6, rtol=RTOL_FOR_SOL), bt, xt)
+        assert rep["status"] == 0, rep
+        x = xt.cpu().numpy()
+        res, _ = oop.true_residual(A, x, s.b)
+        assert res <= RTOL_FOR_SOL * 1.01
+        assert rel_l2(x, osv.reference_solution(A, s.b, s.x0)) <= RTOL_SOL
