@@ -575,9 +575,9 @@ def _starts(nb, p, net, t, b, x0_vn, fl):
 
 def run_learned(weights=None, dev=None, reps=3):
     """Learned warm start against x0 = 0, x0 = v^n (walls b) and v^n with the
-    dummy-wall closure, on scenes the network never saw: the 1.16M-particle
-    lava box (seed 1) with single solves, and the 64-scene ensemble (seed 1,
-    about 9M particles) through the batched solver.  Per start: iterations,
+    dummy-wall closure, on scenes the network never saw: 1.16M-particle lava
+    boxes (seeds 1-3) with single solves, and the 64-scene ensemble (seed 1,
+    about 8.5M particles) through the batched solver.  Per start: iterations,
     true residual and ms, the warm start's own kernels included."""
     import numpy as np
     import torch
@@ -599,44 +599,55 @@ def run_learned(weights=None, dev=None, reps=3):
     out = dict(weights=os.path.relpath(path, ROOT), training=meta.get("train"),
                note="ms = warm start + solve, CUDA events; x0 = 0 and v^n cost a copy")
 
-    # single 1.16M-particle box
-    s = scenes.lava_box(1, n=100)
-    t = binding.scene_tensors(s, dev)
-    t["vel"] = torch.from_numpy(s.vel).to(dev)
-    p = binding.visc_params(s.dt, s.boundary, s.mean)
-    nb = binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
-    b = torch.from_numpy(s.b).to(dev)
-    fl = torch.from_numpy(np.flatnonzero(s.ptype == scenes.FLUID)).to(dev)
-    x0_vn = torch.from_numpy(s.x0).to(dev)
-    x = torch.empty_like(b)
-    res = {}
-    for name, fill in _starts(nb, p, net, t, b, x0_vn, fl).items():
-        fill(x)
-        nb.solve(p, opts, b, x)                        # warm-up (coefficients, autotune)
-        st_ms, so_ms, its, rr = [], [], [], []
-        for _ in range(reps):
-            torch.cuda.synchronize(dev)
-            ev[0].record(stream)
+    # single 1.16M-particle boxes, three unseen seeds (iteration counts move by a few
+    # percent with rounding, so one seed decides nothing)
+    seeds = (1, 2, 3)
+    per = {k: dict(iters=[], start_ms=[], solve_ms=[], r0_rel=[], true_rel_res=[])
+           for k in ("zero", "vn", "vn_walls", "learned")}
+    for sd in seeds:
+        s = scenes.lava_box(sd, n=100)
+        t = binding.scene_tensors(s, dev)
+        t["vel"] = torch.from_numpy(s.vel).to(dev)
+        p = binding.visc_params(s.dt, s.boundary, s.mean)
+        nb = binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
+        b = torch.from_numpy(s.b).to(dev)
+        fl = torch.from_numpy(np.flatnonzero(s.ptype == scenes.FLUID)).to(dev)
+        x0_vn = torch.from_numpy(s.x0).to(dev)
+        x = torch.empty_like(b)
+        for name, fill in _starts(nb, p, net, t, b, x0_vn, fl).items():
             fill(x)
-            ev[1].record(stream)
-            rep = nb.solve(p, opts, b, x)
-            ev[2].record(stream)
-            torch.cuda.synchronize(dev)
-            st_ms.append(ev[0].elapsed_time(ev[1]))
-            so_ms.append(ev[1].elapsed_time(ev[2]))
-            its.append(rep["iters"])
-            rr.append(rep["true_rel_res"])
-        r = torch.empty_like(b)
-        fill(x)
-        nb.residual(p, x, b, r)
-        res[name] = dict(iters=int(np.median(its)), start_ms=float(np.median(st_ms)),
-                         solve_ms=float(np.median(so_ms)), ms=float(np.median(st_ms) + np.median(so_ms)),
-                         true_rel_res=max(rr), r0_rel=float(r.norm() / b.norm()))
-    out["box_1157k"] = dict(workload=f"lava box 100^3 fluid, seed 1 (N={s.n}), nu=10, dt=5e-4, v~N(0,0.1^2)",
+            nb.solve(p, opts, b, x)                    # warm-up (coefficients, autotune)
+            st_ms, so_ms, its, rr = [], [], [], []
+            for _ in range(reps):
+                torch.cuda.synchronize(dev)
+                ev[0].record(stream)
+                fill(x)
+                ev[1].record(stream)
+                rep = nb.solve(p, opts, b, x)
+                ev[2].record(stream)
+                torch.cuda.synchronize(dev)
+                st_ms.append(ev[0].elapsed_time(ev[1]))
+                so_ms.append(ev[1].elapsed_time(ev[2]))
+                its.append(rep["iters"])
+                rr.append(rep["true_rel_res"])
+            r = torch.empty_like(b)
+            fill(x)
+            nb.residual(p, x, b, r)
+            d = per[name]
+            d["iters"].append(int(np.median(its)))
+            d["start_ms"].append(float(np.median(st_ms)))
+            d["solve_ms"].append(float(np.median(so_ms)))
+            d["r0_rel"].append(float(r.norm() / b.norm()))
+            d["true_rel_res"].append(max(rr))
+        nb.close()
+        del t, b, x, x0_vn
+        torch.cuda.empty_cache()
+    res = {k: dict(iters=d["iters"], iters_mean=float(np.mean(d["iters"])),
+                   start_ms_mean=float(np.mean(d["start_ms"])), solve_ms_mean=float(np.mean(d["solve_ms"])),
+                   ms_mean=float(np.mean(d["start_ms"]) + np.mean(d["solve_ms"])), r0_rel=d["r0_rel"],
+                   max_true_rel_res=max(d["true_rel_res"])) for k, d in per.items()}
+    out["box_1157k"] = dict(workload="lava box 100^3 fluid (N=1,157,308), seeds 1-3, nu=10, dt=5e-4, v~N(0,0.1^2)",
                             **res)
-    nb.close()
-    del t, b, x, x0_vn
-    torch.cuda.empty_cache()
 
     # 64-scene ensemble through the batched solver
     ens = scenes.ensemble(1)
@@ -694,7 +705,7 @@ def run_sequence(nb, s, b, t, steps, dev):
 
     p = binding.visc_params(s.dt, s.boundary, s.mean)
     o = binding.solve_opts()
-    fl = torch.from_numpy(s.ptype == 0).to(dev)
+    fl3 = torch.from_numpy(s.ptype == 0).to(dev)[:, None].expand(-1, 3)
     dtg = torch.from_numpy(s.dt * scenes.stirring_force(s)).to(dev)
     bk = b.clone() + dtg
     x = torch.empty_like(b)
@@ -707,13 +718,13 @@ def run_sequence(nb, s, b, t, steps, dev):
     for k in range(steps):
         rep = nb.solve(p, o, bk, x)
         its.append(rep["iters"])
-        bk[fl] = x[fl] + dtg[fl]
+        torch.where(fl3, x + dtg, b, out=bk)       # fluid rows: v^{k+1} + dt g; walls keep b
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
     return dict(steps=steps, total_ms=ms, ms_per_solve=ms / steps, iters_first=its[0], iters_last=its[-1],
                 iters_mean=sum(its) / len(its), last_true_rel_res=rep["true_rel_res"], last_status=rep["status"],
-                rms_velocity_last=float(x[fl].pow(2).mean().sqrt()),
+                rms_velocity_last=float(x[fl3[:, 0]].pow(2).mean().sqrt()),
                 note="same A(dt) every step (positions frozen), b = previous solution + dt g on fluid rows "
                      "(g: fixed stirring force, 160 m/s^2 sine modes), x0 = previous solution")
 

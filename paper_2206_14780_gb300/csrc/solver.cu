@@ -696,6 +696,14 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
 
   std::memset(R, 0, sizeof(*R));
   int total_iters = 0, passes = 0;
+  // Launch chunks: the host checks the device's stop flag after each chunk, and
+  // iterations launched past a pass's convergence exit at once but still cost a
+  // launch each.  Passes of one system take similar iteration counts, so the
+  // first chunk of a pass runs to just short of the same pass of the last solve
+  // (or of the previous pass), then chunks of 4 follow; without a prediction the
+  // chunks double from `chunk`.
+  int prev_pass = 0;
+  int new_len[sph_neighbors::kPassHist] = {};
   double rr[3] = {0, 0, 0};
   sph_status status = SPH_NOT_CONVERGED;
   for (int ref = 0;; ++ref) {
@@ -718,7 +726,8 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
                                               H->partials.p, C + CNT_INIT);
     SPH_TRY_CUDA(cudaGetLastError());
     if (merged) SPH_LAUNCH(k_p_update, grid_rows, kBlock, 0, st)(np, V, S);
-    int chunk = chunk0;
+    const int pred = (passes < sph_neighbors::kPassHist && H->pass_len[passes] > 0) ? H->pass_len[passes] : prev_pass;
+    int chunk = pred > chunk0 + 2 ? pred - 2 : chunk0;
     int iter_seen = 0;
     for (;;) {
       for (int it = 0; it < chunk; ++it) {
@@ -743,10 +752,12 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
         return SPH_ERR_TIMEOUT;
       }
       if (H->host_scal->done) break;
-      chunk = chunk < 64 ? chunk * 2 : chunk;
+      chunk = pred > 0 ? 4 : (chunk < 64 ? chunk * 2 : chunk);
     }
     const SolverScalars& hs = *H->host_scal;
     total_iters += hs.iter;
+    if (passes < sph_neighbors::kPassHist) new_len[passes] = hs.iter;
+    prev_pass = hs.iter;
     passes++;
     for (int c = 0; c < 3; ++c) {
       R->state[c] = (int8_t)hs.state[c];
@@ -761,6 +772,7 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
       break;
     }
   }
+  for (int k = 0; k < sph_neighbors::kPassHist; ++k) H->pass_len[k] = new_len[k];
   SPH_LAUNCH(k_scatter_d3, grid_for(H, H->n), kBlock, 0, st)(H->x64.p, H->perm.p, H->n, x);
   SPH_TRY_CUDA(cudaGetLastError());
   SPH_TRY_CUDA(cudaStreamSynchronize(st));

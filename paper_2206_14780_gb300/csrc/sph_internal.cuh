@@ -184,6 +184,9 @@ struct sph_neighbors {
   bool tuned = false;
   int64_t tuned_n_pad = 0;
   int force_form = -1;               // sph_solve_opts.apply_form - 1 for the current solve
+  // iterations of each inner pass of the last mixed solve (sizes the launch chunks)
+  static constexpr int kPassHist = 16;
+  int pass_len[kPassHist] = {};
   int force_grid = 0;
   sph::DBuf<sph::SolverScalars> scal_tune;
 
