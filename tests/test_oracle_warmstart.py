@@ -83,8 +83,9 @@ def _net(seed):
     return p
 
 
-@pytest.mark.parametrize("jacobi,log", [(True, True), (False, True), (True, False), (False, False)])
-def test_targets_give_the_loss_gradient(jacobi, log):
+@pytest.mark.parametrize("jacobi,log,highpass", [(True, True, False), (False, True, False), (True, False, False),
+                                                  (False, False, False), (True, True, True), (False, False, True)])
+def test_targets_give_the_loss_gradient(jacobi, log, highpass):
     """MSE gradient with the residual targets == central differences of L(theta) with the
     wall rows of x0 held at their closure values (FP64 network, no bf16 rounding)."""
     s = scenes.lava_box(3, n=5)
@@ -94,7 +95,8 @@ def test_targets_give_the_loss_gradient(jacobi, log):
     fl = s.ptype == scenes.FLUID
     p = _net(4)
     y, _ = omlp.forward(p, X)
-    t, x0, L = ows.residual_targets(A, s.b, v, y, s.ptype, U, jacobi, log)
+    S = ows.shepard_matrix(s, off, idx) if highpass else None
+    t, x0, L = ows.residual_targets(A, s.b, v, y, s.ptype, U, jacobi, log, S)
     assert np.isfinite(L)
     _, g, _ = omlp.loss_and_grad(p, X, t, fl.astype(np.uint8))
     gflat = omlp.flatten(g)
@@ -102,6 +104,8 @@ def test_targets_give_the_loss_gradient(jacobi, log):
 
     def L_of(theta):
         yy, _ = omlp.forward(omlp.unflatten(theta), X)
+        if S is not None:
+            yy = yy - S @ yy
         x = x0.copy()
         x[fl] = v[fl, :3].astype(np.float64) + U * yy[fl]
         x[~fl] = walls
@@ -135,3 +139,27 @@ def test_log_loss_is_scale_free():
     t2, _, L2 = ows.residual_targets(A, 8.0 * s.b, v2, y, s.ptype, 8.0 * U)
     assert abs(L1 - L2) <= 1e-12 * abs(L1)
     np.testing.assert_allclose(t1, t2, rtol=1e-10, atol=1e-12)
+
+
+def test_shepard_matrix_rows_and_constants():
+    """S reproduces constants on fluid rows (rows sum to one), so (I - S) removes them;
+    its weights are the kernel's, pinned against a direct sum for one row."""
+    s = scenes.lava_box(5, n=5)
+    off, idx, _ = _system(s)
+    S = ows.shepard_matrix(s, off, idx)
+    fl = s.ptype == scenes.FLUID
+    np.testing.assert_allclose(np.asarray(S.sum(axis=1)).ravel()[fl], 1.0, rtol=1e-14)
+    np.testing.assert_array_equal(np.asarray(S.sum(axis=1)).ravel()[~fl], 0.0)
+    c = np.tile([0.3, -1.0, 2.0], (s.n, 1))
+    np.testing.assert_allclose((c - S @ c)[fl], 0.0, atol=1e-14)
+    b = int(np.flatnonzero(fl)[17])
+    h = float(np.float32(s.h))
+    P = np.asarray(s.pos, np.float32)[:, :3].astype(np.float64)
+    V = np.asarray(s.pos, np.float32)[:, 3].astype(np.float64) / np.asarray(s.rho, np.float32).astype(np.float64)
+    nb = [a for a in idx[off[b]:off[b + 1]] if fl[a]]
+    w = {a: okern.W(np.linalg.norm(P[a] - P[b]), h) * V[a] for a in nb}
+    w[b] = okern.W(0.0, h) * V[b]
+    tot = sum(w.values())
+    row = S.getrow(b).toarray().ravel()
+    for a, wa in w.items():
+        assert abs(row[a] - wa / tot) <= 1e-14
