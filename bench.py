@@ -553,8 +553,8 @@ def run_ensemble(seed=0, dev=None):
 
 # ------------------------------------------------------ learned warm start ----
 
-def _starts(nb, p, net, t, b, x0_vn, fl):
-    """The four initial guesses: name -> callable filling x (device) and returning nothing."""
+def _starts(nb, p, net, t, b, x0_vn, fl, net_hp=None):
+    """The initial guesses: name -> callable filling x (device) and returning nothing."""
     from paper_2206_14780_gb300 import binding
 
     def zero(x):
@@ -570,10 +570,16 @@ def _starts(nb, p, net, t, b, x0_vn, fl):
     def learned(x):
         binding.warm_start(nb, p, net, t["vel"], t["ptype"], b, x)
 
-    return dict(zero=zero, vn=vn, vn_walls=vn_walls, learned=learned)
+    out = dict(zero=zero, vn=vn, vn_walls=vn_walls, learned=learned)
+    if net_hp is not None:
+        def learned_highpass(x):
+            binding.warm_start(nb, p, net_hp, t["vel"], t["ptype"], b, x)
+
+        out["learned_highpass"] = learned_highpass
+    return out
 
 
-def run_learned(weights=None, dev=None, reps=3):
+def run_learned(weights=None, dev=None, reps=3, mode=None):
     """Learned warm start against x0 = 0, x0 = v^n (walls b) and v^n with the
     dummy-wall closure, on scenes the network never saw: 1.16M-particle lava
     boxes (seeds 1-3) with single solves, and the 64-scene ensemble (seed 1,
@@ -593,17 +599,24 @@ def run_learned(weights=None, dev=None, reps=3):
     z = np.load(path)
     net = binding.Mlp(z["params"])
     meta = json.loads(str(z["meta"])) if "meta" in z else {}
+    if mode is None:
+        mode = int(meta.get("mode", 0))
+    net.set_mode(mode)
+    net_hp = None
+    if not mode & binding.MLP_HIGHPASS:        # the same weights with the high-passed correction
+        net_hp = binding.Mlp(z["params"])
+        net_hp.set_mode(mode | binding.MLP_HIGHPASS)
     stream = torch.cuda.current_stream(dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     opts = binding.solve_opts()
-    out = dict(weights=os.path.relpath(path, ROOT), training=meta.get("train"),
+    out = dict(weights=os.path.relpath(path, ROOT), training=meta.get("train"), mode=mode,
                note="ms = warm start + solve, CUDA events; x0 = 0 and v^n cost a copy")
 
     # single 1.16M-particle boxes, three unseen seeds (iteration counts move by a few
     # percent with rounding, so one seed decides nothing)
     seeds = (1, 2, 3)
-    per = {k: dict(iters=[], start_ms=[], solve_ms=[], r0_rel=[], true_rel_res=[])
-           for k in ("zero", "vn", "vn_walls", "learned")}
+    names = ("zero", "vn", "vn_walls", "learned") + (("learned_highpass",) if net_hp is not None else ())
+    per = {k: dict(iters=[], start_ms=[], solve_ms=[], r0_rel=[], true_rel_res=[]) for k in names}
     for sd in seeds:
         s = scenes.lava_box(sd, n=100)
         t = binding.scene_tensors(s, dev)
@@ -614,7 +627,7 @@ def run_learned(weights=None, dev=None, reps=3):
         fl = torch.from_numpy(np.flatnonzero(s.ptype == scenes.FLUID)).to(dev)
         x0_vn = torch.from_numpy(s.x0).to(dev)
         x = torch.empty_like(b)
-        for name, fill in _starts(nb, p, net, t, b, x0_vn, fl).items():
+        for name, fill in _starts(nb, p, net, t, b, x0_vn, fl, net_hp).items():
             fill(x)
             nb.solve(p, opts, b, x)                    # warm-up (coefficients, autotune)
             st_ms, so_ms, its, rr = [], [], [], []
@@ -664,9 +677,9 @@ def run_learned(weights=None, dev=None, reps=3):
         fls.append(torch.from_numpy(np.flatnonzero(sc.ptype == scenes.FLUID)).to(dev))
     xs = [torch.empty_like(bb) for bb in bs]
     batch = binding.Batch(nbs, ps)
-    starts = [_starts(nbs[k], ps[k], net, ts[k], bs[k], x0s[k], fls[k]) for k in range(len(ens))]
+    starts = [_starts(nbs[k], ps[k], net, ts[k], bs[k], x0s[k], fls[k], net_hp) for k in range(len(ens))]
     eres = {}
-    for name in ("zero", "vn", "vn_walls", "learned"):
+    for name in names:
         for k in range(len(ens)):
             starts[k][name](xs[k])
         batch.solve(opts, bs, xs)                      # warm-up

@@ -325,6 +325,15 @@ sph_status sph_mlp_train_step(sph_mlp* mlp, const uint16_t* feats, const float* 
                               const uint8_t* mask, int64_t m, int64_t count, float lr, float* loss_host,
                               void* stream);
 
+/* Network modes (bit flags, sph_mlp_set_mode).  SPH_MLP_HIGHPASS: the fluid
+ * correction is y - S y instead of y, where (S y)_b is the Shepard average
+ * sum_a W_ab V_a y_a / sum_a W_ab V_a over the fluid neighbours a of b and b
+ * itself (V = m / rho): only the part of the correction that varies on the
+ * particle scale enters x0, and its smooth part -- which the previous velocity
+ * already carries and which the iteration removes slowest -- is left to v. */
+#define SPH_MLP_HIGHPASS 1
+sph_status sph_mlp_set_mode(sph_mlp* mlp, int32_t mode);
+
 /* Loss options of sph_mlp_residual_targets (bit flags). */
 #define SPH_RLOSS_JACOBI 1 /* weight the residual by D^-1 (default: unweighted)      */
 #define SPH_RLOSS_LOG 2    /* per-problem log loss log(sum w^2|r|^2 / sum |b|^2)    */
@@ -342,8 +351,10 @@ sph_status sph_mlp_train_step(sph_mlp* mlp, const uint16_t* feats, const float* 
  * (device [n][4] float; mask = fluid, device [n] u8) make the mean-squared-error
  * gradient of sph_mlp_grad / sph_mlp_train_step with count = the fluid count
  * equal to dL/dparameters.  feats (device [n][16] bf16) receives the features;
- * loss_host (may be NULL; synchronises) the loss L.  Unknown flags:
- * SPH_ERR_INVALID. */
+ * loss_host (may be NULL; synchronises) the loss L.  With SPH_MLP_HIGHPASS set
+ * on the network, x0 uses y - S y and the targets carry (I - S)^T in front of
+ * A (w^2 r), the transpose gathered over the same symmetric neighbour sets.
+ * Unknown flags: SPH_ERR_INVALID. */
 sph_status sph_mlp_residual_targets(sph_neighbors* handle, const sph_visc_params* params,
                                     const sph_mlp* mlp, const float* vel, const uint8_t* ptype,
                                     const double* b, int flags, uint16_t* feats, float* targets,

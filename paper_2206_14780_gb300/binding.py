@@ -30,7 +30,7 @@ EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", 
            "sph_batch_create", "sph_batch_solve", "sph_batch_info", "sph_batch_destroy",
            "sph_mlp_create", "sph_mlp_set_params", "sph_mlp_get_params", "sph_mlp_destroy", "sph_mlp_features",
            "sph_mlp_targets", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train_step", "sph_warm_start",
-           "sph_mlp_residual_targets"]
+           "sph_mlp_residual_targets", "sph_mlp_set_mode"]
 MLP_NPARAMS = 9603
 
 
@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH):
         "sph_mlp_grad": [vp, vp, vp, vp, i64, i64, vp, vp, vp],
         "sph_mlp_train_step": [vp, vp, vp, vp, i64, i64, ctypes.c_float, ctypes.POINTER(ctypes.c_float), vp],
         "sph_warm_start": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp, vp, vp, vp],
+        "sph_mlp_set_mode": [vp, ctypes.c_int32],
         "sph_mlp_residual_targets": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp, vp, ctypes.c_int, vp, vp,
                                      vp, ctypes.POINTER(dbl), vp],
         "sph_profile_read": [vp, ctypes.POINTER(sph_profile_counters), i32],
@@ -353,6 +354,10 @@ class Mlp:
         _check(_lib.sph_mlp_get_params(self.handle, p.ctypes.data_as(ctypes.c_void_p)))
         return p
 
+    def set_mode(self, mode):
+        """sph_mlp_set_mode (MLP_HIGHPASS: the x0 correction is y - S y)."""
+        _check(_lib.sph_mlp_set_mode(self.handle, int(mode)))
+
     def forward(self, feats, out, stream=None):
         _check(_lib.sph_mlp_forward(self.handle, _ptr(feats), int(feats.shape[0]), _ptr(out), _stream(stream)))
 
@@ -391,6 +396,7 @@ def mlp_targets(nb, vel, x_star, ptype, targets, mask, stream=None):
                                 _stream(stream)))
 
 
+MLP_HIGHPASS = 1
 RLOSS_JACOBI = 1
 RLOSS_LOG = 2
 

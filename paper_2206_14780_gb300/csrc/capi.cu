@@ -138,6 +138,8 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
   h->feat_scale.release();
   h->feat_out.release();
   h->feat_delta.release();
+  h->feat_hp.release();
+  h->feat_den.release();
   h->v_xh.release();
   h->v_xl.release();
   h->tmp_i32a.release();

@@ -27,6 +27,7 @@ namespace sph {
 
 sph_status mlp_forward_launch(const sph_mlp* M, const __nv_bfloat16* feats, int64_t m, float4* out, int num_sms,
                               cudaStream_t st);
+int mlp_mode(const sph_mlp* M);
 
 namespace {
 
@@ -73,6 +74,129 @@ __global__ void __launch_bounds__(kBlock) k_feat_scale(const float4* __restrict_
     __shared__ double res[2];
     final_sum<2>(partials, counter, res);
     if (threadIdx.x < 2) out[threadIdx.x] = res[threadIdx.x];
+  }
+}
+
+// d_i <- d_i - (S d)_i on fluid rows (caller order in and out, thread per sorted
+// row): the Shepard average over fluid neighbours and the particle itself
+__global__ void __launch_bounds__(kBlock) k_highpass(const float4* __restrict__ pos, const float* __restrict__ rho,
+                                                     const uint8_t* __restrict__ type,
+                                                     const int32_t* __restrict__ cnt,
+                                                     const int64_t* __restrict__ slice_off,
+                                                     const int32_t* __restrict__ nbr, const int32_t* __restrict__ perm,
+                                                     int64_t n, float L0, float L1, float L2, float iL0, float iL1,
+                                                     float iL2, int p0, int p1, int p2, float inv_h,
+                                                     const float4* __restrict__ d, float4* __restrict__ out) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = perm[s];
+    const float4 di = d[i];
+    if (type[s] != SPH_FLUID) {
+      out[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const float4 pb = pos[s];
+    float wsum = pb.w / rho[s];   // W(0) = 1 in the units of the weights below
+    float sx = wsum * di.x, sy = wsum * di.y, sz = wsum * di.z;
+    const int c = cnt[s];
+    const int64_t base = slice_off[s / kSlice] + (s % kSlice);
+    for (int j = 0; j < c; ++j) {
+      const int32_t t = nbr[base + (int64_t)j * kSlice];
+      if (type[t] != SPH_FLUID) continue;
+      const float4 pa = pos[t];
+      float dx = pa.x - pb.x, dy = pa.y - pb.y, dz = pa.z - pb.z;
+      if (p0) dx -= L0 * rintf(dx * iL0);
+      if (p1) dy -= L1 * rintf(dy * iL1);
+      if (p2) dz -= L2 * rintf(dz * iL2);
+      const float q = sqrtf(dx * dx + dy * dy + dz * dz) * inv_h;
+      const float tw = fmaxf(1.f - 0.5f * q, 0.f);
+      const float tw2 = tw * tw;
+      const float w = tw2 * tw2 * fmaf(2.f, q, 1.f) * (pa.w / rho[t]);   // Wendland, constant factor dropped
+      const float4 da = d[perm[t]];
+      sx = fmaf(w, da.x, sx);
+      sy = fmaf(w, da.y, sy);
+      sz = fmaf(w, da.z, sz);
+      wsum += w;
+    }
+    const float iw = 1.f / wsum;
+    out[i] = make_float4(di.x - sx * iw, di.y - sy * iw, di.z - sz * iw, 0.f);
+  }
+}
+
+// Shepard denominators N_s = sum over {s} and its fluid neighbours of W V (sorted,
+// fluid rows; 1 on walls), in the weights of k_highpass
+__global__ void __launch_bounds__(kBlock) k_shep_den(const float4* __restrict__ pos, const float* __restrict__ rho,
+                                                     const uint8_t* __restrict__ type,
+                                                     const int32_t* __restrict__ cnt,
+                                                     const int64_t* __restrict__ slice_off,
+                                                     const int32_t* __restrict__ nbr, int64_t n, float L0, float L1,
+                                                     float L2, float iL0, float iL1, float iL2, int p0, int p1, int p2,
+                                                     float inv_h, float* __restrict__ den) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    if (type[s] != SPH_FLUID) {
+      den[s] = 1.f;
+      continue;
+    }
+    const float4 pb = pos[s];
+    float wsum = pb.w / rho[s];
+    const int c = cnt[s];
+    const int64_t base = slice_off[s / kSlice] + (s % kSlice);
+    for (int j = 0; j < c; ++j) {
+      const int32_t t = nbr[base + (int64_t)j * kSlice];
+      if (type[t] != SPH_FLUID) continue;
+      const float4 pa = pos[t];
+      float dx = pa.x - pb.x, dy = pa.y - pb.y, dz = pa.z - pb.z;
+      if (p0) dx -= L0 * rintf(dx * iL0);
+      if (p1) dy -= L1 * rintf(dy * iL1);
+      if (p2) dz -= L2 * rintf(dz * iL2);
+      const float q = sqrtf(dx * dx + dy * dy + dz * dz) * inv_h;
+      const float tw = fmaxf(1.f - 0.5f * q, 0.f);
+      const float tw2 = tw * tw;
+      wsum += tw2 * tw2 * fmaf(2.f, q, 1.f) * (pa.w / rho[t]);
+    }
+    den[s] = wsum;
+  }
+}
+
+// out_b = q_b - (S^T q)_b on fluid rows (sorted), (S^T q)_b = V_b sum over a in {b}
+// and the fluid neighbours of b of W_ab q_a / N_a; 0 on walls
+__global__ void __launch_bounds__(kBlock) k_highpass_T(const float4* __restrict__ pos, const float* __restrict__ rho,
+                                                       const uint8_t* __restrict__ type,
+                                                       const int32_t* __restrict__ cnt,
+                                                       const int64_t* __restrict__ slice_off,
+                                                       const int32_t* __restrict__ nbr, int64_t n, float L0, float L1,
+                                                       float L2, float iL0, float iL1, float iL2, int p0, int p1,
+                                                       int p2, float inv_h, const float* __restrict__ den,
+                                                       const float4* __restrict__ q, float4* __restrict__ out) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    if (type[s] != SPH_FLUID) {
+      out[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const float4 pb = pos[s];
+    const float4 qb = q[s];
+    const float ib = 1.f / den[s];
+    float sx = qb.x * ib, sy = qb.y * ib, sz = qb.z * ib;   // the a = b term, W(0) = 1
+    const int c = cnt[s];
+    const int64_t base = slice_off[s / kSlice] + (s % kSlice);
+    for (int j = 0; j < c; ++j) {
+      const int32_t t = nbr[base + (int64_t)j * kSlice];
+      if (type[t] != SPH_FLUID) continue;
+      const float4 pa = pos[t];
+      float dx = pa.x - pb.x, dy = pa.y - pb.y, dz = pa.z - pb.z;
+      if (p0) dx -= L0 * rintf(dx * iL0);
+      if (p1) dy -= L1 * rintf(dy * iL1);
+      if (p2) dz -= L2 * rintf(dz * iL2);
+      const float qq = sqrtf(dx * dx + dy * dy + dz * dz) * inv_h;
+      const float tw = fmaxf(1.f - 0.5f * qq, 0.f);
+      const float tw2 = tw * tw;
+      const float w = tw2 * tw2 * fmaf(2.f, qq, 1.f) / den[t];
+      const float4 qa = q[t];
+      sx = fmaf(w, qa.x, sx);
+      sy = fmaf(w, qa.y, sy);
+      sz = fmaf(w, qa.z, sz);
+    }
+    const float Vb = pb.w / rho[s];
+    out[s] = make_float4(qb.x - Vb * sx, qb.y - Vb * sy, qb.z - Vb * sz, 0.f);
   }
 }
 
@@ -316,6 +440,37 @@ static void wall_closure(sph_neighbors* H, double* x0, const double* b, cudaStre
   SPH_LAUNCH(k_wall_close, grid_for(H, H->n), kBlock, 0, st)(ax, b, H->perm.p, H->type_s.p, H->n, x0);
 }
 
+// out = delta - S delta (SPH_MLP_HIGHPASS), caller order, out != delta
+static void highpass(sph_neighbors* H, const float4* delta, float4* out, cudaStream_t st) {
+  float L[3], iL[3];
+  for (int k = 0; k < 3; ++k) {
+    L[k] = (float)H->grid.L[k];
+    iL[k] = (float)(1.0 / H->grid.L[k]);
+  }
+  SPH_LAUNCH(k_highpass, grid_for(H, H->n), kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->type_s.p, H->cnt.p, H->slice_off.p,
+                                                           H->nbr.p, H->perm.p, H->n, L[0], L[1], L[2], iL[0], iL[1],
+                                                           iL[2], H->grid.periodic[0], H->grid.periodic[1],
+                                                           H->grid.periodic[2], (float)(1.0 / (double)H->h), delta,
+                                                           out);
+}
+
+// out = q - S^T q (sorted, fluid rows) with the Shepard denominators in den
+static void highpass_T(sph_neighbors* H, const float4* q, float* den, float4* out, cudaStream_t st) {
+  float L[3], iL[3];
+  for (int k = 0; k < 3; ++k) {
+    L[k] = (float)H->grid.L[k];
+    iL[k] = (float)(1.0 / H->grid.L[k]);
+  }
+  const float ih = (float)(1.0 / (double)H->h);
+  const int* pr = H->grid.periodic;
+  SPH_LAUNCH(k_shep_den, grid_for(H, H->n), kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->type_s.p, H->cnt.p,
+                                                           H->slice_off.p, H->nbr.p, H->n, L[0], L[1], L[2], iL[0],
+                                                           iL[1], iL[2], pr[0], pr[1], pr[2], ih, den);
+  SPH_LAUNCH(k_highpass_T, grid_for(H, H->n), kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->type_s.p, H->cnt.p,
+                                                             H->slice_off.p, H->nbr.p, H->n, L[0], L[1], L[2], iL[0],
+                                                             iL[1], iL[2], pr[0], pr[1], pr[2], ih, den, q, out);
+}
+
 }  // namespace sph
 
 using namespace sph;
@@ -370,6 +525,11 @@ sph_status sph_warm_start(sph_neighbors* h, const sph_visc_params* params, const
     SPH_TRY(features_impl(h, params, vel, f, st));
     SPH_TRY(mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st));
     delta = h->feat_delta.p;
+    if (mlp_mode(mlp) & SPH_MLP_HIGHPASS) {
+      SPH_TRY(h->feat_hp.alloc(h->n));
+      highpass(h, h->feat_delta.p, h->feat_hp.p, st);
+      delta = h->feat_hp.p;
+    }
   } else {
     SPH_TRY(ensure_operator(h, params, st));
     SPH_TRY(ensure_workspace(h));
@@ -405,9 +565,17 @@ sph_status sph_mlp_residual_targets(sph_neighbors* h, const sph_visc_params* par
   SPH_TRY(h->x64.alloc(3 * h->n_pad));
   SPH_TRY(h->r64.alloc(3 * h->n_pad));
   SPH_TRY(mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st));
+  const bool hp = (mlp_mode(mlp) & SPH_MLP_HIGHPASS) != 0;
+  const float4* dx0 = h->feat_delta.p;
+  if (hp) {
+    SPH_TRY(h->feat_hp.alloc(h->n));
+    SPH_TRY(h->feat_den.alloc(h->n_pad));
+    highpass(h, h->feat_delta.p, h->feat_hp.p, st);
+    dx0 = h->feat_hp.p;
+  }
   double* x0 = h->x64.p;
-  SPH_LAUNCH(k_warm_x0, grid_for(h, h->n), kBlock, 0, st)(reinterpret_cast<const float4*>(vel), h->feat_delta.p, ptype,
-                                                          b, h->n, h->feat_scale.p, x0);
+  SPH_LAUNCH(k_warm_x0, grid_for(h, h->n), kBlock, 0, st)(reinterpret_cast<const float4*>(vel), dx0, ptype, b, h->n,
+                                                          h->feat_scale.p, x0);
   wall_closure(h, x0, b, st);
   const int64_t np = h->n_pad;
   float4* xs = h->feat_tmp.p;
@@ -421,7 +589,12 @@ sph_status sph_mlp_residual_targets(sph_neighbors* h, const sph_visc_params* par
   SPH_LAUNCH(k_resid_z, rg, kBlock, 0, st)(ax, b, h->perm.p, h->type_s.p, h->invD.p, (flags & SPH_RLOSS_JACOBI) ? 1 : 0,
                                            h->n, np, z, h->partials.p, h->counters.p + 7, sums);
   launch_apply_f32(h, z, az, false, st);
-  SPH_LAUNCH(k_resid_targets, grid_for(h, h->n), kBlock, 0, st)(h->feat_delta.p, az, h->perm.p, h->type_s.p, h->n,
+  const float4* grad = az;
+  if (hp) {                           // P^T = I - S^T in front of A z (slot 0 is free again)
+    highpass_T(h, az, h->feat_den.p, xs, st);
+    grad = xs;
+  }
+  SPH_LAUNCH(k_resid_targets, grid_for(h, h->n), kBlock, 0, st)(h->feat_delta.p, grad, h->perm.p, h->type_s.p, h->n,
                                                                 h->feat_scale.p, sums, (flags & SPH_RLOSS_LOG) ? 1 : 0,
                                                                 reinterpret_cast<float4*>(targets), mask);
   SPH_TRY_CUDA(cudaGetLastError());

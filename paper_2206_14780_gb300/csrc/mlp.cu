@@ -52,6 +52,7 @@ struct sph_mlp {
   sph::DBuf<sph::MlpPack> pack;
   sph::DBuf<int> fault;          // set when a tensor-core forward gave up a wait
   int64_t step = 0;
+  int mode = 0;                  // SPH_MLP_HIGHPASS: x0 correction is y - S y
   int partial_blocks = 0;
 };
 
@@ -415,6 +416,7 @@ int mlp_train_smem() {
 }
 
 const void* mlp_pack_ptr(const sph_mlp* M) { return M->pack.p; }
+int mlp_mode(const sph_mlp* M) { return M ? M->mode : 0; }
 
 void mlp_pack_layout(size_t* off_w1, size_t* off_w2, size_t* off_w3, size_t* off_w4, size_t* off_b) {
   *off_w1 = offsetof(MlpPack, W1);
@@ -513,6 +515,16 @@ sph_status sph_mlp_get_params(const sph_mlp* M, float* params) {
   }
   SPH_TRY_CUDA(cudaMemcpy(params, M->theta.p, kNP * 4, cudaMemcpyDeviceToHost));
   return check_fault(M);
+}
+
+sph_status sph_mlp_set_mode(sph_mlp* M, int32_t mode) {
+  clear_error();
+  if (!M || (mode & ~SPH_MLP_HIGHPASS)) {
+    set_error("sph_mlp_set_mode: null network or unknown mode bits %d", mode);
+    return SPH_ERR_INVALID;
+  }
+  M->mode = mode;
+  return SPH_OK;
 }
 
 sph_status sph_mlp_destroy(sph_mlp* M) {

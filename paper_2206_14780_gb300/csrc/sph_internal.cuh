@@ -210,6 +210,8 @@ struct sph_neighbors {
   sph::DBuf<double> feat_scale;      // sum |v|^2 and count over the fluid
   sph::DBuf<uint32_t> feat_out;      // bf16 features [n][16]
   sph::DBuf<float4> feat_delta;      // network output [n]
+  sph::DBuf<float4> feat_hp;         // high-passed network output [n] (caller order)
+  sph::DBuf<float> feat_den;         // Shepard denominators [n_pad] (sorted)
 
   // float64 solve vectors r, r0^, p, Ap, r*, Ar* ([n_pad][3] each)
   sph::DBuf<double> w64[7];

@@ -197,7 +197,7 @@ FAMILIES = ["couette", "slope", "box", "couette_big", "slope_big", "box_big"]
 
 
 def train(steps, scenes_per_step, lr0, seed, init_seed=0, log=print, dev=None, flags=2, mse_data=None,
-          mse_batch=32768):
+          mse_batch=32768, mode=0):
     """Adam on the residual loss over freshly drawn problems; with mse_data =
     (feats, targets) every other step is a mean-squared-error step on (x* - v) / U
     instead.  Returns (net, stats)."""
@@ -208,6 +208,7 @@ def train(steps, scenes_per_step, lr0, seed, init_seed=0, log=print, dev=None, f
     rng = np.random.default_rng(seed)
     fams = [Family(k, j, dev) for j, k in enumerate(FAMILIES)]
     net = binding.Mlp(_init_params(init_seed))
+    net.set_mode(mode)
     ones = torch.ones(mse_batch, dtype=torch.uint8, device=dev)
     bufs = []
     for fam in fams:
@@ -239,7 +240,7 @@ def train(steps, scenes_per_step, lr0, seed, init_seed=0, log=print, dev=None, f
         hist.append(float(np.mean(Ls)))
         if (k + 1) % 500 == 0:
             log(f"  step {k + 1}: residual loss {np.mean(hist[-100:]):.4e} ({time.time() - t0:.1f} s)")
-    return net, dict(steps=steps, scenes_per_step=scenes_per_step, lr0=lr0, loss_flags=flags,
+    return net, dict(steps=steps, scenes_per_step=scenes_per_step, lr0=lr0, loss_flags=flags, mode=mode,
                      mixed_mse=mse_data is not None,
                      first_loss=float(np.mean(hist[:50])), final_loss=float(np.mean(hist[-100:])),
                      train_seconds=time.time() - t0)
@@ -315,6 +316,7 @@ def main(argv=None):
     ap.add_argument("--solves", type=int, default=20000, help="generated solves (mse loss)")
     ap.add_argument("--per-solve", type=int, default=256)
     ap.add_argument("--batch", type=int, default=32768)
+    ap.add_argument("--highpass", action="store_true", help="x0 correction y - S y (SPH_MLP_HIGHPASS)")
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     args = ap.parse_args(argv)
     import torch
@@ -340,13 +342,14 @@ def main(argv=None):
         flags = {"plain": 0, "jacobi": binding.RLOSS_JACOBI, "log": binding.RLOSS_LOG,
                  "log-jacobi": binding.RLOSS_LOG | binding.RLOSS_JACOBI}[loss]
         net, tstats = train(args.steps, args.scenes_per_step, args.lr, args.seed, dev=dev, flags=flags,
-                            mse_data=mse_data, mse_batch=args.batch)
+                            mse_data=mse_data, mse_batch=args.batch,
+                            mode=binding.MLP_HIGHPASS if args.highpass else 0)
         if gstats:
             tstats["generation"] = gstats
     ev = evaluate(net, args.eval, 7, dev)
     print("held-out:", json.dumps(ev), flush=True)
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
-    meta = dict(train=tstats, seed=args.seed, heldout=ev)
+    meta = dict(train=tstats, seed=args.seed, heldout=ev, mode=int(tstats.get("mode", 0)))
     np.savez(args.out, params=net.params(), meta=json.dumps(meta))
     print(json.dumps(meta), flush=True)
 

@@ -1,6 +1,7 @@
 """Warm start on the GPU: the dummy-wall closure and the residual training targets
 against the float64 oracle, and the trained network's gain over the previous-step
 start on held-out problems."""
+import json
 import os
 
 import numpy as np
@@ -55,9 +56,10 @@ def test_wall_closure_matches_oracle(make):
     assert np.abs(r[~fl]).max() <= 1e-5 * np.abs(s.b).max() + 1e-5 * np.abs(got).max()
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("flags", [2, 3, 0, 1])
 @pytest.mark.parametrize("make", SCENES[:2] + SCENES[3:])
-def test_residual_targets_match_oracle(make, flags):
+def test_residual_targets_match_oracle(make, flags, mode):
     torch = torch_cuda()
     from paper_2206_14780_gb300 import binding
 
@@ -67,6 +69,7 @@ def test_residual_targets_match_oracle(make, flags):
     vt = torch.from_numpy(v).cuda()
     b = torch.from_numpy(s.b).cuda()
     net = binding.Mlp(_net_params(3))
+    net.set_mode(mode)
     p = params_for(s)
     feats = torch.empty((s.n, 16), dtype=torch.int16, device="cuda")
     tg = torch.empty((s.n, 4), dtype=torch.float32, device="cuda")
@@ -81,7 +84,8 @@ def test_residual_targets_match_oracle(make, flags):
     off, idx = onb.build(s.pos, s.lo, s.hi, s.periodic, s.h)
     A = oop.assemble(s, off, idx)
     jac, lg = bool(flags & binding.RLOSS_JACOBI), bool(flags & binding.RLOSS_LOG)
-    t_ref, _, L_ref = ows.residual_targets(A, s.b, v, yg, s.ptype, U, jac, lg)
+    S = ows.shepard_matrix(s, off, idx) if mode else None
+    t_ref, _, L_ref = ows.residual_targets(A, s.b, v, yg, s.ptype, U, jac, lg, S)
     fl = s.ptype == scenes.FLUID
     np.testing.assert_array_equal(mask.cpu().numpy(), fl.astype(np.uint8))
     step = tg.cpu().numpy()[:, :3].astype(np.float64) - yg[:, :3]
@@ -92,6 +96,40 @@ def test_residual_targets_match_oracle(make, flags):
         assert abs(L - L_ref) <= 2e-3, (L, L_ref)
     else:
         assert abs(L - L_ref) <= 2e-3 * abs(L_ref), (L, L_ref)
+
+
+@pytest.mark.parametrize("make", SCENES)
+def test_highpass_start_matches_oracle(make):
+    """x0 = v + U (y - S y) on fluid rows (Shepard average S), walls closed."""
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    s = make()
+    nb, t = lib_build(s)
+    v = _rough(s, 4)
+    vt = torch.from_numpy(v).cuda()
+    b = torch.from_numpy(s.b).cuda()
+    net = binding.Mlp(_net_params(5))
+    net.set_mode(binding.MLP_HIGHPASS)
+    x0 = torch.empty_like(b)
+    p = params_for(s)
+    binding.warm_start(nb, p, net, vt, t["ptype"], b, x0)
+    feats = torch.empty((s.n, 16), dtype=torch.int16, device="cuda")
+    U = binding.mlp_features(nb, p, vt, feats)
+    y = torch.empty((s.n, 4), dtype=torch.float32, device="cuda")
+    net.forward(feats, y)
+    torch.cuda.synchronize()
+    off, idx = onb.build(s.pos, s.lo, s.hi, s.periodic, s.h)
+    A = oop.assemble(s, off, idx)
+    S = ows.shepard_matrix(s, off, idx)
+    ref = ows.start(A, s.b, v, y.cpu().numpy().astype(np.float64), s.ptype, U, S)
+    got = x0.cpu().numpy()
+    fl = s.ptype == scenes.FLUID
+    corr, corr_ref = got[fl] - v[fl, :3], ref[fl] - v[fl, :3]
+    assert rel_l2(corr, corr_ref) <= 1e-4, rel_l2(corr, corr_ref)
+    assert rel_l2(got[~fl], ref[~fl]) <= 1e-5
+    with pytest.raises(binding.SphError):
+        net.set_mode(2)
 
 
 def test_residual_targets_reject_unknown_flags():
@@ -118,7 +156,9 @@ def test_trained_network_beats_previous_step_start():
     from paper_2206_14780_gb300 import train_warmstart as tw
 
     assert os.path.exists(tw.DEFAULT_WEIGHTS)
-    net = binding.Mlp(np.load(tw.DEFAULT_WEIGHTS)["params"])
+    z = np.load(tw.DEFAULT_WEIGHTS)
+    net = binding.Mlp(z["params"])
+    net.set_mode(int(json.loads(str(z["meta"])).get("mode", 0)) if "meta" in z else 0)
     dev = torch.device("cuda", 0)
     fams = [tw.Family(k, 2000 + j, dev) for j, k in enumerate(["couette", "slope", "box"])]
     rng = np.random.default_rng(2024)
