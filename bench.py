@@ -364,8 +364,10 @@ def run_sphvisc(args):
                            f"(N={rows[0]['n']}), {sec:.1f} s, scaled linearly by particle count to N={s.n}; "
                            f"BiCGSTAB iteration counts depend on dt*nu/dx^2, not on N"))
     apply_forms = None
+    channel = None
     if world == 1:
         apply_forms = run_apply_forms(nb, params, s.n, dev)
+        channel = run_channel(dev)
     sequence = None
     if not args.no_sequence and world == 1:
         sequence = run_sequence(nb, s, b, t, args.sequence_steps, dev)
@@ -399,6 +401,7 @@ def run_sphvisc(args):
                            ms_per_step_min=min(per_step), ms_per_step_max=max(per_step)),
                roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), ensemble=ensemble,
                precision_study=precision, sequence=sequence, learned=learned, apply_forms=apply_forms,
+               channel=channel,
                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"],
                            samples=clk["samples"]),
                wall_s=wall)
@@ -407,6 +410,49 @@ def run_sphvisc(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ channel ---------
+
+def run_channel(dev, reps=10):
+    """Plane Couette channel of 1,000,000 fluid particles (200 x 50 x 100, dx = 0.01 m, 3+3
+    dummy wall layers, periodic x and z, top wall at 1 m/s, nu = 1, dt = 1e-4: the paper's
+    mild stiffness, dt nu / dx^2 = 1): ms per step (neighbours + A(dt) + x0 + solve to 1e-6)."""
+    import torch
+
+    import scenes
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.couette(0, nx=200, ny=50, nz=100)
+    t = binding.scene_tensors(s, dev)
+    t["vel"] = torch.from_numpy(s.vel).to(dev)
+    p = binding.visc_params(s.dt, s.boundary, s.mean)
+    geo = (s.lo, s.hi, s.periodic, s.h)
+    nb = binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], *geo)
+    b = torch.from_numpy(s.b).to(dev)
+    x = torch.empty_like(b)
+    opts = binding.solve_opts()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        nb.rebuild(t["pos"], t["rho"], t["mu"], t["ptype"], *geo)
+        binding.warm_start(nb, p, None, t["vel"], t["ptype"], b, x)
+        return nb.solve(p, opts, b, x)
+
+    for _ in range(3):
+        step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    reps_ = [step() for _ in range(reps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    nb.close()
+    return dict(workload="plane Couette channel 200x50x100 fluid (N=1,120,000), dx=0.01, nu=1, dt=1e-4, "
+                         "top wall 1 m/s, v = linear profile + 1% noise", particles=s.n, ms_per_step=ms,
+                iters=[r["iters"] for r in reps_][:3], passes=reps_[0]["refinements"],
+                max_true_rel_res=max(r["true_rel_res"] for r in reps_))
 
 
 # --------------------------------------------------------- network forward ----

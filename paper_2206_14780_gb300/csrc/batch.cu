@@ -55,7 +55,7 @@ struct BatchCtrl {
 };
 
 struct BatchVecs {
-  float4 *r, *rh, *p, *Ap, *rs, *As, *d, *xh, *xl;
+  float4 *r, *rh, *p, *Ap, *rs, *As, *d, *x2;   // x2: x split hi, lo interleaved [2 rows]
   double *x64, *b64, *r64;
 };
 
@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(kBlock) kb_split(BatchView B, int64_t nrows) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nrows; s += (int64_t)gridDim.x * blockDim.x) {
     const double x0 = B.V.x64[3 * s], x1 = B.V.x64[3 * s + 1], x2 = B.V.x64[3 * s + 2];
     const float h0 = (float)x0, h1 = (float)x1, h2 = (float)x2;
-    B.V.xh[s] = make_float4(h0, h1, h2, 0.f);
-    B.V.xl[s] = make_float4((float)(x0 - (double)h0), (float)(x1 - (double)h1), (float)(x2 - (double)h2), 0.f);
+    B.V.x2[2 * s] = make_float4(h0, h1, h2, 0.f);
+    B.V.x2[2 * s + 1] = make_float4((float)(x0 - (double)h0), (float)(x1 - (double)h1), (float)(x2 - (double)h2), 0.f);
   }
 }
 
@@ -182,12 +182,11 @@ __global__ void __launch_bounds__(kBlock) kb_residual(BatchView B) {
       const int64_t sl = B.tile_slice0[t] + w;
       const int64_t s = sl * kSlice + lane;
       const OpView& op = d.op;
-      const float4* xh = B.V.xh + d.row_off;
-      const float4* xl = B.V.xl + d.row_off;
+      const float4* x2 = B.V.x2 + 2 * d.row_off;
       const uint8_t k = op.kind[s];
       const float kap = (k == KIND_FLUID) ? 1.f : 0.f;
       DFAcc a0, a1, a2;
-      residual_row_df(op, d.op_lo, xh, xl, sl, lane, kap, xh[s], xl[s], a0, a1, a2);
+      residual_row_df(op, d.op_lo, x2, sl, lane, kap, a0, a1, a2);
       const double sg = (k == KIND_FLUID) ? 1.0 : (k == KIND_SHEPARD ? -1.0 : 0.0);
       const int64_t g = d.row_off + s;
       double r[3] = {0.0, 0.0, 0.0};
@@ -523,7 +522,7 @@ BatchView batch_view(sph_batch* Bt, double rtol, double eps) {
   B.nscenes = Bt->nscenes;
   float4* v = Bt->vec.p;
   const int64_t N = Bt->nrows;
-  B.V = BatchVecs{v, v + N, v + 2 * N, v + 3 * N, v + 4 * N, v + 5 * N, v + 6 * N, v + 7 * N, v + 8 * N,
+  B.V = BatchVecs{v, v + N, v + 2 * N, v + 3 * N, v + 4 * N, v + 5 * N, v + 6 * N, v + 7 * N,
                   Bt->dvec.p, Bt->dvec.p + 3 * N, Bt->dvec.p + 6 * N};
   B.S = Bt->S.p;
   B.partials = Bt->partials.p;

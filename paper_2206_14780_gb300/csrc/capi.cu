@@ -140,8 +140,7 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
   h->feat_delta.release();
   h->feat_hp.release();
   h->feat_den.release();
-  h->v_xh.release();
-  h->v_xl.release();
+  h->v_x2.release();
   h->tmp_i32a.release();
   h->tmp_i32b.release();
   h->tmp_i64.release();

@@ -233,13 +233,12 @@ __global__ void k_scatter_f4(const float4* __restrict__ y_s, const int32_t* __re
 }
 
 // x64 -> float32 hi + lo (x = hi + lo to ~2^-48 relative)
-__global__ void k_split_x(const double* __restrict__ x, int64_t n_pad, float4* __restrict__ xh,
-                          float4* __restrict__ xl) {
+__global__ void k_split_x(const double* __restrict__ x, int64_t n_pad, float4* __restrict__ x2) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
-    const double x0 = x[3 * s], x1 = x[3 * s + 1], x2 = x[3 * s + 2];
-    const float h0 = (float)x0, h1 = (float)x1, h2 = (float)x2;
-    xh[s] = make_float4(h0, h1, h2, 0.f);
-    xl[s] = make_float4((float)(x0 - (double)h0), (float)(x1 - (double)h1), (float)(x2 - (double)h2), 0.f);
+    const double x0 = x[3 * s], x1 = x[3 * s + 1], x2c = x[3 * s + 2];
+    const float h0 = (float)x0, h1 = (float)x1, h2 = (float)x2c;
+    x2[2 * s] = make_float4(h0, h1, h2, 0.f);
+    x2[2 * s + 1] = make_float4((float)(x0 - (double)h0), (float)(x1 - (double)h1), (float)(x2c - (double)h2), 0.f);
   }
 }
 
@@ -247,7 +246,7 @@ __global__ void k_split_x(const double* __restrict__ x, int64_t n_pad, float4* _
 // arithmetic per pair and float64 per row; partial sums of r_c^2 (K = 3) go
 // through the grid reduction into res_out[0..3) when partials is given.
 __global__ void __launch_bounds__(kBlock) k_residual_df(OpView op, const float* __restrict__ op_lo,
-                                                        const float4* __restrict__ xh, const float4* __restrict__ xl,
+                                                        const float4* __restrict__ x2,
                                                         const double* __restrict__ x, const double* __restrict__ b,
                                                         double* __restrict__ r, int64_t n, double* __restrict__ partials,
                                                         unsigned int* counter, double* __restrict__ res_out) {
@@ -259,7 +258,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_df(OpView op, const float* 
     const uint8_t k = op.kind[s];
     const float kap = (k == KIND_FLUID) ? 1.f : 0.f;
     DFAcc a0, a1, a2;
-    residual_row_df(op, op_lo, xh, xl, sl, lane, kap, xh[s], xl[s], a0, a1, a2);
+    residual_row_df(op, op_lo, x2, sl, lane, kap, a0, a1, a2);
     const double sg = (k == KIND_FLUID) ? 1.0 : (k == KIND_SHEPARD ? -1.0 : 0.0);
     double r0 = 0.0, r1 = 0.0, r2 = 0.0;
     if (s < n) {
@@ -334,8 +333,8 @@ sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStrea
 
 void launch_residual_f64(const sph_neighbors* H, int grid, const double* x, const double* b, double* r,
                          double* partials, unsigned int* counter, double* res_out, cudaStream_t st) {
-  SPH_LAUNCH(k_split_x, grid_for(H, H->n_pad), kBlock, 0, st)(x, H->n_pad, H->v_xh.p, H->v_xl.p);
-  SPH_LAUNCH(k_residual_df, grid, kBlock, 0, st)(op_view(H), H->op_lo.p, H->v_xh.p, H->v_xl.p, x, b, r, H->n,
+  SPH_LAUNCH(k_split_x, grid_for(H, H->n_pad), kBlock, 0, st)(x, H->n_pad, H->v_x2.p);
+  SPH_LAUNCH(k_residual_df, grid, kBlock, 0, st)(op_view(H), H->op_lo.p, H->v_x2.p, x, b, r, H->n,
                                                  partials, counter, res_out);
 }
 

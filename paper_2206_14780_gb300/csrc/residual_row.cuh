@@ -1,7 +1,8 @@
 // One row of the float64-accurate residual's operator sum, shared by the
 // single-scene and batched residual kernels: sum over the row's stored entries
-// of a_ba (kap x_b - x_a) per component, with a = hi + lo and x = xh + xl, in
-// double-float arithmetic (DFAcc).
+// of a_ba (kap x_b - x_a) per component, with a = hi + lo and x = hi + lo, in
+// double-float arithmetic (DFAcc).  x is interleaved: x2[2 t] = hi, x2[2 t + 1]
+// = lo, so one gather reads both halves from the same 32-byte sector.
 //
 // Entries are taken in groups of kResU: the group's coefficient loads, then its
 // gathers of xh and xl, then the error-free sums, so each thread keeps kResU
@@ -17,10 +18,10 @@ namespace sph {
 constexpr int kResU = 4;
 
 __device__ __forceinline__ void residual_row_df(const OpView& op, const float* __restrict__ op_lo,
-                                                const float4* __restrict__ xh, const float4* __restrict__ xl,
-                                                int64_t sl, int lane, float kap, float4 bh, float4 bl, DFAcc& a0,
-                                                DFAcc& a1, DFAcc& a2) {
+                                                const float4* __restrict__ x2, int64_t sl, int lane, float kap,
+                                                DFAcc& a0, DFAcc& a1, DFAcc& a2) {
   const int64_t s = sl * kSlice + lane;
+  const float4 bh = x2[2 * s], bl = x2[2 * s + 1];
   const int c = op.cnt[s];
   const float kbh0 = kap * bh.x, kbh1 = kap * bh.y, kbh2 = kap * bh.z;
   const float kbl0 = kap * bl.x, kbl1 = kap * bl.y, kbl2 = kap * bl.z;
@@ -38,8 +39,8 @@ __device__ __forceinline__ void residual_row_df(const OpView& op, const float* _
     float4 ah[kResU], al[kResU];
 #pragma unroll
     for (int u = 0; u < kResU; ++u) {
-      ah[u] = __ldg(xh + ih[u].x);
-      al[u] = __ldg(xl + ih[u].x);
+      ah[u] = __ldg(x2 + 2 * (int64_t)ih[u].x);
+      al[u] = __ldg(x2 + 2 * (int64_t)ih[u].x + 1);
     }
 #pragma unroll
     for (int u = 0; u < kResU; ++u) {

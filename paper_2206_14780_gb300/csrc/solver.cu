@@ -590,8 +590,7 @@ sph_status ensure_workspace(sph_neighbors* H) {
   SPH_TRY(H->x64.alloc(3 * np));
   SPH_TRY(H->b64.alloc(3 * np));
   SPH_TRY(H->r64.alloc(3 * np));
-  SPH_TRY(H->v_xh.alloc(np));
-  SPH_TRY(H->v_xl.alloc(np));
+  SPH_TRY(H->v_x2.alloc(2 * np));
   if (H->red_grid == 0) {
     int occ = 0;
     // the largest grid any apply variant runs with (partials are sized for it)

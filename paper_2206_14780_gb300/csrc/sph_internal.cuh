@@ -169,7 +169,7 @@ struct sph_neighbors {
   // solver workspace
   sph::DBuf<float4> v_r, v_rh, v_p, v_Ap, v_rs, v_As, v_d, v_tmp;
   sph::DBuf<double> x64, b64, r64;   // [n_pad][3]
-  sph::DBuf<float4> v_xh, v_xl;      // x64 split into float32 hi + lo (double-float residual)
+  sph::DBuf<float4> v_x2;            // x64 split into float32 hi, lo interleaved [2 n_pad] (residual)
   sph::DBuf<double> partials;        // [grid][kMaxDots]
   sph::DBuf<unsigned int> counters;  // last-block counters
   sph::DBuf<unsigned int> counters64;  // last-block counters of the float64 solve
