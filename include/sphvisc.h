@@ -251,8 +251,9 @@ sph_status sph_visc_solve(sph_neighbors* handle, const sph_visc_params* params,
  * scene (scenes at rtol drop out on the device), pass set-up, ONE persistent
  * cooperative kernel running the iterations of all active scenes, and x += d.
  * Grid barriers inside the persistent kernel wait a bounded time and report
- * SPH_ERR_TIMEOUT instead of hanging.  The persistent kernel's row-loop form is
- * autotuned on the first solve. */
+ * SPH_ERR_TIMEOUT instead of hanging.  The persistent kernel's row-loop form
+ * and block size (256 or 128 threads per 32-slice tile) are autotuned on the
+ * first solve. */
 typedef struct sph_batch sph_batch;
 
 /* handles: (host) [nscenes] built handles; params: (host) [nscenes] A(dt)
@@ -270,9 +271,10 @@ sph_status sph_batch_create(sph_neighbors* const* handles, const sph_visc_params
 sph_status sph_batch_solve(sph_batch* batch, const sph_solve_opts* opts, const double* const* b,
                            double* const* x, sph_solve_report* reports, void* stream);
 
-/* The autotuned row-loop form (0..3, as in sph_profile_counters), whether the
+/* The autotuned persistent-kernel variant (0..7: row-loop form v & 3 as in
+ * sph_profile_counters, block size 256 (v < 4) or 128 threads), whether the
  * pass runs as a captured graph (1) or as direct launches (0), the tuning
- * times (ms, [4]) and the persistent grid size.  Any pointer may be NULL. */
+ * times (ms, [8]) and the chosen variant's grid size.  Any pointer may be NULL. */
 sph_status sph_batch_info(const sph_batch* batch, int32_t* variant, int32_t* graph, float* tune_ms,
                           int32_t* grid);
 

@@ -314,7 +314,7 @@ class Batch:
 
     def info(self):
         v, g, grid = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        t = (ctypes.c_float * 4)()
+        t = (ctypes.c_float * 8)()
         _check(_lib.sph_batch_info(self.handle, ctypes.byref(v), ctypes.byref(g), t, ctypes.byref(grid)))
         return dict(variant=v.value, graph=bool(g.value), tune_ms=list(t), grid=grid.value)
 

@@ -121,7 +121,7 @@ __device__ __forceinline__ bool arrive_scene(unsigned int* cnt, int ntiles_scene
 }
 
 // sum of the partials of tiles [b, e) -> res[0..K) (shared), counter re-armed
-template <int K>
+template <int K, int NB = kBlock>
 __device__ __forceinline__ void scene_sum(const double* partials, int b, int e, unsigned int* cnt, double* res) {
   double acc[K];
 #pragma unroll
@@ -130,7 +130,7 @@ __device__ __forceinline__ void scene_sum(const double* partials, int b, int e, 
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] += __ldcg(partials + (size_t)t * kMaxDots + k);
   }
-  __shared__ double sm[kBlock / 32][K];
+  __shared__ double sm[NB / 32][K];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -143,14 +143,14 @@ __device__ __forceinline__ void scene_sum(const double* partials, int b, int e, 
   if (threadIdx.x < K) {
     double s = 0.0;
 #pragma unroll
-    for (int w = 0; w < kBlock / 32; ++w) s += sm[w][threadIdx.x];
+    for (int w = 0; w < NB / 32; ++w) s += sm[w][threadIdx.x];
     res[threadIdx.x] = s;
   }
   if (threadIdx.x == 0) *cnt = 0u;
   __syncthreads();
 }
 
-// rows of tile t handled by this thread: local rows first, first + 256, ... < end
+// rows of tile t handled by this thread: local rows first, first + blockDim.x, ... < end
 __device__ __forceinline__ void tile_rows(const BatchView& B, int t, int64_t& first, int64_t& end) {
   first = (int64_t)B.tile_slice0[t] * kSlice + threadIdx.x;
   end = ((int64_t)B.tile_slice0[t] + B.tile_nsl[t]) * kSlice;
@@ -268,8 +268,8 @@ __global__ void __launch_bounds__(kBlock) kb_init(BatchView B) {
 
 // One BiCGSTAB pass for every active scene: loops over iterations until no
 // scene progresses, with a grid barrier between the phases of an iteration.
-template <int U, bool PF>
-__global__ void __launch_bounds__(kBlock) kb_pass(BatchView B, int iter_cap) {
+template <int U, bool PF, int NB>
+__global__ void __launch_bounds__(NB) kb_pass(BatchView B, int iter_cap) {
   for (int it = 0; it < iter_cap; ++it) {
     if (*(volatile int32_t*)&B.ctrl->active == 0) break;
     // phase 1: p = r + beta p - alpha' Ap
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kBlock) kb_pass(BatchView B, int iter_cap) {
       const bool useP = b0 != 0.f || b1 != 0.f || b2 != 0.f, useA = a0 != 0.f || a1 != 0.f || a2 != 0.f;
       int64_t s0, s1;
       tile_rows(B, t, s0, s1);
-      for (int64_t s = s0; s < s1; s += kBlock) {
+      for (int64_t s = s0; s < s1; s += NB) {
         const int64_t g = d.row_off + s;
         float4 p = B.V.r[g];
         if (useP) {
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kBlock) kb_pass(BatchView B, int iter_cap) {
       const SceneDesc& d = B.sc[sc];
       float acc[3] = {0.f, 0.f, 0.f};
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      for (int w = warp; w < B.tile_nsl[t]; w += kBlock / 32) {
+      for (int w = warp; w < B.tile_nsl[t]; w += NB / 32) {
         const int64_t sl = B.tile_slice0[t] + w;
         float4 vb;
         const float4 o = apply_row<U, PF, true>(d.op, B.V.p + d.row_off, sl, lane, vb);
@@ -322,10 +322,10 @@ __global__ void __launch_bounds__(kBlock) kb_pass(BatchView B, int iter_cap) {
         acc[1] = fmaf(h.y, o.y, acc[1]);
         acc[2] = fmaf(h.z, o.z, acc[2]);
       }
-      block_partials<3>(acc, B.partials + (size_t)t * kMaxDots);
+      block_partials<3, NB>(acc, B.partials + (size_t)t * kMaxDots);
       if (arrive_scene(B.scene_cnt + sc, d.tile_end - d.tile_begin)) {
         __shared__ double res[3];
-        scene_sum<3>(B.partials, d.tile_begin, d.tile_end, B.scene_cnt + sc, res);
+        scene_sum<3, NB>(B.partials, d.tile_begin, d.tile_end, B.scene_cnt + sc, res);
         if (threadIdx.x == 0) scal_after_delta(S, res);
       }
     }
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kBlock) kb_pass(BatchView B, int iter_cap) {
       const float a0 = (float)S->alpha[0], a1 = (float)S->alpha[1], a2 = (float)S->alpha[2];
       int64_t s0, s1;
       tile_rows(B, t, s0, s1);
-      for (int64_t s = s0; s < s1; s += kBlock) {
+      for (int64_t s = s0; s < s1; s += NB) {
         const int64_t g = d.row_off + s;
         const float4 r = B.V.r[g], ap = B.V.Ap[g];
         B.V.rs[g] = make_float4(fmaf(-a0, ap.x, r.x), fmaf(-a1, ap.y, r.y), fmaf(-a2, ap.z, r.z), 0.f);
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kBlock) kb_pass(BatchView B, int iter_cap) {
       const SceneDesc& d = B.sc[sc];
       float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      for (int w = warp; w < B.tile_nsl[t]; w += kBlock / 32) {
+      for (int w = warp; w < B.tile_nsl[t]; w += NB / 32) {
         const int64_t sl = B.tile_slice0[t] + w;
         float4 vb;
         const float4 o = apply_row<U, PF, true>(d.op, B.V.rs + d.row_off, sl, lane, vb);
@@ -367,10 +367,10 @@ __global__ void __launch_bounds__(kBlock) kb_pass(BatchView B, int iter_cap) {
         acc[4] = fmaf(o.y, o.y, acc[4]);
         acc[5] = fmaf(o.z, o.z, acc[5]);
       }
-      block_partials<6>(acc, B.partials + (size_t)t * kMaxDots);
+      block_partials<6, NB>(acc, B.partials + (size_t)t * kMaxDots);
       if (arrive_scene(B.scene_cnt + sc, d.tile_end - d.tile_begin)) {
         __shared__ double res[6];
-        scene_sum<6>(B.partials, d.tile_begin, d.tile_end, B.scene_cnt + sc, res);
+        scene_sum<6, NB>(B.partials, d.tile_begin, d.tile_end, B.scene_cnt + sc, res);
         if (threadIdx.x == 0) scal_after_omega(S, res);
       }
     }
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(kBlock) kb_pass(BatchView B, int iter_cap) {
       const float l0 = (float)S->alpha[0], l1 = (float)S->alpha[1], l2 = (float)S->alpha[2];
       int64_t s0, s1;
       tile_rows(B, t, s0, s1);
-      for (int64_t s = s0; s < s1; s += kBlock) {
+      for (int64_t s = s0; s < s1; s += NB) {
         const int64_t g = d.row_off + s;
         const float4 rs = B.V.rs[g], as = B.V.As[g], h = B.V.rh[g], p = B.V.p[g];
         float4 dd = B.V.d[g];
@@ -403,10 +403,10 @@ __global__ void __launch_bounds__(kBlock) kb_pass(BatchView B, int iter_cap) {
         acc[4] = fmaf(r.y, r.y, acc[4]);
         acc[5] = fmaf(r.z, r.z, acc[5]);
       }
-      block_partials<6>(acc, B.partials + (size_t)t * kMaxDots);
+      block_partials<6, NB>(acc, B.partials + (size_t)t * kMaxDots);
       if (arrive_scene(B.scene_cnt + sc, d.tile_end - d.tile_begin)) {
         __shared__ double res[6];
-        scene_sum<6>(B.partials, d.tile_begin, d.tile_end, B.scene_cnt + sc, res);
+        scene_sum<6, NB>(B.partials, d.tile_begin, d.tile_end, B.scene_cnt + sc, res);
         if (threadIdx.x == 0) {
           scal_after_update(S, res, res + 3);
           B.total_iters[sc] += 1;
@@ -467,15 +467,23 @@ __global__ void kb_norm2(const double* __restrict__ b, int64_t n_pad, double* ou
   }
 }
 
+// variants 0..7: row-loop form (v & 3: (U, PF) = (8,0), (4,0), (8,1), (4,1)) and
+// block size (v >> 2: 256 or 128 threads, 8 or 4 warps per 32-slice tile)
+constexpr int kPassVariants = 8;
 using PassFn = void (*)(BatchView, int);
 PassFn pass_kernel(int variant) {
   switch (variant) {
-    case 1: return kb_pass<4, false>;
-    case 2: return kb_pass<8, true>;
-    case 3: return kb_pass<4, true>;
-    default: return kb_pass<8, false>;
+    case 1: return kb_pass<4, false, 256>;
+    case 2: return kb_pass<8, true, 256>;
+    case 3: return kb_pass<4, true, 256>;
+    case 4: return kb_pass<8, false, 128>;
+    case 5: return kb_pass<4, false, 128>;
+    case 6: return kb_pass<8, true, 128>;
+    case 7: return kb_pass<4, true, 128>;
+    default: return kb_pass<8, false, 256>;
   }
 }
+int pass_block(int variant) { return (variant >> 2) == 1 ? 128 : 256; }
 
 }  // namespace
 
@@ -501,9 +509,10 @@ struct sph_batch {
   DBuf<int32_t> iters, passes, stalled;
   DBuf<BatchCtrl> ctrl;
   BatchCtrl* host_ctrl = nullptr;
-  int variant = -1;            // autotuned row-loop form of the persistent kernel
-  int grid = 0;
-  float tune_ms[4] = {0, 0, 0, 0};
+  int variant = -1;            // autotuned form (row loop, block size) of the persistent kernel
+  int grid = 0;                // grid of the auxiliary kernels
+  int grids[kPassVariants] = {};   // co-resident grid of each persistent-kernel variant
+  float tune_ms[kPassVariants] = {};
   cudaGraphExec_t graph = nullptr;
   bool graph_ok = false;
   double graph_rtol = -1.0, graph_eps = -1.0;
@@ -543,8 +552,9 @@ sph_status launch_pass(sph_batch* Bt, const BatchView& B, int cap, cudaStream_t 
   int c = cap;
   void* args[] = {&bv, &c};
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(Bt->grid);
-  cfg.blockDim = dim3(kBlock);
+  const int var = Bt->variant < 0 ? 0 : Bt->variant;
+  cfg.gridDim = dim3(Bt->grids[var]);
+  cfg.blockDim = dim3(pass_block(var));
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -658,15 +668,15 @@ sph_status sph_batch_create(sph_neighbors* const* handles, const sph_visc_params
     set_error("sph_batch_create: upload failed");
     return fail(SPH_ERR_CUDA);
   }
-  // grid of the cooperative kernel: every block resident at once
-  int occ = 0;
-  for (int v = 0; v < 4; ++v) {
+  // grid of each cooperative variant: every block resident at once
+  for (int v = 0; v < kPassVariants; ++v) {
     int o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, (const void*)pass_kernel(v), kBlock, 0);
-    occ = (v == 0 || o < occ) ? o : occ;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, (const void*)pass_kernel(v), pass_block(v), 0);
+    int g = Bt->num_sms * (o > 0 ? o : 1);
+    if (g > Bt->ntiles) g = Bt->ntiles;
+    Bt->grids[v] = g;
   }
-  Bt->grid = Bt->num_sms * (occ > 0 ? occ : 1);
-  if (Bt->grid > Bt->ntiles) Bt->grid = Bt->ntiles;
+  Bt->grid = Bt->grids[0];
   *out = Bt;
   return SPH_OK;
 #undef BTRY
@@ -751,8 +761,8 @@ sph_status sph_batch_solve(sph_batch* Bt, const sph_solve_opts* O, const double*
   const BatchView B = batch_view(Bt, rtol, eps);
   const int cap = maxit;
 
-  // autotune the persistent kernel's row-loop form once: one pass per form from
-  // the same start, timed with events, keeping the fastest
+  // autotune the persistent kernel once over its row-loop forms and block sizes:
+  // one pass per variant from the same start, timed with events, keeping the fastest
   if (Bt->variant < 0) {
     cudaEvent_t e0, e1;
     SPH_TRY_CUDA(cudaEventCreate(&e0));
@@ -761,7 +771,7 @@ sph_status sph_batch_solve(sph_batch* Bt, const sph_solve_opts* O, const double*
     SPH_TRY_CUDA(cudaMemcpyAsync(x0save, Bt->dvec.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     float best = 1e30f;
     int bestv = 0;
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < kPassVariants; ++v) {
       Bt->variant = v;
       SPH_TRY_CUDA(cudaMemcpyAsync(Bt->dvec.p, x0save, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
       SPH_TRY_CUDA(cudaMemsetAsync(Bt->iters.p, 0, S * sizeof(int32_t), st));
@@ -881,9 +891,9 @@ sph_status sph_batch_info(const sph_batch* Bt, int32_t* variant, int32_t* graph,
   }
   if (variant) *variant = Bt->variant;
   if (graph) *graph = Bt->graph_ok ? 1 : 0;
-  if (grid) *grid = Bt->grid;
+  if (grid) *grid = Bt->grids[Bt->variant < 0 ? 0 : Bt->variant];
   if (tune_ms4)
-    for (int v = 0; v < 4; ++v) tune_ms4[v] = Bt->tune_ms[v];
+    for (int v = 0; v < kPassVariants; ++v) tune_ms4[v] = Bt->tune_ms[v];
   return SPH_OK;
 }
 

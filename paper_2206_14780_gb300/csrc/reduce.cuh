@@ -11,9 +11,9 @@
 
 namespace sph {
 
-template <int K>
+template <int K, int NB = kBlock>
 __device__ __forceinline__ void block_partials(const float (&v)[K], double* __restrict__ out) {
-  __shared__ double sm[kBlock / 32][K > 0 ? K : 1];
+  __shared__ double sm[NB / 32][K > 0 ? K : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -26,7 +26,7 @@ __device__ __forceinline__ void block_partials(const float (&v)[K], double* __re
   if (threadIdx.x < K) {
     double s = 0.0;
 #pragma unroll
-    for (int w = 0; w < kBlock / 32; ++w) s += sm[w][threadIdx.x];
+    for (int w = 0; w < NB / 32; ++w) s += sm[w][threadIdx.x];
     out[threadIdx.x] = s;
   }
 }

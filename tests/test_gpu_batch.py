@@ -30,7 +30,7 @@ def test_batch_matches_oracle_per_scene():
     st, reps = batch.solve(binding.solve_opts(), bs, xs)
     assert st == 0, reps
     info = batch.info()
-    assert 0 <= info["variant"] < 4 and info["grid"] > 0
+    assert 0 <= info["variant"] < 8 and info["grid"] > 0 and len(info["tune_ms"]) == 8
     for s, x, rep in zip(ens, xs, reps):
         off, idx, A = oracle_system(s)
         xg = x.cpu().numpy()
