@@ -59,6 +59,8 @@ def parse(argv=None):
     ap.add_argument("--merged", type=int, default=0)
     ap.add_argument("--eps-inner", type=float, default=1e-2)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--launch-mode", type=int, default=0, choices=[0, 1],
+                    help="0: dependent launches in the solve loop (default); 1: plain stream order")
     ap.add_argument("--cpu-oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -254,7 +256,7 @@ def run_sphvisc(args):
     binding.load()
     s = scenes.lava_box(replica_seed(rank), n=args.n)
     params = binding.visc_params(s.dt, s.boundary, s.mean)
-    opts = binding.solve_opts(merged_reductions=args.merged, eps_inner=args.eps_inner,
+    opts = binding.solve_opts(merged_reductions=args.merged, eps_inner=args.eps_inner, launch_mode=args.launch_mode,
                               precision=binding.SPH_PREC_FP64 if args.precision == "fp64" else binding.SPH_PREC_MIXED)
     t = binding.scene_tensors(s, dev)
     t["vel"] = torch.from_numpy(s.vel).to(dev)
@@ -352,7 +354,9 @@ def run_sphvisc(args):
                     apply_avg_us_Ap=1e3 * prof["phase_ms"][0] / max(1, prof["phase_launches"][0]),
                     apply_avg_us_Ars=1e3 * prof["phase_ms"][1] / max(1, prof["phase_launches"][1]),
                     apply_variant=prof["apply_variant"], autotune_us=prof["tune_us"][:2],
-                    algorithmic_bytes_per_launch=prof["apply_bytes"])
+                    algorithmic_bytes_per_launch=prof["apply_bytes"],
+                    timing="CUDA events on the solve stream around both applies of every 4th BiCGSTAB "
+                           "iteration inside the timed region (launches after convergence excluded)")
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         rows = cpu_oracle_subprocess(args.cpu_n, reps=1)
@@ -392,6 +396,7 @@ def run_sphvisc(args):
                config=dict(workload=workload_name(args.n), n_particles=s.n, rtol=1e-6,
                            precision="f32 operator+vectors, f64 dots/scalars, f64 true-residual refinement",
                            merged_reductions=args.merged, eps_inner=args.eps_inner,
+                           launch_mode="dependent launches" if args.launch_mode == 0 else "stream order",
                            l2="inputs larger than L2 (A(dt) coefficients ~1.5 GB)",
                            step="neighbour build + A(dt) coefficients + x0 (v^n, dummy-wall closure) + "
                                 "restructured BiCGSTAB to 1e-6",

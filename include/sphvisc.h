@@ -92,7 +92,9 @@ typedef struct sph_neighbors sph_neighbors;
  * the float32 positions (a float32 test with a safety band, then a float64
  * recheck inside the band).
  * max_neighbors: capacity per particle, 1..1024; a larger count returns
- *   SPH_ERR_CAPACITY.
+ *   SPH_ERR_CAPACITY.  The lists are built in one pass into a layout of that
+ *   capacity: 4 * max_neighbors bytes of device memory per particle (512 B at
+ *   the default 128).
  * Copies pos/rho/mu/ptype into the handle: the scene arrays may be freed after
  * the call returns. */
 sph_status sph_build_neighbors(const sph_scene* scene, int32_t max_neighbors,
@@ -211,6 +213,10 @@ typedef struct {
   int32_t apply_form;      /* 0: the autotuner picks the operator apply's row-loop
                               form per phase (default); k = 1..6: use form k - 1
                               (sph_profile_counters.apply_variant numbering)     */
+  int32_t launch_mode;     /* 0: the BiCGSTAB loop's kernels are programmatic
+                              dependent launches, each launch processed while its
+                              predecessor still runs (default); 1: plain
+                              stream-ordered launches.  Same results either way   */
 } sph_solve_opts;
 
 typedef struct {
@@ -386,11 +392,12 @@ sph_status sph_mu_papanastasiou(sph_neighbors* handle, const float* vel, const f
 
 /* Instrumentation (tracing): launch counts and the device time of the operator
  * apply inside solves, measured with CUDA events recorded on the solve's own
- * stream around every apply launch.  Off by default; enabling it adds two event
- * records per apply. */
+ * stream around the two apply launches of every fourth BiCGSTAB iteration (a
+ * sample, so that the event records do not slow the loop they time).  Off by
+ * default; enabling it adds two event records per sampled apply. */
 typedef struct {
   int64_t launches;        /* kernels this library launched (all handles, all calls) */
-  int64_t apply_launches;  /* operator applies timed on this handle                  */
+  int64_t apply_launches;  /* operator applies timed on this handle (the sample)     */
   double apply_ms;         /* summed device time of those applies (ms)               */
   int64_t apply_bytes;     /* algorithmic bytes of one apply: 8 per stored
                               coefficient (index + value) plus, per row, 16 read of

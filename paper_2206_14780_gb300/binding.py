@@ -48,7 +48,7 @@ class sph_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("eps_inner", ctypes.c_double), ("maxit", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("merged_reductions", ctypes.c_int32), ("chunk", ctypes.c_int32), ("jacobi", ctypes.c_int32),
-                ("apply_form", ctypes.c_int32)]
+                ("apply_form", ctypes.c_int32), ("launch_mode", ctypes.c_int32)]
 
 
 class sph_solve_report(ctypes.Structure):
@@ -165,9 +165,9 @@ def visc_params(dt, boundary=SPH_BC_DUMMY, mean=SPH_MEAN_HARMONIC):
 
 
 def solve_opts(rtol=1e-6, eps_inner=1e-2, maxit=20000, max_refine=30, precision=SPH_PREC_MIXED,
-               merged_reductions=0, chunk=8, jacobi=1, apply_form=0):
+               merged_reductions=0, chunk=8, jacobi=1, apply_form=0, launch_mode=0):
     return sph_solve_opts(rtol, eps_inner, maxit, max_refine, precision, merged_reductions, chunk, jacobi,
-                          apply_form)
+                          apply_form, launch_mode)
 
 
 def scene_tensors(scene, device="cuda"):

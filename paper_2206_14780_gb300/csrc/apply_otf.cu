@@ -45,15 +45,17 @@ __device__ __forceinline__ float4 apply_row_otf(const OtfView& o, const float4* 
   const int64_t s = sl * kSlice + lane;
   const uint8_t kd = o.kind[s];
   const float4 vb = v[s];
+  const int c = o.cnt[s];
+  // longest list of the slice (the list layout may be wider than that); taken
+  // before any lane leaves, every lane of the warp is here
+  const int w = __reduce_max_sync(0xffffffffu, kd == KIND_IDENTITY ? 0 : c);
   if (kd == KIND_IDENTITY) return make_float4(vb.x, vb.y, vb.z, 0.f);
   const bool fluid = kd == KIND_FLUID;
-  const int c = o.cnt[s];
   const float4 gb = o.g[s];
   const float imb = o.im[s];
   const float Rb = o.rb[s];
   const float mub_wall = HARMONIC ? 1.f / imb : imb;   // fluid-wall pairs: the row's own mu
   const int64_t o0 = o.off[sl];
-  const int w = (int)((o.off[sl + 1] - o0) / kSlice);
   const int32_t* __restrict__ p = o.nbr + o0 + lane;
   float ax = 0.f, ay = 0.f, az = 0.f, sa = 0.f;
   for (int j0 = 0; j0 < w; j0 += kOtfU) {

@@ -25,14 +25,19 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 void prof_begin(sph_neighbors* H, cudaStream_t st, int phase) {
-  if (!H->prof_on || H->prof_used + 2 > 256) return;
+  const int idx = H->prof_seq++;
+  H->prof_armed = false;
+  if (!H->prof_on || H->prof_used + 2 > 256 || (idx >> 1) % kProfStride != 0) return;
   H->prof_phase[H->prof_used / 2] = phase;
+  H->prof_idx[H->prof_used / 2] = idx;
   cudaEventRecord(H->prof_ev[H->prof_used], st);
+  H->prof_armed = true;
 }
 void prof_end(sph_neighbors* H, cudaStream_t st) {
-  if (!H->prof_on || H->prof_used + 2 > 256) return;
+  if (!H->prof_armed) return;
   cudaEventRecord(H->prof_ev[H->prof_used + 1], st);
   H->prof_used += 2;
+  H->prof_armed = false;
 }
 void standalone_begin(sph_neighbors* H, cudaStream_t st) {
   if (H->prof_on && H->sa_ev[0]) cudaEventRecord(H->sa_ev[0], st);
@@ -47,10 +52,11 @@ sph_status standalone_end(sph_neighbors* H, cudaStream_t st, int form) {
   H->sa_n[form] += 1;
   return SPH_OK;
 }
-void prof_flush(sph_neighbors* H, int valid_pairs) {
+void prof_flush(sph_neighbors* H, int valid_launches) {
   if (!H->prof_on) return;
   const int pairs = H->prof_used / 2;
-  for (int k = 0; k < pairs && k < valid_pairs; ++k) {
+  for (int k = 0; k < pairs; ++k) {
+    if (H->prof_idx[k] >= valid_launches) continue;   // launched after convergence: exits at once
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, H->prof_ev[2 * k], H->prof_ev[2 * k + 1]) == cudaSuccess) {
       H->prof_ms += ms;
@@ -61,6 +67,7 @@ void prof_flush(sph_neighbors* H, int valid_pairs) {
     }
   }
   H->prof_used = 0;
+  H->prof_seq = 0;
 }
 
 sph_status set_viscosity_impl(sph_neighbors* H, const float* mu, cudaStream_t st);
@@ -265,6 +272,8 @@ sph_status sph_profile_enable(sph_neighbors* h, int32_t on) {
   }
   h->prof_on = on != 0;
   h->prof_used = 0;
+  h->prof_seq = 0;
+  h->prof_armed = false;
   return SPH_OK;
 }
 

@@ -187,16 +187,19 @@ struct Band {
   float L[3], invL[3];
 };
 
-template <bool FILL>
+// One pass over the 27 cells around each particle: the count and the list at
+// once.  Lists live in a fixed-capacity SELL-32 layout (every slice maxnb
+// entries wide, entry j of row s at (s / 32) 32 maxnb + 32 j + s % 32), so no
+// counting pass has to size them first; a row with more than maxnb neighbours
+// raises FLAG_CAPACITY and keeps its first maxnb.
 __global__ void __launch_bounds__(kBlock) k_neighbors(const float4* __restrict__ pos_s, const int32_t* __restrict__ key_s,
                                                       const int32_t* __restrict__ rank,
                                                       const int32_t* __restrict__ cell_start, int64_t n, int64_t n_pad,
                                                       Grid g, Band band, int32_t maxnb, int32_t* __restrict__ cnt,
-                                                      const int64_t* __restrict__ slice_off, int32_t* __restrict__ nbr,
-                                                      int32_t* __restrict__ flags) {
+                                                      int32_t* __restrict__ nbr, int32_t* __restrict__ flags) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
     if (s >= n) {
-      if (!FILL) cnt[s] = 0;
+      cnt[s] = 0;
       continue;
     }
     const float4 ps = pos_s[s];
@@ -204,8 +207,7 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(const float4* __restrict__
     const int nx = g.ncell[0], ny = g.ncell[1], nz = g.ncell[2];
     const int cx = key % nx, cy = (key / nx) % ny, cz = key / (nx * ny);
     int32_t count = 0;
-    int32_t cap = FILL ? cnt[s] : 0;
-    int64_t base = FILL ? slice_off[s / kSlice] + (s % kSlice) : 0;
+    const int64_t base = (s / kSlice) * (int64_t)kSlice * maxnb + (s % kSlice);
     for (int dz = -1; dz <= 1; ++dz) {
       int z = cz + dz;
       if (g.periodic[2]) z = (z + nz) % nz;
@@ -233,23 +235,25 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(const float4* __restrict__
             else if (r2 >= band.hi2) in = false;
             else in = pair_inside_f64(pt, ps, g, band.R2);
             if (in) {
-              if (FILL) {
-                if (count < cap) nbr[base + (int64_t)count * kSlice] = t;
-              }
+              if (count < maxnb) nbr[base + (int64_t)count * kSlice] = t;
               ++count;
             }
           }
         }
       }
     }
-    if (!FILL) {
-      if (count > maxnb) {
-        atomicOr(&flags[0], FLAG_CAPACITY);
-        count = maxnb;
-      }
-      cnt[s] = count;
+    if (count > maxnb) {
+      atomicOr(&flags[0], FLAG_CAPACITY);
+      count = maxnb;
     }
+    cnt[s] = count;
   }
+}
+
+// slice offsets of the fixed-capacity list layout
+__global__ void k_fixed_offsets(int64_t nslices, int64_t width, int64_t* __restrict__ off) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= nslices; k += (int64_t)gridDim.x * blockDim.x)
+    off[k] = k * kSlice * width;
 }
 
 // slice widths (max count over the 32 rows), total entries and the largest row
@@ -538,13 +542,23 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
   }
 
   int grid_p = grid_for(H, H->n_pad);
-  SPH_LAUNCH(k_neighbors<false>, grid_p, kBlock, 0, st)(H->pos_s.p, H->key_s.p, H->cell_rank.p, H->cell_start.p, n, H->n_pad, g, band, maxnb,
-                                                H->cnt.p, nullptr, nullptr, H->flags.p);
+  TRYF(H->nbr.alloc(H->n_pad * (int64_t)maxnb));
+  SPH_LAUNCH(k_neighbors, grid_p, kBlock, 0, st)(H->pos_s.p, H->key_s.p, H->cell_rank.p, H->cell_start.p, n, H->n_pad, g,
+                                                 band, maxnb, H->cnt.p, H->nbr.p, H->flags.p);
   TRYF_CUDA(cudaGetLastError());
+  SPH_LAUNCH(k_fixed_offsets, grid_for(H, H->nslices + 1), kBlock, 0, st)(H->nslices, maxnb, H->slice_off.p);
+  TRYF_CUDA(cudaGetLastError());
+  // entry total and the longest row (k_slice_width's widths land in scratch)
+  TRYF(H->tmp_i32b.alloc(H->nslices + 1 > ncells ? H->nslices + 1 : ncells));
+  TRYF_CUDA(cudaMemsetAsync(H->tmp_i64.p, 0, 2 * sizeof(int64_t), st));
+  SPH_LAUNCH(k_slice_width, grid_for(H, H->nslices * 32), kBlock, 0, st)(
+      H->cnt.p, H->nslices, H->tmp_i32b.p, reinterpret_cast<unsigned long long*>(H->tmp_i64.p),
+      reinterpret_cast<int32_t*>(H->tmp_i64.p + 1));
+  TRYF_CUDA(cudaGetLastError());
+  int64_t tot[2];
   TRYF_CUDA(cudaMemcpyAsync(hflags, H->flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  int64_t total_pad = 0, total = 0;
-  int32_t maxc = 0;
-  TRYF(build_slices(H, H->cnt.p, H->slice_off.p, &total_pad, &total, &maxc, st));
+  TRYF_CUDA(cudaMemcpyAsync(tot, H->tmp_i64.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TRYF_CUDA(cudaStreamSynchronize(st));
   if (hflags[0] & FLAG_NONFINITE) {
     set_error("sph_build_neighbors: non-finite or non-positive density / viscosity");
     return fail(SPH_ERR_NONFINITE);
@@ -553,10 +567,8 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
     set_error("sph_build_neighbors: a particle has more than max_neighbors = %d neighbours", maxnb);
     return fail(SPH_ERR_CAPACITY);
   }
-  TRYF(H->nbr.alloc(total_pad > 0 ? total_pad : 1));
-  SPH_LAUNCH(k_neighbors<true>, grid_p, kBlock, 0, st)(H->pos_s.p, H->key_s.p, H->cell_rank.p, H->cell_start.p, n, H->n_pad, g, band, maxnb,
-                                               H->cnt.p, H->slice_off.p, H->nbr.p, H->flags.p);
-  TRYF_CUDA(cudaGetLastError());
+  const int64_t total = tot[0], total_pad = H->n_pad * (int64_t)maxnb;
+  const int32_t maxc = (int32_t)(tot[1] & 0xffffffff);
   H->nnz = total;
   H->nnz_pad = total_pad;
   H->max_cnt = maxc;

@@ -245,7 +245,7 @@ __global__ void k_split_x(const double* __restrict__ x, int64_t n_pad, float4* _
 // float64-accurate residual r = b - A x on sorted [n_pad][3] arrays, float32
 // arithmetic per pair and float64 per row; partial sums of r_c^2 (K = 3) go
 // through the grid reduction into res_out[0..3) when partials is given.
-__global__ void __launch_bounds__(kBlock) k_residual_df(OpView op, const float* __restrict__ op_lo,
+__global__ void __launch_bounds__(kBlock, 3) k_residual_df(OpView op, const float* __restrict__ op_lo,
                                                         const float4* __restrict__ x2,
                                                         const double* __restrict__ x, const double* __restrict__ b,
                                                         double* __restrict__ r, int64_t n, double* __restrict__ partials,
@@ -274,6 +274,47 @@ __global__ void __launch_bounds__(kBlock) k_residual_df(OpView op, const float* 
     acc2[2] += r2 * r2;
   }
   if (partials == nullptr) return;
+  block_partials_f64<3>(acc2, partials + (size_t)blockIdx.x * kMaxDots);
+  if (arrive_last(counter)) {
+    __shared__ double res[3];
+    final_sum<3>(partials, counter, res);
+    if (threadIdx.x < 3) res_out[threadIdx.x] = res[threadIdx.x];
+  }
+}
+
+// r64 -= A d for the float32 correction d of a refinement pass (x64 += d runs
+// beside it), so r64 stays b - A x64 without re-reading x in two halves: A d is
+// formed in double-float arithmetic on a = hi + lo, its error a few 2^-46 of the
+// sum of |a_ba (d_b - d_a)|, far below the residual levels the solve resolves.
+// Partial sums of the new r_c^2 go through the grid reduction into res_out.
+__global__ void __launch_bounds__(kBlock, 4) k_residual_update_df(OpView op, const float* __restrict__ op_lo,
+                                                               const float4* __restrict__ d, double* __restrict__ r,
+                                                               int64_t n, double* __restrict__ partials,
+                                                               unsigned int* counter, double* __restrict__ res_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double acc2[3] = {0.0, 0.0, 0.0};
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
+    const int64_t s = sl * kSlice + lane;
+    const uint8_t k = op.kind[s];
+    const float kap = (k == KIND_FLUID) ? 1.f : 0.f;
+    DFAcc a0, a1, a2;
+    float4 db;
+    residual_row_f32x(op, op_lo, d, sl, lane, kap, db, a0, a1, a2);
+    const double sg = (k == KIND_FLUID) ? 1.0 : (k == KIND_SHEPARD ? -1.0 : 0.0);
+    double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+    if (s < n) {
+      r0 = r[3 * s] - ((double)db.x + sg * a0.value());
+      r1 = r[3 * s + 1] - ((double)db.y + sg * a1.value());
+      r2 = r[3 * s + 2] - ((double)db.z + sg * a2.value());
+    }
+    r[3 * s] = r0;
+    r[3 * s + 1] = r1;
+    r[3 * s + 2] = r2;
+    acc2[0] += r0 * r0;
+    acc2[1] += r1 * r1;
+    acc2[2] += r2 * r2;
+  }
   block_partials_f64<3>(acc2, partials + (size_t)blockIdx.x * kMaxDots);
   if (arrive_last(counter)) {
     __shared__ double res[3];
@@ -336,6 +377,12 @@ void launch_residual_f64(const sph_neighbors* H, int grid, const double* x, cons
   SPH_LAUNCH(k_split_x, grid_for(H, H->n_pad), kBlock, 0, st)(x, H->n_pad, H->v_x2.p);
   SPH_LAUNCH(k_residual_df, grid, kBlock, 0, st)(op_view(H), H->op_lo.p, H->v_x2.p, x, b, r, H->n,
                                                  partials, counter, res_out);
+}
+
+void launch_residual_update(const sph_neighbors* H, int grid, const float4* d, double* r, double* partials,
+                            unsigned int* counter, double* res_out, cudaStream_t st) {
+  SPH_LAUNCH(k_residual_update_df, grid, kBlock, 0, st)(op_view(H), H->op_lo.p, d, r, H->n, partials, counter,
+                                                        res_out);
 }
 
 OpView op_view(const sph_neighbors* H) {

@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kBlock) k_pass_init(const double* __restrict__
 
 // p = r + beta p - alpha' Ap
 __global__ void __launch_bounds__(kBlock) k_p_update(int64_t n_pad, Vecs V, const SolverScalars* __restrict__ S) {
+  griddep_wait();
   if (S->done) return;
   const float b0 = (float)S->beta[0], b1 = (float)S->beta[1], b2 = (float)S->beta[2];
   const float a0 = (float)S->alpha_p[0], a1 = (float)S->alpha_p[1], a2 = (float)S->alpha_p[2];
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_apply_dot(OpView op, const float4
                                                       const float4* __restrict__ rh, SolverScalars* S,
                                                       double* partials, unsigned int* counter) {
   constexpr int K = PhaseDots<PH>::K;
+  griddep_wait();
   if (S->done) return;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -215,6 +217,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_apply_dot_staged(OpView op, const
   constexpr int kWarps = kBlock / 32;
   __shared__ __align__(128) int2 sbuf[kWarps][kStageBuf][kStageCh * kSlice];
   __shared__ __align__(8) uint64_t sbar[kWarps][kStageBuf];
+  griddep_wait();
   if (S->done) return;
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
@@ -338,6 +341,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_apply_dot_union(OpView op, const 
                                                             unsigned int* counter) {
   constexpr int K = PhaseDots<PH>::K;
   extern __shared__ __align__(16) float4 vsm[];   // [kBlock / 32][kUnionCap]
+  griddep_wait();
   if (S->done) return;
   const int lane = threadIdx.x & 31;
   float4* vs = vsm + (threadIdx.x >> 5) * kUnionCap;
@@ -453,6 +457,7 @@ namespace {
 
 // r* = r - alpha Ap (the matching d += alpha p is folded into the x/r update)
 __global__ void __launch_bounds__(kBlock) k_rstar(int64_t n_pad, Vecs V, const SolverScalars* __restrict__ S) {
+  griddep_wait();
   if (S->done) return;
   const float a0 = (float)S->alpha[0], a1 = (float)S->alpha[1], a2 = (float)S->alpha[2];
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
@@ -464,6 +469,7 @@ __global__ void __launch_bounds__(kBlock) k_rstar(int64_t n_pad, Vecs V, const S
 // r = r* - omega Ar* ; d += alpha p + omega r* ; dots r0^.r, r.r (paper-exact gamma')
 __global__ void __launch_bounds__(kBlock) k_xr_update(int64_t n_pad, Vecs V, SolverScalars* S, double* partials,
                                                       unsigned int* counter) {
+  griddep_wait();
   if (S->done) return;
   const float w0 = (float)S->omega[0], w1 = (float)S->omega[1], w2 = (float)S->omega[2];
   const float al0 = (float)S->alpha[0], al1 = (float)S->alpha[1], al2 = (float)S->alpha[2];
@@ -497,6 +503,7 @@ __global__ void __launch_bounds__(kBlock) k_xr_update(int64_t n_pad, Vecs V, Sol
 // iteration completes); `pad` carries "skip" and is re-armed by the last block.
 __global__ void __launch_bounds__(kBlock) k_xrp_update(int64_t n_pad, Vecs V, SolverScalars* S,
                                                        unsigned int* counter) {
+  griddep_wait();
   if (S->pad) return;
   const float w0 = (float)S->omega[0], w1 = (float)S->omega[1], w2 = (float)S->omega[2];
   const float b0 = (float)S->beta[0], b1 = (float)S->beta[1], b2 = (float)S->beta[2];
@@ -620,6 +627,17 @@ static int red_grid_for(const sph_neighbors* H, int64_t items) {
   return want < 1 ? 1 : (int)want;
 }
 
+// r64 -= A d after x64 += d, and the new rr[3] (synchronises)
+static sph_status residual_update(sph_neighbors* H, cudaStream_t st, const float4* d, double rr[3]) {
+  const int grid = red_grid_for(H, H->n_pad);
+  double* dev_out = reinterpret_cast<double*>(H->scal.p) + offsetof(SolverScalars, dots) / sizeof(double);
+  launch_residual_update(H, grid, d, H->r64.p, H->partials.p, H->counters.p + CNT_RES, dev_out, st);
+  SPH_TRY_CUDA(cudaGetLastError());
+  SPH_TRY_CUDA(cudaMemcpyAsync(rr, dev_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SPH_TRY_CUDA(cudaStreamSynchronize(st));
+  return SPH_OK;
+}
+
 // r64 = b64 - A x64 and rr[3] into H->host_flags area (synchronises)
 static sph_status true_residual(sph_neighbors* H, cudaStream_t st, double rr[3]) {
   const int grid = red_grid_for(H, H->n_pad);
@@ -631,17 +649,29 @@ static sph_status true_residual(sph_neighbors* H, cudaStream_t st, double rr[3])
   return SPH_OK;
 }
 
+// a kernel of the BiCGSTAB loop: a programmatic dependent launch unless the
+// solve asked for plain stream order (every such kernel starts with griddep_wait)
+template <typename... KArgs, typename... Args>
+static cudaError_t loop_launch(bool pdl, void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t st,
+                               Args... args) {
+  if (pdl) return launch_pdl(kernel, grid, kBlock, smem, st, args...);
+  SPH_LAUNCH(kernel, grid, kBlock, smem, st)(static_cast<KArgs>(args)...);
+  return cudaGetLastError();
+}
+
 template <int PH>
-static void launch_apply_dot(sph_neighbors* H, int grid, const OpView& op, const float4* v, float4* y,
-                             const float4* rh, SolverScalars* S, unsigned int* counter, cudaStream_t st) {
+static cudaError_t launch_apply_dot(sph_neighbors* H, bool pdl, int grid, const OpView& op, const float4* v,
+                                    float4* y, const float4* rh, SolverScalars* S, unsigned int* counter,
+                                    cudaStream_t st) {
   const bool forced = H->force_form >= 0;
   const int var = forced ? H->force_form : H->apply_var[PH];
   const int tg = forced ? H->force_grid : H->apply_grid[PH];
   const int g = tg > 0 && tg < grid ? tg : grid;
   const ApplyDotFn kern = apply_kernel(PH, var);
   prof_begin(H, st, PH == PH_DELTA ? 0 : 1);
-  SPH_LAUNCH(kern, g, kBlock, apply_smem(var), st)(op, v, y, rh, S, H->partials.p, counter);
+  const cudaError_t e = loop_launch(pdl, kern, g, apply_smem(var), st, op, v, y, rh, S, H->partials.p, counter);
   prof_end(H, st);
+  return e;
 }
 
 sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_solve_opts* O, const double* b,
@@ -656,6 +686,10 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
   SPH_TRY(apply_prepare(H, H->apply_var[PH_DELTA], st));
   SPH_TRY(apply_prepare(H, H->apply_var[O->merged_reductions ? PH_OMEGA_MERGED : PH_OMEGA], st));
   H->force_form = -1;
+  if (O->launch_mode < 0 || O->launch_mode > 1) {
+    set_error("sph_visc_solve: launch_mode %d is neither 0 nor 1", O->launch_mode);
+    return SPH_ERR_INVALID;
+  }
   if (O->apply_form < 0 || O->apply_form > kApplyVariants) {
     set_error("sph_visc_solve: apply_form %d outside 0..%d", O->apply_form, kApplyVariants);
     return SPH_ERR_INVALID;
@@ -692,6 +726,7 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
   const int chunk0 = O->chunk > 0 ? O->chunk : 8;
   const bool merged = O->merged_reductions != 0;
   const int jacobi = O->jacobi ? 1 : 0;
+  const bool pdl = O->launch_mode == 0;
 
   std::memset(R, 0, sizeof(*R));
   int total_iters = 0, passes = 0;
@@ -705,14 +740,32 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
   int new_len[sph_neighbors::kPassHist] = {};
   double rr[3] = {0, 0, 0};
   sph_status status = SPH_NOT_CONVERGED;
+  // r64 after a pass comes from the update r64 -= A d (rr_full = false); the
+  // first residual, the one that accepts the solution and the one reported are
+  // recomputed as b - A x64 from x (rr_full = true)
+  bool rr_full = false, have_rr = false;
   for (int ref = 0;; ++ref) {
-    SPH_TRY(true_residual(H, st, rr));
+    if (!have_rr) {
+      SPH_TRY(true_residual(H, st, rr));
+      rr_full = true;
+    }
+    have_rr = false;
     if (!std::isfinite(rr[0]) || !std::isfinite(rr[1]) || !std::isfinite(rr[2])) {
       set_error("sph_visc_solve: the true residual is not finite");
       status = SPH_ERR_NONFINITE;
       break;
     }
-    const double rnorm = std::sqrt(rr[0] + rr[1] + rr[2]);
+    double rnorm = std::sqrt(rr[0] + rr[1] + rr[2]);
+    if (rnorm <= rtol * bnorm && !rr_full) {
+      SPH_TRY(true_residual(H, st, rr));
+      rr_full = true;
+      rnorm = std::sqrt(rr[0] + rr[1] + rr[2]);
+      if (!std::isfinite(rnorm)) {
+        set_error("sph_visc_solve: the true residual is not finite");
+        status = SPH_ERR_NONFINITE;
+        break;
+      }
+    }
     if (rnorm <= rtol * bnorm) {
       status = SPH_OK;
       break;
@@ -729,18 +782,23 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
     int chunk = pred > chunk0 + 2 ? pred - 2 : chunk0;
     int iter_seen = 0;
     for (;;) {
+      cudaError_t le = cudaSuccess;
+      auto keep = [&le](cudaError_t e) {
+        if (le == cudaSuccess) le = e;
+      };
       for (int it = 0; it < chunk; ++it) {
-        if (!merged) SPH_LAUNCH(k_p_update, grid_rows, kBlock, 0, st)(np, V, S);
-        launch_apply_dot<PH_DELTA>(H, grid_slices, op, V.p, V.Ap, V.rh, S, C + CNT_DELTA, st);
-        SPH_LAUNCH(k_rstar, grid_rows, kBlock, 0, st)(np, V, S);
+        if (!merged) keep(loop_launch(pdl, k_p_update, grid_rows, 0, st, np, V, S));
+        keep(launch_apply_dot<PH_DELTA>(H, pdl, grid_slices, op, V.p, V.Ap, V.rh, S, C + CNT_DELTA, st));
+        keep(loop_launch(pdl, k_rstar, grid_rows, 0, st, np, V, S));
         if (merged) {
-          launch_apply_dot<PH_OMEGA_MERGED>(H, grid_slices, op, V.rs, V.As, V.rh, S, C + CNT_OMEGA, st);
-          SPH_LAUNCH(k_xrp_update, grid_rows, kBlock, 0, st)(np, V, S, C + CNT_XRP);
+          keep(launch_apply_dot<PH_OMEGA_MERGED>(H, pdl, grid_slices, op, V.rs, V.As, V.rh, S, C + CNT_OMEGA, st));
+          keep(loop_launch(pdl, k_xrp_update, grid_rows, 0, st, np, V, S, C + CNT_XRP));
         } else {
-          launch_apply_dot<PH_OMEGA>(H, grid_slices, op, V.rs, V.As, V.rh, S, C + CNT_OMEGA, st);
-          SPH_LAUNCH(k_xr_update, grid_rows, kBlock, 0, st)(np, V, S, H->partials.p, C + CNT_XR);
+          keep(launch_apply_dot<PH_OMEGA>(H, pdl, grid_slices, op, V.rs, V.As, V.rh, S, C + CNT_OMEGA, st));
+          keep(loop_launch(pdl, k_xr_update, grid_rows, 0, st, np, V, S, H->partials.p, C + CNT_XR));
         }
       }
+      SPH_TRY_CUDA(le);
       SPH_TRY_CUDA(cudaGetLastError());
       SPH_TRY_CUDA(cudaMemcpyAsync(H->host_scal, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
       SPH_TRY_CUDA(cudaStreamSynchronize(st));
@@ -766,11 +824,16 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
     SPH_TRY_CUDA(cudaGetLastError());
     if (hs.iter == 0) {  // nothing progressed: a further pass would repeat it
       SPH_TRY(true_residual(H, st, rr));
+      rr_full = true;
       const double rnorm2 = std::sqrt(rr[0] + rr[1] + rr[2]);
       status = rnorm2 <= rtol * bnorm ? SPH_OK : SPH_NOT_CONVERGED;
       break;
     }
+    SPH_TRY(residual_update(H, st, V.d, rr));
+    have_rr = true;
+    rr_full = false;
   }
+  if (!rr_full && status != SPH_ERR_NONFINITE) SPH_TRY(true_residual(H, st, rr));
   for (int k = 0; k < sph_neighbors::kPassHist; ++k) H->pass_len[k] = new_len[k];
   SPH_LAUNCH(k_scatter_d3, grid_for(H, H->n), kBlock, 0, st)(H->x64.p, H->perm.p, H->n, x);
   SPH_TRY_CUDA(cudaGetLastError());

@@ -7,7 +7,9 @@
 //   neighbour lists: sliced ELL with slices of 32 rows (SELL-32): row s of
 //   slice k = s / 32 keeps its j-th entry at slice_off[k] + 32 j + (s % 32),
 //   so a warp reading entry j of its 32 rows touches 128 consecutive bytes.
-//   The operator keeps its own SELL-32 (only the entries with a coefficient).
+//   The lists have a fixed capacity (slice_off[k] = 32 k max_neighbors: built
+//   in one pass); the operator keeps its own SELL-32 with each slice as wide as
+//   its longest row (only the entries with a coefficient).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,6 +33,32 @@ void note_launches(int k); // graph replays: the kernels each replay runs
 
 // every kernel launch of the library goes through this macro so it is counted
 #define SPH_LAUNCH(kernel, ...) ::sph::note_launch(), kernel<<<__VA_ARGS__>>>
+
+// Programmatic dependent launch of a kernel of the BiCGSTAB loop: the launch is
+// processed while its predecessor on the stream is still running, and the
+// kernel's first statement, griddep_wait(), holds its threads until that
+// predecessor has completed and its memory is visible (so the data order is
+// the stream's).  No kernel triggers its dependants early: a dependant is
+// scheduled once every block of its predecessor has exited.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  note_launch();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// first statement of every kernel launch_pdl may launch (a no-op otherwise)
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 #define SPH_TRY_CUDA(call)                                                               \
   do {                                                                                   \
@@ -129,7 +157,7 @@ struct sph_neighbors {
   // neighbour SELL-32
   sph::DBuf<int32_t> cnt;          // [n_pad]
   sph::DBuf<int64_t> slice_off;    // [nslices + 1]
-  sph::DBuf<int32_t> nbr;          // [nnz_pad] sorted neighbour index
+  sph::DBuf<int32_t> nbr;          // [nnz_pad = n_pad max_neighbors] neighbour rows
   int64_t nnz = 0, nnz_pad = 0;
   int32_t max_cnt = 0;
 
@@ -197,6 +225,9 @@ struct sph_neighbors {
   double prof_ms = 0.0;
   int64_t prof_n = 0;
   int prof_phase[128] = {};
+  int prof_idx[128] = {};      // launch index within the chunk of each recorded pair
+  int prof_seq = 0;            // apply launches since the last flush
+  bool prof_armed = false;     // the current launch has its begin event recorded
   double prof_ms_ph[2] = {0.0, 0.0};
   int64_t prof_n_ph[2] = {0, 0};
   int64_t op_nnz = 0;
@@ -232,6 +263,9 @@ sph_status export_neighbors(const sph_neighbors* H, int64_t* offsets, int32_t* i
 // operator.cu
 void launch_residual_f64(const sph_neighbors* H, int grid, const double* x, const double* b, double* r,
                          double* partials, unsigned int* counter, double* res_out, cudaStream_t st);
+// r -= A d (sorted [n_pad][3] float64 r, float32 d), same reduction outputs
+void launch_residual_update(const sph_neighbors* H, int grid, const float4* d, double* r, double* partials,
+                            unsigned int* counter, double* res_out, cudaStream_t st);
 sph_status visc_apply(sph_neighbors* H, const sph_visc_params* P, const float* v, float* y, cudaStream_t st);
 sph_status visc_apply_noalloc(sph_neighbors* H, const sph_visc_params* P, const float* v, float* y,
                               cudaStream_t st);
@@ -265,10 +299,13 @@ sph_status solve_fp64(sph_neighbors* H, const sph_visc_params* P, const sph_solv
 
 int grid_for(const sph_neighbors* H, int64_t work_items, int block = kBlock);
 
-// event pair around one apply launch when profiling is on; prof_flush folds
-// the recorded pairs into prof_ms (call only after a stream synchronisation)
+// event pair around the two apply launches of every kProfStride-th iteration
+// when profiling is on (sampling keeps the event records from slowing the
+// loop they time); prof_flush folds the recorded pairs of launches that did
+// work into prof_ms (call only after a stream synchronisation)
+constexpr int kProfStride = 4;
 void prof_begin(sph_neighbors* H, cudaStream_t st, int phase = 0);
 void prof_end(sph_neighbors* H, cudaStream_t st);
-void prof_flush(sph_neighbors* H, int valid_pairs);
+void prof_flush(sph_neighbors* H, int valid_launches);
 
 }  // namespace sph

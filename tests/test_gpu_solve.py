@@ -82,6 +82,26 @@ def test_apply_form_out_of_range_is_rejected():
         gpu_solve(nb, s, binding.solve_opts(apply_form=7))
 
 
+@pytest.mark.parametrize("merged", [0, 1])
+@pytest.mark.parametrize("name", ["couette_dummy", "lava_box_12"])
+def test_dependent_launches_change_nothing(name, merged):
+    """The loop's kernels launched as programmatic dependent launches (the default) and
+    in plain stream order run the same arithmetic in the same order (deterministic
+    reductions): the same x bit for bit, the same iterations and residual."""
+    from paper_2206_14780_gb300 import binding
+
+    s = SCENES_SMALL[name]()
+    nb, _ = lib_build(s)
+    runs = [gpu_solve(nb, s, binding.solve_opts(merged_reductions=merged, launch_mode=m)) for m in (1, 0, 1)]
+    (x1, r1), (x0, r0), (x1b, _) = runs
+    assert r0["status"] == 0 and r1["status"] == 0, (r0, r1)
+    np.testing.assert_array_equal(x1, x1b)
+    np.testing.assert_array_equal(x0, x1)
+    assert r0["iters"] == r1["iters"] and r0["true_rel_res"] == r1["true_rel_res"]
+    with pytest.raises(binding.SphError):
+        gpu_solve(nb, s, binding.solve_opts(launch_mode=2))
+
+
 def test_stiff_box_several_tiles():
     # c2-like stiffness (nu = 10, dt = 5e-4: dt sum c ~ 670) on a 20^3 box
     s = scenes.lava_box(5, n=20)
