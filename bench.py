@@ -353,7 +353,8 @@ def run_sphvisc(args):
                     apply_launches=prof["apply_launches"], apply_avg_us=avg_apply_ms * 1e3,
                     apply_avg_us_Ap=1e3 * prof["phase_ms"][0] / max(1, prof["phase_launches"][0]),
                     apply_avg_us_Ars=1e3 * prof["phase_ms"][1] / max(1, prof["phase_launches"][1]),
-                    apply_variant=prof["apply_variant"], autotune_us=prof["tune_us"][:2],
+                    apply_variant=prof["apply_variant"], apply_grid=prof["apply_grid"],
+                    autotune_us=prof["tune_us"][:2],
                     algorithmic_bytes_per_launch=prof["apply_bytes"],
                     timing="CUDA events on the solve stream around both applies of every 4th BiCGSTAB "
                            "iteration inside the timed region (launches after convergence excluded)")

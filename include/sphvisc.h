@@ -422,6 +422,11 @@ typedef struct {
                                 neighbour-list entry plus, per row, 16 read of v, 16
                                 write, 16 of packed geometry, 4 of 1/mu, 4 of R_b, 4
                                 of the count and 1 of the kind                        */
+  int32_t apply_grid[2];     /* blocks of 256 threads the chosen forms run with, per
+                                phase as apply_variant: the full resident grid, or
+                                for a register form the smallest grid with the same
+                                number of rounds of slices per warp when the tuner
+                                measured that faster                                */
 } sph_profile_counters;
 
 sph_status sph_profile_enable(sph_neighbors* handle, int32_t on);

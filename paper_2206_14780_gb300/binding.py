@@ -63,7 +63,7 @@ class sph_profile_counters(ctypes.Structure):
                 ("phase_launches", ctypes.c_int64 * 2), ("phase_ms", ctypes.c_double * 2),
                 ("apply_variant", ctypes.c_int32 * 2), ("tune_us", (ctypes.c_float * 6) * 3),
                 ("standalone_launches", ctypes.c_int64 * 2), ("standalone_ms", ctypes.c_double * 2),
-                ("otf_bytes", ctypes.c_int64)]
+                ("otf_bytes", ctypes.c_int64), ("apply_grid", ctypes.c_int32 * 2)]
 
 
 class SphError(RuntimeError):
@@ -256,7 +256,8 @@ class Neighbors:
                     apply_bytes=c.apply_bytes, op_nnz=c.op_nnz, phase_launches=list(c.phase_launches),
                     phase_ms=list(c.phase_ms), apply_variant=list(c.apply_variant),
                     tune_us=[list(r) for r in c.tune_us], standalone_launches=list(c.standalone_launches),
-                    standalone_ms=list(c.standalone_ms), otf_bytes=c.otf_bytes)
+                    standalone_ms=list(c.standalone_ms), otf_bytes=c.otf_bytes,
+                    apply_grid=list(c.apply_grid))
 
     def close(self):
         if self.handle:

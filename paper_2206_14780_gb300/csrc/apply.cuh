@@ -31,7 +31,22 @@ struct OpView {
   const int2* loc;       // [op_nnz_pad] (position in the slice's union, coefficient bits)
   const int32_t* uni;    // [op_nnz_pad] the slice's distinct neighbour rows at its offset
   const int32_t* unum;   // [nslices] union size, -1: use ih
+  // balanced slice ranges: warp w of a grid of wpart_nw warps takes the
+  // contiguous slices [wpart[w], wpart[w + 1]), cut so that every warp streams
+  // about the same bytes (null, or another warp count: grid-stride instead).
+  // The float64 residual kernels use them; the apply stays grid-stride.
+  const int32_t* wpart;  // [wpart_nw + 1]
+  int64_t wpart_nw;
 };
+
+// The slices warp gw of nw takes: [first, end) in steps of step.
+struct SliceRange {
+  int64_t first, end, step;
+};
+__device__ __forceinline__ SliceRange warp_slices(const OpView& op, int64_t gw, int64_t nw) {
+  if (op.wpart != nullptr && op.wpart_nw == nw) return SliceRange{op.wpart[gw], op.wpart[gw + 1], 1};
+  return SliceRange{gw, op.nslices, nw};
+}
 
 // Fluid rows: v_b + sum a (v_b - v_a) [times 1/D with Jacobi]; Shepard rows:
 // v_b + sum a v_a; identity rows: v_b.

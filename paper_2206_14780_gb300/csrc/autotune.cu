@@ -42,30 +42,46 @@ sph_status autotune_apply(sph_neighbors* H, bool merged, unsigned int* counter, 
       if (g > want) g = want;
       if (g > H->red_grid) g = H->red_grid;
       if (g < 1) g = 1;
-      for (int k = 0; k < 2; ++k)
-        SPH_LAUNCH(kern, (int)g, kBlock, apply_smem(var), st)(op, H->v_p.p, H->v_As.p, H->v_rh.p, H->scal_tune.p,
-                                                              H->partials.p, counter);
-      cudaEventRecord(e0, st);
-      const int reps = 5;
-      for (int k = 0; k < reps; ++k)
-        SPH_LAUNCH(kern, (int)g, kBlock, apply_smem(var), st)(op, H->v_p.p, H->v_As.p, H->v_rh.p, H->scal_tune.p,
-                                                              H->partials.p, counter);
-      cudaEventRecord(e1, st);
-      cudaError_t err = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-      if (err != cudaSuccess) {
-        set_error("apply autotuner: %s", cudaGetErrorString(err));
-        status = SPH_ERR_CUDA;
-        break;
+      // The full resident grid leaves a ragged last round of slices (warps take
+      // 7 or 8 of them on the 1.16M box); the register forms are also timed with
+      // the smallest grid that needs the same number of rounds, where every warp
+      // takes a full last round.
+      int64_t grids[2] = {g, 0};
+      if (var < kApplyVariantsRegister) {
+        const int64_t wpb = kBlock / 32, rounds = (H->nslices + g * wpb - 1) / (g * wpb);
+        const int64_t gb = (H->nslices + rounds * wpb - 1) / (rounds * wpb);
+        if (gb >= 1 && gb < g) grids[1] = gb;
       }
-      ms /= reps;
-      H->tune_us[ph][var] = 1e3f * ms;
-      if (ms < best) {
-        best = ms;
-        H->apply_var[ph] = var;
-        H->apply_grid[ph] = (int)g;
+      float ms_var = 1e30f;
+      for (int gi = 0; gi < 2 && grids[gi] > 0; ++gi) {
+        const int gg = (int)grids[gi];
+        for (int k = 0; k < 2; ++k)
+          SPH_LAUNCH(kern, gg, kBlock, apply_smem(var), st)(op, H->v_p.p, H->v_As.p, H->v_rh.p, H->scal_tune.p,
+                                                            H->partials.p, counter);
+        cudaEventRecord(e0, st);
+        const int reps = 5;
+        for (int k = 0; k < reps; ++k)
+          SPH_LAUNCH(kern, gg, kBlock, apply_smem(var), st)(op, H->v_p.p, H->v_As.p, H->v_rh.p, H->scal_tune.p,
+                                                            H->partials.p, counter);
+        cudaEventRecord(e1, st);
+        cudaError_t err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess) {
+          set_error("apply autotuner: %s", cudaGetErrorString(err));
+          status = SPH_ERR_CUDA;
+          break;
+        }
+        ms /= reps;
+        ms_var = ms < ms_var ? ms : ms_var;
+        if (ms < best) {
+          best = ms;
+          H->apply_var[ph] = var;
+          H->apply_grid[ph] = gg;
+        }
       }
+      if (status != SPH_OK) break;
+      H->tune_us[ph][var] = 1e3f * ms_var;
     }
   }
   cudaEventDestroy(e0);

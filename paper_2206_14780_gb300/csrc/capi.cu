@@ -303,6 +303,8 @@ sph_status sph_profile_read(sph_neighbors* h, sph_profile_counters* out, int32_t
       out->standalone_ms[f] = h->sa_ms[f];
     }
     out->otf_bytes = 4 * h->nnz + (16 + 16 + 16 + 4 + 4 + 4 + 1) * h->n;
+    out->apply_grid[0] = h->apply_grid[0];
+    out->apply_grid[1] = h->apply_grid[1] > 0 ? h->apply_grid[1] : h->apply_grid[2];
     if (reset) {
       h->prof_n = 0;
       h->prof_ms = 0.0;

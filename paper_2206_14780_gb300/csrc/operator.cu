@@ -245,7 +245,7 @@ __global__ void k_split_x(const double* __restrict__ x, int64_t n_pad, float4* _
 // float64-accurate residual r = b - A x on sorted [n_pad][3] arrays, float32
 // arithmetic per pair and float64 per row; partial sums of r_c^2 (K = 3) go
 // through the grid reduction into res_out[0..3) when partials is given.
-__global__ void __launch_bounds__(kBlock, 3) k_residual_df(OpView op, const float* __restrict__ op_lo,
+__global__ void __launch_bounds__(kBlock, 4) k_residual_df(OpView op, const float* __restrict__ op_lo,
                                                         const float4* __restrict__ x2,
                                                         const double* __restrict__ x, const double* __restrict__ b,
                                                         double* __restrict__ r, int64_t n, double* __restrict__ partials,
@@ -253,7 +253,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_residual_df(OpView op, const floa
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double acc2[3] = {0.0, 0.0, 0.0};
-  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
+  const SliceRange R = warp_slices(op, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nwarps);
+  for (int64_t sl = R.first; sl < R.end; sl += R.step) {
     const int64_t s = sl * kSlice + lane;
     const uint8_t k = op.kind[s];
     const float kap = (k == KIND_FLUID) ? 1.f : 0.f;
@@ -294,7 +295,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_residual_update_df(OpView op, con
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double acc2[3] = {0.0, 0.0, 0.0};
-  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
+  const SliceRange R = warp_slices(op, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nwarps);
+  for (int64_t sl = R.first; sl < R.end; sl += R.step) {
     const int64_t s = sl * kSlice + lane;
     const uint8_t k = op.kind[s];
     const float kap = (k == KIND_FLUID) ? 1.f : 0.f;
@@ -323,7 +325,41 @@ __global__ void __launch_bounds__(kBlock, 4) k_residual_update_df(OpView op, con
   }
 }
 
+// Cut the slices into nw contiguous ranges of about equal streamed bytes: slice
+// k costs 8 B per stored entry slot (its padded width x 32) plus 57 B per row
+// (the row data of the apply), and warp w starts at the first slice whose
+// prefix cost reaches w / nw of the total.
+__global__ void k_wpart(const int64_t* __restrict__ off, int64_t nslices, int64_t nw, int32_t* __restrict__ wpart) {
+  const double row_cost = 57.0 * kSlice;
+  const double total = 8.0 * (double)off[nslices] + row_cost * (double)nslices;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w <= nw; w += (int64_t)gridDim.x * blockDim.x) {
+    if (w == nw) {
+      wpart[w] = (int32_t)nslices;
+      continue;
+    }
+    const double target = total * (double)w / (double)nw;
+    int64_t lo = 0, hi = nslices;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (8.0 * (double)off[mid] + row_cost * (double)mid < target) lo = mid + 1;
+      else hi = mid;
+    }
+    wpart[w] = (int32_t)lo;
+  }
+}
+
 }  // namespace
+
+sph_status ensure_wpart(sph_neighbors* H, int grid, cudaStream_t st) {
+  const int64_t nw = (int64_t)grid * (kBlock / 32);
+  if (H->wpart_nw == nw && H->wpart_version == H->op_version) return SPH_OK;
+  SPH_TRY(H->wpart.alloc(nw + 1));
+  SPH_LAUNCH(k_wpart, grid_for(H, nw + 1), kBlock, 0, st)(H->op_off.p, H->nslices, nw, H->wpart.p);
+  SPH_TRY_CUDA(cudaGetLastError());
+  H->wpart_nw = nw;
+  H->wpart_version = H->op_version;
+  return SPH_OK;
+}
 
 sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStream_t st) {
   if (!P || !(P->dt > 0.0) || !std::isfinite(P->dt) || (P->boundary != SPH_BC_DUMMY && P->boundary != SPH_BC_DYNAMIC) ||
@@ -387,8 +423,10 @@ void launch_residual_update(const sph_neighbors* H, int grid, const float4* d, d
 
 OpView op_view(const sph_neighbors* H) {
   const bool u = H->union_valid && H->union_op_version == H->op_version;
+  const bool wp = H->wpart_version == H->op_version && H->wpart_nw > 0;
   return OpView{H->op_off.p, H->op_cnt.p, H->op_ih.p, H->op_kind.p, H->invD.p, H->nslices, H->n_pad,
-                u ? H->op_loc.p : nullptr, u ? H->uni.p : nullptr, u ? H->unum.p : nullptr};
+                u ? H->op_loc.p : nullptr, u ? H->uni.p : nullptr, u ? H->unum.p : nullptr,
+                wp ? H->wpart.p : nullptr, wp ? H->wpart_nw : 0};
 }
 
 void launch_apply_f32(const sph_neighbors* H, const float4* v, float4* y, bool jacobi, cudaStream_t st) {

@@ -181,6 +181,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_apply_dot(OpView op, const float4
   float acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.f;
+  // grid-stride: at any moment the grid works on one band of consecutive slices,
+  // so the neighbour vectors they gather are shared in L2 across the SMs
+  // (contiguous per-warp ranges, balanced by bytes, measured 9% slower)
   for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
     const int64_t s = sl * kSlice + lane;
     float4 vb;
@@ -678,6 +681,8 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
                        double* x, sph_solve_report* R, cudaStream_t st) {
   SPH_TRY(ensure_operator(H, P, st));
   SPH_TRY(ensure_workspace(H));
+  // balanced slice ranges for the grid of the float64 residual kernels
+  SPH_TRY(ensure_wpart(H, red_grid_for(H, H->n_pad), st));
   SPH_TRY(autotune_apply(H, O->merged_reductions != 0, H->counters.p + CNT_TUNE, st));
   const int64_t np = H->n_pad;
   const int grid_rows = red_grid_for(H, np);
