@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "apply.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -172,6 +173,7 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
   h->op_loc.release();
   h->uni.release();
   h->unum.release();
+  h->wpart.release();
   h->otf_g.release();
   h->otf_im.release();
   h->otf_rb.release();
@@ -297,7 +299,7 @@ sph_status sph_profile_read(sph_neighbors* h, sph_profile_counters* out, int32_t
     out->apply_variant[0] = h->apply_var[0];
     out->apply_variant[1] = h->apply_var[1] > h->apply_var[2] ? h->apply_var[1] : h->apply_var[2];
     for (int ph = 0; ph < 3; ++ph)
-      for (int v = 0; v < 6; ++v) out->tune_us[ph][v] = h->tune_us[ph][v];
+      for (int v = 0; v < kApplyVariants; ++v) out->tune_us[ph][v] = h->tune_us[ph][v];
     for (int f = 0; f < 2; ++f) {
       out->standalone_launches[f] = h->sa_n[f];
       out->standalone_ms[f] = h->sa_ms[f];
