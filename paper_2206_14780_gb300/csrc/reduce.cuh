@@ -11,6 +11,23 @@
 
 namespace sph {
 
+// out[k] = sum over the W warps of sm[w][k] (k < K), as a shuffle tree inside
+// groups of W consecutive lanes: log2(W) dependent float64 additions instead of
+// W - 1.  Every thread of the block calls it (the first warps do the work).
+template <int K, int W>
+__device__ __forceinline__ void cross_warp_sum(const double (*sm)[K > 0 ? K : 1], double* __restrict__ out) {
+  constexpr int N = K * W;
+  constexpr int NT = (N + 31) / 32 * 32;
+  static_assert(32 % W == 0, "W must divide the warp");
+  const int t = threadIdx.x;
+  if (t < NT) {
+    double x = t < N ? sm[t % W][t / W] : 0.0;
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (t < N && t % W == 0) out[t / W] = x;
+  }
+}
+
 template <int K, int NB = kBlock>
 __device__ __forceinline__ void block_partials(const float (&v)[K], double* __restrict__ out) {
   __shared__ double sm[NB / 32][K > 0 ? K : 1];
@@ -23,12 +40,7 @@ __device__ __forceinline__ void block_partials(const float (&v)[K], double* __re
     if (lane == 0) sm[warp][k] = (double)x;
   }
   __syncthreads();
-  if (threadIdx.x < K) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < NB / 32; ++w) s += sm[w][threadIdx.x];
-    out[threadIdx.x] = s;
-  }
+  cross_warp_sum<K, NB / 32>(sm, out);
 }
 
 template <int K>
@@ -43,12 +55,7 @@ __device__ __forceinline__ void block_partials_f64(const double (&v)[K], double*
     if (lane == 0) sm[warp][k] = x;
   }
   __syncthreads();
-  if (threadIdx.x < K) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kBlock / 32; ++w) s += sm[w][threadIdx.x];
-    out[threadIdx.x] = s;
-  }
+  cross_warp_sum<K, kBlock / 32>(sm, out);
 }
 
 // True in every thread of the last block to finish (after its partial is stored).
@@ -82,12 +89,7 @@ __device__ __forceinline__ void final_sum(const double* partials, unsigned int* 
     if (lane == 0) sm[warp][k] = x;
   }
   __syncthreads();
-  if (threadIdx.x < K) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kBlock / 32; ++w) s += sm[w][threadIdx.x];
-    res[threadIdx.x] = s;
-  }
+  cross_warp_sum<K, kBlock / 32>(sm, res);
   if (threadIdx.x == 0) *counter = 0u;
   __syncthreads();
 }

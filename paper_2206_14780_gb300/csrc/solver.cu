@@ -150,19 +150,20 @@ __device__ __forceinline__ void dots_finish(const float (&acc)[PhaseDots<PH>::K]
   if (arrive_last(counter)) {
     __shared__ double res[K];
     final_sum<K>(partials, counter, res);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       if (PH == PH_DELTA) {
-        scal_after_delta(S, res);
+        scal_after_delta_w(S, res);
       } else {
-        scal_after_omega(S, res);
+        scal_after_omega_w(S, res);
         if (PH == PH_OMEGA_MERGED) {
+          __syncwarp();
           double gn[3], rr[3];
           for (int c = 0; c < 3; ++c) {
             const double om = S->omega[c];
             gn[c] = res[6 + c] - om * res[9 + c];
             rr[c] = res[12 + c] - 2.0 * om * res[c] + om * om * res[3 + c];
           }
-          scal_after_update(S, gn, rr);
+          scal_after_update_w(S, gn, rr);
         }
       }
     }
@@ -497,7 +498,7 @@ __global__ void __launch_bounds__(kBlock) k_xr_update(int64_t n_pad, Vecs V, Sol
   if (arrive_last(counter)) {
     __shared__ double res[6];
     final_sum<6>(partials, counter, res);
-    if (threadIdx.x == 0) scal_after_update(S, res, res + 3);
+    if (threadIdx.x < 32) scal_after_update_w(S, res, res + 3);
   }
 }
 
