@@ -443,9 +443,15 @@ size_t apply_smem(int variant) { return variant == 5 ? union_smem_bytes() : 0; }
 static sph_status apply_attrs() {
   static bool done = false;
   if (done) return SPH_OK;
-  for (int ph = 0; ph < 3; ++ph)
+  for (int ph = 0; ph < 3; ++ph) {
     SPH_TRY_CUDA(cudaFuncSetAttribute((const void*)apply_kernel(ph, 5), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)apply_smem(5)));
+    // the register forms use no shared memory beyond their reductions: ask for
+    // the largest L1, which holds the gathered neighbour vectors
+    for (int v = 0; v < kApplyVariantsRegister; ++v)
+      SPH_TRY_CUDA(cudaFuncSetAttribute((const void*)apply_kernel(ph, v),
+                                        cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1));
+  }
   done = true;
   return SPH_OK;
 }
