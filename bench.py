@@ -57,7 +57,7 @@ def parse(argv=None):
     ap.add_argument("--learned-only", action="store_true")
     ap.add_argument("--weights", default=None, help="warm-start network (.npz); default: the committed weights")
     ap.add_argument("--merged", type=int, default=0)
-    ap.add_argument("--eps-inner", type=float, default=1e-2)
+    ap.add_argument("--eps-inner", type=float, default=2e-2)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--launch-mode", type=int, default=0, choices=[0, 1],
                     help="0: dependent launches in the solve loop (default); 1: plain stream order")

@@ -195,7 +195,7 @@ typedef struct {
                               BiCGSTAB pass on its Jacobi-scaled recursive
                               residual (the paper's tau^2 = max(eps^2 b.b,
                               FLT_MIN), Sec. 4.1); each pass asks for
-                              max(eps_inner, rtol ||b|| / (4 ||r64||)); 0 = 1e-2.
+                              max(eps_inner, rtol ||b|| / (4 ||r64||)); 0 = 2e-2.
                               Each pass restarts BiCGSTAB from the float64 true
                               residual with a fresh shadow vector r0^, which on
                               stiff systems takes fewer iterations in total than

@@ -164,7 +164,7 @@ def visc_params(dt, boundary=SPH_BC_DUMMY, mean=SPH_MEAN_HARMONIC):
     return sph_visc_params(float(dt), int(boundary), int(mean))
 
 
-def solve_opts(rtol=1e-6, eps_inner=1e-2, maxit=20000, max_refine=30, precision=SPH_PREC_MIXED,
+def solve_opts(rtol=1e-6, eps_inner=2e-2, maxit=20000, max_refine=30, precision=SPH_PREC_MIXED,
                merged_reductions=0, chunk=8, jacobi=1, apply_form=0, launch_mode=0):
     return sph_solve_opts(rtol, eps_inner, maxit, max_refine, precision, merged_reductions, chunk, jacobi,
                           apply_form, launch_mode)

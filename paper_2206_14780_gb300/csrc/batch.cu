@@ -717,7 +717,7 @@ sph_status sph_batch_solve(sph_batch* Bt, const sph_solve_opts* O, const double*
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const double rtol = O->rtol > 0.0 ? O->rtol : 1e-6;
-  const double eps = O->eps_inner > 0.0 ? O->eps_inner : 1e-2;
+  const double eps = O->eps_inner > 0.0 ? O->eps_inner : 2e-2;
   const int maxit = O->maxit > 0 ? O->maxit : 10000;
   const int max_ref = O->max_refine > 0 ? O->max_refine : 30;
   const int S = Bt->nscenes;

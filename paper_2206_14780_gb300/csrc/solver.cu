@@ -732,7 +732,7 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
   const double bnorm = std::sqrt(bb[0] + bb[1] + bb[2]);
 
   const double rtol = O->rtol > 0.0 ? O->rtol : 1e-6;
-  const double eps_floor = O->eps_inner > 0.0 ? O->eps_inner : 1e-2;
+  const double eps_floor = O->eps_inner > 0.0 ? O->eps_inner : 2e-2;
   const int maxit = O->maxit > 0 ? O->maxit : 10000;
   const int max_ref = O->max_refine > 0 ? O->max_refine : 20;
   const int chunk0 = O->chunk > 0 ? O->chunk : 8;
