@@ -140,12 +140,7 @@ __device__ __forceinline__ void scene_sum(const double* partials, int b, int e, 
     if (lane == 0) sm[warp][k] = x;
   }
   __syncthreads();
-  if (threadIdx.x < K) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < NB / 32; ++w) s += sm[w][threadIdx.x];
-    res[threadIdx.x] = s;
-  }
+  cross_warp_sum<K, NB / 32>(sm, res);
   if (threadIdx.x == 0) *cnt = 0u;
   __syncthreads();
 }
@@ -326,7 +321,7 @@ __global__ void __launch_bounds__(NB) kb_pass(BatchView B, int iter_cap) {
       if (arrive_scene(B.scene_cnt + sc, d.tile_end - d.tile_begin)) {
         __shared__ double res[3];
         scene_sum<3, NB>(B.partials, d.tile_begin, d.tile_end, B.scene_cnt + sc, res);
-        if (threadIdx.x == 0) scal_after_delta(S, res);
+        if (threadIdx.x < 32) scal_after_delta_w(S, res);
       }
     }
     if (!grid_sync(B.ctrl)) return;
@@ -371,7 +366,7 @@ __global__ void __launch_bounds__(NB) kb_pass(BatchView B, int iter_cap) {
       if (arrive_scene(B.scene_cnt + sc, d.tile_end - d.tile_begin)) {
         __shared__ double res[6];
         scene_sum<6, NB>(B.partials, d.tile_begin, d.tile_end, B.scene_cnt + sc, res);
-        if (threadIdx.x == 0) scal_after_omega(S, res);
+        if (threadIdx.x < 32) scal_after_omega_w(S, res);
       }
     }
     if (!grid_sync(B.ctrl)) return;
@@ -407,8 +402,9 @@ __global__ void __launch_bounds__(NB) kb_pass(BatchView B, int iter_cap) {
       if (arrive_scene(B.scene_cnt + sc, d.tile_end - d.tile_begin)) {
         __shared__ double res[6];
         scene_sum<6, NB>(B.partials, d.tile_begin, d.tile_end, B.scene_cnt + sc, res);
+        if (threadIdx.x < 32) scal_after_update_w(S, res, res + 3);
+        __syncwarp();
         if (threadIdx.x == 0) {
-          scal_after_update(S, res, res + 3);
           B.total_iters[sc] += 1;
           for (int c = 0; c < 3; ++c)
             if (S->stalled_any[c]) B.stalled_any[3 * sc + c] = 1;
