@@ -1,10 +1,13 @@
 // Grid-wide float64 reductions without an extra launch.
 //
 // Every thread carries K float32 partial sums of its rows.  A warp folds them
-// with shuffles in float32 (32 terms), the block folds its warps in float64 and
-// writes one float64 partial per value; the last block to arrive (a ticket on
-// a global counter after a memory fence) folds all block partials in a fixed
-// order, so the result is deterministic, and runs the scalar update.
+// with shuffles in float32 (32 terms), the block folds its warps in float64 (a
+// shuffle tree) and writes one float64 partial per value; the last block to
+// arrive (a ticket on a global counter after a memory fence) folds all block
+// partials in a fixed order, so the result is deterministic, and runs the
+// scalar update.  Float64 runs at a small fraction of the float32 rate on this
+// part, so the number of dependent float64 additions in that serial tail is
+// kept small.
 #pragma once
 
 #include "sph_internal.cuh"

@@ -22,8 +22,14 @@
 //     the next iteration fused into the x/r update:
 //     k_apply_dot<DELTA>, k_rstar, k_apply_dot<OMEGA_MERGED>, k_xrp_update
 //
+// The loop's kernels go out as programmatic dependent launches (launch_pdl):
+// each one's launch is processed while its predecessor runs, and it waits at its
+// first instruction for the predecessor's completion.
+//
 // Outer loop: r64 = b - A x in float64 (hi + lo coefficients), stop when
-// ||r64|| / ||b|| <= rtol, else run a pass on D^-1 r64 and add d to x (float64).
+// ||r64|| / ||b|| <= rtol, else run a pass on D^-1 r64, add d to x (float64)
+// and update r64 -= A d in double-float arithmetic; the residual that accepts
+// the solution is recomputed from x.
 #include <cmath>
 #include <cstring>
 
