@@ -303,26 +303,20 @@ def run_sphvisc(args):
     ms_max = max_over_ranks(ms, world, dev)
     barrier(world, dev)
 
-    # end to end through host buffers: H2D of the particle set (with v^n) and b; D2H of x
+    # end to end through the C-ABI's host-buffer call (sph_visc_solve_host): H2D of the
+    # particle set (with v^n) and b from pinned host memory, neighbours, A(dt), x0, solve, D2H of x
     e2e = None
     if not args.no_e2e:
         host = {k: v.cpu().pin_memory() for k, v in t.items()}
         hb = b.cpu().pin_memory()
         hx = torch.empty_like(hb).pin_memory()
-        dt_ = {k: torch.empty_like(v) for k, v in t.items()}
         h2d = sum(v.numel() * v.element_size() for v in host.values()) + hb.numel() * 8
         d2h = hx.numel() * 8
-        bb = torch.empty_like(b)
+        e2e_nb = [None]
 
         def e2e_step():
-            for k in host:
-                dt_[k].copy_(host[k], non_blocking=True)
-            bb.copy_(hb, non_blocking=True)
-            nb.rebuild(dt_["pos"], dt_["rho"], dt_["mu"], dt_["ptype"], *geo)
-            binding.warm_start(nb, params, None, dt_["vel"], dt_["ptype"], bb, x)
-            nb.solve(params, opts, bb, x)
-            hx.copy_(x, non_blocking=True)
-            torch.cuda.current_stream(dev).synchronize()
+            _, e2e_nb[0] = binding.solve_host(host["pos"], host["rho"], host["mu"], host["ptype"], *geo, params, opts,
+                                              host["vel"], hb, hx, nb=e2e_nb[0])
 
         e2e_step()
         barrier(world, dev)
@@ -335,7 +329,8 @@ def run_sphvisc(args):
         torch.cuda.synchronize(dev)
         ems = max_over_ranks(e0.elapsed_time(e1), world, dev)
         e2e = dict(value=whole_job_ms_per_solve(ems, args.steps, world), unit=UNIT, h2d_bytes_per_step=int(h2d),
-                   d2h_bytes_per_step=int(d2h))
+                   d2h_bytes_per_step=int(d2h), api="sph_visc_solve_host (pinned host buffers in and out)")
+        e2e_nb[0].close()
 
     if rank != 0:
         if world > 1:

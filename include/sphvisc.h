@@ -249,6 +249,26 @@ sph_status sph_visc_solve(sph_neighbors* handle, const sph_visc_params* params,
                           const sph_solve_opts* opts, const double* b, double* x,
                           sph_solve_report* report, void* stream);
 
+/* One time step's viscous solve from HOST buffers (no counterpart in the paper;
+ * the call a host-side time integrator makes): copies the scene (pos, rho, mu,
+ * ptype: HOST pointers here, same layouts as sph_scene), b and either vel or x
+ * to library-owned device staging, builds or rebuilds *handle's neighbour
+ * lists (as sph_build_neighbors with max_neighbors), starts from
+ * x0 = v^n with the dummy-wall closure (as sph_warm_start without a network)
+ * when vel is non-NULL, else from x, solves as sph_visc_solve and copies the
+ * solution back into x.
+ * vel: (host) [n][4] float or NULL; b: (host) [n][3] double; x: (host) [n][3]
+ * double, in: the initial guess when vel is NULL, out: the solution.  Pinned
+ * (page-locked) host buffers make the copies asynchronous.
+ * *handle: NULL on the first call (a handle is created and returned; release it
+ * with sph_neighbors_destroy), or a handle from an earlier call.  The staging
+ * is allocated on first use and grows with n; it is freed with the handle.
+ * report: (host).  Synchronises the stream.  Returns as sph_visc_solve, or the
+ * status of the neighbour build. */
+sph_status sph_visc_solve_host(const sph_scene* scene, int32_t max_neighbors, const sph_visc_params* params,
+                               const sph_solve_opts* opts, const float* vel, const double* b, double* x,
+                               sph_neighbors** handle, sph_solve_report* report, void* stream);
+
 /* ---- Batched ensemble solve -------------------------------------------------
  * S independent scenes (each its own handle and A(dt)) solved together: every
  * scene runs the restructured BiCGSTAB of Sec. 4.2 with its own scalars, states

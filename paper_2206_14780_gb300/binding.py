@@ -30,7 +30,7 @@ EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", 
            "sph_batch_create", "sph_batch_solve", "sph_batch_info", "sph_batch_destroy",
            "sph_mlp_create", "sph_mlp_set_params", "sph_mlp_get_params", "sph_mlp_destroy", "sph_mlp_features",
            "sph_mlp_targets", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train_step", "sph_warm_start",
-           "sph_mlp_residual_targets", "sph_mlp_set_mode"]
+           "sph_mlp_residual_targets", "sph_mlp_set_mode", "sph_visc_solve_host"]
 MLP_NPARAMS = 9603
 
 
@@ -269,6 +269,49 @@ class Neighbors:
             self.close()
         except Exception:
             pass
+
+
+def _host_ptr(t):
+    """Pointer of a contiguous host (CPU) torch tensor or numpy array."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("expected a contiguous host tensor")
+        return ctypes.c_void_p(t.data_ptr())
+    if not t.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous host array")
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def solve_host(pos, rho, mu, ptype, lo, hi, periodic, h, params, opts, vel, b, x, nb=None, max_neighbors=128,
+               stream=None):
+    """sph_visc_solve_host on HOST arrays (torch CPU tensors, pinned for asynchronous copies, or
+    numpy): neighbour build, x0 = v^n with the wall closure (vel given) or x, solve, x copied
+    back.  nb: a Neighbors from an earlier call (or None: one is created).  Returns
+    (report dict, Neighbors)."""
+    load()
+    sc = sph_scene()
+    sc.n = int(pos.shape[0])
+    sc.pos, sc.rho, sc.mu, sc.ptype = _host_ptr(pos), _host_ptr(rho), _host_ptr(mu), _host_ptr(ptype)
+    for ax in range(3):
+        sc.lo[ax] = float(lo[ax])
+        sc.hi[ax] = float(hi[ax])
+        sc.periodic[ax] = int(periodic[ax])
+    sc.h = float(h)
+    handle = ctypes.c_void_p(nb.handle.value if nb is not None else None)
+    rep = sph_solve_report()
+    st = _lib.sph_visc_solve_host(ctypes.byref(sc), int(max_neighbors), ctypes.byref(params), ctypes.byref(opts),
+                                  _host_ptr(vel), _host_ptr(b), _host_ptr(x), ctypes.byref(handle),
+                                  ctypes.byref(rep), _stream(stream))
+    if nb is None and handle.value:
+        nb = Neighbors(handle, sc.n, keep=())
+    elif nb is not None:
+        nb.handle = handle
+        nb.n = sc.n
+    if st not in (SPH_OK, 6):
+        _check(st)
+    return _report(rep), nb
 
 
 def _scene_struct(pos, rho, mu, ptype, lo, hi, periodic, h):

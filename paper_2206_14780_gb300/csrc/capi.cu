@@ -174,6 +174,10 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
   h->uni.release();
   h->unum.release();
   h->wpart.release();
+  if (h->stage) {
+    h->stage->release();
+    delete h->stage;
+  }
   h->otf_g.release();
   h->otf_im.release();
   h->otf_rb.release();

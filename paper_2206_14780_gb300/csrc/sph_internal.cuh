@@ -138,6 +138,25 @@ struct Grid {
 
 }  // namespace sph
 
+namespace sph {
+// device staging of sph_visc_solve_host (owned by the handle)
+struct HostStage {
+  DBuf<float4> pos, vel;
+  DBuf<float> rho, mu;
+  DBuf<uint8_t> type;
+  DBuf<double> b, x;
+  void release() {
+    pos.release();
+    vel.release();
+    rho.release();
+    mu.release();
+    type.release();
+    b.release();
+    x.release();
+  }
+};
+}  // namespace sph
+
 // The opaque handle of the C ABI.
 struct sph_neighbors {
   int64_t n = 0;
@@ -179,6 +198,7 @@ struct sph_neighbors {
   int64_t op_nnz_pad = 0;
   uint64_t op_version = 0;         // bumped whenever the operator is rebuilt
   sph::DBuf<int32_t> wpart;        // balanced per-warp slice ranges (OpView::wpart)
+  sph::HostStage* stage = nullptr; // sph_visc_solve_host's device copies of its host buffers
   int64_t wpart_nw = 0;
   uint64_t wpart_version = ~0ull;  // op_version they were cut for
 
