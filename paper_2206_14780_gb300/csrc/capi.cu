@@ -244,6 +244,11 @@ sph_status sph_visc_solve(sph_neighbors* h, const sph_visc_params* params, const
     set_error("sph_visc_solve: invalid options (rtol >= 0, 0 <= eps_inner < 1, maxit/max_refine/chunk >= 0)");
     return SPH_ERR_INVALID;
   }
+  if (opts->apply_form < 0 || opts->apply_form > kApplyVariants || opts->launch_mode < 0 || opts->launch_mode > 1) {
+    set_error("sph_visc_solve: apply_form %d outside 0..%d or launch_mode %d neither 0 nor 1", opts->apply_form,
+              kApplyVariants, opts->launch_mode);
+    return SPH_ERR_INVALID;
+  }
   if (opts->precision == SPH_PREC_MIXED) return solve_mixed(h, params, opts, b, x, report, as_stream(stream));
   if (opts->precision == SPH_PREC_FP64) return solve_fp64(h, params, opts, b, x, report, as_stream(stream));
   set_error("sph_visc_solve: unknown precision %d", opts->precision);
