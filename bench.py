@@ -49,6 +49,7 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-only", action="store_true")
+    ap.add_argument("--ensemble-scenes", type=int, default=64, help="scenes of the ensemble leg (64: the workload)")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-sequence", action="store_true")
     ap.add_argument("--sequence-steps", type=int, default=200)
@@ -375,7 +376,7 @@ def run_sphvisc(args):
     if not args.no_ensemble and world == 1:
         nb.close()
         torch.cuda.empty_cache()
-        ensemble = run_ensemble(0, dev)
+        ensemble = run_ensemble(0, dev, scenes_n=args.ensemble_scenes)
     precision = None
     if not args.no_precision and world == 1:
         torch.cuda.empty_cache()
@@ -527,7 +528,7 @@ def run_apply_forms(nb, params, n, dev, reps=20):
 
 # ------------------------------------------------------------- ensemble ------
 
-def run_ensemble(seed=0, dev=None):
+def run_ensemble(seed=0, dev=None, scenes_n=64):
     """64 independent scenes (log-uniform 10k-500k particles, nu in 1-1e3, dt in 1e-4-5e-4):
     one batched solve (persistent kernel in a CUDA graph) vs 64 sequential plain solves."""
     import torch
@@ -536,7 +537,7 @@ def run_ensemble(seed=0, dev=None):
     from paper_2206_14780_gb300 import binding
 
     dev = dev or torch.device("cuda", 0)
-    ens = scenes.ensemble(seed)
+    ens = scenes.ensemble(seed, S=scenes_n)
     nbs, bs, ts, params = [], [], [], []
     for s in ens:
         t = binding.scene_tensors(s, dev)
@@ -581,7 +582,7 @@ def run_ensemble(seed=0, dev=None):
     torch.cuda.synchronize(dev)
     bat_ms = e0.elapsed_time(e1)
     info = batch.info()
-    out = dict(workload="64 scenes (channel/box alternating), totals log-uniform 1e4-5e5 particles, "
+    out = dict(workload=f"{len(ens)} scenes (channel/box alternating), totals log-uniform 1e4-5e5 particles, "
                         "nu log-uniform 1-1e3 m^2/s, dt log-uniform 1e-4-5e-4 s; x0 = v^n with the dummy-wall "
                         "closure, inside the timed region of both forms",
                particles=int(sum(s.n for s in ens)), scenes=len(ens),
@@ -890,7 +891,7 @@ def main():
         cpu_worker(args)
         return
     if args.ensemble_only:
-        print(json.dumps(run_ensemble(0)))
+        print(json.dumps(run_ensemble(0, scenes_n=args.ensemble_scenes)))
         return
     if args.precision_only:
         print(json.dumps(run_precision()))
