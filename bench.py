@@ -121,6 +121,10 @@ def read_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# the sources of the operator apply kernel (k_apply_dot and what it includes)
+TRAFFIC_SOURCES = ("apply.cuh", "solver.cu", "reduce.cuh", "bicgstab_scalars.cuh", "sph_internal.cuh")
+
+
 def apply_traffic(alg_bytes):
     """DRAM bytes per apply launch: the ncu-measured ratio of DRAM traffic to algorithmic
     bytes (profiles/apply_traffic.txt) times this launch's algorithmic bytes, or None when
@@ -134,7 +138,7 @@ def apply_traffic(alg_bytes):
                 k, v = line.strip().split("=", 1)
                 kv[k] = v
         src = b"".join(open(os.path.join(ROOT, "paper_2206_14780_gb300", "csrc", f), "rb").read()
-                       for f in ("apply.cuh", "solver.cu"))
+                       for f in TRAFFIC_SOURCES)
         if hashlib.sha256(src).hexdigest()[:16] != kv["sources_sha256_16"]:
             return None, "kernel changed since the ncu capture"
         return float(kv["dram_bytes_per_algorithmic_byte"]) * alg_bytes, \

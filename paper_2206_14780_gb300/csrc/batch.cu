@@ -132,12 +132,11 @@ __device__ __forceinline__ void scene_sum(const double* partials, int b, int e, 
   }
   __shared__ double sm[NB / 32][K];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double x = acc[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) sm[warp][k] = x;
+  {
+    constexpr int P = K <= 1 ? 1 : (K <= 2 ? 2 : (K <= 4 ? 4 : (K <= 8 ? 8 : (K <= 16 ? 16 : 32))));
+    int idx;
+    const double x = warp_sum_multi<K>(acc, idx);
+    if ((lane & (32 / P - 1)) == 0 && idx < K) sm[warp][idx] = x;
   }
   __syncthreads();
   cross_warp_sum<K, NB / 32>(sm, res);

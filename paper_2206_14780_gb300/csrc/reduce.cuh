@@ -31,6 +31,41 @@ __device__ __forceinline__ void cross_warp_sum(const double (*sm)[K > 0 ? K : 1]
   }
 }
 
+// Sums of K float64 values over the 32 lanes of a warp at once, by a transposing
+// butterfly: with P the power of two >= K, each of the first log2(P) levels
+// hands half of a lane's remaining values to its partner and adds the other
+// half, so a lane ends with one value (the sum over the lanes that differ in
+// those bits); the remaining levels are plain shuffle additions.  That is
+// P - 1 + 5 - log2(P) float64 additions per lane instead of 5 K.  Returns the
+// lane's total and sets `index` to the value it holds; only lanes whose low
+// 5 - log2(P) bits are zero hold a finished total (index < K: a real value).
+template <int K>
+__device__ __forceinline__ double warp_sum_multi(const double (&in)[K], int& index) {
+  constexpr int P = K <= 1 ? 1 : (K <= 2 ? 2 : (K <= 4 ? 4 : (K <= 8 ? 8 : (K <= 16 ? 16 : 32))));
+  constexpr int LP = P == 1 ? 0 : (P == 2 ? 1 : (P == 4 ? 2 : (P == 8 ? 3 : (P == 16 ? 4 : 5))));
+  const int lane = threadIdx.x & 31;
+  double v[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) v[i] = i < K ? in[i] : 0.0;
+  int idx = 0;
+#pragma unroll
+  for (int L = 0; L < LP; ++L) {
+    const int o = 16 >> L, c = P >> (L + 1);
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < c; ++i) {
+      const double send = hi ? v[i] : v[i + c];
+      const double keep = hi ? v[i + c] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    if (hi) idx += c;
+  }
+#pragma unroll
+  for (int o = 16 >> LP; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  index = idx;
+  return v[0];
+}
+
 template <int K, int NB = kBlock>
 __device__ __forceinline__ void block_partials(const float (&v)[K], double* __restrict__ out) {
   __shared__ double sm[NB / 32][K > 0 ? K : 1];
@@ -50,12 +85,11 @@ template <int K>
 __device__ __forceinline__ void block_partials_f64(const double (&v)[K], double* __restrict__ out) {
   __shared__ double sm[kBlock / 32][K > 0 ? K : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double x = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) sm[warp][k] = x;
+  {
+    constexpr int P = K <= 1 ? 1 : (K <= 2 ? 2 : (K <= 4 ? 4 : (K <= 8 ? 8 : (K <= 16 ? 16 : 32))));
+    int idx;
+    const double x = warp_sum_multi<K>(v, idx);
+    if ((lane & (32 / P - 1)) == 0 && idx < K) sm[warp][idx] = x;
   }
   __syncthreads();
   cross_warp_sum<K, kBlock / 32>(sm, out);
@@ -84,12 +118,11 @@ __device__ __forceinline__ void final_sum(const double* partials, unsigned int* 
   }
   __shared__ double sm[kBlock / 32][K > 0 ? K : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double x = acc[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) sm[warp][k] = x;
+  {
+    constexpr int P = K <= 1 ? 1 : (K <= 2 ? 2 : (K <= 4 ? 4 : (K <= 8 ? 8 : (K <= 16 ? 16 : 32))));
+    int idx;
+    const double x = warp_sum_multi<K>(acc, idx);
+    if ((lane & (32 / P - 1)) == 0 && idx < K) sm[warp][idx] = x;
   }
   __syncthreads();
   cross_warp_sum<K, kBlock / 32>(sm, res);
