@@ -95,6 +95,15 @@ __device__ __forceinline__ void block_partials_f64(const double (&v)[K], double*
   cross_warp_sum<K, kBlock / 32>(sm, out);
 }
 
+// Pulls the solver scalars (written by earlier kernels, read by the scalar
+// update at the end of the last block's tail) into L1 while the final sum runs,
+// so the update's dependent loads do not each wait for L2.
+__device__ __forceinline__ void prefetch_scalars(const void* S, size_t bytes) {
+  const int i = threadIdx.x;
+  if ((size_t)i * 128 < bytes)
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(S) + 128 * i));
+}
+
 // True in every thread of the last block to finish (after its partial is stored).
 __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
   __shared__ unsigned int ticket;

@@ -155,6 +155,7 @@ __device__ __forceinline__ void dots_finish(const float (&acc)[PhaseDots<PH>::K]
   block_partials<K>(acc, partials + (size_t)blockIdx.x * kMaxDots);
   if (arrive_last(counter)) {
     __shared__ double res[K];
+    prefetch_scalars(S, sizeof(SolverScalars));
     final_sum<K>(partials, counter, res);
     if (threadIdx.x < 32) {
       if (PH == PH_DELTA) {
@@ -509,6 +510,7 @@ __global__ void __launch_bounds__(kBlock) k_xr_update(int64_t n_pad, Vecs V, Sol
   block_partials<6>(acc, partials + (size_t)blockIdx.x * kMaxDots);
   if (arrive_last(counter)) {
     __shared__ double res[6];
+    prefetch_scalars(S, sizeof(SolverScalars));
     final_sum<6>(partials, counter, res);
     if (threadIdx.x < 32) scal_after_update_w(S, res, res + 3);
   }
