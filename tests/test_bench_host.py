@@ -1,0 +1,40 @@
+"""Host-side logic of bench.py that needs no GPU: the DRAM-traffic record is used only
+while the apply kernel's sources still hash to the captured version, the whole-job value
+divides by every solve of every rank, and the peak falls back when the measured file is
+absent."""
+import os
+
+import pytest
+
+import bench
+
+
+def test_traffic_record_scales_and_goes_null_on_a_source_change(monkeypatch):
+    t, why = bench.apply_traffic(712_000_000)
+    if t is None:
+        # a kernel source changed since the capture: the record must say so, not a number
+        assert "changed" in why or "unavailable" in why
+    else:
+        ratio = t / 712_000_000
+        assert 1.0 <= ratio < 1.5, ratio
+        assert "scaled" in why
+    # any other source list hashes differently: the bench then reports no traffic
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES", ("apply.cuh",))
+    t2, why2 = bench.apply_traffic(712_000_000)
+    assert t2 is None and "changed" in why2
+
+
+def test_whole_job_value_counts_every_solve_of_every_rank():
+    assert bench.whole_job_ms_per_solve(600.0, 10, 1) == pytest.approx(60.0)
+    assert bench.whole_job_ms_per_solve(600.0, 10, 4) == pytest.approx(15.0)
+    assert bench.replica_seed(3) == 3 and bench.max_over_ranks(2.5, 1) == 2.5
+
+
+def test_peak_falls_back_without_the_measured_file(monkeypatch):
+    real = bench.ROOT
+    if os.path.exists(os.path.join(real, "MEASURED_PEAKS.json")):
+        peak, kind = bench.read_peaks()
+        assert kind == "measured" and peak > 1000.0
+    monkeypatch.setattr(bench, "ROOT", os.path.join(real, "no_such_directory"))
+    peak, kind = bench.read_peaks()
+    assert kind == "fallback" and peak == bench.FALLBACK_HBM_GBS
