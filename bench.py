@@ -750,10 +750,31 @@ def run_learned(weights=None, dev=None, reps=3, mode=None):
                           status=st)
     out["ensemble_64"] = dict(workload=f"64 scenes, seed 1, {sum(sc.n for sc in ens)} particles, batched solve",
                               **eres)
+    out["learned_vs_plain"] = learned_vs_plain(out)
     batch.close()
     for nb_ in nbs:
         nb_.close()
     return out
+
+
+def learned_vs_plain(out):
+    """Iterations and ms of each learned start relative to the plain ones (the paper's
+    previous-step start v^n, and v^n with the dummy-wall closure), on the unseen boxes
+    (means over the seeds) and the unseen ensemble (sums): < 1 means the learned start
+    needs fewer."""
+    res = {}
+    for case, it_key, ms_key in (("box_1157k", "iters_mean", "ms_mean"), ("ensemble_64", "iters_sum", "ms")):
+        c = out.get(case, {})
+        row = {}
+        for learned in ("learned", "learned_highpass"):
+            if learned not in c:
+                continue
+            for plain in ("vn", "vn_walls"):
+                if plain in c:
+                    row[f"{learned}/{plain}"] = dict(iters=c[learned][it_key] / c[plain][it_key],
+                                                     ms=c[learned][ms_key] / c[plain][ms_key])
+        res[case] = row
+    return res
 
 
 # ----------------------------------------------------- 200-step sequence ----

@@ -38,3 +38,16 @@ def test_peak_falls_back_without_the_measured_file(monkeypatch):
     monkeypatch.setattr(bench, "ROOT", os.path.join(real, "no_such_directory"))
     peak, kind = bench.read_peaks()
     assert kind == "fallback" and peak == bench.FALLBACK_HBM_GBS
+
+
+def test_learned_vs_plain_ratios():
+    out = {"box_1157k": {"vn": {"iters_mean": 150.0, "ms_mean": 50.0},
+                         "vn_walls": {"iters_mean": 140.0, "ms_mean": 48.0},
+                         "learned": {"iters_mean": 120.0, "ms_mean": 45.0}},
+           "ensemble_64": {"vn": {"iters_sum": 5000, "ms": 300.0},
+                           "learned_highpass": {"iters_sum": 4500, "ms": 290.0}}}
+    r = bench.learned_vs_plain(out)
+    assert r["box_1157k"]["learned/vn"]["iters"] == pytest.approx(0.8)
+    assert r["box_1157k"]["learned/vn_walls"]["ms"] == pytest.approx(45.0 / 48.0)
+    assert r["ensemble_64"]["learned_highpass/vn"]["iters"] == pytest.approx(0.9)
+    assert "learned_highpass/vn_walls" not in r["ensemble_64"]
