@@ -1,4 +1,5 @@
-"""Pins of the warm-start network reference (oracle/mlp.py): finite differences, bf16 rounding."""
+"""Pins of the warm-start network reference (oracle/mlp.py): finite differences, bf16 rounding,
+a hand-wired network with closed-form activations."""
 import numpy as np
 import pytest
 
@@ -47,3 +48,29 @@ def test_silu_derivative():
     z = np.linspace(-6, 6, 101)
     e = 1e-6
     np.testing.assert_allclose(mlp.dsilu(z), (mlp.silu(z + e) - mlp.silu(z - e)) / (2 * e), rtol=1e-7, atol=1e-9)
+
+
+def test_forward_of_a_hand_wired_network():
+    """A network wired by hand through one unit per layer, with pre-activations set to ln k
+    where SiLU has the closed form silu(ln k) = ln k * k / (k + 1).  This pins the layer
+    order, the orientation of each W (out x in), the bias of every layer, SiLU on the hidden
+    layers only and the linear output, independently of the formula in the oracle."""
+    p = {name: np.zeros(shp) for name, shp in mlp.SHAPES}
+    ln3, ln7, ln15 = np.log(3.0), np.log(7.0), np.log(15.0)
+    p["W1"][0, 5] = 1.0                        # hidden unit 0 reads input 5
+    p["W2"][1, 0] = 2.0                        # unit 1 of layer 2 reads unit 0 of layer 1
+    p["b2"][1] = ln7 - 2.0 * 0.75 * ln3
+    p["W3"][2, 1] = 1.0
+    p["b3"][2] = ln15 - 0.875 * ln7
+    p["W4"][:, 2] = [1.0, 2.0, 3.0]
+    p["b4"][:] = [0.5, -1.0, 2.0]
+    X = np.random.default_rng(4).normal(size=(6, 16))
+    X[:, 5] = ln3
+    y, cache = mlp.forward(p, X)
+    a3 = 15.0 / 16.0 * ln15
+    want = np.array([a3 + 0.5, 2.0 * a3 - 1.0, 3.0 * a3 + 2.0])
+    np.testing.assert_allclose(y, np.broadcast_to(want, y.shape), rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(cache["a1"][:, 0], 0.75 * ln3, rtol=1e-14)
+    np.testing.assert_allclose(cache["a2"][:, 1], 0.875 * ln7, rtol=1e-14)
+    # every other hidden unit has a zero pre-activation, and silu(0) = 0
+    assert np.count_nonzero(cache["a1"]) == 6 and np.count_nonzero(cache["a3"]) == 6
