@@ -121,7 +121,26 @@ __device__ __forceinline__ void final_sum(const double* partials, unsigned int* 
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+  // The first kRounds rounds of partials (all of them up to kRounds x the block
+  // size) are loaded before any is added, so their L2 latencies overlap; a
+  // round past the grid adds an exact zero, so the sums are those of the plain
+  // loop, in the same order.
+  constexpr int kRounds = 3;
+  {
+    double q[kRounds][K];
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+      const int b = threadIdx.x + r * blockDim.x;
+#pragma unroll
+      for (int k = 0; k < K; ++k) q[r][k] = b < (int)gridDim.x ? __ldcg(partials + (size_t)b * kMaxDots + k) : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] += q[r][k];
+    }
+  }
+  for (int b = threadIdx.x + kRounds * blockDim.x; b < (int)gridDim.x; b += blockDim.x) {
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] += __ldcg(partials + (size_t)b * kMaxDots + k);
   }
