@@ -73,3 +73,46 @@ def test_mu_pass_range_on_slope_subset():
     fl = s.ptype == scenes.FLUID
     tau0, mu0, m = s.rheology
     assert np.all(mu[fl] <= m * tau0 + mu0 + 1e-6) and np.all(mu[fl] > mu0)
+
+
+def test_bingham_slab_reaches_the_analytic_steady_profile():
+    """A Papanastasiou slab driven by a body force g along x on a dummy-wall floor, periodic
+    in x and z with a free top, marched with lagged viscosity (Sec. 3.3) and the implicit
+    viscous system until it stops changing.  The steady state of a Bingham fluid is known in
+    closed form: with the wall plane at y = 0, depth H and y_p = H - tau0 / (rho g),
+    u = (rho g / mu0) (y_p y - y^2 / 2) below y_p and a rigid plug at (rho g / mu0) y_p^2 / 2
+    above.  This pins the mu pass (velocity gradient, the D = sqrt(2 gdot:gdot) convention of
+    reading X4, the regularised viscosity) together with the operator and the dummy walls:
+    with D = sqrt(gdot:gdot) the same march yields a plug 37% slower."""
+    from oracle import operator as oop
+    import scipy.sparse.linalg as spla
+
+    dx, ny, tau0, mu0, m, rho0, g, dt = 0.01, 30, 100.0, 10.0, 1000.0, 1000.0, 1.0, 5.0
+    s = scenes.slope(0, nx=8, ny=ny, nz=8, dx=dx, rho0=rho0, tau0=tau0, mu0=mu0, m_reg=m, dt=dt,
+                     noise=0.0, jitter=0.0)
+    off, idx = neighbors.build(s.pos, s.lo, s.hi, s.periodic, s.h)
+    nf = s.n_fluid
+    y = s.pos[:nf, 1].astype(np.float64)
+    yp = ny * dx - tau0 / (rho0 * g)
+    ua = np.where(y <= yp, rho0 * g / mu0 * (yp * y - 0.5 * y * y), rho0 * g / mu0 * 0.5 * yp * yp)
+    v = np.zeros((s.n, 4), np.float32)
+    v[:nf, 0] = ua                       # the march's fixed point does not depend on the start
+    for _ in range(200):
+        mu, _ = rheology.mu_pass(s, off, idx, v)
+        A = oop.assemble(s, off, idx, dt=dt, mu=mu)
+        b = np.zeros((s.n, 3))
+        b[:nf] = v[:nf, :3]
+        b[:nf, 0] += dt * g
+        x = spla.splu(A.tocsc()).solve(b)
+        change = np.max(np.abs(x[:nf] - v[:nf, :3]))
+        v[:, :3] = x.astype(np.float32)
+        if change < 1e-6:
+            break
+    assert change < 1e-6
+    u = x[:nf, 0]
+    u_plug = rho0 * g / mu0 * 0.5 * yp * yp
+    assert np.max(np.abs(u - ua)) <= 0.02 * u_plug
+    plug = y > yp + 2 * s.h
+    assert abs(u[plug].mean() - u_plug) <= 0.02 * u_plug
+    assert np.std(u[plug]) <= 1e-3 * u_plug                # rigid
+    np.testing.assert_array_equal(x[:nf, 1:], 0.0)       # no cross-flow from a pure shear
