@@ -385,6 +385,8 @@ def run_sphvisc(args):
     if not args.no_precision and world == 1:
         torch.cuda.empty_cache()
         precision = run_precision(dev)
+        torch.cuda.empty_cache()
+        precision["low_plastic_viscosity"] = run_precision(dev, mu0=1.0, U=3.3)
     learned = None
     if not args.no_learned and world == 1:
         torch.cuda.empty_cache()
@@ -822,16 +824,19 @@ def run_sequence(nb, s, b, t, steps, dev):
 
 # ----------------------------------------------------- precision study ------
 
-def run_precision(dev=None, full=True):
+def run_precision(dev=None, full=True, mu0=1e3, U=0.1):
     """Papanastasiou slope (200x100x200 jittered fluid on a 3-layer floor, 4.12M particles): the mu
-    pass, then the mixed (float32 operator, float64 dots and refinement) and all-float64 solves."""
+    pass, then the mixed (float32 operator, float64 dots and refinement) and all-float64 solves.
+    mu0 is the plastic viscosity and U the speed of the seeded shear profile: the defaults give
+    mu in 1e3..1e5 Pa s; mu0 = 1 Pa s with U = 3.3 m/s (shear rates up to ~90 1/s) spreads it
+    over about 2..7e4 Pa s."""
     import torch
 
     import scenes
     from paper_2206_14780_gb300 import binding
 
     dev = dev or torch.device("cuda", 0)
-    s = scenes.slope(0) if full else scenes.slope_subset(0)
+    s = scenes.slope(0, mu0=mu0, U=U) if full else scenes.slope_subset(0, mu0=mu0, U=U)
     t = binding.scene_tensors(s, dev)
     nb = binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
     vel, wv = torch.from_numpy(s.vel).to(dev), torch.from_numpy(s.wall_vel).to(dev)
@@ -872,8 +877,8 @@ def run_precision(dev=None, full=True):
         res[name]["rel_l2_vs_fp64_tight"] = float(torch.linalg.norm(xs[name] - ref) / torch.linalg.norm(ref))
     nb.close()
     return dict(workload=("slope: %dx%dx%d jittered fluid on a 3-layer floor, periodic x/z, Papanastasiou "
-                          "tau0=100 Pa, mu0=1e3 Pa s, m=1000 s, dt=5e-4 s" % (200, 100, 200) if full else
-                          "slope subset 50x20x50"),
+                          "tau0=100 Pa, mu0=%g Pa s, m=1000 s, dt=5e-4 s, shear profile U=%g m/s"
+                          % (200, 100, 200, mu0, U) if full else "slope subset 50x20x50, mu0=%g, U=%g" % (mu0, U)),
                 particles=s.n, mu_pass_ms=mu_ms, mu_min=float(mu_f.min()), mu_max=float(mu_f.max()), **res)
 
 
@@ -919,7 +924,9 @@ def main():
         print(json.dumps(run_ensemble(0, scenes_n=args.ensemble_scenes)))
         return
     if args.precision_only:
-        print(json.dumps(run_precision()))
+        out = run_precision()
+        out["low_plastic_viscosity"] = run_precision(mu0=1.0, U=3.3)
+        print(json.dumps(out))
         return
     if args.learned_only:
         import torch
