@@ -40,7 +40,9 @@ def test_forward_matches_oracle():
     y = out.cpu().numpy()
     p32 = omlp.unflatten(omlp.flatten(p).astype(np.float32).astype(np.float64))
     ref, _ = omlp.forward(p32, X, bf16=True)
-    assert np.linalg.norm(y[:, :3] - ref) <= 5e-3 * np.linalg.norm(ref)
+    # the same bf16 rounding points as the oracle: what differs is the float32 accumulation
+    # order before each rounding, which flips an occasional activation by one bf16 ulp
+    assert np.linalg.norm(y[:, :3] - ref) <= 2e-3 * np.linalg.norm(ref)
     np.testing.assert_array_equal(y[:, 3], 0.0)
 
 
@@ -61,13 +63,13 @@ def test_gradient_matches_oracle():
     g_ref = omlp.flatten(g_ref)
     gg = g.cpu().numpy().astype(np.float64)
     assert abs(float(loss.item()) - l_ref) <= 1e-4 * l_ref
-    assert np.linalg.norm(gg - g_ref) <= 1e-2 * np.linalg.norm(g_ref)
+    assert np.linalg.norm(gg - g_ref) <= 1e-3 * np.linalg.norm(g_ref)
     # every parameter block is exercised (a transposed fragment would scramble one of them)
     off = 0
     for name, shp in omlp.SHAPES:
         k = int(np.prod(shp))
         blk, ref = gg[off:off + k], g_ref[off:off + k]
-        assert np.linalg.norm(blk - ref) <= 2e-2 * np.linalg.norm(ref) + 1e-7, name
+        assert np.linalg.norm(blk - ref) <= 2e-3 * np.linalg.norm(ref) + 1e-7, name
         off += k
 
 
