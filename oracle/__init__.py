@@ -26,7 +26,7 @@ Everything here is plain, slow and in float64, written from the paper:
 * ``warmstart``  x0 = v + U y with the dummy-wall closure (Eq. dummyvel), the
                  residual training loss and its MSE pseudo-targets
 
-Readings of the paper where it is garbled or silent (all listed in the design doc):
+Readings of the paper where it is garbled or silent:
 X1 the kernel gradient factor F enters K_ab as a magnitude, so the fluid rows are
 diag 1 + dt sum c, off-diagonal -dt c; X2 the tolerance floor is a max; X4 the
 second invariant is D = sqrt(2 g:g); X6 fluid-wall pairs use the fluid row's own
