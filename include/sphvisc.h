@@ -311,7 +311,7 @@ sph_status sph_batch_destroy(sph_batch* batch);
  * per-particle MLP, 16 -> 64 -> 64 -> 64 -> 3 with SiLU (9,603 parameters),
  * predicts delta = (x* - v^n) / U from 16 local features; the solve then starts
  * from x0 = v^n + U delta on fluid rows (walls start at b), and the unchanged
- * BiCGSTAB with its float64 true residual stays the judge of the result.
+ * BiCGSTAB with its float64 true residual stays the arbiter of the result.
  * Inference and training run on BF16 tensor cores with FP32 accumulation.
  * Parameters are exchanged as 9,603 float32 values, row-major [out][in]:
  * W1 64x16, b1 64, W2 64x64, b2 64, W3 64x64, b3 64, W4 3x64, b4 3. */
