@@ -29,3 +29,15 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
     assert sorted(binding.EXPORTS) == _declared()
     assert b"sm_103a" in lib.sph_version()
+
+
+def test_missing_library_fails_loudly():
+    """No fallback: without the compiled library the binding raises instead of computing."""
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("from paper_2206_14780_gb300 import binding; "
+            "binding.load(binding.LIB_PATH + '.absent')")
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True)
+    assert out.returncode != 0 and "is missing" in out.stderr, (out.returncode, out.stderr[-300:])
