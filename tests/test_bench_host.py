@@ -51,3 +51,27 @@ def test_learned_vs_plain_ratios():
     assert r["box_1157k"]["learned/vn_walls"]["ms"] == pytest.approx(45.0 / 48.0)
     assert r["ensemble_64"]["learned_highpass/vn"]["iters"] == pytest.approx(0.9)
     assert "learned_highpass/vn_walls" not in r["ensemble_64"]
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the FP64 oracle on the host (a tiny box here) and
+    prints one JSON line with the same metric, the reference marker, its CPU baseline and an
+    end-to-end object with no host-device traffic."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3",
+                          "--cpu-n", "8", "--n", "12"], cwd=root, capture_output=True, text=True, timeout=600,
+                         check=True)
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is False and d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] == d["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == dict(value=d["value"], unit=d["unit"], h2d_bytes_per_step=0, d2h_bytes_per_step=0)
+    assert d["config"]["n_particles"] == bench._box_count(12)
