@@ -99,11 +99,92 @@ def bicgstab_textbook(A, b, x0=None, eps=1e-12, maxit=10000, jacobi=False):
 
 
 class PaperResult:
-    def __init__(self, x, iters, state, history):
+    def __init__(self, x, iters, state, history, stalled_any=None):
         self.x = x
         self.iters = iters
         self.state = state
         self.history = history
+        self.stalled_any = stalled_any
+
+
+# ---- scalar side of the restructured BiCGSTAB (Sec. 4.2, "Stopping criterion") ----
+# One function per point of the iteration where a reduction completes; each works
+# component by component in float64.  Reading X8 of "any of the coefficients
+# zeroes out": a delta that is zero or not finite, or an alpha that is not
+# finite, stalls the component; an omega whose denominator Ar*.Ar* is not a
+# positive finite number, or whose quotient is not finite, is zero; alpha' and
+# beta are zero after a stall or a zero omega, and both are zero when either is
+# not finite; the state is then converged (r.r < tau^2, checked first), stalled
+# (a stall this iteration, omega = 0, or r.r not finite) or progressing.
+# Components that are not live (frozen) keep every scalar and their state.
+
+def scalar_after_delta(delta, gam, live):
+    """alpha = gamma / delta per component; returns (alpha, stall_now)."""
+    k = len(gam)
+    alpha = np.zeros(k)
+    stall = np.zeros(k, bool)
+    with np.errstate(all="ignore"):
+        for c in range(k):
+            if not live[c]:
+                continue
+            d = np.float64(delta[c])
+            if d == 0.0 or not np.isfinite(d):
+                stall[c] = True
+                continue
+            a = np.float64(gam[c]) / d
+            if not np.isfinite(a):
+                stall[c] = True
+                continue
+            alpha[c] = a
+    return alpha, stall
+
+
+def scalar_after_omega(sA, AA, live):
+    """omega = (r*.Ar*) / (Ar*.Ar*) per component, zero when it cannot be formed."""
+    k = len(sA)
+    omega = np.zeros(k)
+    with np.errstate(all="ignore"):
+        for c in range(k):
+            if not live[c]:
+                continue
+            den = np.float64(AA[c])
+            if not (den > 0.0 and np.isfinite(den)):
+                continue
+            om = np.float64(sA[c]) / den
+            omega[c] = om if np.isfinite(om) else 0.0
+    return omega
+
+
+def scalar_after_update(state, stall_now, omega, delta, gam, gam_n, rr, t2, live):
+    """alpha' = gamma'/delta, beta = alpha'/omega and the new states.
+
+    Returns (alpha_p, beta, gamma, state): gamma and the state change only on
+    live components."""
+    k = len(gam)
+    alpha_p = np.zeros(k)
+    beta = np.zeros(k)
+    gam_out = np.array(gam, np.float64, copy=True)
+    st_out = np.array(state, copy=True)
+    with np.errstate(all="ignore"):
+        for c in range(k):
+            if not live[c]:
+                continue
+            ok = (not stall_now[c]) and omega[c] != 0.0
+            ap = np.float64(gam_n[c]) / np.float64(delta[c]) if ok else 0.0
+            be = ap / np.float64(omega[c]) if ok else 0.0
+            if not (np.isfinite(ap) and np.isfinite(be)):
+                ap = be = 0.0
+            alpha_p[c] = ap
+            beta[c] = be
+            gam_out[c] = gam_n[c]
+            r2 = np.float64(rr[c])
+            if r2 < t2[c]:
+                st_out[c] = CONVERGED
+            elif stall_now[c] or omega[c] == 0.0 or not np.isfinite(r2):
+                st_out[c] = STALLED
+            else:
+                st_out[c] = PROGRESSING
+    return alpha_p, beta, gam_out, st_out
 
 
 def bicgstab_paper(A, b, x0=None, eps=2.0 ** -23, maxit=10000, jacobi=True, merged=False,
@@ -114,8 +195,10 @@ def bicgstab_paper(A, b, x0=None, eps=2.0 ** -23, maxit=10000, jacobi=True, merg
     ``freeze_done`` a converged or stalled component keeps its x and r (its
     alpha and omega are zero); without it every component runs every iteration
     as the paper describes.  Returns a PaperResult with x (float64), the
-    iteration count, the final per-component state and, if ``record``, the
-    per-iteration (x, r.r, state) history.
+    iteration count, the final per-component state, whether each component
+    stalled at some iteration and, if ``record``, one dict per iteration with
+    x, r.r, the state and the raw dots and scalars of that iteration (delta,
+    alpha, r*.Ar*, Ar*.Ar*, omega, gamma', alpha', beta, live).
     """
     A = sp.csr_matrix(A, dtype=np.float64)
     b = np.asarray(b, np.float64)
@@ -141,6 +224,7 @@ def bicgstab_paper(A, b, x0=None, eps=2.0 ** -23, maxit=10000, jacobi=True, merg
     beta = np.zeros(k)
     rr = _coldots(r, r)
     state = np.where((bb == 0.0) | (rr < t2), CONVERGED, PROGRESSING)
+    stalled_any = np.zeros(k, bool)
     p = np.zeros((n, k), dtype)
     Ap = np.zeros((n, k), dtype)
     hist = []
@@ -158,16 +242,13 @@ def bicgstab_paper(A, b, x0=None, eps=2.0 ** -23, maxit=10000, jacobi=True, merg
         p = pn.astype(dtype)
         Ap = mv(p)
         delta = _coldots(rh, Ap)
-        stalled = ~np.isfinite(delta) | (delta == 0.0)
-        alpha = np.where(stalled | ~live, 0.0, gam / np.where(stalled, 1.0, delta))
+        alpha, stall_now = scalar_after_delta(delta, gam, live)
         rs = (r.astype(np.float64) - alpha * Ap.astype(np.float64)).astype(dtype)
         xs = x.astype(np.float64) + alpha * p.astype(np.float64)
         As = mv(rs)
         s_AA = _coldots(As, As)
         s_sA = _coldots(rs, As)
-        om_bad = (s_AA == 0.0) | ~np.isfinite(s_AA)
-        omega = np.where(om_bad | ~live, 0.0, s_sA / np.where(om_bad, 1.0, s_AA))
-        omega = np.where(np.isfinite(omega), omega, 0.0)
+        omega = scalar_after_omega(s_sA, s_AA, live)
         if merged:
             s_hs = _coldots(rh, rs)
             s_hA = _coldots(rh, As)
@@ -180,16 +261,15 @@ def bicgstab_paper(A, b, x0=None, eps=2.0 ** -23, maxit=10000, jacobi=True, merg
         else:
             gam_n = _coldots(rh, r)
             rr = _coldots(r, r)
-        ok = ~stalled & (omega != 0.0)
-        alpha_p = np.where(ok, gam_n / np.where(stalled, 1.0, delta), 0.0)
-        beta = np.where(ok, alpha_p / np.where(omega == 0.0, 1.0, omega), 0.0)
-        gam = gam_n
-        new_state = np.where(rr < t2, CONVERGED,
-                             np.where(stalled | (omega == 0.0), STALLED, PROGRESSING))
-        state = np.where(live, new_state, state)
+        alpha_p, beta, gam, state = scalar_after_update(state, stall_now, omega, delta, gam, gam_n, rr, t2,
+                                                        live)
+        stalled_any |= state == STALLED
         if record:
-            hist.append((x.astype(np.float64).copy(), rr.copy(), state.copy()))
-    return PaperResult(x.astype(np.float64), it, state, hist)
+            hist.append(dict(x=x.astype(np.float64).copy(), rr=np.array(rr, np.float64), state=state.copy(),
+                             delta=np.array(delta), alpha=alpha.copy(), sA=np.array(s_sA), AA=np.array(s_AA),
+                             omega=omega.copy(), gam_n=np.array(gam_n, np.float64), alpha_p=alpha_p.copy(),
+                             beta=beta.copy(), live=live.copy()))
+    return PaperResult(x.astype(np.float64), it, state, hist, stalled_any)
 
 
 def cg_rotated(A, b, x0=None, eps=2.0 ** -23, maxit=10000):

@@ -51,9 +51,9 @@ def test_merged_reductions_match_direct_dots():
     s, A = _tiny(3, nf=150)
     r1 = solvers.bicgstab_paper(A, s.b, s.x0, eps=1e-30, maxit=6, record=True)
     r2 = solvers.bicgstab_paper(A, s.b, s.x0, eps=1e-30, maxit=6, merged=True, record=True)
-    for (x1, rr1, _), (x2, rr2, _) in zip(r1.history, r2.history):
-        np.testing.assert_allclose(x1, x2, rtol=0, atol=1e-9 * np.abs(x1).max())
-        np.testing.assert_allclose(rr1, rr2, rtol=1e-6)
+    for h1, h2 in zip(r1.history, r2.history):
+        np.testing.assert_allclose(h1["x"], h2["x"], rtol=0, atol=1e-9 * np.abs(h1["x"]).max())
+        np.testing.assert_allclose(h1["rr"], h2["rr"], rtol=1e-6)
 
 
 def test_stall_when_delta_is_zero():
@@ -115,3 +115,109 @@ def test_merged_and_direct_reductions_on_channel_and_slope():
                 counts[name, dtype, merged] = r.iters
     assert counts["couette", np.float32, True] == counts["couette", np.float32, False]
     assert counts["slope", np.float32, True] > counts["slope", np.float32, False]
+
+
+# ---- breakdown safeguards of Sec. 4.2 ("Stopping criterion"), reading X8, derived by hand ----
+
+C, S, P = solvers.CONVERGED, solvers.STALLED, solvers.PROGRESSING
+
+
+@pytest.mark.parametrize("freeze", [False, True])
+def test_two_by_two_iterates_by_hand(freeze):
+    """A = diag(1, 2), b = [e1, (1, 1)], x0 = 0, no Jacobi, worked out in exact arithmetic.
+
+    Column 0: p = r0 = e1, A p = e1, delta = 1, alpha = 1, r* = 0, A r* = 0, so omega
+    cannot be formed (0/0) and is zero; r.r = 0 < tau^2: converged after one iteration
+    with x = e1.  Column 1: gamma0 = 2, A p = (1, 2), delta = 3, alpha = 2/3,
+    r* = (1/3, -1/3), A r* = (1/3, -2/3), omega = (1/3)/(5/9) = 3/5, r = (2/15, 1/15),
+    x = (13/15, 7/15), gamma' = 1/5, alpha' = 1/15, beta = 1/9; then p = (8/45, 2/45),
+    delta = 4/15, alpha = 3/4 and r* = 0: x = (1, 1/2), converged after two.  Without
+    freezing, column 0 runs the second iteration too: p = 0 gives delta = 0 (a stall),
+    but r.r = 0 < tau^2 is checked first, so it stays converged and x is unchanged."""
+    A = sp.csr_matrix(np.diag([1.0, 2.0]))
+    b = np.array([[1.0, 1.0], [0.0, 1.0]])
+    res = solvers.bicgstab_paper(A, b, np.zeros((2, 2)), eps=1e-12, jacobi=False, freeze_done=freeze,
+                                 record=True)
+    assert res.iters == 2
+    np.testing.assert_array_equal(res.state, [C, C])
+    np.testing.assert_array_equal(res.stalled_any, [False, False])
+    h1, h2 = res.history
+    tol = dict(rtol=4e-16, atol=4e-16)
+    np.testing.assert_allclose(h1["x"], [[1.0, 13 / 15], [0.0, 7 / 15]], **tol)
+    np.testing.assert_allclose(h1["delta"], [1.0, 3.0], **tol)
+    np.testing.assert_allclose(h1["alpha"], [1.0, 2 / 3], **tol)
+    np.testing.assert_allclose(h1["omega"], [0.0, 3 / 5], **tol)
+    np.testing.assert_allclose(h1["gam_n"], [0.0, 1 / 5], **tol)
+    np.testing.assert_allclose(h1["alpha_p"], [0.0, 1 / 15], **tol)
+    np.testing.assert_allclose(h1["beta"], [0.0, 1 / 9], **tol)
+    np.testing.assert_array_equal(h1["state"], [C, P])
+    np.testing.assert_allclose(h2["delta"][1], 4 / 15, **tol)
+    np.testing.assert_allclose(h2["alpha"][1], 3 / 4, **tol)
+    np.testing.assert_allclose(res.x, [[1.0, 1.0], [0.0, 0.5]], rtol=0, atol=1e-15)
+    assert h2["alpha"][0] == 0.0 and h2["omega"][0] == 0.0
+    np.testing.assert_array_equal(h2["live"], [not freeze, True])
+
+
+def test_omega_zero_on_identity_is_converged():
+    """A = I: one iteration gives alpha = 1, r* = 0 and A r* = 0, so omega = 0; r.r = 0
+    makes the component converged (not stalled) with x = b exactly."""
+    A = sp.identity(3, format="csr")
+    b = np.array([[1.0], [2.0], [3.0]])
+    res = solvers.bicgstab_paper(A, b, np.zeros((3, 1)), record=True)
+    assert res.iters == 1 and res.state[0] == C and not res.stalled_any[0]
+    assert res.history[0]["omega"][0] == 0.0 and res.history[0]["alpha"][0] == 1.0
+    np.testing.assert_array_equal(res.x, b)
+
+
+def test_omega_from_an_overflowing_denominator_is_zero_and_stalls():
+    """A = diag(1e200, 1), b = (1, 1): delta = 1e200 + 1, alpha = 2/delta, r* = (-1, 1)
+    to rounding, A r* = (-1e200, 1) so Ar*.Ar* overflows to +inf: omega = 0, r = r*
+    with r.r = 2 > tau^2, hence stalled after one iteration with x = alpha (1, 1)."""
+    A = sp.csr_matrix(np.diag([1e200, 1.0]))
+    b = np.ones((2, 1))
+    res = solvers.bicgstab_paper(A, b, np.zeros((2, 1)), jacobi=False, record=True)
+    h = res.history[0]
+    assert res.iters == 1 and res.state[0] == S and res.stalled_any[0]
+    assert np.isinf(h["AA"][0]) and h["omega"][0] == 0.0
+    assert h["alpha_p"][0] == 0.0 and h["beta"][0] == 0.0
+    np.testing.assert_allclose(res.x[:, 0], 2e-200, rtol=1e-15)
+    np.testing.assert_allclose(h["rr"][0], 2.0, rtol=1e-15)
+
+
+def test_nonfinite_alpha_stalls():
+    """A = (1e-320) (a subnormal), b = 1: gamma = 1, delta = 1e-320 and gamma/delta
+    overflows: alpha = 0 and the component stalls with x = x0 = 0."""
+    A = sp.csr_matrix(np.array([[1e-320]]))
+    res = solvers.bicgstab_paper(A, np.ones((1, 1)), np.zeros((1, 1)), jacobi=False, record=True)
+    assert res.iters == 1 and res.state[0] == S
+    assert res.history[0]["alpha"][0] == 0.0
+    np.testing.assert_array_equal(res.x, 0.0)
+
+
+def test_scalar_steps_on_chosen_values():
+    """Each branch of the scalar steps on hand-chosen dots (reading X8)."""
+    live = np.ones(4, bool)
+    a, st = solvers.scalar_after_delta([0.0, np.nan, np.inf, 2.0], [1.0, 1.0, 1.0, 4.0], live)
+    np.testing.assert_array_equal(a, [0.0, 0.0, 0.0, 2.0])
+    np.testing.assert_array_equal(st, [True, True, True, False])
+    a, st = solvers.scalar_after_delta([1e-310, 3.0], [1e10, 1.0], np.array([True, False]))
+    np.testing.assert_array_equal(a, [0.0, 0.0])          # 1e10 / 1e-310 overflows; a frozen one stays 0
+    np.testing.assert_array_equal(st, [True, False])
+    om = solvers.scalar_after_omega([1.0, 1.0, 1.0, np.nan, 3.0, 1e300], [0.0, -1.0, np.inf, 2.0, 1.5, 1e-300],
+                                    np.ones(6, bool))
+    np.testing.assert_array_equal(om, [0.0, 0.0, 0.0, 0.0, 2.0, 0.0])
+    # update: converged first, then stalled (stall now / omega = 0 / r.r not finite), else progressing
+    state = np.array([P, P, P, P, P, P, C])
+    stall = np.array([True, False, False, False, False, False, False])
+    omega = np.array([0.5, 0.0, 0.5, 0.5, 0.5, 1e-300, 0.5])
+    delta = np.array([2.0, 2.0, 2.0, 2.0, 4.0, 1e-300, 2.0])
+    gam = np.full(7, 9.0)
+    gam_n = np.array([1.0, 1.0, 1.0, 1.0, 2.0, 1e10, 1.0])
+    rr = np.array([1.0, 1.0, 1e-30, np.nan, 1.0, 1.0, 1.0])
+    t2 = np.full(7, 1e-20)
+    live = np.array([True] * 6 + [False])
+    ap, be, g, s = solvers.scalar_after_update(state, stall, omega, delta, gam, gam_n, rr, t2, live)
+    np.testing.assert_array_equal(s, [S, S, C, S, P, P, C])
+    np.testing.assert_array_equal(ap, [0.0, 0.0, 0.5, 0.5, 0.5, 0.0, 0.0])
+    np.testing.assert_array_equal(be, [0.0, 0.0, 1.0, 1.0, 1.0, 0.0, 0.0])  # 1e10/1e-300 overflows: both 0
+    np.testing.assert_array_equal(g, [1.0, 1.0, 1.0, 1.0, 2.0, 1e10, 9.0])
