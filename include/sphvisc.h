@@ -249,6 +249,35 @@ sph_status sph_visc_solve(sph_neighbors* handle, const sph_visc_params* params,
                           const sph_solve_opts* opts, const double* b, double* x,
                           sph_solve_report* report, void* stream);
 
+/* Diagnostic for the breakdown safeguards: replays the scalar steps that
+ * sph_visc_solve runs after each of its grid reductions (Sec. 4.2, restructured
+ * listing and "Stopping criterion"), with the same device code on one warp, on
+ * dot products given by the caller instead of computed from a matrix:
+ *   after delta = r0^.A p:      alpha = gamma / delta; delta zero or not finite,
+ *                               or alpha not finite: alpha = 0, the component
+ *                               stalls this iteration;
+ *   after r*.Ar* and Ar*.Ar*:   omega = (r*.Ar*) / (Ar*.Ar*), 0 unless the
+ *                               denominator is positive and finite and the
+ *                               quotient finite;
+ *   after gamma' and r.r:       alpha' = gamma' / delta, beta = alpha' / omega
+ *                               (both 0 after a stall, for omega = 0, or when
+ *                               either is not finite); state converged if
+ *                               r.r < tau^2, else stalled on a stall, omega = 0
+ *                               or r.r not finite, else progressing.
+ * Components that are not progressing are frozen (all scalars 0, state kept);
+ * the pass is done when none progresses or the iteration count reaches maxit,
+ * after which no further step runs (as in the solver's loop).
+ * gamma0: (host) [3] r0.r0 of the pass, which is also the base of
+ *   tau^2 = max(eps^2 gamma0, FLT_MIN);
+ * dots: (host) [nsteps][15]: delta[3], r*.Ar*[3], Ar*.Ar*[3], gamma'[3], r.r[3];
+ * out: (host) [nsteps + 1][20]: row 0 after the pass initialisation, row i
+ *   after iteration i: alpha[3], omega[3], alpha'[3], beta[3], state[3],
+ *   stalled_any[3], iterations, done (all as doubles).
+ * 0 <= nsteps <= 100000, maxit >= 1.  Allocates a small device buffer;
+ * synchronises the stream. */
+sph_status sph_bicgstab_replay(const double* gamma0, double eps, int32_t maxit, int32_t nsteps, const double* dots,
+                               double* out, void* stream);
+
 /* One time step's viscous solve from HOST buffers (no counterpart in the paper;
  * the call a host-side time integrator makes): copies the scene (pos, rho, mu,
  * ptype: HOST pointers here, same layouts as sph_scene), b and either vel or x

@@ -30,7 +30,7 @@ EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", 
            "sph_batch_create", "sph_batch_solve", "sph_batch_info", "sph_batch_destroy",
            "sph_mlp_create", "sph_mlp_set_params", "sph_mlp_get_params", "sph_mlp_destroy", "sph_mlp_features",
            "sph_mlp_targets", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train_step", "sph_warm_start",
-           "sph_mlp_residual_targets", "sph_mlp_set_mode", "sph_visc_solve_host"]
+           "sph_mlp_residual_targets", "sph_mlp_set_mode", "sph_visc_solve_host", "sph_bicgstab_replay"]
 MLP_NPARAMS = 9603
 
 
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH):
         "sph_mlp_residual_targets": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp, vp, ctypes.c_int, vp, vp,
                                      vp, ctypes.POINTER(dbl), vp],
         "sph_profile_read": [vp, ctypes.POINTER(sph_profile_counters), i32],
+        "sph_bicgstab_replay": [vp, dbl, i32, i32, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -158,6 +159,20 @@ def launch_count():
     c = sph_profile_counters()
     _check(_lib.sph_profile_read(None, ctypes.byref(c), 0))
     return c.launches
+
+
+def bicgstab_replay(gamma0, eps, maxit, dots, stream=None):
+    """sph_bicgstab_replay: the solver's scalar steps on given dots ([k][15] float64).
+    Returns the [k + 1][20] table (alpha, omega, alpha', beta, state, stalled_any per
+    component, iterations, done) after the initialisation and after each step."""
+    load()
+    g = np.ascontiguousarray(gamma0, np.float64).reshape(3)
+    d = np.ascontiguousarray(dots, np.float64).reshape(-1, 15)
+    out = np.empty((d.shape[0] + 1, 20), np.float64)
+    _check(_lib.sph_bicgstab_replay(g.ctypes.data_as(ctypes.c_void_p), float(eps), int(maxit), int(d.shape[0]),
+                                    d.ctypes.data_as(ctypes.c_void_p) if d.shape[0] else None,
+                                    out.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return out
 
 
 def visc_params(dt, boundary=SPH_BC_DUMMY, mean=SPH_MEAN_HARMONIC):

@@ -269,6 +269,12 @@ sph_status sph_mu_papanastasiou(sph_neighbors* h, const float* vel, const float*
   return mu_papanastasiou(h, vel, wall_vel, tau0, mu0, m, mu_out, set_handle, as_stream(stream));
 }
 
+sph_status sph_bicgstab_replay(const double* gamma0, double eps, int32_t maxit, int32_t nsteps, const double* dots,
+                               double* out, void* stream) {
+  clear_error();
+  return bicgstab_replay(gamma0, eps, maxit, nsteps, dots, out, as_stream(stream));
+}
+
 sph_status sph_profile_enable(sph_neighbors* h, int32_t on) {
   clear_error();
   if (!h) {

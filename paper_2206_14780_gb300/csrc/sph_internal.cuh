@@ -328,6 +328,10 @@ sph_status solve_fp64(sph_neighbors* H, const sph_visc_params* P, const sph_solv
 
 int grid_for(const sph_neighbors* H, int64_t work_items, int block = kBlock);
 
+// replay.cu: the solver's scalar steps on caller-given dots (sph_bicgstab_replay)
+sph_status bicgstab_replay(const double* gamma0, double eps, int32_t maxit, int32_t nsteps, const double* dots,
+                           double* out, cudaStream_t st);
+
 // event pair around the two apply launches of every kProfStride-th iteration
 // when profiling is on (sampling keeps the event records from slowing the
 // loop they time); prof_flush folds the recorded pairs of launches that did
