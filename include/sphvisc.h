@@ -209,7 +209,9 @@ typedef struct {
                               gamma' = r0^.r* - w r0^.Ar*, |r|^2 = |r*|^2 - 2w
                               r*.Ar* + w^2 |Ar*|^2                               */
   int32_t chunk;           /* iterations launched between host checks (>= 1)      */
-  int32_t jacobi;          /* 1: left Jacobi scaling (App. B); 0: none            */
+  int32_t jacobi;          /* 1: Jacobi scaling (App. B): left scaling of the
+                              BiCGSTAB system, z = D^-1 r in the CG; 0: none
+                              (CG only: BiCGSTAB returns SPH_ERR_INVALID)        */
   int32_t apply_form;      /* 0: the autotuner picks the operator apply's row-loop
                               form per phase (default); k = 1..6: use form k - 1
                               (sph_profile_counters.apply_variant numbering)     */
@@ -217,7 +219,23 @@ typedef struct {
                               dependent launches, each launch processed while its
                               predecessor still runs (default); 1: plain
                               stream-ordered launches.  Same results either way   */
+  int32_t method;          /* SPH_SOLVER_BICGSTAB (default) or SPH_SOLVER_CG      */
 } sph_solve_opts;
+
+/* Inner iteration of sph_visc_solve (sph_solve_opts.method).
+ * SPH_SOLVER_BICGSTAB: the restructured BiCGSTAB of Sec. 4.2 on the Jacobi-scaled
+ *   system (App. B); needs jacobi = 1.
+ * SPH_SOLVER_CG: the rotated conjugate gradient of Sec. 4.1 (second listing: p
+ *   update first, beta and the convergence check last, alpha = 0 while r is
+ *   not small is a stall, single exit), preconditioned with z = D^-1 r when
+ *   jacobi = 1 (App. B).  It needs a symmetric matrix: the dynamic boundary
+ *   model (the dummy model returns SPH_ERR_INVALID) with one particle mass, for
+ *   which the fluid block is symmetric (Sec. 4).  Identity rows start at x = b,
+ *   their exact value, so every residual vanishes on the walls and the
+ *   iteration runs on the reduced fluid system of Sec. 4 whatever the wall
+ *   velocities.  One operator apply per iteration instead of two.  Mixed
+ *   precision only; apply_form 0..4; merged_reductions is ignored. */
+enum { SPH_SOLVER_BICGSTAB = 0, SPH_SOLVER_CG = 1 };
 
 typedef struct {
   int32_t status;          /* same value the call returns                        */

@@ -10,7 +10,8 @@
   Jacobi scaling (App. B), merged reductions (the two identities
   gamma' = r0^.r* - omega r0^.Ar* and |r|^2 = |r*|^2 - 2 omega r*.Ar* + omega^2 |Ar*|^2),
   and float32 vector storage to mimic a single-precision implementation.
-* ``cg_rotated``         the rotated CG (Sec. 4.1, second listing).
+* ``cg_rotated``         the rotated CG (Sec. 4.1, second listing), optionally
+  preconditioned with the Jacobi diagonal (z = D^-1 r, App. B).
 * ``dense_solve``        numpy's LU (library routine) on the dense matrix.
 * ``gauss_elim``         Gaussian elimination with partial pivoting, by hand.
 
@@ -272,38 +273,71 @@ def bicgstab_paper(A, b, x0=None, eps=2.0 ** -23, maxit=10000, jacobi=True, merg
     return PaperResult(x.astype(np.float64), it, state, hist, stalled_any)
 
 
-def cg_rotated(A, b, x0=None, eps=2.0 ** -23, maxit=10000):
-    """Rotated CG of Sec. 4.1 on each column: p update first, beta and the check last."""
+def cg_rotated(A, b, x0=None, eps=2.0 ** -23, maxit=10000, jacobi=False, record=False):
+    """Rotated CG of Sec. 4.1 on each column: p update first, beta and the check last.
+
+    Per iteration i: p_i = z_i + beta_i p_{i-1} (beta_0 = 0, so p_{-1} is never read),
+    alpha_i = r_i.z_i / p_i.A p_i, r_{i+1} = r_i - alpha_i A p_i,
+    x_{i+1} = x_i + alpha_i p_i, beta_{i+1} = r_{i+1}.z_{i+1} / r_i.z_i, and the
+    column is converged when r_{i+1}.r_{i+1} < tau^2 (tau^2 from the column's b).
+    Without ``jacobi`` z = r (the printed listing); with it z = D^-1 r, the Jacobi
+    preconditioner of App. B applied so that the iteration stays symmetric.
+    "Stopping criterion": alpha = 0 in finite precision while r.r >= tau^2 is a
+    stall (a zero or non-finite p.Ap, or a non-finite alpha, gives alpha = 0); the
+    iteration completes and the column exits.  Returns (x, iterations per column);
+    with ``record`` also the final states and, per column, x after each iteration.
+    """
     A = sp.csr_matrix(A, dtype=np.float64)
     b = np.asarray(b, np.float64)
     if b.ndim == 1:
         b = b[:, None]
     n, k = b.shape
+    w = 1.0 / A.diagonal() if jacobi else np.ones(n)
     X = np.zeros_like(b) if x0 is None else np.asarray(x0, np.float64).reshape(n, k).copy()
     its = np.zeros(k, np.int64)
-    for c in range(k):
-        x = X[:, c]
-        r = b[:, c] - A @ x
-        t2 = float(tau2(_dot(b[:, c], b[:, c]), eps))
-        rr = _dot(r, r)
-        beta = 0.0
-        p = None
-        i = 0
-        while rr >= t2 and i < maxit:
-            p = r.copy() if beta == 0.0 else r + beta * p
-            Ap = A @ p
-            pAp = _dot(p, Ap)
-            alpha = rr / pAp if pAp != 0.0 else 0.0
-            r = r - alpha * Ap
-            x = x + alpha * p
-            rr_new = _dot(r, r)
-            beta = rr_new / rr
-            rr = rr_new
-            i += 1
-            if alpha == 0.0:
-                break
-        X[:, c] = x
-        its[c] = i
+    states = np.full(k, CONVERGED)
+    hist = [[] for _ in range(k)]
+    with np.errstate(all="ignore"):
+        for c in range(k):
+            x = X[:, c]
+            r = b[:, c] - A @ x
+            t2 = float(tau2(_dot(b[:, c], b[:, c]), eps))
+            z = w * r
+            gam = _dot(r, z)
+            rr = _dot(r, r)
+            beta = 0.0
+            p = None
+            i = 0
+            state = CONVERGED if rr < t2 else PROGRESSING
+            while state == PROGRESSING and i < maxit:
+                p = z.copy() if beta == 0.0 else z + beta * p
+                Ap = A @ p
+                pAp = _dot(p, Ap)
+                alpha = np.float64(gam) / np.float64(pAp) if (pAp != 0.0 and np.isfinite(pAp)) else 0.0
+                if not np.isfinite(alpha):
+                    alpha = 0.0
+                stall = alpha == 0.0
+                r = r - alpha * Ap
+                x = x + alpha * p
+                z = w * r
+                gam_n = _dot(r, z)
+                rr = _dot(r, r)
+                beta = 0.0 if stall else np.float64(gam_n) / np.float64(gam)
+                if not np.isfinite(beta):
+                    beta = 0.0
+                gam = gam_n
+                i += 1
+                if rr < t2:
+                    state = CONVERGED
+                elif stall or not np.isfinite(rr):
+                    state = STALLED
+                if record:
+                    hist[c].append(x.copy())
+            X[:, c] = x
+            its[c] = i
+            states[c] = state
+    if record:
+        return X, its, states, hist
     return X, its
 
 
@@ -336,20 +370,28 @@ def gauss_elim(A, b):
     return X
 
 
-def reference_solution(A, b, x0=None, rtol=1e-13, maxit=20000):
+def reference_solution(A, b, x0=None, rtol=1e-13, maxit=20000, stats=None):
     """x = A^{-1} b to a float64 true relative residual of about rtol.
 
     Textbook BiCGSTAB with Jacobi scaling, restarted from the true residual until
-    ||b - A x|| / ||b|| <= rtol (joint over components).
+    ||b - A x|| / ||b|| <= rtol (joint over components).  ``stats`` (a dict, optional)
+    receives the restarts and the BiCGSTAB iterations per component.
     """
     A = sp.csr_matrix(A, dtype=np.float64)
     b = np.asarray(b, np.float64)
     x = np.zeros_like(b) if x0 is None else np.asarray(x0, np.float64).copy()
     nb = np.linalg.norm(b)
+    its_total = np.zeros(b.shape[1] if b.ndim > 1 else 1, np.int64)
+    passes = 0
     for _ in range(20):
         r = b - A @ x
         if np.linalg.norm(r) <= rtol * nb:
             break
-        d, _ = bicgstab_textbook(A, r, None, eps=rtol * 0.1, maxit=maxit, jacobi=True)
+        d, its = bicgstab_textbook(A, r, None, eps=rtol * 0.1, maxit=maxit, jacobi=True)
+        its_total += its
+        passes += 1
         x = x + d
+    if stats is not None:
+        stats["passes"] = passes
+        stats["iterations"] = [int(v) for v in its_total]
     return x

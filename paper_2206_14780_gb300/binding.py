@@ -22,6 +22,7 @@ SPH_BC_DUMMY, SPH_BC_DYNAMIC = 0, 1
 SPH_MEAN_HARMONIC, SPH_MEAN_ARITHMETIC = 0, 1
 SPH_PREC_MIXED, SPH_PREC_FP64 = 0, 1
 SPH_CONVERGED, SPH_STALLED, SPH_PROGRESSING = 0, 1, 2
+SPH_SOLVER_BICGSTAB, SPH_SOLVER_CG = 0, 1
 
 # every symbol include/sphvisc.h declares
 EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", "sph_set_viscosity",
@@ -48,7 +49,7 @@ class sph_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("eps_inner", ctypes.c_double), ("maxit", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("merged_reductions", ctypes.c_int32), ("chunk", ctypes.c_int32), ("jacobi", ctypes.c_int32),
-                ("apply_form", ctypes.c_int32), ("launch_mode", ctypes.c_int32)]
+                ("apply_form", ctypes.c_int32), ("launch_mode", ctypes.c_int32), ("method", ctypes.c_int32)]
 
 
 class sph_solve_report(ctypes.Structure):
@@ -180,9 +181,10 @@ def visc_params(dt, boundary=SPH_BC_DUMMY, mean=SPH_MEAN_HARMONIC):
 
 
 def solve_opts(rtol=1e-6, eps_inner=2e-2, maxit=20000, max_refine=30, precision=SPH_PREC_MIXED,
-               merged_reductions=0, chunk=8, jacobi=1, apply_form=0, launch_mode=0):
+               merged_reductions=0, chunk=8, jacobi=1, apply_form=0, launch_mode=0, method=0):
+    """sph_solve_opts; method 0 = BiCGSTAB, 1 = the rotated conjugate gradient (SPH_SOLVER_CG)."""
     return sph_solve_opts(rtol, eps_inner, maxit, max_refine, precision, merged_reductions, chunk, jacobi,
-                          apply_form, launch_mode)
+                          apply_form, launch_mode, method)
 
 
 def scene_tensors(scene, device="cuda"):

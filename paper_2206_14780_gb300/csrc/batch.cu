@@ -710,6 +710,10 @@ sph_status sph_batch_solve(sph_batch* Bt, const sph_solve_opts* O, const double*
     set_error("sph_batch_solve: only SPH_PREC_MIXED is batched");
     return SPH_ERR_INVALID;
   }
+  if (O->method != SPH_SOLVER_BICGSTAB || !O->jacobi) {
+    set_error("sph_batch_solve: the batch runs the Jacobi-scaled BiCGSTAB (method 0, jacobi 1)");
+    return SPH_ERR_INVALID;
+  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const double rtol = O->rtol > 0.0 ? O->rtol : 1e-6;
   const double eps = O->eps_inner > 0.0 ? O->eps_inner : 2e-2;

@@ -1,4 +1,5 @@
-// Scalar side of the restructured BiCGSTAB (paper Sec. 4.2): run by thread 0 of
+// Scalar side of the restructured BiCGSTAB (paper Sec. 4.2) and of the rotated
+// CG (Sec. 4.1, at the end of this file): run by thread 0 of
 // the last block after each grid reduction, shared by the float32 and float64
 // solves.  States per component follow the "Stopping criterion" paragraph:
 // converged (r.r < tau^2), stalled (delta = 0, or a coefficient that zeroes out)
@@ -127,6 +128,84 @@ __device__ inline void scal_init(SolverScalars* S, const double* g, double eps2,
     S->stall_now[c] = 0;
     S->stalled_any[c] = 0;
     const int st = (g[c] == 0.0 || g[c] < S->tau2[c]) ? SPH_CONVERGED : SPH_PROGRESSING;
+    S->state[c] = st;
+    progressing += (st == SPH_PROGRESSING);
+  }
+  S->iter = 0;
+  S->maxit = maxit;
+  S->nonfinite = 0;
+  S->done = progressing == 0 ? 1 : 0;
+  S->pad = S->done;
+}
+
+// ---- rotated conjugate gradient (Sec. 4.1, second listing) ---------------------
+// Per iteration: p = z + beta p (z = D^-1 r with Jacobi, App. B; z = r without);
+// alpha = gamma / (p.Ap) with gamma = r.z; r -= alpha Ap; x += alpha p;
+// gamma' = r.z'; beta = gamma' / gamma; converged when r.r < tau^2.  "Stopping
+// criterion" of Sec. 4.1: alpha = 0 in finite precision while r is not small is a
+// stall (a p.Ap that is zero or not finite, or an alpha that is not finite, gives
+// alpha = 0); the iteration completes and the pass exits at its single end point.
+
+__device__ inline void scal_cg_alpha_c(SolverScalars* S, const double* dots, int c) {
+  if (S->state[c] != SPH_PROGRESSING) {
+    S->alpha[c] = 0.0;
+    S->stall_now[c] = 0;
+    return;
+  }
+  const double d = dots[c];
+  S->delta[c] = d;
+  double a = (d != 0.0 && isfinite(d)) ? S->gamma[c] / d : 0.0;
+  if (!isfinite(a)) a = 0.0;
+  S->alpha[c] = a;
+  S->stall_now[c] = a == 0.0 ? 1 : 0;
+}
+
+__device__ inline int scal_cg_update_c(SolverScalars* S, const double* gam_new, const double* rr, int c) {
+  if (S->state[c] != SPH_PROGRESSING) {
+    S->beta[c] = 0.0;
+    return S->state[c];
+  }
+  double be = S->stall_now[c] ? 0.0 : gam_new[c] / S->gamma[c];
+  if (!isfinite(be)) be = 0.0;
+  if (!isfinite(gam_new[c]) || !isfinite(rr[c])) S->nonfinite = 1;
+  S->beta[c] = be;
+  S->gamma[c] = gam_new[c];
+  S->rr[c] = rr[c];
+  int st;
+  if (rr[c] < S->tau2[c]) st = SPH_CONVERGED;
+  else if (S->stall_now[c] || !isfinite(rr[c])) st = SPH_STALLED;
+  else st = SPH_PROGRESSING;
+  if (st == SPH_STALLED) S->stalled_any[c] = 1;
+  S->state[c] = st;
+  return st;
+}
+
+__device__ inline void scal_cg_alpha_w(SolverScalars* S, const double* dots) {
+  const int lane = threadIdx.x & 31;
+  if (lane < 3) scal_cg_alpha_c(S, dots, lane);
+}
+
+__device__ inline void scal_cg_update_w(SolverScalars* S, const double* gam_new, const double* rr) {
+  const int lane = threadIdx.x & 31;
+  const int st = lane < 3 ? scal_cg_update_c(S, gam_new, rr, lane) : SPH_CONVERGED;
+  const unsigned prog = __ballot_sync(0xffffffffu, st == SPH_PROGRESSING);
+  if (lane == 0) {
+    S->iter += 1;
+    S->done = (prog == 0u || S->iter >= S->maxit) ? 1 : 0;
+  }
+}
+
+// CG pass initialisation: gamma = r0.z0, tau^2 base = r0.r0
+__device__ inline void scal_cg_init(SolverScalars* S, const double* gz, const double* rr, double eps2, int maxit) {
+  int progressing = 0;
+  for (int c = 0; c < 3; ++c) {
+    S->gamma[c] = gz[c];
+    S->rr[c] = rr[c];
+    S->tau2[c] = fmax(eps2 * rr[c], kFltMin);
+    S->alpha[c] = S->alpha_p[c] = S->beta[c] = S->omega[c] = S->delta[c] = 0.0;
+    S->stall_now[c] = 0;
+    S->stalled_any[c] = 0;
+    const int st = (rr[c] == 0.0 || rr[c] < S->tau2[c]) ? SPH_CONVERGED : SPH_PROGRESSING;
     S->state[c] = st;
     progressing += (st == SPH_PROGRESSING);
   }

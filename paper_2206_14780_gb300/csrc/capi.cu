@@ -249,6 +249,10 @@ sph_status sph_visc_solve(sph_neighbors* h, const sph_visc_params* params, const
               kApplyVariants, opts->launch_mode);
     return SPH_ERR_INVALID;
   }
+  if (opts->precision == SPH_PREC_FP64 && (opts->method != SPH_SOLVER_BICGSTAB || !opts->jacobi)) {
+    set_error("sph_visc_solve: the float64 solve is the Jacobi-scaled BiCGSTAB (method 0, jacobi 1)");
+    return SPH_ERR_INVALID;
+  }
   if (opts->precision == SPH_PREC_MIXED) return solve_mixed(h, params, opts, b, x, report, as_stream(stream));
   if (opts->precision == SPH_PREC_FP64) return solve_fp64(h, params, opts, b, x, report, as_stream(stream));
   set_error("sph_visc_solve: unknown precision %d", opts->precision);

@@ -44,7 +44,7 @@ namespace sph {
 
 namespace {
 
-enum Phase : int { PH_DELTA = 0, PH_OMEGA = 1, PH_OMEGA_MERGED = 2 };
+enum Phase : int { PH_DELTA = 0, PH_OMEGA = 1, PH_OMEGA_MERGED = 2, PH_CG = 3 };
 
 struct Vecs {
   float4* r;
@@ -113,9 +113,12 @@ __global__ void __launch_bounds__(kBlock) k_p_update(int64_t n_pad, Vecs V, cons
 //   PH_DELTA:        v = p,  y = Ap; dots r0^.Ap                       (K = 3)
 //   PH_OMEGA:        v = r*, y = Ar*; dots r*.Ar*, Ar*.Ar*             (K = 6)
 //   PH_OMEGA_MERGED: + r0^.r*, r0^.Ar*, r*.r*                          (K = 15)
+//   PH_CG:           y = A v without the Jacobi scaling (the rotated CG keeps
+//                    the matrix symmetric and preconditions through z = D^-1 r);
+//                    v = p, y = Ap; dots p.Ap                          (K = 3)
 template <int PH>
 struct PhaseDots {
-  static constexpr int K = PH == PH_DELTA ? 3 : (PH == PH_OMEGA ? 6 : 15);
+  static constexpr int K = (PH == PH_DELTA || PH == PH_CG) ? 3 : (PH == PH_OMEGA ? 6 : 15);
 };
 
 template <int PH>
@@ -125,6 +128,10 @@ __device__ __forceinline__ void dots_row(float* acc, float4 o, float4 vb, const 
     acc[0] = fmaf(h.x, o.x, acc[0]);
     acc[1] = fmaf(h.y, o.y, acc[1]);
     acc[2] = fmaf(h.z, o.z, acc[2]);
+  } else if (PH == PH_CG) {
+    acc[0] = fmaf(vb.x, o.x, acc[0]);
+    acc[1] = fmaf(vb.y, o.y, acc[1]);
+    acc[2] = fmaf(vb.z, o.z, acc[2]);
   } else {
     acc[0] = fmaf(vb.x, o.x, acc[0]);
     acc[1] = fmaf(vb.y, o.y, acc[1]);
@@ -160,6 +167,8 @@ __device__ __forceinline__ void dots_finish(const float (&acc)[PhaseDots<PH>::K]
     if (threadIdx.x < 32) {
       if (PH == PH_DELTA) {
         scal_after_delta_w(S, res);
+      } else if (PH == PH_CG) {
+        scal_cg_alpha_w(S, res);
       } else {
         scal_after_omega_w(S, res);
         if (PH == PH_OMEGA_MERGED) {
@@ -195,7 +204,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_apply_dot(OpView op, const float4
   for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nwarps) {
     const int64_t s = sl * kSlice + lane;
     float4 vb;
-    const float4 o = apply_row<U, PF, true>(op, v, sl, lane, vb);
+    const float4 o = apply_row<U, PF, PH != PH_CG>(op, v, sl, lane, vb);
     y[s] = o;
     dots_row<PH>(acc, o, vb, rh, s);
   }
@@ -431,17 +440,20 @@ __global__ void __launch_bounds__(kBlock, 3) k_apply_dot_union(OpView op, const 
 
 // [phase][variant] with variants (U, PF) = (8,0), (4,0), (8,1), (4,1) as in apply.cuh,
 // 4 = the stream staged through shared memory by bulk copies, 5 = per-slice
-// neighbour unions in shared memory
+// neighbour unions in shared memory; the CG phase has the register forms only
+// (its 4 and 5 are the (4,1) form)
 ApplyDotFn apply_kernel(int phase, int variant) {
-  static const ApplyDotFn table[3][kApplyVariants] = {
+  static const ApplyDotFn table[4][kApplyVariants] = {
       {k_apply_dot<PH_DELTA, 8, false>, k_apply_dot<PH_DELTA, 4, false>, k_apply_dot<PH_DELTA, 8, true>,
        k_apply_dot<PH_DELTA, 4, true>, k_apply_dot_staged<PH_DELTA>, k_apply_dot_union<PH_DELTA>},
       {k_apply_dot<PH_OMEGA, 8, false>, k_apply_dot<PH_OMEGA, 4, false>, k_apply_dot<PH_OMEGA, 8, true>,
        k_apply_dot<PH_OMEGA, 4, true>, k_apply_dot_staged<PH_OMEGA>, k_apply_dot_union<PH_OMEGA>},
       {k_apply_dot<PH_OMEGA_MERGED, 8, false>, k_apply_dot<PH_OMEGA_MERGED, 4, false>,
        k_apply_dot<PH_OMEGA_MERGED, 8, true>, k_apply_dot<PH_OMEGA_MERGED, 4, true>,
-       k_apply_dot_staged<PH_OMEGA_MERGED>, k_apply_dot_union<PH_OMEGA_MERGED>}};
-  return table[phase < 0 ? 0 : (phase > 2 ? 2 : phase)][variant < 0 || variant >= kApplyVariants ? 0 : variant];
+       k_apply_dot_staged<PH_OMEGA_MERGED>, k_apply_dot_union<PH_OMEGA_MERGED>},
+      {k_apply_dot<PH_CG, 8, false>, k_apply_dot<PH_CG, 4, false>, k_apply_dot<PH_CG, 8, true>,
+       k_apply_dot<PH_CG, 4, true>, k_apply_dot<PH_CG, 4, true>, k_apply_dot<PH_CG, 4, true>}};
+  return table[phase < 0 ? 0 : (phase > 3 ? 3 : phase)][variant < 0 || variant >= kApplyVariants ? 0 : variant];
 }
 
 size_t apply_smem(int variant) { return variant == 5 ? union_smem_bytes() : 0; }
@@ -459,6 +471,9 @@ static sph_status apply_attrs() {
       SPH_TRY_CUDA(cudaFuncSetAttribute((const void*)apply_kernel(ph, v),
                                         cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1));
   }
+  for (int v = 0; v < kApplyVariantsRegister; ++v)
+    SPH_TRY_CUDA(cudaFuncSetAttribute((const void*)apply_kernel(PH_CG, v), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxL1));
   done = true;
   return SPH_OK;
 }
@@ -547,6 +562,107 @@ __global__ void __launch_bounds__(kBlock) k_xrp_update(int64_t n_pad, Vecs V, So
   }
 }
 
+// ---- rotated CG (Sec. 4.1), Jacobi-preconditioned through z = D^-1 r (App. B) ----
+// One pass solves A d = r64 (the matrix itself, kept symmetric); per iteration
+//   k_cg_p:            p = z + beta p   (z = w r, w = 1/D or 1; beta = 0 reads no p)
+//   k_apply_dot<PH_CG>: Ap = A p, p.Ap  -> alpha = gamma / p.Ap
+//   k_cg_xr:           r -= alpha Ap, d += alpha p; r.z and r.r -> beta, states
+
+// r = float32(r64), d = 0; gamma = r.z, r.r
+__global__ void __launch_bounds__(kBlock) k_cg_init(const double* __restrict__ r64, const float* __restrict__ invD,
+                                                    int jacobi, int64_t n_pad, Vecs V, double eps2, int maxit,
+                                                    SolverScalars* S, double* partials, unsigned int* counter) {
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    const float4 r = make_float4((float)r64[3 * s], (float)r64[3 * s + 1], (float)r64[3 * s + 2], 0.f);
+    const float w = jacobi ? invD[s] : 1.f;
+    V.r[s] = r;
+    V.d[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    acc[0] = fmaf(r.x, w * r.x, acc[0]);
+    acc[1] = fmaf(r.y, w * r.y, acc[1]);
+    acc[2] = fmaf(r.z, w * r.z, acc[2]);
+    acc[3] = fmaf(r.x, r.x, acc[3]);
+    acc[4] = fmaf(r.y, r.y, acc[4]);
+    acc[5] = fmaf(r.z, r.z, acc[5]);
+  }
+  block_partials<6>(acc, partials + (size_t)blockIdx.x * kMaxDots);
+  if (arrive_last(counter)) {
+    __shared__ double res[6];
+    final_sum<6>(partials, counter, res);
+    if (threadIdx.x == 0) scal_cg_init(S, res, res + 3, eps2, maxit);
+  }
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(kBlock) k_cg_p(int64_t n_pad, Vecs V, const float* __restrict__ invD, int jacobi,
+                                                 const SolverScalars* __restrict__ S) {
+  griddep_wait();
+  if (S->done) return;
+  const float b0 = (float)S->beta[0], b1 = (float)S->beta[1], b2 = (float)S->beta[2];
+  const bool useP = (b0 != 0.f) || (b1 != 0.f) || (b2 != 0.f);
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    const float4 r = V.r[s];
+    const float w = jacobi ? invD[s] : 1.f;
+    float4 p = make_float4(w * r.x, w * r.y, w * r.z, 0.f);
+    if (useP) {
+      const float4 q = V.p[s];
+      p.x = fmaf(b0, q.x, p.x);
+      p.y = fmaf(b1, q.y, p.y);
+      p.z = fmaf(b2, q.z, p.z);
+    }
+    V.p[s] = p;
+  }
+}
+
+// r -= alpha Ap; d += alpha p; dots r.z, r.r
+__global__ void __launch_bounds__(kBlock) k_cg_xr(int64_t n_pad, Vecs V, const float* __restrict__ invD, int jacobi,
+                                                  SolverScalars* S, double* partials, unsigned int* counter) {
+  griddep_wait();
+  if (S->done) return;
+  const float a0 = (float)S->alpha[0], a1 = (float)S->alpha[1], a2 = (float)S->alpha[2];
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    const float4 ap = V.Ap[s], p = V.p[s];
+    float4 r = V.r[s], d = V.d[s];
+    r.x = fmaf(-a0, ap.x, r.x);
+    r.y = fmaf(-a1, ap.y, r.y);
+    r.z = fmaf(-a2, ap.z, r.z);
+    d.x = fmaf(a0, p.x, d.x);
+    d.y = fmaf(a1, p.y, d.y);
+    d.z = fmaf(a2, p.z, d.z);
+    V.r[s] = r;
+    V.d[s] = d;
+    const float w = jacobi ? invD[s] : 1.f;
+    acc[0] = fmaf(r.x, w * r.x, acc[0]);
+    acc[1] = fmaf(r.y, w * r.y, acc[1]);
+    acc[2] = fmaf(r.z, w * r.z, acc[2]);
+    acc[3] = fmaf(r.x, r.x, acc[3]);
+    acc[4] = fmaf(r.y, r.y, acc[4]);
+    acc[5] = fmaf(r.z, r.z, acc[5]);
+  }
+  block_partials<6>(acc, partials + (size_t)blockIdx.x * kMaxDots);
+  if (arrive_last(counter)) {
+    __shared__ double res[6];
+    prefetch_scalars(S, sizeof(SolverScalars));
+    final_sum<6>(partials, counter, res);
+    if (threadIdx.x < 32) scal_cg_update_w(S, res, res + 3);
+  }
+}
+
+// identity rows (dynamic walls) take x = b before a CG solve: their exact value,
+// which keeps the wall rows of every residual zero, so the iteration only ever
+// sees the symmetric fluid block (the reduced system of Sec. 4)
+__global__ void k_identity_rows_take_b(const uint8_t* __restrict__ kind, int64_t n_pad, const double* __restrict__ b,
+                                       double* __restrict__ x) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    if (kind[s] == KIND_IDENTITY) {
+      x[3 * s] = b[3 * s];
+      x[3 * s + 1] = b[3 * s + 1];
+      x[3 * s + 2] = b[3 * s + 2];
+    }
+  }
+}
+
 // x64 += d
 __global__ void k_add_correction(int64_t n_pad, const float4* __restrict__ d, double* __restrict__ x) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
@@ -601,7 +717,7 @@ __global__ void __launch_bounds__(kBlock) k_norm2_d3(const double* __restrict__ 
 }  // namespace
 
 // Counters: one per reduction site, so consecutive kernels never share one.
-enum { CNT_INIT = 0, CNT_DELTA, CNT_OMEGA, CNT_XR, CNT_XRP, CNT_RES, CNT_NORM, CNT_TUNE, CNT_COUNT };
+enum { CNT_INIT = 0, CNT_DELTA, CNT_OMEGA, CNT_XR, CNT_XRP, CNT_RES, CNT_NORM, CNT_TUNE, CNT_CG_A, CNT_CG_XR, CNT_COUNT };
 
 sph_status ensure_workspace(sph_neighbors* H) {
   const int64_t np = H->n_pad;
@@ -682,8 +798,14 @@ static cudaError_t launch_apply_dot(sph_neighbors* H, bool pdl, int grid, const 
                                     float4* y, const float4* rh, SolverScalars* S, unsigned int* counter,
                                     cudaStream_t st) {
   const bool forced = H->force_form >= 0;
-  const int var = forced ? H->force_form : H->apply_var[PH];
-  const int tg = forced ? H->force_grid : H->apply_grid[PH];
+  // the CG phase runs the register form the tuner chose for the delta phase (same dots)
+  const int tp = PH == PH_CG ? PH_DELTA : PH;
+  int var = forced ? H->force_form : H->apply_var[tp];
+  int tg = forced ? H->force_grid : H->apply_grid[tp];
+  if (PH == PH_CG && var >= kApplyVariantsRegister) {
+    var = kApplyVariantsRegister - 1;
+    tg = 0;
+  }
   const int g = tg > 0 && tg < grid ? tg : grid;
   const ApplyDotFn kern = apply_kernel(PH, var);
   prof_begin(H, st, PH == PH_DELTA ? 0 : 1);
@@ -714,6 +836,25 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
     set_error("sph_visc_solve: apply_form %d outside 0..%d", O->apply_form, kApplyVariants);
     return SPH_ERR_INVALID;
   }
+  const bool cg = O->method == SPH_SOLVER_CG;
+  if (O->method != SPH_SOLVER_BICGSTAB && O->method != SPH_SOLVER_CG) {
+    set_error("sph_visc_solve: unknown method %d", O->method);
+    return SPH_ERR_INVALID;
+  }
+  if (cg && P->boundary != SPH_BC_DYNAMIC) {
+    set_error("sph_visc_solve: the conjugate gradient needs a symmetric matrix, which the dummy boundary "
+              "model does not give (Sec. 4): use SPH_BC_DYNAMIC or BiCGSTAB");
+    return SPH_ERR_INVALID;
+  }
+  if (cg && O->apply_form > kApplyVariantsRegister) {
+    set_error("sph_visc_solve: apply_form %d is a BiCGSTAB form; the conjugate gradient takes 0..%d", O->apply_form,
+              kApplyVariantsRegister);
+    return SPH_ERR_INVALID;
+  }
+  if (!cg && !O->jacobi) {
+    set_error("sph_visc_solve: the mixed-precision BiCGSTAB always scales by the Jacobi diagonal (jacobi = 1)");
+    return SPH_ERR_INVALID;
+  }
   if (O->apply_form > 0) {
     SPH_TRY(apply_prepare(H, O->apply_form - 1, st));
     int occ = 1;
@@ -730,6 +871,7 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
 
   SPH_LAUNCH(k_gather_d3, grid_for(H, np), kBlock, 0, st)(b, H->perm.p, H->n, np, H->b64.p);
   SPH_LAUNCH(k_gather_d3, grid_for(H, np), kBlock, 0, st)(x, H->perm.p, H->n, np, H->x64.p);
+  if (cg) SPH_LAUNCH(k_identity_rows_take_b, grid_for(H, np), kBlock, 0, st)(H->op_kind.p, np, H->b64.p, H->x64.p);
   SPH_TRY_CUDA(cudaGetLastError());
   double* dev_dots = reinterpret_cast<double*>(S) + offsetof(SolverScalars, dots) / sizeof(double);
   SPH_LAUNCH(k_norm2_d3, grid_rows, kBlock, 0, st)(H->b64.p, np, H->partials.p, C + CNT_NORM, dev_dots);
@@ -794,10 +936,16 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
     // inner pass: ask it for what the outer loop still needs (with a 4x margin),
     // but never for more than eps_floor (float32 recursions stall below that)
     const double eps = std::fmax(eps_floor, 0.25 * rtol * bnorm / rnorm);
-    SPH_LAUNCH(k_pass_init, grid_rows, kBlock, 0, st)(H->r64.p, H->D64.p, jacobi, np, V, eps * eps, maxit - total_iters, S,
-                                              H->partials.p, C + CNT_INIT);
+    const float* invD = H->invD.p;
+    if (cg) {
+      SPH_LAUNCH(k_cg_init, grid_rows, kBlock, 0, st)(H->r64.p, invD, jacobi, np, V, eps * eps, maxit - total_iters, S,
+                                                      H->partials.p, C + CNT_INIT);
+    } else {
+      SPH_LAUNCH(k_pass_init, grid_rows, kBlock, 0, st)(H->r64.p, H->D64.p, jacobi, np, V, eps * eps, maxit - total_iters,
+                                                        S, H->partials.p, C + CNT_INIT);
+    }
     SPH_TRY_CUDA(cudaGetLastError());
-    if (merged) SPH_LAUNCH(k_p_update, grid_rows, kBlock, 0, st)(np, V, S);
+    if (merged && !cg) SPH_LAUNCH(k_p_update, grid_rows, kBlock, 0, st)(np, V, S);
     const int pred = (passes < sph_neighbors::kPassHist && H->pass_len[passes] > 0) ? H->pass_len[passes] : prev_pass;
     int chunk = pred > chunk0 + 2 ? pred - 2 : chunk0;
     int iter_seen = 0;
@@ -807,6 +955,12 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
         if (le == cudaSuccess) le = e;
       };
       for (int it = 0; it < chunk; ++it) {
+        if (cg) {
+          keep(loop_launch(pdl, k_cg_p, grid_rows, 0, st, np, V, invD, jacobi, S));
+          keep(launch_apply_dot<PH_CG>(H, pdl, grid_slices, op, V.p, V.Ap, V.rh, S, C + CNT_CG_A, st));
+          keep(loop_launch(pdl, k_cg_xr, grid_rows, 0, st, np, V, invD, jacobi, S, H->partials.p, C + CNT_CG_XR));
+          continue;
+        }
         if (!merged) keep(loop_launch(pdl, k_p_update, grid_rows, 0, st, np, V, S));
         keep(launch_apply_dot<PH_DELTA>(H, pdl, grid_slices, op, V.p, V.Ap, V.rh, S, C + CNT_DELTA, st));
         keep(loop_launch(pdl, k_rstar, grid_rows, 0, st, np, V, S));
@@ -822,7 +976,7 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
       SPH_TRY_CUDA(cudaGetLastError());
       SPH_TRY_CUDA(cudaMemcpyAsync(H->host_scal, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
       SPH_TRY_CUDA(cudaStreamSynchronize(st));
-      prof_flush(H, 2 * (H->host_scal->iter - iter_seen));
+      prof_flush(H, (cg ? 1 : 2) * (H->host_scal->iter - iter_seen));
       iter_seen = H->host_scal->iter;
       if (H->host_scal->fault) {
         set_error("sph_visc_solve: an operator apply gave up waiting for its staged coefficients");

@@ -54,24 +54,27 @@ def test_learned_vs_plain_ratios():
 
 
 def test_reference_arm_prints_the_contract_line():
-    """`bench.py --impl reference` times the FP64 oracle on the host (a tiny box here) and
-    prints one JSON line with the same metric, the reference marker, its CPU baseline and an
-    end-to-end object with no host-device traffic."""
+    """`bench.py --impl reference` times the FP64 oracle on the host (one full solve of a
+    tiny box here) and prints one JSON line with the same metric, the reference marker,
+    steps = 1 with the requested count beside it, the workload config of the GPU arm, its
+    CPU baseline and an end-to-end object with no host-device traffic."""
     import json
     import subprocess
     import sys
 
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3",
-                          "--cpu-n", "8", "--n", "12"], cwd=root, capture_output=True, text=True, timeout=600,
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "20", "--warmup", "5",
+                          "--box-side", "12"], cwd=root, capture_output=True, text=True, timeout=600,
                          check=True)
     lines = [l for l in out.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
-    assert d["higher_is_better"] is False and d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["higher_is_better"] is False and d["steps"] == 1 and d["warmup"] == 0 and d["n_gpus"] == 1
+    assert d["steps_requested"] == 20 and d["warmup_requested"] == 5
     assert d["value"] > 0 and d["ms_per_step"] == d["value"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == dict(value=d["value"], unit=d["unit"], h2d_bytes_per_step=0, d2h_bytes_per_step=0)
-    assert d["config"]["n_particles"] == bench._box_count(12)
+    assert d["config"] == bench.workload_config(12, bench._box_count(12))
+    assert d["true_rel_res"] <= 1e-6 and len(d["iterations"]) == 3

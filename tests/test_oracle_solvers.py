@@ -221,3 +221,56 @@ def test_scalar_steps_on_chosen_values():
     np.testing.assert_array_equal(ap, [0.0, 0.0, 0.5, 0.5, 0.5, 0.0, 0.0])
     np.testing.assert_array_equal(be, [0.0, 0.0, 1.0, 1.0, 1.0, 0.0, 0.0])  # 1e10/1e-300 overflows: both 0
     np.testing.assert_array_equal(g, [1.0, 1.0, 1.0, 1.0, 2.0, 1e10, 9.0])
+
+
+# ---- rotated CG (Sec. 4.1, second listing), by hand and against LU ----
+
+def test_rotated_cg_iterates_by_hand():
+    """A = [[2, 1], [1, 3]], b = (1, 2), x0 = 0, no preconditioner: r0 = p0 = (1, 2),
+    A p0 = (4, 7), alpha0 = 5/18, x1 = (5/18, 5/9), r1 = (-1/9, 1/18),
+    beta1 = (5/324)/5 = 1/324, p1 = (-35/324, 20/324), alpha1 = 18/25 and
+    x2 = (1/5, 3/5), the exact solution, after two iterations."""
+    A = sp.csr_matrix(np.array([[2.0, 1.0], [1.0, 3.0]]))
+    x, its, st, hist = solvers.cg_rotated(A, np.array([1.0, 2.0]), eps=1e-12, record=True)
+    assert its[0] == 2 and st[0] == solvers.CONVERGED
+    np.testing.assert_allclose(hist[0][0], [5 / 18, 5 / 9], rtol=4e-16)
+    np.testing.assert_allclose(hist[0][1], [0.2, 0.6], rtol=1e-15)
+
+
+def test_jacobi_cg_solves_a_diagonal_system_in_one_iteration():
+    """With z = D^-1 r on A = D: p = z is the exact error, A p = r, alpha = 1."""
+    A = sp.diags([2.0, 5.0, 7.0]).tocsr()
+    b = np.array([[1.0, -2.0], [3.0, 0.5], [4.0, 1.0]])
+    x0 = np.array([[0.5, 0.0], [0.0, 1.0], [1.0, 0.0]])
+    x, its, st, _ = solvers.cg_rotated(A, b, x0, eps=1e-14, jacobi=True, record=True)
+    np.testing.assert_array_equal(its, [1, 1])
+    np.testing.assert_allclose(x, b / np.array([[2.0], [5.0], [7.0]]), rtol=1e-15)
+
+
+def test_cg_stalls_when_alpha_is_zero():
+    """A skew matrix gives p.Ap = 0 in the first iteration: alpha = 0, a stall, x = x0."""
+    A = sp.csr_matrix(np.array([[0.0, 1.0], [-1.0, 0.0]]))
+    x, its, st, _ = solvers.cg_rotated(A, np.array([1.0, 0.0]), record=True)
+    assert its[0] == 1 and st[0] == solvers.STALLED
+    np.testing.assert_array_equal(x, 0.0)
+
+
+@pytest.mark.parametrize("jacobi", [False, True])
+def test_cg_on_the_dynamic_wall_channel_matches_lu(jacobi):
+    """Dynamic walls with a moving top wall: the full matrix is not symmetric (fluid rows
+    see the walls, wall rows are the identity), but with the wall rows of x0 at their
+    exact value b the residual vanishes on the walls and CG runs on the symmetric
+    fluid block (the reduced system of Sec. 4); it reaches the LU solution."""
+    s = scenes.couette(5, nx=8, ny=6, nz=6, boundary=scenes.BC_DYNAMIC)
+    off, idx = neighbors.build(s.pos, s.lo, s.hi, s.periodic, s.h)
+    A = operator.assemble(s, off, idx)
+    wall = s.ptype == scenes.WALL
+    x0 = s.x0.copy()
+    x0[wall] = s.b[wall]
+    x, its, st, _ = solvers.cg_rotated(A, s.b, x0, eps=1e-13, jacobi=jacobi, record=True)
+    xl = solvers.dense_solve(A, s.b)
+    assert np.all(st == solvers.CONVERGED)
+    np.testing.assert_allclose(x, xl, rtol=0, atol=1e-9 * np.abs(xl).max())
+    if jacobi:
+        _, its_plain = solvers.cg_rotated(A, s.b, x0, eps=1e-13)
+        assert np.all(its <= its_plain)
