@@ -1,21 +1,24 @@
 """Neighbour sets of the SPH particles, in float64 (paper Sec. 5.2; reading X10).
 
 Predicate (the definition both search routines below apply):
-    alpha is a neighbour of beta  <=>  alpha != beta  and  r2 < (2h)^2
+    alpha is a neighbour of beta  <=>  alpha != beta  and  r2 < (R h)^2
+with R = 2 for the Wendland kernel and R = 3 for the truncated Gaussian (Sec. 5.2),
 where, with the float32 inputs cast exactly to float64,
     d_a = x_alpha[a] - x_beta[a]                       for each axis a
     d_a = d_a - L_a * rint(d_a / L_a)                  on periodic axes (minimum image),
                                                        L_a = hi[a] - lo[a]
     r2  = (d_x*d_x + d_y*d_y) + d_z*d_z
-    (2h)^2 = (2 h) * (2 h),  h = float64(h_float32)
+    (R h)^2 = (R h) * (R h),  h = float64(h_float32)
 Every operation is one IEEE float64 rounding in exactly this order, with no fused
-multiply-add, so the set is reproducible bit for bit.  The kernel vanishes at
-q = 2, so a strict inequality loses nothing (W = F = 0 there).
+multiply-add, so the set is reproducible bit for bit.  The kernels vanish at
+q = R, so a strict inequality loses nothing (W = F = 0 there).
 
 Output: CSR in caller order, ``offsets`` int64 [N+1], ``idx`` int32 [nnz], each row
 ascending.
 """
 import numpy as np
+
+from . import kernel as _kernel
 
 
 def _min_image(d, L):
@@ -34,18 +37,18 @@ def pair_r2(pos, a, b, lo, hi, periodic):
     return (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
 
 
-def support2(h):
-    h2 = 2.0 * np.float64(np.float32(h))
+def support2(h, kernel_id=0):
+    h2 = _kernel.support(kernel_id) * np.float64(np.float32(h))
     return h2 * h2
 
 
-def bruteforce(pos, lo, hi, periodic, h, chunk=64):
+def bruteforce(pos, lo, hi, periodic, h, chunk=64, kernel_id=0):
     """All-pairs O(N^2) search: the definition of the neighbour sets."""
     P = np.asarray(pos, dtype=np.float32)[:, :3].astype(np.float64)
     n = P.shape[0]
     lo = np.asarray(lo, np.float64)
     hi = np.asarray(hi, np.float64)
-    R2 = support2(h)
+    R2 = support2(h, kernel_id)
     rows = []
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
@@ -61,7 +64,7 @@ def bruteforce(pos, lo, hi, periodic, h, chunk=64):
     return _to_csr(rows, n)
 
 
-def kdtree(pos, lo, hi, periodic, h):
+def kdtree(pos, lo, hi, periodic, h, kernel_id=0):
     """k-d tree candidates (scipy, a library search) filtered by the exact predicate.
 
     The tree is queried with a slightly larger radius so that no pair that passes
@@ -87,12 +90,12 @@ def kdtree(pos, lo, hi, periodic, h):
             box[ax] = 4.0 * (np.ptp(Q[:, ax]) + (hi[ax] - lo[ax]) + 1.0)
             Q[:, ax] -= Q[:, ax].min()
     tree = cKDTree(Q, boxsize=box)
-    rad = 2.0 * float(np.float32(h)) * (1.0 + 1e-6)
+    rad = _kernel.support(kernel_id) * float(np.float32(h)) * (1.0 + 1e-6)
     pairs = tree.query_pairs(rad, output_type="ndarray")
     a = np.concatenate([pairs[:, 0], pairs[:, 1]])
     b = np.concatenate([pairs[:, 1], pairs[:, 0]])
     r2 = pair_r2(pos, a, b, lo, hi, periodic)
-    keep = r2 < support2(h)
+    keep = r2 < support2(h, kernel_id)
     a, b = a[keep], b[keep]
     order = np.lexsort((a, b))
     a, b = a[order], b[order]
@@ -102,22 +105,23 @@ def kdtree(pos, lo, hi, periodic, h):
     return offsets, a.astype(np.int32)
 
 
-def build(pos, lo, hi, periodic, h, method="auto"):
+def build(pos, lo, hi, periodic, h, method="auto", kernel_id=0):
     n = np.asarray(pos).shape[0]
     if method == "bruteforce" or (method == "auto" and n <= 6000):
-        return bruteforce(pos, lo, hi, periodic, h)
-    return kdtree(pos, lo, hi, periodic, h)
+        return bruteforce(pos, lo, hi, periodic, h, kernel_id=kernel_id)
+    return kdtree(pos, lo, hi, periodic, h, kernel_id=kernel_id)
 
 
 def for_scene(scene, method="auto"):
-    return build(scene.pos, scene.lo, scene.hi, scene.periodic, scene.h, method)
+    return build(scene.pos, scene.lo, scene.hi, scene.periodic, scene.h, method,
+                 kernel_id=getattr(scene, "kernel", 0))
 
 
 def rows_for(scene, rows):
     """Neighbour sets of a few rows by direct O(N) scans (for sampled checks at full size)."""
     n = scene.n
     out = []
-    R2 = support2(scene.h)
+    R2 = support2(scene.h, getattr(scene, "kernel", 0))
     allidx = np.arange(n)
     for b in np.asarray(rows, dtype=np.int64):
         r2 = pair_r2(scene.pos, allidx, np.full(n, b), scene.lo, scene.hi, scene.periodic)

@@ -58,10 +58,11 @@ def pair_terms(scene, b, a, mu=None):
     m = np.asarray(scene.pos, dtype=np.float32)[:, 3].astype(np.float64)
     ptype = np.asarray(scene.ptype)
     h = float(np.float32(scene.h))
-    absF = np.abs(kernel.F(r, h))
+    kid = getattr(scene, "kernel", 0)
+    absF = np.abs(kernel.F(r, h, kid))
     mub = np.where(ptype[a] == FLUID, mean_mu(mu[a], mu[b], scene.mean), mu[b])
     c = 2.0 * mub * m[a] * absF / (rho[a] * rho[b])
-    return c, kernel.W(r, h)
+    return c, kernel.W(r, h, kid)
 
 
 def assemble(scene, offsets, idx, dt=None, mu=None, boundary=None):

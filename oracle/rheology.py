@@ -41,7 +41,7 @@ def velocity_gradient(scene, offsets, idx, vel=None):
             d[:, ax] = d[:, ax] - L * np.rint(d[:, ax] / L)
     r = np.sqrt((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2])
     h = float(np.float32(scene.h))
-    absF = np.abs(kernel.F(r, h))
+    absF = np.abs(kernel.F(r, h, getattr(scene, "kernel", 0)))
     V = (np.asarray(scene.pos, np.float32)[:, 3].astype(np.float64)
          / np.asarray(scene.rho, np.float32).astype(np.float64))
     wgt = V[a] * absF

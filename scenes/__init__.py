@@ -21,7 +21,9 @@ needs (Sec. 3.2, "shared formulation"):
                                App. B; walls start at their right-hand side)
 * ``lo, hi``   float64 [3]     the box; on periodic axes hi - lo is the period
 * ``periodic`` int32 [3]
-* ``h``        float32         smoothing length (support radius 2h, Wendland)
+* ``h``        float32         smoothing length
+* ``kernel``   int             0 = Wendland (support radius 2h), 1 = truncated
+                               Gaussian (support radius 3h), paper Sec. 5.2
 * ``dt``       float64         time step of the viscous system
 
 Random draws use numpy's PCG64 seeded with ``SeedSequence([config_id, seed])``.
@@ -44,6 +46,9 @@ BC_DYNAMIC = 1
 
 MEAN_HARMONIC = 0
 MEAN_ARITHMETIC = 1
+
+KERNEL_WENDLAND = 0
+KERNEL_GAUSSIAN = 1
 
 # config ids used to seed the generators (one stream per workload family)
 CFG_COUETTE = 1
@@ -77,6 +82,7 @@ class Scene:
     # Papanastasiou parameters (tau0, mu0, m) when mu must come from the mu pass
     rheology: Optional[tuple] = None
     meta: dict = dataclasses.field(default_factory=dict)
+    kernel: int = KERNEL_WENDLAND
 
     @property
     def n(self) -> int:
@@ -121,7 +127,7 @@ def _wrap_periodic(p, lo, hi, periodic):
 
 def _assemble(name, fluid_p, wall_p, wall_u, dx, rho0, mu_fluid, dt, lo, hi, periodic,
               v_fluid, g=(0.0, 0.0, 0.0), boundary=BC_DUMMY, mean=MEAN_HARMONIC,
-              h_factor=1.3, rheology=None, meta=None):
+              h_factor=1.3, rheology=None, meta=None, kernel=KERNEL_WENDLAND):
     """Stack fluid and wall particles into a Scene (fluid first, walls after)."""
     nf, nw = fluid_p.shape[0], wall_p.shape[0]
     n = nf + nw
@@ -165,12 +171,13 @@ def _assemble(name, fluid_p, wall_p, wall_u, dx, rho0, mu_fluid, dt, lo, hi, per
     return Scene(name=name, pos=pos, rho=rho, mu=mu, ptype=ptype, wall_vel=wall_vel, vel=vel,
                  b=b, x0=x0, lo=lo, hi=hi, periodic=periodic,
                  h=float(np.float32(h_factor * dx)), dt=float(dt), boundary=boundary, mean=mean,
-                 dx=float(dx), rheology=rheology, meta=dict(meta or {}))
+                 dx=float(dx), rheology=rheology, meta=dict(meta or {}), kernel=int(kernel))
 
 
 def couette(seed: int = 0, nx: int = 20, ny: int = 10, nz: int = 10, dx: float = 0.01,
             rho0: float = 1000.0, nu: float = 1.0, dt: float = 1e-4, U: float = 1.0,
-            noise: float = 0.01, layers: int = 3, boundary: int = BC_DUMMY) -> Scene:
+            noise: float = 0.01, layers: int = 3, boundary: int = BC_DUMMY,
+            kernel: int = KERNEL_WENDLAND) -> Scene:
     """Plane Couette channel: fluid between two walls normal to y, periodic in x, z.
 
     Fluid at y = (j + 1/2) dx, j < ny (channel height H = ny dx); wall layers at
@@ -197,12 +204,12 @@ def couette(seed: int = 0, nx: int = 20, ny: int = 10, nz: int = 10, dx: float =
     lo = (0.0, -layers * dx, 0.0)
     hi = (nx * dx, H + layers * dx, nz * dx)
     return _assemble("couette", fluid, walls, wall_u, dx, rho0, rho0 * nu, dt, lo, hi, (1, 0, 1),
-                     v, boundary=boundary, meta=dict(seed=seed, U=U, H=H, nu=nu))
+                     v, boundary=boundary, meta=dict(seed=seed, U=U, H=H, nu=nu), kernel=kernel)
 
 
 def lava_box(seed: int = 0, n: int = 100, dx: float = 0.005, rho0: float = 1000.0, nu: float = 10.0,
              dt: float = 5e-4, sigma: float = 0.1, jitter: float = 0.1, layers: int = 3,
-             boundary: int = BC_DUMMY) -> Scene:
+             boundary: int = BC_DUMMY, kernel: int = KERNEL_WENDLAND) -> Scene:
     """Lava-like open box: an n^3 jittered fluid lattice on a dummy floor and four side walls.
 
     Floor: (n + 2 layers)^2 x layers particles below z = 0; side walls normal to x
@@ -225,7 +232,7 @@ def lava_box(seed: int = 0, n: int = 100, dx: float = 0.005, rho0: float = 1000.
     lo = (-layers * dx, -layers * dx, -layers * dx)
     hi = (L + layers * dx, L + layers * dx, L + 4 * dx)
     return _assemble("lava_box", fluid, walls, np.zeros((walls.shape[0], 3)), dx, rho0, rho0 * nu, dt,
-                     lo, hi, (0, 0, 0), v, boundary=boundary, meta=dict(seed=seed, n=n, nu=nu))
+                     lo, hi, (0, 0, 0), v, boundary=boundary, meta=dict(seed=seed, n=n, nu=nu), kernel=kernel)
 
 
 def slope(seed: int = 0, nx: int = 200, ny: int = 100, nz: int = 200, dx: float = 0.005,
@@ -274,7 +281,7 @@ def slope_subset(seed: int = 0, **kw) -> Scene:
 
 def periodic_lattice(n: int = 8, dx: float = 0.01, rho0: float = 1000.0, nu: float = 1.0,
                      dt: float = 1e-4, jitter: float = 0.0, seed: int = 0, sigma: float = 0.1,
-                     aniso=(1, 1, 1), mu_spread: float = 0.0) -> Scene:
+                     aniso=(1, 1, 1), mu_spread: float = 0.0, kernel: int = KERNEL_WENDLAND) -> Scene:
     """Fluid-only cube periodic on all three axes (no walls).
 
     With jitter = 0 and uniform mu, rho, m the operator is circulant (Fourier pin).
@@ -292,12 +299,13 @@ def periodic_lattice(n: int = 8, dx: float = 0.01, rho0: float = 1000.0, nu: flo
     lo = (0.0, 0.0, 0.0)
     hi = tuple(k * dx for k in nxyz)
     return _assemble("periodic_lattice", fluid, np.zeros((0, 3)), np.zeros((0, 3)), dx, rho0, mu, dt,
-                     lo, hi, (1, 1, 1), v)
+                     lo, hi, (1, 1, 1), v, kernel=kernel)
 
 
 def random_box(seed: int = 0, nf: int = 200, nw_layers: int = 2, dx: float = 0.01, rho0: float = 1000.0,
                nu: float = 1.0, dt: float = 1e-4, periodic=(1, 0, 1), boundary: int = BC_DUMMY,
-               mean: int = MEAN_HARMONIC, mu_spread: float = 0.0, mass_spread: float = 0.0) -> Scene:
+               mean: int = MEAN_HARMONIC, mu_spread: float = 0.0, mass_spread: float = 0.0,
+               kernel: int = KERNEL_WENDLAND) -> Scene:
     """Small irregular scene: random fluid positions in a slab over a wall floor.
 
     Used for exhaustive small-N checks (neighbour sets, operator rows, solves):
@@ -322,7 +330,7 @@ def random_box(seed: int = 0, nf: int = 200, nw_layers: int = 2, dx: float = 0.0
     hi = (Lx, Ly + 2 * dx, Lz)
     # periodic lengths must be at least three cells of side 2h
     s = _assemble("random_box", fluid, walls, wall_u, dx, rho0, mu, dt, lo, hi, periodic, v,
-                  boundary=boundary, mean=mean)
+                  boundary=boundary, mean=mean, kernel=kernel)
     if mass_spread:
         s.pos[:, 3] *= np.exp(rng.uniform(0.0, math.log1p(mass_spread), size=s.n)).astype(np.float32)
     return s

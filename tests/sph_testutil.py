@@ -29,7 +29,8 @@ def params_for(scene, dt=None):
 
 
 def oracle_system(scene, method="auto"):
-    off, idx = onb.build(scene.pos, scene.lo, scene.hi, scene.periodic, scene.h, method)
+    off, idx = onb.build(scene.pos, scene.lo, scene.hi, scene.periodic, scene.h, method,
+                         kernel_id=getattr(scene, "kernel", 0))
     return off, idx, oop.assemble(scene, off, idx)
 
 

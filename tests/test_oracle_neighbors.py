@@ -27,6 +27,28 @@ def test_lattice_count_is_80():
     assert np.all(counts == 80)
 
 
+def test_gaussian_lattice_count_is_250():
+    # truncated Gaussian, support 3h = 3.9 dx: the paper says "around 250"; the exact
+    # lattice count is 250, and brute force and the k-d tree find it on every particle
+    assert len(_lattice_offsets(3.9)) == 250
+    s = scenes.periodic_lattice(12, kernel=scenes.KERNEL_GAUSSIAN)
+    for method in ("bruteforce", "kdtree"):
+        off, idx = neighbors.build(s.pos, s.lo, s.hi, s.periodic, s.h, method, kernel_id=s.kernel)
+        assert np.all(np.diff(off) == 250)
+
+
+def test_gaussian_sets_contain_the_wendland_sets():
+    s = scenes.random_box(8, nf=1600)
+    sg = s.copy()
+    sg.kernel = scenes.KERNEL_GAUSSIAN
+    ow, iw = neighbors.bruteforce(s.pos, s.lo, s.hi, s.periodic, s.h)
+    og, ig = neighbors.bruteforce(sg.pos, sg.lo, sg.hi, sg.periodic, sg.h, kernel_id=sg.kernel)
+    ok, ik = neighbors.kdtree(sg.pos, sg.lo, sg.hi, sg.periodic, sg.h, kernel_id=sg.kernel)
+    assert np.array_equal(og, ok) and np.array_equal(ig, ik)
+    for b in range(s.n):
+        assert set(iw[ow[b]:ow[b + 1]]) <= set(ig[og[b]:og[b + 1]])
+
+
 def test_dummy_wall_layers_see_30_9_0():
     # wall layers at (k + 1/2) dx below the fluid: fluid neighbours 30, 9 and 0
     s = scenes.couette(0)

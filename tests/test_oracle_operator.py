@@ -9,7 +9,7 @@ from oracle import kernel, neighbors, operator, solvers
 
 
 def _build(s):
-    off, idx = neighbors.build(s.pos, s.lo, s.hi, s.periodic, s.h)
+    off, idx = neighbors.build(s.pos, s.lo, s.hi, s.periodic, s.h, kernel_id=s.kernel)
     return off, idx, operator.assemble(s, off, idx)
 
 
@@ -31,6 +31,19 @@ def test_zero_action_on_constants(boundary):
         np.testing.assert_array_equal(y[wall & (S == 0)], 1.0)
     else:
         np.testing.assert_array_equal(y[wall], 1.0)
+
+
+def test_zero_action_on_constants_gaussian():
+    """The same invariant with the truncated Gaussian (support 3h) on a box with four
+    dummy layers (the 3.9 dx support reaches the fourth layer)."""
+    s = scenes.lava_box(1, n=8, layers=4, kernel=scenes.KERNEL_GAUSSIAN)
+    off, idx, A = _build(s)
+    assert np.diff(off)[s.ptype == scenes.FLUID].max() > 200
+    y = A @ np.ones(s.n)
+    fl = s.ptype == scenes.FLUID
+    assert np.all(np.abs(y[fl] - 1.0) <= 1e-13 * A.diagonal()[fl])
+    S = operator.shepard_sums(s, off, idx)
+    np.testing.assert_allclose(y[~fl & (S > 0)], 2.0, rtol=1e-14)
 
 
 def test_sdd_margin_is_one_and_wall_rows_wcdd():
@@ -77,21 +90,23 @@ def _stencil_eigenvalue(s, kvec):
     m = float(np.float32(s.pos[0, 3]))
     rho = float(np.float32(s.rho[0]))
     h = float(np.float32(s.h))
-    for v in itertools.product(range(-3, 4), repeat=3):
+    R = kernel.support(s.kernel)
+    for v in itertools.product(range(-4, 5), repeat=3):
         d = np.array(v, np.float64) * dx
         r = np.sqrt(d @ d)
-        if v == (0, 0, 0) or r >= 2 * h:
+        if v == (0, 0, 0) or r >= R * h:
             continue
-        c = 2.0 * mu * m * abs(float(kernel.F(r, h))) / (rho * rho)
+        c = 2.0 * mu * m * abs(float(kernel.F(r, h, s.kernel))) / (rho * rho)
         lam += s.dt * c * (1.0 - np.cos(kvec @ d))
     return lam
 
 
 @pytest.mark.parametrize("modes", [(1, 0, 0), (0, 2, 1), (3, 3, 3), (4, 0, 4), (1, 2, 3)])
-def test_fourier_closed_form(modes):
+@pytest.mark.parametrize("kern", [scenes.KERNEL_WENDLAND, scenes.KERNEL_GAUSSIAN])
+def test_fourier_closed_form(modes, kern):
     # perfect periodic lattice, uniform mu/rho/m: the operator is circulant, so
-    # A cos(k.r) = lambda(k) cos(k.r) with the stencil-sum eigenvalue
-    s = scenes.periodic_lattice(8, dt=3e-4)
+    # A cos(k.r) = lambda(k) cos(k.r) with the stencil-sum eigenvalue (any kernel)
+    s = scenes.periodic_lattice(8 if kern == scenes.KERNEL_WENDLAND else 12, dt=3e-4, kernel=kern)
     off, idx, A = _build(s)
     L = s.hi - s.lo
     kvec = 2 * np.pi * np.array(modes) / L
