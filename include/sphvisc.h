@@ -74,12 +74,30 @@ typedef struct {
                               advises storing mu rather than nu*rho             */
   const uint8_t* ptype;    /* [n]: SPH_FLUID or SPH_WALL                        */
   double lo[3], hi[3];     /* box; on a periodic axis hi-lo is the period and
-                              hi-lo >= 3 * 2h; particles on open axes may lie
+                              hi-lo >= 3 R h (R h: the kernel's support
+                              radius); particles on open axes may lie
                               outside [lo, hi) (they are clamped into the edge
                               cells, which keeps the search exact)              */
   int32_t periodic[3];     /* 1 = periodic axis (minimum image)                 */
-  float h;                 /* smoothing length; Wendland support radius 2h      */
+  float h;                 /* smoothing length                                  */
+  int32_t kernel;          /* SPH_KERNEL_WENDLAND (support radius 2h, default)
+                              or SPH_KERNEL_GAUSSIAN (support radius 3h)        */
 } sph_scene;
+
+/* Smoothing kernels (Sec. 5.2, "Smoothing kernel choice"), W = w(r/h)/h^3 and
+ * the gradient factor |F| = |f(r/h)|/h^5:
+ *   SPH_KERNEL_WENDLAND: w = 21/(16 pi) (1 - q/2)^4 (2q + 1),
+ *                        |f| = 105/(128 pi) (2 - q)^3, zero for q >= 2;
+ *   SPH_KERNEL_GAUSSIAN: the normalised Gaussian truncated at k = 3,
+ *                        w = (e^{-q^2} - e^{-9}) / w_G, |f| = 2 e^{-q^2} / w_G,
+ *                        w_G = pi^{3/2} erf(3) - (2 pi / 3) e^{-9} 3 (3 + 18);
+ *                        about 250 neighbours at h = 1.3 dx (max_neighbors of
+ *                        at least 320 or so for jittered particles).
+ * The neighbour lists, the coefficients of A(dt), the dummy-wall Shepard rows,
+ * the v^n start with its wall closure and the Papanastasiou pass follow the
+ * chosen kernel; the on-the-fly apply and the learned warm start's features
+ * are written for the Wendland kernel and return SPH_ERR_INVALID otherwise. */
+enum { SPH_KERNEL_WENDLAND = 0, SPH_KERNEL_GAUSSIAN = 1 };
 
 /* Opaque neighbour structure: cell-sorted particle copy, permutation and the
    sliced-ELL neighbour lists (Sec. 5.2: a particle sees about 80 neighbours at
@@ -87,7 +105,8 @@ typedef struct {
 typedef struct sph_neighbors sph_neighbors;
 
 /* Build (or rebuild in place, if *handle is non-NULL) the neighbour lists.
- * alpha is a neighbour of beta iff alpha != beta and |r_ab|^2 < (2h)^2, with
+ * alpha is a neighbour of beta iff alpha != beta and |r_ab|^2 < (R h)^2, R = 2
+ * (Wendland) or 3 (Gaussian), with
  * r_ab the minimum image on periodic axes, decided exactly as in float64 on
  * the float32 positions (a float32 test with a safety band, then a float64
  * recheck inside the band).
@@ -352,6 +371,55 @@ sph_status sph_batch_info(const sph_batch* batch, int32_t* variant, int32_t* gra
                           int32_t* grid);
 
 sph_status sph_batch_destroy(sph_batch* batch);
+
+/* ---- One system over several sub-domains (Sec. 7, Sec. 7.1) -----------------
+ * The domain decomposition of the paper's multi-GPU solver: the cells of the
+ * neighbour grid are grouped into layers along the longest axis of the box
+ * (cell side >= 2h, so neighbours share a layer or sit in adjacent ones), and
+ * each of `ranks` sub-domains owns a contiguous run of layers, balanced by
+ * particle count.  A sub-domain keeps its own copy of the operator rows of its
+ * particles (columns renumbered locally) and of every solver vector, plus a
+ * halo: the particles of other sub-domains that its rows reference (the outer
+ * edge of Sec. 7.1).  Per BiCGSTAB iteration the halo values of p and of r* are
+ * exchanged before the two operator applies (the paper exchanges A p and A r*:
+ * the same volume), and the dot products reduce as per-layer partials summed
+ * in layer order, so the iterates are bit-identical for any number of
+ * sub-domains.  All sub-domains run on the calling GPU (each in its own
+ * allocations; the exchange is a device gather and the reduction a device
+ * sum, standing for the send/recv and the all-gather of a multi-GPU run). */
+typedef struct sph_shard sph_shard;
+
+/* The partition on the host (no GPU needed): rows in layers, numbered layer by
+ * layer in their given order with each layer padded to a multiple of 32 rows,
+ * and the layers split into `ranks` contiguous runs of about n / ranks rows.
+ * layer: (host) [n], each in 0..nlayers-1; virt: (host) [n] out, the new row
+ * number of each row; rank_first_layer: (host) [ranks + 1] out; layer_first_virt:
+ * (host) [nlayers + 1] out, the first row number of each layer (the last entry
+ * is the padded total).  1 <= ranks <= min(64, nlayers). */
+sph_status sph_shard_plan(int64_t n, const int32_t* layer, int32_t nlayers, int32_t ranks, int64_t* virt,
+                          int32_t* rank_first_layer, int64_t* layer_first_virt);
+
+/* Partition the system of `handle` with the coefficients for params (set up
+ * here if needed) over `ranks` sub-domains (1..64, at most the layer count).
+ * Copies the operator: the shard does not follow later rebuilds of the handle
+ * (sph_shard_solve then fails with SPH_ERR_INVALID).  Synchronises. */
+sph_status sph_shard_create(sph_neighbors* handle, const sph_visc_params* params, int32_t ranks,
+                            sph_shard** shard, void* stream);
+
+/* axis: the slab axis; layers: cell layers along it; owned, halo: (host)
+ * [ranks] rows owned (with layer padding) and halo rows per sub-domain;
+ * exchanged: halo rows filled per exchanged vector.  Any pointer may be NULL. */
+sph_status sph_shard_info(const sph_shard* shard, int32_t* axis, int32_t* layers, int64_t* owned,
+                          int64_t* halo, int64_t* exchanged);
+
+/* As sph_visc_solve (b, x, report in caller order, device) with the mixed
+ * precision BiCGSTAB, Jacobi scaling and direct reductions (other options:
+ * SPH_ERR_INVALID); the float64 true residual is also recomputed over the
+ * sub-domains (halo exchange of x's float32 hi/lo split).  Synchronises. */
+sph_status sph_shard_solve(sph_shard* shard, const sph_solve_opts* opts, const double* b, double* x,
+                           sph_solve_report* report, void* stream);
+
+sph_status sph_shard_destroy(sph_shard* shard);
 
 /* ---- Learned warm start ---------------------------------------------------
  * The paper names a better initial guess as future work (Sec. 8).  A

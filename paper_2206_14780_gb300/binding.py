@@ -23,6 +23,7 @@ SPH_MEAN_HARMONIC, SPH_MEAN_ARITHMETIC = 0, 1
 SPH_PREC_MIXED, SPH_PREC_FP64 = 0, 1
 SPH_CONVERGED, SPH_STALLED, SPH_PROGRESSING = 0, 1, 2
 SPH_SOLVER_BICGSTAB, SPH_SOLVER_CG = 0, 1
+SPH_KERNEL_WENDLAND, SPH_KERNEL_GAUSSIAN = 0, 1
 
 # every symbol include/sphvisc.h declares
 EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", "sph_set_viscosity",
@@ -31,14 +32,15 @@ EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", 
            "sph_batch_create", "sph_batch_solve", "sph_batch_info", "sph_batch_destroy",
            "sph_mlp_create", "sph_mlp_set_params", "sph_mlp_get_params", "sph_mlp_destroy", "sph_mlp_features",
            "sph_mlp_targets", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train_step", "sph_warm_start",
-           "sph_mlp_residual_targets", "sph_mlp_set_mode", "sph_visc_solve_host", "sph_bicgstab_replay"]
+           "sph_mlp_residual_targets", "sph_mlp_set_mode", "sph_visc_solve_host", "sph_bicgstab_replay",
+           "sph_shard_plan", "sph_shard_create", "sph_shard_info", "sph_shard_solve", "sph_shard_destroy"]
 MLP_NPARAMS = 9603
 
 
 class sph_scene(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("pos", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("mu", ctypes.c_void_p),
                 ("ptype", ctypes.c_void_p), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
-                ("periodic", ctypes.c_int32 * 3), ("h", ctypes.c_float)]
+                ("periodic", ctypes.c_int32 * 3), ("h", ctypes.c_float), ("kernel", ctypes.c_int32)]
 
 
 class sph_visc_params(ctypes.Structure):
@@ -121,6 +123,11 @@ def load(path: str = LIB_PATH):
                                      vp, ctypes.POINTER(dbl), vp],
         "sph_profile_read": [vp, ctypes.POINTER(sph_profile_counters), i32],
         "sph_bicgstab_replay": [vp, dbl, i32, i32, vp, vp, vp],
+        "sph_shard_plan": [i64, vp, i32, i32, vp, vp, vp],
+        "sph_shard_create": [vp, ctypes.POINTER(sph_visc_params), i32, ctypes.POINTER(vp), vp],
+        "sph_shard_info": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), vp, vp, ctypes.POINTER(i64)],
+        "sph_shard_solve": [vp, ctypes.POINTER(sph_solve_opts), vp, vp, ctypes.POINTER(sph_solve_report), vp],
+        "sph_shard_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -176,6 +183,60 @@ def bicgstab_replay(gamma0, eps, maxit, dots, stream=None):
     return out
 
 
+def shard_plan(layer, nlayers, ranks):
+    """sph_shard_plan (host only): returns (virt [n] int64, rank_first_layer [ranks + 1],
+    layer_first_virt [nlayers + 1])."""
+    load()
+    lay = np.ascontiguousarray(layer, np.int32)
+    virt = np.empty(lay.size, np.int64)
+    rfl = np.empty(ranks + 1, np.int32)
+    lfv = np.empty(nlayers + 1, np.int64)
+    _check(_lib.sph_shard_plan(lay.size, lay.ctypes.data_as(ctypes.c_void_p), int(nlayers), int(ranks),
+                               virt.ctypes.data_as(ctypes.c_void_p), rfl.ctypes.data_as(ctypes.c_void_p),
+                               lfv.ctypes.data_as(ctypes.c_void_p)))
+    return virt, rfl, lfv
+
+
+class Shard:
+    """Owner of an sph_shard: one system partitioned over `ranks` sub-domains."""
+
+    def __init__(self, nb, params, ranks, stream=None):
+        load()
+        h = ctypes.c_void_p()
+        _check(_lib.sph_shard_create(nb.handle, ctypes.byref(params), int(ranks), ctypes.byref(h), _stream(stream)))
+        self.handle = h
+        self.ranks = int(ranks)
+        self._nb = nb
+
+    def info(self):
+        ax, nl, ex = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        owned = np.empty(self.ranks, np.int64)
+        halo = np.empty(self.ranks, np.int64)
+        _check(_lib.sph_shard_info(self.handle, ctypes.byref(ax), ctypes.byref(nl),
+                                   owned.ctypes.data_as(ctypes.c_void_p), halo.ctypes.data_as(ctypes.c_void_p),
+                                   ctypes.byref(ex)))
+        return dict(axis=ax.value, layers=nl.value, owned=owned.tolist(), halo=halo.tolist(), exchanged=ex.value)
+
+    def solve(self, opts, b, x, stream=None):
+        rep = sph_solve_report()
+        st = _lib.sph_shard_solve(self.handle, ctypes.byref(opts), _ptr(b), _ptr(x), ctypes.byref(rep),
+                                  _stream(stream))
+        if st not in (SPH_OK, 6):
+            _check(st)
+        return _report(rep)
+
+    def close(self):
+        if self.handle:
+            _lib.sph_shard_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def visc_params(dt, boundary=SPH_BC_DUMMY, mean=SPH_MEAN_HARMONIC):
     return sph_visc_params(float(dt), int(boundary), int(mean))
 
@@ -205,9 +266,9 @@ class Neighbors:
         self.n = n
         self._keep = keep
 
-    def rebuild(self, pos, rho, mu, ptype, lo, hi, periodic, h, max_neighbors=128, stream=None):
+    def rebuild(self, pos, rho, mu, ptype, lo, hi, periodic, h, max_neighbors=128, stream=None, kernel=0):
         """sph_build_neighbors on this handle (rebuild in place, keeps the workspace)."""
-        sc = _scene_struct(pos, rho, mu, ptype, lo, hi, periodic, h)
+        sc = _scene_struct(pos, rho, mu, ptype, lo, hi, periodic, h, kernel)
         handle = ctypes.c_void_p(self.handle.value if isinstance(self.handle, ctypes.c_void_p) else self.handle)
         _check(_lib.sph_build_neighbors(ctypes.byref(sc), int(max_neighbors), ctypes.byref(handle), _stream(stream)))
         self.handle = handle
@@ -331,7 +392,7 @@ def solve_host(pos, rho, mu, ptype, lo, hi, periodic, h, params, opts, vel, b, x
     return _report(rep), nb
 
 
-def _scene_struct(pos, rho, mu, ptype, lo, hi, periodic, h):
+def _scene_struct(pos, rho, mu, ptype, lo, hi, periodic, h, kernel=0):
     sc = sph_scene()
     sc.n = int(pos.shape[0])
     sc.pos, sc.rho, sc.mu, sc.ptype = _ptr(pos), _ptr(rho), _ptr(mu), _ptr(ptype)
@@ -340,6 +401,7 @@ def _scene_struct(pos, rho, mu, ptype, lo, hi, periodic, h):
         sc.hi[ax] = float(hi[ax])
         sc.periodic[ax] = int(periodic[ax])
     sc.h = float(h)
+    sc.kernel = int(kernel)
     return sc
 
 
@@ -477,10 +539,10 @@ def warm_start(nb, params, mlp, vel, ptype, b, x0, stream=None):
                                _ptr(ptype), _ptr(b), _ptr(x0), _stream(stream)))
 
 
-def build_neighbors(pos, rho, mu, ptype, lo, hi, periodic, h, max_neighbors=128, stream=None):
-    """sph_build_neighbors on device tensors; returns a Neighbors owner."""
+def build_neighbors(pos, rho, mu, ptype, lo, hi, periodic, h, max_neighbors=128, stream=None, kernel=0):
+    """sph_build_neighbors on device tensors; returns a Neighbors owner.  kernel: 0 Wendland, 1 Gaussian."""
     load()
-    sc = _scene_struct(pos, rho, mu, ptype, lo, hi, periodic, h)
+    sc = _scene_struct(pos, rho, mu, ptype, lo, hi, periodic, h, kernel)
     handle = ctypes.c_void_p()
     _check(_lib.sph_build_neighbors(ctypes.byref(sc), int(max_neighbors), ctypes.byref(handle), _stream(stream)))
     return Neighbors(handle, sc.n, keep=(pos, rho, mu, ptype))
@@ -489,4 +551,4 @@ def build_neighbors(pos, rho, mu, ptype, lo, hi, periodic, h, max_neighbors=128,
 def build_for_scene(scene, max_neighbors=128, device="cuda", stream=None):
     t = scene_tensors(scene, device)
     return build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], scene.lo, scene.hi, scene.periodic, scene.h,
-                           max_neighbors, stream), t
+                           max_neighbors, stream, kernel=getattr(scene, "kernel", 0)), t

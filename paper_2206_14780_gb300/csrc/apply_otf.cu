@@ -210,6 +210,10 @@ sph_status visc_apply_otf(sph_neighbors* H, const sph_visc_params* P, const floa
     set_error("sph_visc_apply_otf: null argument");
     return SPH_ERR_INVALID;
   }
+  if (H->kernel != SPH_KERNEL_WENDLAND) {
+    set_error("sph_visc_apply_otf: the on-the-fly coefficients are written for the Wendland kernel");
+    return SPH_ERR_INVALID;
+  }
   SPH_TRY(ensure_otf(H, P, st));
   SPH_TRY(H->v_tmp.alloc(2 * H->n_pad));
   float4* vs = H->v_tmp.p;

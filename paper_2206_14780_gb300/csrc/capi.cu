@@ -273,6 +273,35 @@ sph_status sph_mu_papanastasiou(sph_neighbors* h, const float* vel, const float*
   return mu_papanastasiou(h, vel, wall_vel, tau0, mu0, m, mu_out, set_handle, as_stream(stream));
 }
 
+sph_status sph_shard_plan(int64_t n, const int32_t* layer, int32_t nlayers, int32_t ranks, int64_t* virt,
+                          int32_t* rank_first_layer, int64_t* layer_first_virt) {
+  clear_error();
+  return shard_plan(n, layer, nlayers, ranks, virt, rank_first_layer, layer_first_virt);
+}
+
+sph_status sph_shard_create(sph_neighbors* h, const sph_visc_params* params, int32_t ranks, sph_shard** shard,
+                            void* stream) {
+  clear_error();
+  return shard_create(h, params, ranks, shard, as_stream(stream));
+}
+
+sph_status sph_shard_info(const sph_shard* shard, int32_t* axis, int32_t* layers, int64_t* owned, int64_t* halo,
+                          int64_t* exchanged) {
+  clear_error();
+  return shard_info(shard, axis, layers, owned, halo, exchanged);
+}
+
+sph_status sph_shard_solve(sph_shard* shard, const sph_solve_opts* opts, const double* b, double* x,
+                           sph_solve_report* report, void* stream) {
+  clear_error();
+  return shard_solve(shard, opts, b, x, report, as_stream(stream));
+}
+
+sph_status sph_shard_destroy(sph_shard* shard) {
+  clear_error();
+  return shard_destroy(shard);
+}
+
 sph_status sph_bicgstab_replay(const double* gamma0, double eps, int32_t maxit, int32_t nsteps, const double* dots,
                                double* out, void* stream) {
   clear_error();

@@ -484,6 +484,10 @@ sph_status sph_mlp_features(sph_neighbors* h, const sph_visc_params* params, con
     set_error("sph_mlp_features: null argument");
     return SPH_ERR_INVALID;
   }
+  if (h->kernel != SPH_KERNEL_WENDLAND) {
+    set_error("sph_mlp_features: the network's features are written for the Wendland kernel");
+    return SPH_ERR_INVALID;
+  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   SPH_TRY(features_impl(h, params, vel, reinterpret_cast<__nv_bfloat16*>(feats), st));
   if (scale_out) {
@@ -518,6 +522,10 @@ sph_status sph_warm_start(sph_neighbors* h, const sph_visc_params* params, const
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const float4* delta = nullptr;
+  if (mlp && h->kernel != SPH_KERNEL_WENDLAND) {
+    set_error("sph_warm_start: the network's features are written for the Wendland kernel (pass no network)");
+    return SPH_ERR_INVALID;
+  }
   if (mlp) {
     SPH_TRY(h->feat_out.alloc(h->n * 8));      // bf16 features [n][16]
     SPH_TRY(h->feat_delta.alloc(h->n));        // float4 network outputs
@@ -556,6 +564,10 @@ sph_status sph_mlp_residual_targets(sph_neighbors* h, const sph_visc_params* par
   }
   if (flags & ~(SPH_RLOSS_JACOBI | SPH_RLOSS_LOG)) {
     set_error("sph_mlp_residual_targets: unknown flags %d", flags);
+    return SPH_ERR_INVALID;
+  }
+  if (h->kernel != SPH_KERNEL_WENDLAND) {
+    set_error("sph_mlp_residual_targets: the network's features are written for the Wendland kernel");
     return SPH_ERR_INVALID;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -18,7 +18,7 @@
 //   fill      the lists, in the same deterministic order as count
 //
 // The predicate is decided exactly as the float64 definition: a float32 test
-// decides every pair outside a band around (2h)^2 whose half-width bounds the
+// decides every pair outside a band around (R h)^2 (R h: the kernel support radius) whose half-width bounds the
 // float32 rounding of r^2; pairs inside the band are recomputed in float64 with
 // the same operations, in the same order and without contraction.
 #include <algorithm>
@@ -183,7 +183,7 @@ __device__ __forceinline__ bool pair_inside_f64(float4 pt, float4 ps, const Grid
 
 struct Band {
   float lo2, hi2;   // float32 r^2 below lo2: inside; at or above hi2: outside
-  double R2;        // (2h)^2 in float64
+  double R2;        // (R h)^2 in float64, R h the support radius
   float L[3], invL[3];
 };
 
@@ -396,8 +396,13 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
     set_error("sph_build_neighbors: max_neighbors must be in [1, 1024]");
     return SPH_ERR_INVALID;
   }
+  if (sc->kernel != SPH_KERNEL_WENDLAND && sc->kernel != SPH_KERNEL_GAUSSIAN) {
+    set_error("sph_build_neighbors: unknown kernel %d", sc->kernel);
+    return SPH_ERR_INVALID;
+  }
   Grid g{};
-  const double two_h = 2.0 * (double)sc->h;
+  // the support radius: 2h (Wendland) or 3h (truncated Gaussian)
+  const double rsup = (sc->kernel == SPH_KERNEL_GAUSSIAN ? 3.0 : 2.0) * (double)sc->h;
   int64_t ncells = 1;
   for (int ax = 0; ax < 3; ++ax) {
     double L = sc->hi[ax] - sc->lo[ax];
@@ -405,14 +410,14 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
       set_error("sph_build_neighbors: hi[%d] must exceed lo[%d]", ax, ax);
       return SPH_ERR_INVALID;
     }
-    // cells strictly larger than 2h (with a relative margin for rounding)
-    double nc = std::floor(L / (two_h * (1.0 + 1e-6)));
+    // cells strictly larger than the support radius (with a relative margin for rounding)
+    double nc = std::floor(L / (rsup * (1.0 + 1e-6)));
     if (nc < 1.0) nc = 1.0;
     if (nc > 1.0e6) nc = 1.0e6;
     g.periodic[ax] = sc->periodic[ax] ? 1 : 0;
     if (g.periodic[ax] && nc < 3.0) {
-      set_error("sph_build_neighbors: periodic axis %d is shorter than three cells of 2h (L = %g, 2h = %g)", ax, L,
-                two_h);
+      set_error("sph_build_neighbors: periodic axis %d is shorter than three cells of the support radius "
+                "(L = %g, radius = %g)", ax, L, rsup);
       return SPH_ERR_INVALID;
     }
     g.ncell[ax] = (int)nc;
@@ -458,6 +463,7 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
   H->nslices = H->n_pad / kSlice;
   H->grid = g;
   H->h = sc->h;
+  H->kernel = sc->kernel;
   H->op_valid = false;
   H->mu_version++;
 
@@ -523,7 +529,7 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
 
   // band of the float32 filter: coordinate differences carry at most a few
   // float32 roundings of the largest coordinate or period E; r^2 then errs by
-  // at most 2 sqrt(3) (2h) E + 3 E^2 plus its own three roundings
+  // at most 2 sqrt(3) (R h) E + 3 E^2 plus its own three roundings
   double big = (double)max_abs;
   for (int ax = 0; ax < 3; ++ax) {
     big = std::fmax(big, std::fabs(sc->lo[ax]));
@@ -532,8 +538,8 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
   }
   const double E = 4.0 * big * std::ldexp(1.0, -23);
   Band band{};
-  band.R2 = two_h * two_h;
-  const double B = 4.0 * two_h * E + 3.0 * E * E + 1e-6 * band.R2;
+  band.R2 = rsup * rsup;
+  const double B = 4.0 * rsup * E + 3.0 * E * E + 1e-6 * band.R2;
   band.lo2 = (float)std::fmax(0.0, (band.R2 - B) * (1.0 - 1e-7));
   band.hi2 = (float)((band.R2 + B) * (1.0 + 1e-7));
   for (int ax = 0; ax < 3; ++ax) {

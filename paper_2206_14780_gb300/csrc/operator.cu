@@ -78,6 +78,25 @@ __device__ __forceinline__ dfl wendland_w_df(dfl q) {
   return df_mul(df_mul(t2, t2), df_add(dfl{1.f, 0.f}, dfl{2.f * q.hi, 2.f * q.lo}));
 }
 
+// truncated Gaussian (Sec. 5.2, radius 3h): e^{-q^2} from the double-float q,
+// the exponential in float64 once per pair (the set-up runs once per A(dt))
+__device__ __forceinline__ dfl gauss_e_df(dfl q) { return df_from_double(exp(-df_to_double(df_mul(q, q)))); }
+
+// the fluid coefficient's kernel factor: (2 - q)^3 (Wendland) or e^{-q^2} (Gaussian),
+// each without the constant of |f| (it is in R_b)
+__device__ __forceinline__ dfl fluid_kernel_df(dfl q, int gauss) {
+  if (gauss) return gauss_e_df(q);
+  dfl tq = df_add(dfl{2.f, 0.f}, df_neg(q));
+  if (tq.hi <= 0.f) tq = dfl{0.f, 0.f};
+  return df_mul(df_mul(tq, tq), tq);
+}
+
+// the Shepard weight w(q) without its constant: Wendland, or e^{-q^2} - e^{-9}
+__device__ __forceinline__ dfl shepard_w_df(dfl q, int gauss, double gauss_tail) {
+  if (gauss) return df_from_double(exp(-df_to_double(df_mul(q, q))) - gauss_tail);
+  return wendland_w_df(q);
+}
+
 __global__ void k_op_count(const uint8_t* __restrict__ type, const int32_t* __restrict__ cnt,
                            const int64_t* __restrict__ slice_off, const int32_t* __restrict__ nbr, int64_t n,
                            int64_t n_pad, int boundary, int32_t* __restrict__ op_cnt, uint8_t* __restrict__ kind) {
@@ -112,17 +131,18 @@ __global__ void k_op_count(const uint8_t* __restrict__ type, const int32_t* __re
 // Coefficients of A(dt) (Eq. kab with |F|, Eqs. diag, offdiag and dummyvel) in
 // double-float arithmetic (relative error a few 2^-45), stored as the float32
 // pair (hi, lo) that the float32 apply and the double-float residual read;
-// float64 is used once per row (R_b, D) only.
-//   fluid row b:  a_ba = dt c_ab = R_b V_a mubar (2 - q)^3,
-//                 R_b = 2 dt (105 / (128 pi)) / (h^5 rho_b), D_b = 1 + sum a
+// float64 is used once per row (R_b, D) only, and for the Gaussian's exponential.
+//   fluid row b:  a_ba = dt c_ab = R_b V_a mubar k(q), D_b = 1 + sum a, with
+//                 Wendland  k = (2 - q)^3,  R_b = 2 dt (105 / (128 pi)) / (h^5 rho_b)
+//                 Gaussian  k = e^{-q^2},   R_b = 2 dt (2 / w_G) / (h^5 rho_b)
 //   dummy wall:   a_ba = W_ba / S_b over fluid neighbours
 __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restrict__ rho, const float* __restrict__ mu,
                           const uint8_t* __restrict__ type, const float4* __restrict__ aux,
                           const int32_t* __restrict__ cnt, const int64_t* __restrict__ slice_off,
                           const int32_t* __restrict__ nbr, const uint8_t* __restrict__ kind,
                           const int64_t* __restrict__ op_off, int64_t n, int64_t n_pad, OpGeom g64, double dt, int mean,
-                          int2* __restrict__ op_ih, float* __restrict__ op_lo, float* __restrict__ invD,
-                          double* __restrict__ D64) {
+                          int gauss, double kf, double gauss_tail, int2* __restrict__ op_ih, float* __restrict__ op_lo,
+                          float* __restrict__ invD, double* __restrict__ D64) {
   OpGeomDF g;
   for (int ax = 0; ax < 3; ++ax) {
     g.L[ax] = df_from_double(g64.L[ax]);
@@ -130,8 +150,6 @@ __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restric
     g.periodic[ax] = g64.periodic[ax];
   }
   g.inv_h = df_from_double(g64.inv_h);
-  const double inv_h5 = g64.inv_h * g64.inv_h * g64.inv_h * g64.inv_h * g64.inv_h;
-  const double kf = 2.0 * dt * (105.0 / (128.0 * M_PI)) * inv_h5;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
     if (s >= n || kind[s] == KIND_IDENTITY) {
       invD[s] = 1.f;
@@ -154,9 +172,7 @@ __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restric
         const float4 pa = pos[t];
         const float4 at = aux[t];
         const dfl q = df_mul(pair_r_df(pa, pb, g), g.inv_h);
-        dfl tq = df_add(dfl{2.f, 0.f}, df_neg(q));
-        if (tq.hi <= 0.f) tq = dfl{0.f, 0.f};
-        const dfl tq3 = df_mul(df_mul(tq, tq), tq);
+        const dfl tq3 = fluid_kernel_df(q, gauss);
         dfl mub{mu_b, 0.f};
         if (type[t] == SPH_FLUID) {
           if (mean == SPH_MEAN_ARITHMETIC) {
@@ -182,7 +198,7 @@ __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restric
       for (int j = 0; j < c; ++j) {
         const int32_t t = nbr[base + (int64_t)j * kSlice];
         if (type[t] != SPH_FLUID) continue;
-        S = df_add(S, wendland_w_df(df_mul(pair_r_df(pos[t], pb, g), g.inv_h)));
+        S = df_add(S, shepard_w_df(df_mul(pair_r_df(pos[t], pb, g), g.inv_h), gauss, gauss_tail));
       }
       // S rounds to zero only if every fluid neighbour sits at q = 2 to within
       // rounding: zero coefficients then make the row an identity row (as an
@@ -191,7 +207,7 @@ __global__ void k_op_fill(const float4* __restrict__ pos, const float* __restric
       for (int j = 0; j < c; ++j) {
         const int32_t t = nbr[base + (int64_t)j * kSlice];
         if (type[t] != SPH_FLUID) continue;
-        const dfl a = df_mul(wendland_w_df(df_mul(pair_r_df(pos[t], pb, g), g.inv_h)), invS);
+        const dfl a = df_mul(shepard_w_df(df_mul(pair_r_df(pos[t], pb, g), g.inv_h), gauss, gauss_tail), invS);
         const int64_t e = obase + (int64_t)o * kSlice;
         op_ih[e] = make_int2(t, __float_as_int(a.hi));
         op_lo[e] = a.lo;
@@ -396,10 +412,13 @@ sph_status ensure_operator(sph_neighbors* H, const sph_visc_params* P, cudaStrea
   H->op_nnz = total;
   SPH_TRY(H->aux_df.alloc(H->n_pad));
   SPH_LAUNCH(k_op_aux, grid, kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->n_pad, H->aux_df.p);
+  const int gauss = H->kernel == SPH_KERNEL_GAUSSIAN ? 1 : 0;
+  const double inv_h5 = g.inv_h * g.inv_h * g.inv_h * g.inv_h * g.inv_h;
+  const double kf = 2.0 * P->dt * (gauss ? 2.0 / gauss_norm() : 105.0 / (128.0 * M_PI)) * inv_h5;
   SPH_LAUNCH(k_op_fill, grid, kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->type_s.p, H->aux_df.p, H->cnt.p,
-                                             H->slice_off.p,
-                                     H->nbr.p, H->op_kind.p, H->op_off.p, H->n, H->n_pad, g, P->dt, P->mean,
-                                     H->op_ih.p, H->op_lo.p, H->invD.p, H->D64.p);
+                                             H->slice_off.p, H->nbr.p, H->op_kind.p, H->op_off.p, H->n, H->n_pad, g,
+                                             P->dt, P->mean, gauss, kf, std::exp(-kGaussK * kGaussK), H->op_ih.p,
+                                             H->op_lo.p, H->invD.p, H->D64.p);
   SPH_TRY_CUDA(cudaGetLastError());
   H->op_valid = true;
   H->op_params = *P;

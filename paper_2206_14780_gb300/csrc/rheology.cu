@@ -44,7 +44,8 @@ struct MuGeom {
   float L[3], invL[3];
   int periodic[3];
   float inv_h;
-  float absf_scale;  // 105/(128 pi) / h^5
+  float absf_scale;  // |f| constant / h^5: 105/(128 pi) (Wendland) or 2 / w_G (Gaussian)
+  int gauss;         // 1: truncated Gaussian, |f| ~ e^{-q^2}; 0: Wendland, |f| ~ (2 - q)^3
 };
 
 __global__ void __launch_bounds__(kBlock) k_mu_pass(const float4* __restrict__ pos_s, const float* __restrict__ rho_s,
@@ -80,7 +81,8 @@ __global__ void __launch_bounds__(kBlock) k_mu_pass(const float4* __restrict__ p
       const float r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
       const float q = r * g.inv_h;
       const float tq = fmaxf(2.f - q, 0.f);
-      const float w = (pa.w / rho_s[t]) * g.absf_scale * tq * tq * tq;
+      const float kq = g.gauss ? expf(-q * q) : tq * tq * tq;
+      const float w = (pa.w / rho_s[t]) * g.absf_scale * kq;
       const float du[3] = {ua.x - ub.x, ua.y - ub.y, ua.z - ub.z};
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -133,7 +135,8 @@ sph_status mu_papanastasiou(sph_neighbors* H, const float* vel, const float* wal
   }
   const double h = (double)H->h;
   g.inv_h = (float)(1.0 / h);
-  g.absf_scale = (float)(105.0 / (128.0 * M_PI) / (h * h * h * h * h));
+  g.gauss = H->kernel == SPH_KERNEL_GAUSSIAN ? 1 : 0;
+  g.absf_scale = (float)((g.gauss ? 2.0 / gauss_norm() : 105.0 / (128.0 * M_PI)) / (h * h * h * h * h));
   SPH_LAUNCH(k_mu_pass, grid_for(H, H->n), kBlock, 0, st)(
       H->pos_s.p, H->rho_s.p, H->type_s.p, H->cnt.p, H->slice_off.p, H->nbr.p, H->perm.p,
       reinterpret_cast<const float4*>(vel), reinterpret_cast<const float4*>(wall_vel), H->n, g, (float)tau0,

@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -25,6 +26,14 @@ namespace sph {
 constexpr int kSlice = 32;        // rows per SELL slice (one warp)
 constexpr int kBlock = 256;       // threads per block of the row kernels
 constexpr int kMaxDots = 15;      // float64 partial sums one reduction may carry
+
+// truncated Gaussian kernel (Sec. 5.2): radius k = 3 and its normalisation
+// w_G = pi^{3/2} erf(k) - (2 pi / 3) e^{-k^2} k (3 + 2 k^2)
+constexpr double kGaussK = 3.0;
+inline double gauss_norm() {
+  const double k = kGaussK, pi = 3.14159265358979323846;
+  return std::pow(pi, 1.5) * std::erf(k) - 2.0 * pi / 3.0 * std::exp(-k * k) * k * (3.0 + 2.0 * k * k);
+}
 
 void set_error(const char* fmt, ...);
 void clear_error();
@@ -164,6 +173,7 @@ struct sph_neighbors {
   int64_t nslices = 0;
   sph::Grid grid{};
   float h = 0.f;
+  int kernel = SPH_KERNEL_WENDLAND;   // smoothing kernel (support radius 2h or 3h)
   int device = 0;
   int num_sms = 0;
 
@@ -327,6 +337,16 @@ sph_status solve_fp64(sph_neighbors* H, const sph_visc_params* P, const sph_solv
                       const double* b, double* x, sph_solve_report* R, cudaStream_t st);
 
 int grid_for(const sph_neighbors* H, int64_t work_items, int block = kBlock);
+
+// shard.cu: one system over several sub-domains (sph_shard_*)
+sph_status shard_plan(int64_t n, const int32_t* layer, int32_t nlayers, int32_t ranks, int64_t* virt,
+                      int32_t* rank_first_layer, int64_t* layer_first_virt);
+sph_status shard_create(sph_neighbors* H, const sph_visc_params* P, int32_t ranks, sph_shard** out, cudaStream_t st);
+sph_status shard_destroy(sph_shard* Z);
+sph_status shard_info(const sph_shard* Z, int32_t* axis, int32_t* layers, int64_t* owned, int64_t* halo,
+                      int64_t* exchanged);
+sph_status shard_solve(sph_shard* Z, const sph_solve_opts* O, const double* b, double* x, sph_solve_report* R,
+                       cudaStream_t st);
 
 // replay.cu: the solver's scalar steps on caller-given dots (sph_bicgstab_replay)
 sph_status bicgstab_replay(const double* gamma0, double eps, int32_t maxit, int32_t nsteps, const double* dots,

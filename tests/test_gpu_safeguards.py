@@ -187,7 +187,7 @@ def test_identity_system_solve_omega_zero_is_converged():
     rounding of delta against gamma avoids here, is driven by the replay tests.)"""
     from paper_2206_14780_gb300 import binding
 
-    s = scenes.random_box(21, nf=300).copy()
+    s = scenes.random_box(21, nf=500).copy()
     s.ptype[:] = scenes.WALL
     s.boundary = scenes.BC_DYNAMIC
     rng = np.random.default_rng(3)
