@@ -25,6 +25,9 @@ Everything here is plain, slow and in float64, written from the paper:
 * ``features``   the sixteen per-particle inputs of that network
 * ``warmstart``  x0 = v + U y with the dummy-wall closure (Eq. dummyvel), the
                  residual training loss and its MSE pseudo-targets
+* ``step``       one semi-implicit predictor/corrector step (Sec. 3.3): Cole's
+                 equation of state, the dummy-wall pressure (Eq. dummyP), the
+                 inviscid acceleration and continuity, two viscous solves
 
 Readings of the paper where it is garbled or silent:
 X1 the kernel gradient factor F enters K_ab as a magnitude, so the fluid rows are
@@ -39,4 +42,4 @@ against closed forms, invariants, brute force or library routines.  Iteration
 counts of the paper's experiments are NOT pinned (different stiffness regime):
 parity unpinned for iteration counts only.
 """
-from . import kernel, neighbors, operator, solvers, rheology, mlp, features, warmstart  # noqa: F401
+from . import kernel, neighbors, operator, solvers, rheology, mlp, features, warmstart, step  # noqa: F401
