@@ -47,6 +47,8 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-gaussian", action="store_true")
+    ap.add_argument("--no-poiseuille", action="store_true")
     ap.add_argument("--ensemble-only", action="store_true")
     ap.add_argument("--ensemble-scenes", type=int, default=64, help="scenes of the ensemble leg (64: the workload)")
     ap.add_argument("--no-precision", action="store_true")
@@ -464,6 +466,12 @@ def run_sphvisc(args):
     if world == 1:
         apply_forms = run_apply_forms(nb, params, s.n, dev)
         channel = run_channel(dev)
+    gaussian = None
+    if world == 1 and not args.no_gaussian:
+        gaussian = run_gaussian(dev, n=args.box_side)
+    poiseuille = None
+    if world == 1 and not args.no_poiseuille:
+        poiseuille = run_poiseuille(dev)
     sequence = None
     if not args.no_sequence and world == 1:
         sequence = run_sequence(nb, s, b, t, args.sequence_steps, dev)
@@ -534,7 +542,7 @@ def run_sphvisc(args):
                            ms_per_step_min=min(per_step), ms_per_step_max=max(per_step)),
                roofline=roofline, cpu_baseline=cpu, oracle_error=oracle_error, e2e=e2e, gpu_launches=int(launches), ensemble=ensemble,
                precision_study=precision, sequence=sequence, learned=learned, apply_forms=apply_forms,
-               channel=channel,
+               channel=channel, gaussian=gaussian, poiseuille=poiseuille,
                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"],
                            samples=clk["samples"]),
                wall_s=wall)
@@ -586,6 +594,109 @@ def run_channel(dev, reps=10):
                          "top wall 1 m/s, v = linear profile + 1% noise", particles=s.n, ms_per_step=ms,
                 iters=[r["iters"] for r in reps_][:3], passes=reps_[0]["refinements"],
                 max_true_rel_res=max(r["true_rel_res"] for r in reps_))
+
+
+# ------------------------------------------------------- Gaussian kernel ------
+
+def run_gaussian(dev, n=100, reps=3):
+    """The lava box with the truncated Gaussian kernel of Sec. 5.2 (support 3h = 3.9 dx,
+    ~250 neighbours, four dummy layers): ms per step (neighbours + A(dt) + x0 + solve
+    to 1e-6), iterations, and the apply's algorithmic GB/s inside the solves."""
+    import torch
+
+    import scenes
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.lava_box(0, n=n, layers=4, kernel=scenes.KERNEL_GAUSSIAN)
+    t = binding.scene_tensors(s, dev)
+    t["vel"] = torch.from_numpy(s.vel).to(dev)
+    p = binding.visc_params(s.dt, s.boundary, s.mean)
+    geo = (s.lo, s.hi, s.periodic, s.h)
+    nb = binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], *geo, max_neighbors=512, kernel=s.kernel)
+    b = torch.from_numpy(s.b).to(dev)
+    x = torch.empty_like(b)
+    opts = binding.solve_opts()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        nb.rebuild(t["pos"], t["rho"], t["mu"], t["ptype"], *geo, max_neighbors=512, kernel=s.kernel)
+        binding.warm_start(nb, p, None, t["vel"], t["ptype"], b, x)
+        return nb.solve(p, opts, b, x)
+
+    for _ in range(2):
+        step()
+    nb.profile(True)
+    nb.profile_read(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    reps_ = [step() for _ in range(reps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    prof = nb.profile_read(reset=True)
+    nb.profile(False)
+    _, nnz, maxc = nb.info()
+    nb.close()
+    us = 1e3 * prof["apply_ms"] / max(1, prof["apply_launches"])
+    hbm, kind = read_peaks()
+    gbs = prof["apply_bytes"] / (us * 1e-6) / 1e9 if prof["apply_launches"] else None
+    return dict(workload=f"lava box {n}^3 fluid, truncated Gaussian (k = 3, h = 1.3 dx), 4 dummy layers "
+                         f"(N={s.n})", particles=s.n, neighbour_pairs=int(nnz), max_neighbours=int(maxc),
+                ms_per_step=e0.elapsed_time(e1) / reps, iters=[r["iters"] for r in reps_],
+                passes=reps_[0]["refinements"], max_true_rel_res=max(r["true_rel_res"] for r in reps_),
+                apply_us=us, apply_algorithmic_bytes=prof["apply_bytes"], apply_gbs=gbs,
+                apply_frac_of_hbm=(gbs / hbm) if gbs else None, peak_source=kind)
+
+
+# ------------------------------------------------------ Poiseuille flow -------
+
+POISEUILLE_PAPER = {"l1": 1.227e-3, "l2": 1.282e-3, "l1_102": 3.916e-4, "l2_102": 3.929e-4}
+
+
+def run_poiseuille(dev, t_end=10.0, dt=2.5e-3):
+    """The plane Poiseuille flow of Sec. 5 with the full semi-implicit step (sph_step):
+    Newtonian, Wendland h = 1.3 dp, dummy walls, dp = 1/16, L = 1 m, g = 0.05 m/s^2,
+    mu = 0.1 Pa s, rho0 = 1 kg/m^3, c0 = 6.32 m/s, from rest to t = 10 s.  The l1 and l2
+    errors of the steady profile against u(z) = rho0 g / (2 mu) (L^2/4 - z^2) and
+    against 102% of it, next to the paper's table (Sec. 5.3, Wendland, dummy, 1/16)."""
+    import numpy as np
+    import torch
+
+    import scenes
+    from paper_2206_14780_gb300 import binding
+
+    dx, g, mu, L = 1.0 / 16, 0.05, 0.1, 1.0
+    s = scenes.couette(0, nx=8, ny=16, nz=8, dx=dx, rho0=1.0, nu=mu, dt=dt, U=0.0, noise=0.0)
+    s.vel[:] = 0.0
+    t = {k: torch.from_numpy(getattr(s, k).copy()).to(dev) for k in ("pos", "vel", "rho", "mu", "ptype")}
+    st = binding.Stepper(t["pos"], t["vel"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
+    prm = binding.step_params(dt, 1.0, 6.32, 7.0, (g, 0.0, 0.0), s.boundary, s.mean)
+    opts = binding.solve_opts(rtol=1e-8)
+    steps = int(round(t_end / dt))
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    its = 0
+    for _ in range(steps):
+        rep = st.step(prm, opts)
+        its += rep["half"]["iters"] + rep["full"]["iters"]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    st.close()
+    fl = s.ptype == scenes.FLUID
+    z = t["pos"].cpu().numpy()[fl, 1].astype(np.float64) - 0.5 * L
+    u = t["vel"].cpu().numpy()[fl, 0].astype(np.float64)
+    exact = 0.5 * g / mu * (0.25 * L * L - z * z)
+    out = dict(workload=f"plane Poiseuille, dp = 1/16, {int(fl.sum())} fluid + {int((~fl).sum())} dummy wall particles, "
+                        f"{steps} steps of dt = {dt} to t = {t_end} s", steps=steps,
+               ms_per_step=e0.elapsed_time(e1) / steps, iterations_per_step=its / steps,
+               u_max=float(u.max()), u_max_exact=float(exact.max()), paper=POISEUILLE_PAPER)
+    for f, k1, k2 in ((1.0, "l1", "l2"), (1.02, "l1_102", "l2_102")):
+        e = u - f * exact
+        out[k1] = float(np.abs(e).mean())
+        out[k2] = float(np.sqrt((e * e).mean()))
+    return out
 
 
 # --------------------------------------------------------- network forward ----

@@ -193,7 +193,12 @@ sph_status sph_visc_apply_otf(sph_neighbors* handle, const sph_visc_params* para
  *  - n rounded up to 32 above SPH_NOALLOC_MAX_ROWS: SPH_ERR_INVALID.
  *  - The first call on a device looks up the array's device address there
  *    (cudaGetSymbolAddress, once per device, with that device current); make
- *    that first call before any stream capture.
+ *    that first call before any stream capture.  The address is kept for the
+ *    life of the process: after a cudaDeviceReset of that device it is stale,
+ *    so a process that resets a device must not call this entry point on it
+ *    again.
+ *  - v and y must not overlap (any overlap of their n x 16-byte ranges:
+ *    SPH_ERR_INVALID).
  *  - All calls share the one array: calls whose work overlaps on the GPU (other
  *    streams, other host threads) race on it.  Every row it reads is written
  *    by the same call first, so stale contents from a previous call are never
@@ -334,6 +339,68 @@ sph_status sph_bicgstab_replay(const double* gamma0, double eps, int32_t maxit, 
 sph_status sph_visc_solve_host(const sph_scene* scene, int32_t max_neighbors, const sph_visc_params* params,
                                const sph_solve_opts* opts, const float* vel, const double* b, double* x,
                                sph_neighbors** handle, sph_solve_report* report, void* stream);
+
+/* ---- The semi-implicit time step (Sec. 3.3) ---------------------------------
+ * The predictor/corrector step of Sec. 3.3 around the viscous solve, on a
+ * particle state kept on the device:
+ *   abar^n, drho^n; solve A^n(dt/2) V = B(dt/2) (B_fluid = u^n + dt/2 abar^n,
+ *   walls 2 u_w dummy / u_w dynamic) for u^{n+1/2}; r^{n+1/2} = r^n + dt/2 u^n,
+ *   rho^{n+1/2} = rho^n + dt/2 drho^n, mu^{n+1/2} (Papanastasiou); abar, drho
+ *   there; solve A^{n+1/2}(dt) V = u^n + dt abar^{n+1/2} for u^{n+1};
+ *   r^{n+1} = r^n + dt/2 (u^n + u^{n+1}), rho^{n+1} = rho^n + dt drho^{n+1/2}.
+ * Pressure: Cole's equation of state (Eq. cole-pressure),
+ *   P = c0^2 rho0 / zeta ((rho / rho0)^zeta - 1);
+ * dummy walls (Eq. dummyP, walls at constant velocity): P_w = (sum_F P_a W_wa +
+ *   g . sum_F rho_a (r_w - r_a) W_wa) / sum_F W_wa, rho_w = EOS^-1(P_w);
+ * inviscid acceleration and continuity (Eqs. part_NS, part_continuity), with
+ *   grad_b W_ab = |F_ab| (r_a - r_b):
+ *   abar_b = g - sum_a m_a (P_a / rho_a^2 + P_b / rho_b^2) |F_ab| (r_a - r_b),
+ *   drho_b/dt = sum_a m_a (u_b - u_a) . (r_a - r_b) |F_ab|
+ *   (the printed signs, with the printed F <= 0, would make pressure attract;
+ *   these are the signs under which it repels and compression raises rho).
+ * Fluid rows get abar; fluid and dynamic-wall rows evolve their density; walls
+ * move with their prescribed velocity.  Positions and densities are updated in
+ * float64 and stored as float32 (periodic axes folded into [lo, hi)). */
+typedef struct {
+  int64_t n;               /* particles, >= 1                                        */
+  float* pos;              /* (device) [n][4] x, y, z, m; in: r^n, out: r^{n+1}       */
+  float* vel;              /* (device) [n][4]; fluid rows in: u^n, out: u^{n+1}; wall
+                              rows: the prescribed wall velocity u_w (read only)      */
+  float* rho;              /* (device) [n]; in/out (dummy walls: set by the closure)  */
+  float* mu;               /* (device) [n]; in/out: recomputed from the velocities
+                              after each neighbour build when rheology = 1            */
+  const uint8_t* ptype;    /* (device) [n] SPH_FLUID / SPH_WALL                      */
+  double lo[3], hi[3];     /* box, as sph_scene                                       */
+  int32_t periodic[3];
+  float h;
+  int32_t kernel;          /* SPH_KERNEL_WENDLAND or SPH_KERNEL_GAUSSIAN              */
+} sph_state;
+
+typedef struct {
+  double dt;               /* time step                                               */
+  double rho0, c0, zeta;   /* equation of state: rest density, sound speed, exponent  */
+  double g[3];             /* body force per unit mass                                */
+  int32_t boundary;        /* SPH_BC_DUMMY or SPH_BC_DYNAMIC                          */
+  int32_t mean;            /* SPH_MEAN_HARMONIC or SPH_MEAN_ARITHMETIC                */
+  int32_t rheology;        /* 0: Newtonian (mu as given); 1: Papanastasiou (Eq. papa)  */
+  double tau0, mu0, m;     /* Papanastasiou yield stress, plastic viscosity, exponent */
+  int32_t max_neighbors;   /* capacity of the neighbour lists (0 = 128)               */
+} sph_step_params;
+
+typedef struct {
+  sph_solve_report half;   /* the solve with A^n(dt/2)                                */
+  sph_solve_report full;   /* the solve with A^{n+1/2}(dt)                            */
+} sph_step_report;
+
+/* One step on `state` (device arrays, updated in place).  *handle: NULL on the
+ * first call (created and returned; release with sph_neighbors_destroy) or the
+ * handle of the previous step; the neighbour lists are rebuilt at r^n and at
+ * r^{n+1/2}.  Both solves use opts (its method must suit the boundary model, as
+ * for sph_visc_solve).  The step's buffers are owned by the handle.  report:
+ * (host).  Synchronises.  Returns SPH_OK, SPH_NOT_CONVERGED when a solve stopped
+ * above rtol (the state is still advanced), or the error of a failed call. */
+sph_status sph_step(sph_state* state, const sph_step_params* params, const sph_solve_opts* opts,
+                    sph_neighbors** handle, sph_step_report* report, void* stream);
 
 /* ---- Batched ensemble solve -------------------------------------------------
  * S independent scenes (each its own handle and A(dt)) solved together: every

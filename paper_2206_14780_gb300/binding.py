@@ -33,7 +33,8 @@ EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", 
            "sph_mlp_create", "sph_mlp_set_params", "sph_mlp_get_params", "sph_mlp_destroy", "sph_mlp_features",
            "sph_mlp_targets", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train_step", "sph_warm_start",
            "sph_mlp_residual_targets", "sph_mlp_set_mode", "sph_visc_solve_host", "sph_bicgstab_replay",
-           "sph_shard_plan", "sph_shard_create", "sph_shard_info", "sph_shard_solve", "sph_shard_destroy"]
+           "sph_shard_plan", "sph_shard_create", "sph_shard_info", "sph_shard_solve", "sph_shard_destroy",
+           "sph_step"]
 MLP_NPARAMS = 9603
 
 
@@ -67,6 +68,24 @@ class sph_profile_counters(ctypes.Structure):
                 ("apply_variant", ctypes.c_int32 * 2), ("tune_us", (ctypes.c_float * 6) * 3),
                 ("standalone_launches", ctypes.c_int64 * 2), ("standalone_ms", ctypes.c_double * 2),
                 ("otf_bytes", ctypes.c_int64), ("apply_grid", ctypes.c_int32 * 2)]
+
+
+class sph_state(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("rho", ctypes.c_void_p),
+                ("mu", ctypes.c_void_p), ("ptype", ctypes.c_void_p), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("periodic", ctypes.c_int32 * 3), ("h", ctypes.c_float),
+                ("kernel", ctypes.c_int32)]
+
+
+class sph_step_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("rho0", ctypes.c_double), ("c0", ctypes.c_double),
+                ("zeta", ctypes.c_double), ("g", ctypes.c_double * 3), ("boundary", ctypes.c_int32),
+                ("mean", ctypes.c_int32), ("rheology", ctypes.c_int32), ("tau0", ctypes.c_double),
+                ("mu0", ctypes.c_double), ("m", ctypes.c_double), ("max_neighbors", ctypes.c_int32)]
+
+
+class sph_step_report(ctypes.Structure):
+    _fields_ = [("half", sph_solve_report), ("full", sph_solve_report)]
 
 
 class SphError(RuntimeError):
@@ -128,6 +147,8 @@ def load(path: str = LIB_PATH):
         "sph_shard_info": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), vp, vp, ctypes.POINTER(i64)],
         "sph_shard_solve": [vp, ctypes.POINTER(sph_solve_opts), vp, vp, ctypes.POINTER(sph_solve_report), vp],
         "sph_shard_destroy": [vp],
+        "sph_step": [ctypes.POINTER(sph_state), ctypes.POINTER(sph_step_params), ctypes.POINTER(sph_solve_opts),
+                     ctypes.POINTER(vp), ctypes.POINTER(sph_step_report), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -537,6 +558,60 @@ def warm_start(nb, params, mlp, vel, ptype, b, x0, stream=None):
     """sph_warm_start; mlp=None gives v^n with the dummy-wall closure."""
     _check(_lib.sph_warm_start(nb.handle, ctypes.byref(params), mlp.handle if mlp is not None else None, _ptr(vel),
                                _ptr(ptype), _ptr(b), _ptr(x0), _stream(stream)))
+
+
+def step_params(dt, rho0, c0, zeta=7.0, g=(0.0, 0.0, 0.0), boundary=SPH_BC_DUMMY, mean=SPH_MEAN_HARMONIC,
+                rheology=None, max_neighbors=128):
+    """sph_step_params; rheology = (tau0, mu0, m) for Papanastasiou, None for Newtonian."""
+    p = sph_step_params()
+    p.dt, p.rho0, p.c0, p.zeta = float(dt), float(rho0), float(c0), float(zeta)
+    for k in range(3):
+        p.g[k] = float(g[k])
+    p.boundary, p.mean = int(boundary), int(mean)
+    p.rheology = 0 if rheology is None else 1
+    if rheology is not None:
+        p.tau0, p.mu0, p.m = (float(v) for v in rheology)
+    p.max_neighbors = int(max_neighbors)
+    return p
+
+
+class Stepper:
+    """sph_step on a particle state held in device tensors (pos [n,4], vel [n,4], rho, mu
+    float32, ptype uint8), advanced in place; owns the neighbour handle between steps."""
+
+    def __init__(self, pos, vel, rho, mu, ptype, lo, hi, periodic, h, kernel=0):
+        load()
+        self.t = dict(pos=pos, vel=vel, rho=rho, mu=mu, ptype=ptype)
+        st = sph_state()
+        st.n = int(pos.shape[0])
+        st.pos, st.vel, st.rho, st.mu, st.ptype = _ptr(pos), _ptr(vel), _ptr(rho), _ptr(mu), _ptr(ptype)
+        for ax in range(3):
+            st.lo[ax] = float(lo[ax])
+            st.hi[ax] = float(hi[ax])
+            st.periodic[ax] = int(periodic[ax])
+        st.h = float(h)
+        st.kernel = int(kernel)
+        self.state = st
+        self.handle = ctypes.c_void_p()
+
+    def step(self, params, opts, stream=None):
+        rep = sph_step_report()
+        s = _lib.sph_step(ctypes.byref(self.state), ctypes.byref(params), ctypes.byref(opts),
+                          ctypes.byref(self.handle), ctypes.byref(rep), _stream(stream))
+        if s not in (SPH_OK, 6):
+            _check(s)
+        return dict(status=s, half=_report(rep.half), full=_report(rep.full))
+
+    def close(self):
+        if self.handle:
+            _lib.sph_neighbors_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def build_neighbors(pos, rho, mu, ptype, lo, hi, periodic, h, max_neighbors=128, stream=None, kernel=0):

@@ -178,6 +178,7 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
     h->stage->release();
     delete h->stage;
   }
+  release_step_stage(h);
   h->otf_g.release();
   h->otf_im.release();
   h->otf_rb.release();
@@ -271,6 +272,12 @@ sph_status sph_mu_papanastasiou(sph_neighbors* h, const float* vel, const float*
     return SPH_ERR_INVALID;
   }
   return mu_papanastasiou(h, vel, wall_vel, tau0, mu0, m, mu_out, set_handle, as_stream(stream));
+}
+
+sph_status sph_step(sph_state* state, const sph_step_params* params, const sph_solve_opts* opts,
+                    sph_neighbors** handle, sph_step_report* report, void* stream) {
+  clear_error();
+  return time_step(state, params, opts, handle, report, as_stream(stream));
 }
 
 sph_status sph_shard_plan(int64_t n, const int32_t* layer, int32_t nlayers, int32_t ranks, int64_t* virt,

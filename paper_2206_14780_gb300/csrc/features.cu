@@ -513,6 +513,25 @@ sph_status sph_mlp_targets(sph_neighbors* h, const float* vel, const double* x_s
   return SPH_OK;
 }
 
+}  // extern "C"
+
+namespace sph {
+// x0 = v^n on fluid rows with the dummy-wall closure (sph_warm_start without a network)
+sph_status warm_start_plain(sph_neighbors* h, const sph_visc_params* params, const float* vel, const uint8_t* ptype,
+                            const double* b, double* x0, cudaStream_t st) {
+  SPH_TRY(ensure_operator(h, params, st));
+  SPH_TRY(ensure_workspace(h));
+  SPH_TRY(h->feat_tmp.alloc(4 * h->n_pad));
+  SPH_LAUNCH(k_warm_x0, grid_for(h, h->n), kBlock, 0, st)(reinterpret_cast<const float4*>(vel), nullptr, ptype, b,
+                                                          h->n, h->feat_scale.p, x0);
+  wall_closure(h, x0, b, st);
+  SPH_TRY_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+}  // namespace sph
+
+extern "C" {
+
 sph_status sph_warm_start(sph_neighbors* h, const sph_visc_params* params, const sph_mlp* mlp, const float* vel,
                           const uint8_t* ptype, const double* b, double* x0, void* stream) {
   clear_error();

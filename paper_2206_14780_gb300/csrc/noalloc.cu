@@ -18,6 +18,10 @@ constexpr int kMaxDevices = 64;
 // [0, kMaxRows): sorted v; [kMaxRows, 2 kMaxRows): sorted y.  8 MiB.
 __device__ __align__(256) float4 g_noalloc_scratch[2 * kMaxRows];
 
+// The address is looked up once per device and kept: it stays valid for the
+// life of the device's primary context.  cudaDeviceReset destroys that context
+// (and the array's storage with it), so a process that resets a device must not
+// call sph_visc_apply_noalloc on it afterwards.
 std::mutex g_mutex;
 float4* g_scratch_ptr[kMaxDevices] = {};
 
@@ -68,9 +72,14 @@ sph_status visc_apply_noalloc(sph_neighbors* H, const sph_visc_params* P, const 
     set_error("sph_visc_apply_noalloc: null argument");
     return SPH_ERR_INVALID;
   }
-  if (v == y) {
-    set_error("sph_visc_apply_noalloc: v and y must not overlap");
-    return SPH_ERR_INVALID;
+  {
+    // [v, v + 16 n) and [y, y + 16 n) must be disjoint
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(v), b0 = reinterpret_cast<uintptr_t>(y);
+    const uintptr_t len = (uintptr_t)H->n * sizeof(float4);
+    if (a0 < b0 + len && b0 < a0 + len) {
+      set_error("sph_visc_apply_noalloc: v and y must not overlap");
+      return SPH_ERR_INVALID;
+    }
   }
   if (!H->op_valid || H->op_params.dt != P->dt || H->op_params.boundary != P->boundary ||
       H->op_params.mean != P->mean || H->op_mu_version != H->mu_version) {

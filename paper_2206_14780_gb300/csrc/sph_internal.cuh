@@ -148,6 +148,7 @@ struct Grid {
 }  // namespace sph
 
 namespace sph {
+struct StepStage;   // step.cu: the time step's buffers (owned by the handle)
 // device staging of sph_visc_solve_host (owned by the handle)
 struct HostStage {
   DBuf<float4> pos, vel;
@@ -209,6 +210,7 @@ struct sph_neighbors {
   uint64_t op_version = 0;         // bumped whenever the operator is rebuilt
   sph::DBuf<int32_t> wpart;        // balanced per-warp slice ranges (OpView::wpart)
   sph::HostStage* stage = nullptr; // sph_visc_solve_host's device copies of its host buffers
+  sph::StepStage* step = nullptr;  // sph_step's buffers
   int64_t wpart_nw = 0;
   uint64_t wpart_version = ~0ull;  // op_version they were cut for
 
@@ -347,6 +349,16 @@ sph_status shard_info(const sph_shard* Z, int32_t* axis, int32_t* layers, int64_
                       int64_t* exchanged);
 sph_status shard_solve(sph_shard* Z, const sph_solve_opts* O, const double* b, double* x, sph_solve_report* R,
                        cudaStream_t st);
+
+// step.cu: the semi-implicit predictor/corrector step (sph_step)
+sph_status time_step(sph_state* S, const sph_step_params* P, const sph_solve_opts* O, sph_neighbors** handle,
+                     sph_step_report* R, cudaStream_t st);
+void release_step_stage(sph_neighbors* H);
+// features.cu: x0 = v^n with the dummy-wall closure
+sph_status warm_start_plain(sph_neighbors* h, const sph_visc_params* params, const float* vel, const uint8_t* ptype,
+                            const double* b, double* x0, cudaStream_t st);
+sph_status mu_papanastasiou(sph_neighbors* H, const float* vel, const float* wall_vel, double tau0, double mu0,
+                            double m, float* mu_out, int set_handle, cudaStream_t st);
 
 // replay.cu: the solver's scalar steps on caller-given dots (sph_bicgstab_replay)
 sph_status bicgstab_replay(const double* gamma0, double eps, int32_t maxit, int32_t nsteps, const double* dots,

@@ -15,7 +15,8 @@ OUT = os.path.join(ROOT, "paper_2206_14780_gb300", "_build", "abi_probe")
 def _structs():
     from paper_2206_14780_gb300 import binding as b
 
-    return [b.sph_scene, b.sph_visc_params, b.sph_solve_opts, b.sph_solve_report, b.sph_profile_counters]
+    return [b.sph_scene, b.sph_visc_params, b.sph_solve_opts, b.sph_solve_report, b.sph_profile_counters,
+            b.sph_state, b.sph_step_params, b.sph_step_report]
 
 
 def _c_layout(structs):

@@ -1,0 +1,145 @@
+"""The semi-implicit predictor/corrector step (paper Sec. 3.3) on the GPU: one step against
+the oracle's step, and the plane Poiseuille flow run to steady state against the
+analytic profile and the paper's error table."""
+import os
+
+import numpy as np
+import pytest
+
+import scenes
+from oracle import step as ostep
+from sph_testutil import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _stepper(s):
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    t = dict(pos=torch.from_numpy(s.pos.copy()).cuda(), vel=torch.from_numpy(s.vel.copy()).cuda(),
+             rho=torch.from_numpy(s.rho.copy()).cuda(), mu=torch.from_numpy(s.mu.copy()).cuda(),
+             ptype=torch.from_numpy(s.ptype.copy()).cuda())
+    return binding.Stepper(t["pos"], t["vel"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h,
+                           kernel=s.kernel), t
+
+
+def _params(s, prm):
+    from paper_2206_14780_gb300 import binding
+
+    return binding.step_params(prm["dt"], prm["rho0"], prm["c0"], prm["zeta"], prm["g"], s.boundary, s.mean,
+                               rheology=s.rheology, max_neighbors=prm.get("max_neighbors", 128))
+
+
+def _perturb(s, seed, drho=2e-3):
+    rng = np.random.default_rng(seed)
+    s = s.copy()
+    fl = s.ptype == scenes.FLUID
+    s.rho = s.rho.copy()
+    s.rho[fl] = (s.rho[fl].astype(np.float64) * (1 + drho * rng.standard_normal(fl.sum()))).astype(np.float32)
+    return s
+
+
+STEP_CASES = {
+    # dummy walls, moving lid, body force along the channel, density noise
+    "couette_dummy": (lambda: _perturb(scenes.couette(1, nx=10, ny=8, nz=10), 1),
+                      dict(dt=2e-4, rho0=1000.0, c0=20.0, zeta=7.0, g=(0.5, 0.0, 0.0))),
+    # dynamic walls (their density evolves), gravity across the channel
+    "couette_dynamic": (lambda: _perturb(scenes.couette(2, nx=10, ny=8, nz=10, boundary=scenes.BC_DYNAMIC), 2),
+                        dict(dt=2e-4, rho0=1000.0, c0=20.0, zeta=7.0, g=(0.0, -9.81, 0.0))),
+    # an open box under gravity: the dummy-wall pressure carries the hydrostatic term
+    "lava_box_gravity": (lambda: _perturb(scenes.lava_box(3, n=8, nu=1.0, dt=5e-4), 3),
+                         dict(dt=5e-4, rho0=1000.0, c0=30.0, zeta=7.0, g=(0.0, 0.0, -9.81))),
+    # Papanastasiou viscosity recomputed after each neighbour build
+    "slope_papanastasiou": (lambda: _perturb(scenes.slope_subset(4, nx=12, ny=8, nz=12), 4, 1e-3),
+                            dict(dt=5e-4, rho0=1000.0, c0=20.0, zeta=7.0, g=(1.7, -9.66, 0.0))),
+    # the truncated Gaussian kernel
+    "lattice_gaussian": (lambda: _perturb(scenes.periodic_lattice(12, jitter=0.05, seed=2,
+                                                                   kernel=scenes.KERNEL_GAUSSIAN), 5),
+                         dict(dt=1e-4, rho0=1000.0, c0=20.0, zeta=7.0, g=(0.0, 0.0, 0.0), max_neighbors=512)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(STEP_CASES))
+def test_one_step_matches_oracle(name):
+    from paper_2206_14780_gb300 import binding
+
+    make, prm = STEP_CASES[name]
+    s = make()
+    st, t = _stepper(s)
+    rep = st.step(_params(s, prm), binding.solve_opts(rtol=1e-10, eps_inner=1e-3))
+    st.close()
+    assert rep["status"] == 0, rep
+    new, info = ostep.step(s, prm)
+    fl = s.ptype == scenes.FLUID
+    u = t["vel"].cpu().numpy()[:, :3].astype(np.float64)
+    u_ref = info["u_new"]
+    err_u = np.linalg.norm(u[fl] - u_ref[fl]) / max(np.linalg.norm(u_ref[fl]), 1e-30)
+    assert err_u < 1e-5, err_u
+    rho = t["rho"].cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(rho, new.rho.astype(np.float64), rtol=2e-6)
+    pos = t["pos"].cpu().numpy()
+    # r^{n+1} = r^n + dt/2 (u^n + u^{n+1}) rounded to float32: the solves agree to ~1e-9,
+    # so the positions to a float32 ulp of the coordinate
+    np.testing.assert_allclose(pos[:, :3], new.pos[:, :3], rtol=0, atol=2 * np.spacing(np.float32(1.0)))
+    np.testing.assert_array_equal(pos[:, 3], s.pos[:, 3])
+    if s.rheology is not None:
+        mu = t["mu"].cpu().numpy().astype(np.float64)
+        np.testing.assert_allclose(mu[fl], info["half"]["mu"][fl].astype(np.float64), rtol=1e-4)
+
+
+def test_fluid_at_rest_stays_at_rest_on_the_gpu():
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.couette(2, nx=8, ny=6, nz=8, noise=0.0, U=0.0, rho0=1000.0)
+    s.vel[:] = 0.0
+    s.wall_vel[:] = 0.0
+    st, t = _stepper(s)
+    prm = dict(dt=1e-3, rho0=1000.0, c0=20.0, zeta=7.0, g=(0.0, 0.0, 0.0))
+    for _ in range(3):
+        rep = st.step(_params(s, prm), binding.solve_opts())
+        assert rep["status"] == 0
+    st.close()
+    np.testing.assert_array_equal(t["pos"].cpu().numpy(), s.pos)
+    np.testing.assert_array_equal(t["vel"].cpu().numpy()[s.ptype == scenes.FLUID], 0.0)
+
+
+@pytest.mark.slow
+def test_poiseuille_flow_reaches_the_analytic_profile():
+    """The plane Poiseuille flow of Sec. 5 (Newtonian, Wendland h = 1.3 dp, dummy walls,
+    dp = 1/16): L = 1 m, g = 0.05 m/s^2, mu = 0.1 Pa s, rho0 = 1 kg/m^3, c0 = 6.32 m/s,
+    from rest to t = 10 s (the viscous relaxation time) with the full step.  The
+    steady profile is u(z) = rho0 g / (2 mu) (L^2/4 - z^2) (u_max = 6.25e-2 m/s); its l1
+    and l2 errors are compared with the paper's table for this configuration."""
+    from paper_2206_14780_gb300 import binding
+
+    gold = dict(l.split() for l in open(os.path.join(GOLDEN, "poiseuille_newton_wendland_dummy_dp16.txt"))
+                if l.strip() and not l.startswith("#"))
+    gold = {k: float(v) for k, v in gold.items()}
+    dx, g, mu, L = 1.0 / 16, 0.05, 0.1, 1.0
+    s = scenes.couette(0, nx=8, ny=16, nz=8, dx=dx, rho0=1.0, nu=mu, dt=1e-2, U=0.0, noise=0.0)
+    s.vel[:] = 0.0
+    st, t = _stepper(s)
+    dt = 2.5e-3
+    prm = binding.step_params(dt, 1.0, 6.32, 7.0, (g, 0.0, 0.0), s.boundary, s.mean)
+    opts = binding.solve_opts(rtol=1e-8)
+    for _ in range(int(round(10.0 / dt))):
+        rep = st.step(prm, opts)
+        assert rep["status"] == 0
+    st.close()
+    fl = s.ptype == scenes.FLUID
+    pos = t["pos"].cpu().numpy()[fl].astype(np.float64)
+    u = t["vel"].cpu().numpy()[fl, 0].astype(np.float64)
+    z = pos[:, 1] - 0.5 * L
+    exact = 0.5 * g / mu * (0.25 * L * L - z * z)
+    e = u - exact
+    l1, l2 = np.abs(e).mean(), np.sqrt((e * e).mean())
+    assert np.abs(e).max() < 0.05 * exact.max()
+    assert l1 < 2.0 * gold["l1"] and l2 < 2.0 * gold["l2"], (l1, l2, gold)
+    # the flow stays one-directional (the weakly compressible fluid keeps acoustic
+    # noise of ~1e-3 u_max across the channel) and the density near rest
+    assert np.abs(t["vel"].cpu().numpy()[fl, 1:3]).max() < 5e-3 * exact.max()
+    rho = t["rho"].cpu().numpy()[fl]
+    assert np.abs(rho - 1.0).max() < 1e-3
