@@ -49,6 +49,8 @@ def parse(argv=None):
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-gaussian", action="store_true")
     ap.add_argument("--no-poiseuille", action="store_true")
+    ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--no-shard", action="store_true")
     ap.add_argument("--ensemble-only", action="store_true")
     ap.add_argument("--ensemble-scenes", type=int, default=64, help="scenes of the ensemble leg (64: the workload)")
     ap.add_argument("--no-precision", action="store_true")
@@ -472,6 +474,11 @@ def run_sphvisc(args):
     poiseuille = None
     if world == 1 and not args.no_poiseuille:
         poiseuille = run_poiseuille(dev)
+    cg = shard = None
+    if world == 1 and not args.no_cg:
+        cg = run_cg(dev)
+    if world == 1 and not args.no_shard:
+        shard = run_shard(dev)
     sequence = None
     if not args.no_sequence and world == 1:
         sequence = run_sequence(nb, s, b, t, args.sequence_steps, dev)
@@ -542,7 +549,7 @@ def run_sphvisc(args):
                            ms_per_step_min=min(per_step), ms_per_step_max=max(per_step)),
                roofline=roofline, cpu_baseline=cpu, oracle_error=oracle_error, e2e=e2e, gpu_launches=int(launches), ensemble=ensemble,
                precision_study=precision, sequence=sequence, learned=learned, apply_forms=apply_forms,
-               channel=channel, gaussian=gaussian, poiseuille=poiseuille,
+               channel=channel, gaussian=gaussian, poiseuille=poiseuille, cg=cg, shard=shard,
                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"],
                            samples=clk["samples"]),
                wall_s=wall)
@@ -646,6 +653,105 @@ def run_gaussian(dev, n=100, reps=3):
                 passes=reps_[0]["refinements"], max_true_rel_res=max(r["true_rel_res"] for r in reps_),
                 apply_us=us, apply_algorithmic_bytes=prof["apply_bytes"], apply_gbs=gbs,
                 apply_frac_of_hbm=(gbs / hbm) if gbs else None, peak_source=kind)
+
+
+# ------------------------------------------------- CG and sharded solve -------
+
+def run_cg(dev, reps=3):
+    """Rotated CG (Sec. 4.1) against BiCGSTAB on dynamic-wall systems, where the fluid
+    block is symmetric: the 1.12M Couette channel (dt nu / dx^2 = 1) and the 1.16M lava
+    box (200): ms per solve (CUDA events, after a warm-up solve) and iterations; CG
+    applies the operator once per iteration, BiCGSTAB twice."""
+    import torch
+
+    import scenes
+    from paper_2206_14780_gb300 import binding
+
+    out = {}
+    for name, s in (("channel_1120k", scenes.couette(0, nx=200, ny=50, nz=100, boundary=scenes.BC_DYNAMIC)),
+                    ("box_1157k", scenes.lava_box(0, n=100, boundary=scenes.BC_DYNAMIC))):
+        t = binding.scene_tensors(s, dev)
+        t["vel"] = torch.from_numpy(s.vel).to(dev)
+        p = binding.visc_params(s.dt, s.boundary, s.mean)
+        nb = binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
+        b = torch.from_numpy(s.b).to(dev)
+        x = torch.empty_like(b)
+        stream = torch.cuda.current_stream(dev)
+        row = {}
+        for meth, key in ((binding.SPH_SOLVER_BICGSTAB, "bicgstab"), (binding.SPH_SOLVER_CG, "cg")):
+            o = binding.solve_opts(method=meth)
+            binding.warm_start(nb, p, None, t["vel"], t["ptype"], b, x)
+            nb.solve(p, o, b, x)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms, its, res = [], [], []
+            for _ in range(reps):
+                binding.warm_start(nb, p, None, t["vel"], t["ptype"], b, x)
+                torch.cuda.synchronize(dev)
+                e0.record(stream)
+                rep = nb.solve(p, o, b, x)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms.append(e0.elapsed_time(e1))
+                its.append(rep["iters"])
+                res.append(rep["true_rel_res"])
+            row[key] = dict(ms_per_solve=statistics.median(ms), iters=its[0], passes=rep["refinements"],
+                            true_rel_res=max(res))
+        row["cg_over_bicgstab_ms"] = row["cg"]["ms_per_solve"] / row["bicgstab"]["ms_per_solve"]
+        out[name] = dict(particles=s.n, **row)
+        nb.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_shard(dev, n=60, ranks=(1, 2, 4)):
+    """One system over k emulated sub-domains (sph_shard_*, Sec. 7) on the 60^3 lava box
+    (274k particles): ms per solve for each k, iterations, and whether x is the same bit
+    for bit as with one sub-domain (it must be); the single-domain solver beside it."""
+    import torch
+
+    import scenes
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.lava_box(0, n=n)
+    t = binding.scene_tensors(s, dev)
+    p = binding.visc_params(s.dt, s.boundary, s.mean)
+    nb = binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
+    b = torch.from_numpy(s.b).to(dev)
+    x0 = torch.from_numpy(s.x0).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = dict(workload=f"lava box {n}^3 fluid (N={s.n}), one system over k sub-domains on one GPU", particles=s.n)
+    x_one = None
+    for k in ranks:
+        w0 = time.perf_counter()
+        sh = binding.Shard(nb, p, k)
+        create_s = time.perf_counter() - w0
+        x = x0.clone()
+        sh.solve(binding.solve_opts(), b, x)
+        x = x0.clone()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        rep = sh.solve(binding.solve_opts(), b, x)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        info = sh.info()
+        sh.close()
+        if x_one is None:
+            x_one = x.clone()
+        out[f"k{k}"] = dict(ms_per_solve=e0.elapsed_time(e1), iters=rep["iters"], true_rel_res=rep["true_rel_res"],
+                            halo_rows=info["halo"], layers=info["layers"], create_s=create_s,
+                            bit_identical_to_k1=bool(torch.equal(x, x_one)))
+    x = x0.clone()
+    nb.solve(p, binding.solve_opts(), b, x)
+    x = x0.clone()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    rep = nb.solve(p, binding.solve_opts(), b, x)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    out["single_domain_solver"] = dict(ms_per_solve=e0.elapsed_time(e1), iters=rep["iters"])
+    nb.close()
+    return out
 
 
 # ------------------------------------------------------ Poiseuille flow -------

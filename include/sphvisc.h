@@ -385,11 +385,21 @@ typedef struct {
   int32_t rheology;        /* 0: Newtonian (mu as given); 1: Papanastasiou (Eq. papa)  */
   double tau0, mu0, m;     /* Papanastasiou yield stress, plastic viscosity, exponent */
   int32_t max_neighbors;   /* capacity of the neighbour lists (0 = 128)               */
+  int32_t picard;          /* rheology = 1 only: fixed-point passes that bring the
+                              viscosity into the implicit system (the non-linear
+                              form Sec. 8 names): after the corrector's solve, mu is
+                              recomputed from r^{n+1/2} and the new velocities and
+                              the system solved again, at most `picard` times; 0 =
+                              the paper's lagged viscosity                           */
+  double picard_tol;       /* stop when ||u_k - u_{k-1}|| / ||u_k|| <= picard_tol
+                              (0 = 1e-6)                                              */
 } sph_step_params;
 
 typedef struct {
   sph_solve_report half;   /* the solve with A^n(dt/2)                                */
-  sph_solve_report full;   /* the solve with A^{n+1/2}(dt)                            */
+  sph_solve_report full;   /* the (last) solve with A^{n+1/2}(dt)                     */
+  int32_t picard_passes;   /* fixed-point passes run                                  */
+  double picard_change;    /* ||u_k - u_{k-1}|| / ||u_k|| of the last pass            */
 } sph_step_report;
 
 /* One step on `state` (device arrays, updated in place).  *handle: NULL on the

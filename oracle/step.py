@@ -146,8 +146,13 @@ def _evaluate(s, prm, g):
 
 def step(scene, prm, rtol=1e-13):
     """One step of Sec. 3.3 on a copy of scene (pos, vel, rho, mu float32; wall rows of
-    vel hold the wall velocity).  prm: dt, rho0, c0, zeta, g.  Returns the new scene
-    and a dict with the half-step state and both solutions (float64)."""
+    vel hold the wall velocity).  prm: dt, rho0, c0, zeta, g, and optionally picard
+    (>= 0) and picard_tol: with a rheology, the viscosity of the corrector's system
+    is recomputed from the new velocities at r^{n+1/2} and the system solved again,
+    up to picard times or until ||u_k - u_{k-1}|| / ||u_k|| <= picard_tol over the
+    fluid rows (the non-linear form Sec. 8 proposes; picard = 0 keeps the paper's
+    lagged viscosity).  Returns the new scene and a dict with the half-step state,
+    both solutions (float64) and the fixed-point passes."""
     s = scene.copy()
     dt = float(prm["dt"])
     g = np.asarray(prm["g"], np.float64)
@@ -180,6 +185,20 @@ def step(scene, prm, rtol=1e-13):
     x0 = B.copy()
     x0[fl] = u_half[fl]
     u_new = solvers.reference_solution(A, B, x0, rtol=rtol)
+    passes, change = 0, None
+    if s.rheology is not None:
+        for _ in range(int(prm.get("picard", 0))):
+            vk = np.asarray(s.vel, np.float32).copy()
+            vk[fl, :3] = u_new[fl].astype(np.float32)
+            mu_k = rheology.mu_pass(s, off, idx, vk)[0]
+            s.mu = mu_k.astype(np.float32)
+            A = operator.assemble(s, off, idx, dt=dt)
+            u_prev = u_new
+            u_new = solvers.reference_solution(A, B, u_prev, rtol=rtol)
+            passes += 1
+            change = np.linalg.norm(u_new[fl] - u_prev[fl]) / np.linalg.norm(u_new[fl])
+            if change <= prm.get("picard_tol", 1e-6):
+                break
     vsum = np.where(fl[:, None], u_n + u_new, 2.0 * uw)
     s.pos = _advance(s, r_n, vsum, 0.5 * dt)
     # dummy walls have drho = 0: they keep the closure density of step n, which the
@@ -188,4 +207,5 @@ def step(scene, prm, rtol=1e-13):
     vel = np.asarray(s.vel, np.float32).copy()
     vel[fl, :3] = u_new[fl].astype(np.float32)
     s.vel = vel
-    return s, dict(half=half, u_new=u_new, acc_half=acc_h, drho_half=drho_h)
+    return s, dict(half=half, u_new=u_new, acc_half=acc_h, drho_half=drho_h, rhs=B, picard_passes=passes,
+                   picard_change=change, off=off, idx=idx)

@@ -81,11 +81,13 @@ class sph_step_params(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("rho0", ctypes.c_double), ("c0", ctypes.c_double),
                 ("zeta", ctypes.c_double), ("g", ctypes.c_double * 3), ("boundary", ctypes.c_int32),
                 ("mean", ctypes.c_int32), ("rheology", ctypes.c_int32), ("tau0", ctypes.c_double),
-                ("mu0", ctypes.c_double), ("m", ctypes.c_double), ("max_neighbors", ctypes.c_int32)]
+                ("mu0", ctypes.c_double), ("m", ctypes.c_double), ("max_neighbors", ctypes.c_int32),
+                ("picard", ctypes.c_int32), ("picard_tol", ctypes.c_double)]
 
 
 class sph_step_report(ctypes.Structure):
-    _fields_ = [("half", sph_solve_report), ("full", sph_solve_report)]
+    _fields_ = [("half", sph_solve_report), ("full", sph_solve_report), ("picard_passes", ctypes.c_int32),
+                ("picard_change", ctypes.c_double)]
 
 
 class SphError(RuntimeError):
@@ -561,8 +563,9 @@ def warm_start(nb, params, mlp, vel, ptype, b, x0, stream=None):
 
 
 def step_params(dt, rho0, c0, zeta=7.0, g=(0.0, 0.0, 0.0), boundary=SPH_BC_DUMMY, mean=SPH_MEAN_HARMONIC,
-                rheology=None, max_neighbors=128):
-    """sph_step_params; rheology = (tau0, mu0, m) for Papanastasiou, None for Newtonian."""
+                rheology=None, max_neighbors=128, picard=0, picard_tol=0.0):
+    """sph_step_params; rheology = (tau0, mu0, m) for Papanastasiou, None for Newtonian;
+    picard: fixed-point passes bringing mu into the implicit system (0: lagged mu)."""
     p = sph_step_params()
     p.dt, p.rho0, p.c0, p.zeta = float(dt), float(rho0), float(c0), float(zeta)
     for k in range(3):
@@ -572,6 +575,8 @@ def step_params(dt, rho0, c0, zeta=7.0, g=(0.0, 0.0, 0.0), boundary=SPH_BC_DUMMY
     if rheology is not None:
         p.tau0, p.mu0, p.m = (float(v) for v in rheology)
     p.max_neighbors = int(max_neighbors)
+    p.picard = int(picard)
+    p.picard_tol = float(picard_tol)
     return p
 
 
@@ -600,7 +605,8 @@ class Stepper:
                           ctypes.byref(self.handle), ctypes.byref(rep), _stream(stream))
         if s not in (SPH_OK, 6):
             _check(s)
-        return dict(status=s, half=_report(rep.half), full=_report(rep.full))
+        return dict(status=s, half=_report(rep.half), full=_report(rep.full), picard_passes=rep.picard_passes,
+                    picard_change=rep.picard_change)
 
     def close(self):
         if self.handle:

@@ -32,10 +32,13 @@ namespace sph {
 
 // the step's device buffers, owned by the handle (caller order unless noted)
 struct StepStage {
-  DBuf<float4> r_n, u_n, acc;
+  DBuf<float4> r_n, u_n, acc, u_k;
   DBuf<float> rho_n, drho, P_s;   // P_s: sorted order
-  DBuf<double> b, x;
+  DBuf<double> b, x, x_prev, sums;
   void release() {
+    u_k.release();
+    x_prev.release();
+    sums.release();
     r_n.release();
     u_n.release();
     acc.release();
@@ -230,6 +233,35 @@ __global__ void k_step_move(const float4* __restrict__ r_n, const float4* __rest
   }
 }
 
+// u_k = x on fluid rows (the prescribed wall velocity on wall rows), for the mu pass
+__global__ void k_step_uk(const double* __restrict__ x, const float4* __restrict__ u_n, const uint8_t* __restrict__ type,
+                          int64_t n, float4* __restrict__ u_k) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    u_k[i] = type[i] == SPH_FLUID ? make_float4((float)x[3 * i], (float)x[3 * i + 1], (float)x[3 * i + 2], 0.f) : u_n[i];
+}
+
+// sums[0] += |x - x_prev|^2, sums[1] += |x|^2 over fluid rows
+__global__ void k_step_change(const double* __restrict__ x, const double* __restrict__ xp,
+                              const uint8_t* __restrict__ type, int64_t n, double* __restrict__ sums) {
+  double a = 0.0, c = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (type[i] != SPH_FLUID) continue;
+    for (int k = 0; k < 3; ++k) {
+      const double d = x[3 * i + k] - xp[3 * i + k];
+      a += d * d;
+      c += x[3 * i + k] * x[3 * i + k];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(sums, a);
+    atomicAdd(sums + 1, c);
+  }
+}
+
 StepGeom step_geom(const sph_neighbors* H, const sph_state* S) {
   StepGeom g{};
   for (int ax = 0; ax < 3; ++ax) {
@@ -346,6 +378,29 @@ sph_status time_step(sph_state* S, const sph_step_params* Pp, const sph_solve_op
   SPH_TRY(warm_start_plain(H, &full, S->vel, S->ptype, T2.b.p, T2.x.p, st));
   sph_status s2 = solve_mixed(H, &full, O, T2.b.p, T2.x.p, &R->full, st);
   if (s2 != SPH_OK && s2 != SPH_NOT_CONVERGED) return s2;
+  // the non-linear form: mu from the new velocities at r^{n+1/2}, solve again
+  if (Pp->rheology == 1 && Pp->picard > 0) {
+    const double tol = Pp->picard_tol > 0.0 ? Pp->picard_tol : 1e-6;
+    SPH_TRY(T2.u_k.alloc(n));
+    SPH_TRY(T2.x_prev.alloc(3 * n));
+    SPH_TRY(T2.sums.alloc(2));
+    for (int k = 0; k < Pp->picard; ++k) {
+      SPH_LAUNCH(k_step_uk, grid, kBlock, 0, st)(T2.x.p, T2.u_n.p, S->ptype, n, T2.u_k.p);
+      SPH_TRY(mu_papanastasiou(H, reinterpret_cast<const float*>(T2.u_k.p), reinterpret_cast<const float*>(T2.u_k.p),
+                               Pp->tau0, Pp->mu0, Pp->m, S->mu, 1, st));
+      SPH_TRY_CUDA(cudaMemcpyAsync(T2.x_prev.p, T2.x.p, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      s2 = solve_mixed(H, &full, O, T2.b.p, T2.x.p, &R->full, st);
+      if (s2 != SPH_OK && s2 != SPH_NOT_CONVERGED) return s2;
+      SPH_TRY_CUDA(cudaMemsetAsync(T2.sums.p, 0, 2 * sizeof(double), st));
+      SPH_LAUNCH(k_step_change, grid, kBlock, 0, st)(T2.x.p, T2.x_prev.p, S->ptype, n, T2.sums.p);
+      double sums[2];
+      SPH_TRY_CUDA(cudaMemcpyAsync(sums, T2.sums.p, sizeof(sums), cudaMemcpyDeviceToHost, st));
+      SPH_TRY_CUDA(cudaStreamSynchronize(st));
+      R->picard_passes = k + 1;
+      R->picard_change = sums[1] > 0.0 ? std::sqrt(sums[0] / sums[1]) : std::sqrt(sums[0]);
+      if (R->picard_change <= tol) break;
+    }
+  }
   SPH_LAUNCH(k_step_move, grid, kBlock, 0, st)(T2.r_n.p, T2.u_n.p, T2.rho_n.p, T2.drho.p, T2.x.p, S->ptype, n, hdt, dt,
                                                1, g0, reinterpret_cast<float4*>(S->pos),
                                                reinterpret_cast<float4*>(S->vel), S->rho);

@@ -143,3 +143,29 @@ def test_poiseuille_flow_reaches_the_analytic_profile():
     assert np.abs(t["vel"].cpu().numpy()[fl, 1:3]).max() < 5e-3 * exact.max()
     rho = t["rho"].cpu().numpy()[fl]
     assert np.abs(rho - 1.0).max() < 1e-3
+
+
+def test_picard_step_matches_oracle():
+    """The non-linear form (Sec. 8): four fixed-point passes of the corrector's system
+    with the viscosity recomputed from the new velocities, on the GPU and in the
+    oracle; the change between passes falls and the results agree as the lagged
+    step's do."""
+    from paper_2206_14780_gb300 import binding
+
+    make, prm = STEP_CASES["slope_papanastasiou"]
+    s = make()
+    prm = dict(prm, picard=4, picard_tol=1e-14)
+    st, t = _stepper(s)
+    p = binding.step_params(prm["dt"], prm["rho0"], prm["c0"], prm["zeta"], prm["g"], s.boundary, s.mean,
+                            rheology=s.rheology, picard=4, picard_tol=1e-14)
+    rep = st.step(p, binding.solve_opts(rtol=1e-10, eps_inner=1e-3))
+    st.close()
+    assert rep["status"] == 0 and rep["picard_passes"] == 4
+    new, info = ostep.step(s, prm)
+    assert info["picard_passes"] == 4
+    assert rep["picard_change"] < 1e-3 and abs(np.log10(rep["picard_change"] / info["picard_change"])) < 1.0
+    fl = s.ptype == scenes.FLUID
+    u = t["vel"].cpu().numpy()[:, :3].astype(np.float64)
+    err = np.linalg.norm(u[fl] - info["u_new"][fl]) / np.linalg.norm(info["u_new"][fl])
+    assert err < 1e-5, err
+    np.testing.assert_allclose(t["mu"].cpu().numpy()[fl], new.mu[fl], rtol=1e-4)

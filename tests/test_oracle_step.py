@@ -136,3 +136,35 @@ def test_momentum_changes_by_dt_times_the_body_force():
     p0 = (m[:, None] * s.vel[:, :3].astype(np.float64)).sum(axis=0)
     p1 = (m[:, None] * info["u_new"]).sum(axis=0)
     np.testing.assert_allclose(p1 - p0, 2e-4 * m.sum() * np.asarray(g), rtol=1e-7, atol=1e-12)
+
+
+def test_picard_passes_reach_the_nonlinear_fixed_point():
+    """With the viscosity brought into the implicit system (Sec. 8), the converged
+    velocity u satisfies A(dt; mu(u)) u = B with mu recomputed from u itself: checked by
+    recomputing mu from the returned u and applying that matrix.  A Newtonian fluid
+    ignores the passes (mu does not depend on u)."""
+    from oracle import rheology
+
+    s = scenes.slope_subset(4, nx=12, ny=8, nz=12)
+    prm = dict(dt=5e-4, rho0=1000.0, c0=20.0, zeta=7.0, g=(1.7, -9.66, 0.0), picard=30, picard_tol=1e-11)
+    new, info = step.step(s, prm)
+    assert 1 < info["picard_passes"] < 30 and info["picard_change"] <= 1e-11
+    half = s.copy()
+    half.pos, half.rho = info["half"]["pos"], info["half"]["rho_closed"]
+    fl = s.ptype == scenes.FLUID
+    vk = np.asarray(s.vel, np.float32).copy()
+    vk[fl, :3] = info["u_new"][fl].astype(np.float32)
+    mu_star = rheology.mu_pass(half, info["off"], info["idx"], vk)[0]
+    A = operator.assemble(half, info["off"], info["idx"], dt=prm["dt"], mu=mu_star)
+    res = np.linalg.norm(A @ info["u_new"] - info["rhs"]) / np.linalg.norm(info["rhs"])
+    assert res < 1e-9, res
+    # the lagged step is not at that fixed point
+    new0, info0 = step.step(s, dict(prm, picard=0))
+    assert np.linalg.norm(info0["u_new"][fl] - info["u_new"][fl]) > 1e-8 * np.linalg.norm(info["u_new"][fl])
+    # Newtonian: no pass changes anything
+    c = scenes.couette(1, nx=10, ny=8, nz=10)
+    prm_c = dict(dt=2e-4, rho0=1000.0, c0=20.0, zeta=7.0, g=(0.5, 0.0, 0.0), picard=3)
+    a, ia = step.step(c, prm_c)
+    b, ib = step.step(c, dict(prm_c, picard=0))
+    assert ia["picard_passes"] == 0
+    np.testing.assert_array_equal(ia["u_new"], ib["u_new"])
