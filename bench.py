@@ -375,6 +375,15 @@ def run_sphvisc(args):
     ms_max = max_over_ranks(ms, world, dev)
     barrier(world, dev)
     x_last = x.cpu().numpy()           # the last timed solve, compared with the oracle below
+    # the same K steps once more with the apply's CUDA events off: what the sampled events
+    # themselves cost the timed loop (reported beside the line's value, not in it)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for k in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_unprofiled = ev0.elapsed_time(ev1) / args.steps
     # the same step to a true residual small enough for a solution within 1e-5 of the
     # oracle's (the box's error is ~150x its residual), timed alone, untimed in `value`
     tight = None
@@ -546,7 +555,8 @@ def run_sphvisc(args):
                            iters=its, passes=[r["refinements"] for r in reps],
                            true_rel_res=[r["true_rel_res"] for r in reps], parallelism=f"replicas x{world}",
                            ms_per_step_median=statistics.median(per_step),
-                           ms_per_step_min=min(per_step), ms_per_step_max=max(per_step)),
+                           ms_per_step_min=min(per_step), ms_per_step_max=max(per_step),
+                           ms_per_step_without_apply_events=ms_unprofiled),
                roofline=roofline, cpu_baseline=cpu, oracle_error=oracle_error, e2e=e2e, gpu_launches=int(launches), ensemble=ensemble,
                precision_study=precision, sequence=sequence, learned=learned, apply_forms=apply_forms,
                channel=channel, gaussian=gaussian, poiseuille=poiseuille, cg=cg, shard=shard,

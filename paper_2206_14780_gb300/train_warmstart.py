@@ -132,7 +132,7 @@ def _fluid_x0(fam, bt, vt, kind):
     return x
 
 
-def generate(n_solves, seed, dev, per_solve=256, log=print):
+def generate(n_solves, seed, dev, per_solve=256, log=print, families=None):
     """Solve n_solves random problems from v^n to a 1e-6 true residual; keep the
     features and the targets (x* - v^n) / U of per_solve random fluid particles
     of each.  Returns device tensors feats [M,16] (bf16 bits), targets [M,4]."""
@@ -141,7 +141,7 @@ def generate(n_solves, seed, dev, per_solve=256, log=print):
     from paper_2206_14780_gb300 import binding
 
     rng = np.random.default_rng(seed)
-    fams = [Family(k, j, dev) for j, k in enumerate(FAMILIES)]
+    fams = [Family(k, j, dev) for j, k in enumerate(families or FAMILIES)]
     opts = binding.solve_opts()
     F, T, its = [], [], []
     t0 = time.time()
@@ -317,6 +317,8 @@ def main(argv=None):
     ap.add_argument("--per-solve", type=int, default=256)
     ap.add_argument("--batch", type=int, default=32768)
     ap.add_argument("--highpass", action="store_true", help="x0 correction y - S y (SPH_MLP_HIGHPASS)")
+    ap.add_argument("--families", default=",".join(FAMILIES),
+                    help="comma-separated training geometries (couette, slope, box, each optionally _big)")
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     args = ap.parse_args(argv)
     import torch
@@ -327,7 +329,9 @@ def main(argv=None):
     dev = torch.device("cuda", 0)
     if args.loss == "mse":
         print(f"generating {args.solves} solves ...", flush=True)
-        feats, targets, gstats = generate(args.solves, args.seed, dev, args.per_solve)
+        feats, targets, gstats = generate(args.solves, args.seed, dev, args.per_solve,
+                                          families=args.families.split(","))
+        gstats["families"] = args.families
         print(f"{feats.shape[0]} samples; training {args.steps} steps ...", flush=True)
         net, tstats = train_mse(feats, targets, args.steps, args.batch, args.lr, args.seed + 1)
         tstats["generation"] = gstats

@@ -178,3 +178,38 @@ def test_trained_network_beats_previous_step_start():
             its[key].append(rep["iters"])
     gain = np.mean(its["vn"]) - np.mean(its["learned"])
     assert gain > 0.5, (np.mean(its["vn"]), np.mean(its["learned"]))
+
+
+def test_learned_start_on_an_unseen_million_particle_box(record_property):
+    """The c5 evaluation scale: an unseen 1.16M-particle lava box (seed 11, never drawn in
+    training).  Every start reaches the 1e-6 true residual; the iterations from the
+    learned start, from v^n and from v^n with the dummy-wall closure are recorded (in
+    the test's properties) whatever their order.  What the start is measured to do at
+    this scale: it does NOT beat v^n with the wall closure on these boxes (the bench's
+    learned leg reports the same comparison on three seeds and the ensemble), so the
+    assertion bounds it instead: within 25% of the closure start's iterations."""
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+    from paper_2206_14780_gb300 import train_warmstart as tw
+
+    z = np.load(tw.DEFAULT_WEIGHTS)
+    net = binding.Mlp(z["params"])
+    net.set_mode(int(json.loads(str(z["meta"])).get("mode", 0)) if "meta" in z else 0)
+    s = scenes.lava_box(11, n=100)
+    nb, t = lib_build(s)
+    p = params_for(s)
+    vel = torch.from_numpy(s.vel).cuda()
+    b = torch.from_numpy(s.b).cuda()
+    its = {}
+    for key in ("vn", "vn_walls", "learned"):
+        x = torch.from_numpy(s.x0).cuda()
+        if key == "vn_walls":
+            binding.warm_start(nb, p, None, vel, t["ptype"], b, x)
+        elif key == "learned":
+            binding.warm_start(nb, p, net, vel, t["ptype"], b, x)
+        rep = nb.solve(p, binding.solve_opts(), b, x)
+        assert rep["status"] == 0 and rep["true_rel_res"] <= 1e-6, (key, rep)
+        its[key] = rep["iters"]
+        record_property(f"iters_{key}", rep["iters"])
+    print("unseen 1.16M box, iterations:", its)
+    assert its["learned"] <= 1.25 * its["vn_walls"], its
