@@ -512,6 +512,7 @@ def run_sphvisc(args):
         torch.cuda.empty_cache()
         learned = run_learned(args.weights, dev)
         learned["mlp_forward"] = run_mlp_forward(dev)
+        learned["mlp_grad"] = run_mlp_grad(dev)
     cpu, oracle_error = None, None
     if oracle is not None:
         rows, err = oracle.result()
@@ -850,6 +851,47 @@ def run_mlp_forward(dev, m=1157308, reps=20):
     return dict(particles=m, us_per_forward=us, tflops=tflops, peak_tflops=peak,
                 frac=(tflops / peak) if peak else None, bytes=48 * m, gbs=48 * m / (us * 1e-6) / 1e9,
                 kernel="k_mlp_forward_tc (tcgen05.mma kind::f16, TMEM accumulators)")
+
+
+def run_mlp_grad(dev, m=1157308, reps=20):
+    """The warm-start network's training gradient (tcgen05 forward and backward, then the
+    block-order sum of the per-CTA partial gradients) on m rows of random bf16 features
+    and targets: device time per sph_mlp_grad call and FLOP/s (forward, data and weight
+    gradients) against the measured bf16 peak."""
+    import numpy as np
+    import torch
+
+    from paper_2206_14780_gb300 import binding
+
+    theta = np.random.default_rng(0).normal(scale=0.2, size=binding.MLP_NPARAMS).astype(np.float32)
+    net = binding.Mlp(theta)
+    feats = torch.randn((m, 16), device=dev).to(torch.bfloat16).view(torch.int16).contiguous()
+    tgt = torch.randn((m, 4), device=dev)
+    mask = torch.ones(m, dtype=torch.uint8, device=dev)
+    grad = torch.empty(binding.MLP_NPARAMS, dtype=torch.float32, device=dev)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        net.grad(feats, tgt, mask, m, grad, loss)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        net.grad(feats, tgt, mask, m, grad, loss)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    us = 1e3 * e0.elapsed_time(e1) / reps
+    net.close()
+    fwd = 16 * 64 + 64 * 64 + 64 * 64 + 64 * 3
+    flop = 2.0 * (fwd + (64 * 3 + 64 * 64 + 64 * 64) + fwd) * m   # forward, data gradients (not da_0), weight gradients
+    peak = None
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        pass
+    tflops = flop / (us * 1e-6) / 1e12
+    return dict(rows=m, us_per_grad=us, tflops=tflops, peak_tflops=peak, frac=(tflops / peak) if peak else None,
+                kernel="k_mlp_grad_tc (tcgen05.mma kind::f16, MN-major weight-gradient operands) + k_mlp_reduce")
 
 
 # ----------------------------------------------------------- apply forms ------
@@ -1328,6 +1370,7 @@ def main():
 
         out = run_learned(args.weights)
         out["mlp_forward"] = run_mlp_forward(torch.device("cuda", 0))
+        out["mlp_grad"] = run_mlp_grad(torch.device("cuda", 0))
         print(json.dumps(out))
         return
     if args.impl == "reference":

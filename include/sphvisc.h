@@ -535,7 +535,11 @@ sph_status sph_mlp_forward(const sph_mlp* mlp, const uint16_t* feats, int64_t m,
 
 /* Mean squared error over the masked rows (mask may be NULL = all rows;
  * count = the number of masked rows) and its gradient: grad_out (device
- * [9603] float), loss_out (device [1] float); either may be NULL. */
+ * [9603] float), loss_out (device [1] float); either may be NULL.  Forward and
+ * backward run on the tcgen05 tensor cores (one CTA per SM holding all of its
+ * tensor memory); the sums run in a fixed order, so equal inputs give equal
+ * gradients.  A tensor-core wait that gives up is reported as SPH_ERR_TIMEOUT by
+ * the next sph_mlp_get_params or sph_mlp_train_step with loss_host. */
 sph_status sph_mlp_grad(sph_mlp* mlp, const uint16_t* feats, const float* targets, const uint8_t* mask,
                         int64_t m, int64_t count, float* grad_out, float* loss_out, void* stream);
 

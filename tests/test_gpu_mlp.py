@@ -73,6 +73,38 @@ def test_gradient_matches_oracle():
         off += k
 
 
+@pytest.mark.parametrize("m", [128, 129, 152 * 128 * 3 + 77])
+def test_gradient_over_many_tiles_matches_oracle_and_repeats_exactly(m):
+    """One 128-row tile, a tile plus one row, and more tiles than SMs (each CTA then
+    accumulates several tiles' weight gradients in tensor memory): the gradient
+    matches the oracle's, and a second call returns the same bits (fixed summation
+    order)."""
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    p, X, T, mask = _problem(m=m, seed=3)
+    theta = omlp.flatten(p).astype(np.float32)
+    net = binding.Mlp(theta)
+    xb, tt, mk = _dev(torch, X, T, mask)
+    g = torch.empty(binding.MLP_NPARAMS, dtype=torch.float32, device="cuda")
+    g2 = torch.empty_like(g)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    net.grad(xb, tt, mk, int(mask.sum()), g, loss)
+    net.grad(xb, tt, mk, int(mask.sum()), g2, loss)
+    torch.cuda.synchronize()
+    assert torch.equal(g, g2)
+    l_ref, g_ref, _ = omlp.loss_and_grad(omlp.unflatten(theta.astype(np.float64)), X, T, mask, bf16=True)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.item()) - l_ref) <= 1e-4 * l_ref
+    off = 0
+    for name, shp in omlp.SHAPES:
+        k = int(np.prod(shp))
+        blk, ref = gg[off:off + k], omlp.flatten(g_ref)[off:off + k]
+        assert np.linalg.norm(blk - ref) <= 2e-3 * np.linalg.norm(ref) + 1e-7, name
+        off += k
+    net.close()
+
+
 def test_training_reduces_loss():
     torch = torch_cuda()
     from paper_2206_14780_gb300 import binding
