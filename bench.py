@@ -513,6 +513,8 @@ def run_sphvisc(args):
         learned = run_learned(args.weights, dev)
         learned["mlp_forward"] = run_mlp_forward(dev)
         learned["mlp_grad"] = run_mlp_grad(dev)
+        torch.cuda.empty_cache()
+        learned["precond_scale"] = run_precond_scale(dev)
     cpu, oracle_error = None, None
     if oracle is not None:
         rows, err = oracle.result()
@@ -1153,6 +1155,137 @@ def run_learned(weights=None, dev=None, reps=3, mode=None):
     return out
 
 
+def run_precond_scale(dev=None, reps=3, powers=(2.0, 3.0, 4.0), heads=None):
+    """The diagonal preconditioner scale on top of Jacobi (S D^-1 from the left) against
+    Jacobi alone, both from v^n with the dummy-wall closure, on the unseen 1.16M-particle
+    boxes (seeds 1-3, single solves) and the unseen 64-scene ensemble (seed 1, batched
+    solve).  Scales: the closed form norm2^-p on the dummy-wall rows (sph_wall_row_scale)
+    for each p, and optional learned heads (name -> callable(nb, p, t, out) filling the
+    scale).  ms = the scale's own kernels + the solve."""
+    import numpy as np
+    import torch
+
+    import scenes
+    from paper_2206_14780_gb300 import binding
+
+    dev = dev or torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev4 = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    opts = binding.solve_opts()
+    heads = heads or {}
+
+    def scalers():
+        out = {"jacobi": None}
+        for pw in powers:
+            out[f"wall_p{pw:g}"] = (lambda pw_: lambda nb, p, t, sc: nb.wall_row_scale(p, pw_, sc))(pw)
+        out.update(heads)
+        return out
+
+    names = list(scalers())
+    per = {k: dict(iters=[], scale_ms=[], solve_ms=[], true_rel_res=[]) for k in names}
+    for sd in (1, 2, 3):
+        s = scenes.lava_box(sd, n=100)
+        t = binding.scene_tensors(s, dev)
+        t["vel"] = torch.from_numpy(s.vel).to(dev)
+        p = binding.visc_params(s.dt, s.boundary, s.mean)
+        nb = binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
+        b = torch.from_numpy(s.b).to(dev)
+        x = torch.empty_like(b)
+        sc = torch.empty(s.n, dtype=torch.float32, device=dev)
+        for name, fill_scale in scalers().items():
+            sms, so_ms, its, rr = [], [], [], []
+            for k in range(reps + 1):                     # the first is a warm-up
+                torch.cuda.synchronize(dev)
+                ev4[0].record(stream)
+                if fill_scale is None:
+                    nb.set_row_scale(None)
+                else:
+                    fill_scale(nb, p, t, sc)
+                    nb.set_row_scale(sc)
+                ev4[1].record(stream)
+                binding.warm_start(nb, p, None, t["vel"], t["ptype"], b, x)
+                ev4[2].record(stream)
+                rep = nb.solve(p, opts, b, x)
+                ev4[3].record(stream)
+                torch.cuda.synchronize(dev)
+                if k == 0:
+                    continue
+                sms.append(ev4[0].elapsed_time(ev4[1]))
+                so_ms.append(ev4[2].elapsed_time(ev4[3]))
+                its.append(rep["iters"])
+                rr.append(rep["true_rel_res"])
+            d = per[name]
+            d["iters"].append(int(np.median(its)))
+            d["scale_ms"].append(float(np.median(sms)))
+            d["solve_ms"].append(float(np.median(so_ms)))
+            d["true_rel_res"].append(max(rr))
+        nb.set_row_scale(None)
+        nb.close()
+        del t, b, x, sc
+        torch.cuda.empty_cache()
+    box = {k: dict(iters=d["iters"], iters_mean=float(np.mean(d["iters"])), scale_ms_mean=float(np.mean(d["scale_ms"])),
+                   solve_ms_mean=float(np.mean(d["solve_ms"])),
+                   ms_mean=float(np.mean(d["scale_ms"]) + np.mean(d["solve_ms"])),
+                   max_true_rel_res=max(d["true_rel_res"])) for k, d in per.items()}
+    for k in names:
+        box[k]["vs_jacobi"] = dict(iters=box[k]["iters_mean"] / box["jacobi"]["iters_mean"],
+                                   ms=box[k]["ms_mean"] / box["jacobi"]["ms_mean"])
+    out = dict(note=("x0 = v^n with the dummy-wall closure for every scale; ms = scale kernels (and, on the "
+                     "ensemble, one synchronising validation per scene) + solve, CUDA events"),
+               box_1157k=dict(workload="lava box 100^3 fluid (N=1,157,308), seeds 1-3", **box))
+
+    ens = scenes.ensemble(1)
+    nbs, ts, bs, ps = [], [], [], []
+    for sc_ in ens:
+        tt = binding.scene_tensors(sc_, dev)
+        tt["vel"] = torch.from_numpy(sc_.vel).to(dev)
+        ts.append(tt)
+        nbs.append(binding.build_neighbors(tt["pos"], tt["rho"], tt["mu"], tt["ptype"], sc_.lo, sc_.hi, sc_.periodic,
+                                           sc_.h))
+        bs.append(torch.from_numpy(sc_.b).to(dev))
+        ps.append(binding.visc_params(sc_.dt, sc_.boundary, sc_.mean))
+    xs = [torch.empty_like(bb) for bb in bs]
+    scs = [torch.empty(sc_.n, dtype=torch.float32, device=dev) for sc_ in ens]
+    eres = {}
+    for name, fill_scale in scalers().items():
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for k in range(len(ens)):
+            if fill_scale is None:
+                nbs[k].set_row_scale(None)
+            else:
+                fill_scale(nbs[k], ps[k], ts[k], scs[k])
+                nbs[k].set_row_scale(scs[k])
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        scale_ms = ev[0].elapsed_time(ev[1])
+        batch = binding.Batch(nbs, ps)
+        for k in range(len(ens)):
+            binding.warm_start(nbs[k], ps[k], None, ts[k]["vel"], ts[k]["ptype"], bs[k], xs[k])
+        batch.solve(opts, bs, xs)                          # warm-up
+        for k in range(len(ens)):
+            binding.warm_start(nbs[k], ps[k], None, ts[k]["vel"], ts[k]["ptype"], bs[k], xs[k])
+        torch.cuda.synchronize(dev)
+        ev[1].record(stream)
+        st, reps_ = batch.solve(opts, bs, xs)
+        ev[2].record(stream)
+        torch.cuda.synchronize(dev)
+        batch.close()
+        eres[name] = dict(iters_sum=int(sum(r["iters"] for r in reps_)), iters_max=int(max(r["iters"] for r in reps_)),
+                          scale_ms=scale_ms, solve_ms=ev[1].elapsed_time(ev[2]),
+                          ms=scale_ms + ev[1].elapsed_time(ev[2]),
+                          max_true_rel_res=max(r["true_rel_res"] for r in reps_), status=st)
+    for k in names:
+        eres[k]["vs_jacobi"] = dict(iters=eres[k]["iters_sum"] / eres["jacobi"]["iters_sum"],
+                                    ms=eres[k]["ms"] / eres["jacobi"]["ms"])
+    out["ensemble_64"] = dict(workload=f"64 scenes, seed 1, {sum(sc_.n for sc_ in ens)} particles, batched solve",
+                              **eres)
+    for nb_ in nbs:
+        nb_.close()
+    return out
+
+
 def learned_vs_plain(out):
     """Iterations and ms of each learned start relative to the plain ones (the paper's
     previous-step start v^n, and v^n with the dummy-wall closure), on the unseen boxes
@@ -1371,6 +1504,7 @@ def main():
         out = run_learned(args.weights)
         out["mlp_forward"] = run_mlp_forward(torch.device("cuda", 0))
         out["mlp_grad"] = run_mlp_grad(torch.device("cuda", 0))
+        out["precond_scale"] = run_precond_scale(torch.device("cuda", 0))
         print(json.dumps(out))
         return
     if args.impl == "reference":

@@ -594,6 +594,35 @@ sph_status sph_warm_start(sph_neighbors* handle, const sph_visc_params* params, 
                           const float* vel, const uint8_t* ptype, const double* b, double* x0,
                           void* stream);
 
+/* Diagonal preconditioner scale: the alternative to the warm start.  The
+ * mixed-precision solves precondition from the left by the Jacobi diagonal
+ * (App. B); a row scale s > 0 per particle (the three velocity components share
+ * the operator, so its diagonal block is one number) makes that S D^-1: the
+ * inner BiCGSTAB or CG works on (S D^-1 A) d = S D^-1 r, with the same solution,
+ * and the stop stays on the float64 true residual of A x = b.  scale: (device)
+ * [n] float, caller order, copied; NULL clears it.  The scale stays with the
+ * handle across operator rebuilds until cleared.  Values that are not positive
+ * finite numbers: SPH_ERR_NONFINITE (synchronises to check).  The batched solve
+ * takes each handle's scale as it stands at sph_batch_create (setting or clearing
+ * one afterwards makes sph_batch_solve return SPH_ERR_INVALID); the float64 and
+ * the sharded solves use the Jacobi diagonal alone and return SPH_ERR_INVALID
+ * while a scale is set; sph_visc_apply is not affected. */
+sph_status sph_set_row_scale(sph_neighbors* handle, const float* scale, void* stream);
+
+/* norm2 (device [n] float, caller order) = squared Euclidean norm of each row of
+ * D^-1 A(dt) for params: 1 + sum (a / D)^2 over a fluid row's coefficients, 1 +
+ * sum S^2 over a dummy-wall row's Shepard weights, 1 for an identity row
+ * (float32 sums of the stored float32 coefficients). */
+sph_status sph_row_norms(sph_neighbors* handle, const sph_visc_params* params, float* norm2, void* stream);
+
+/* The closed-form wall scale: scale (device [n] float, caller order) =
+ * norm2^-power on dummy-wall (Shepard) rows and 1 on fluid and identity rows,
+ * norm2 as in sph_row_norms; 0 <= power <= 64, else SPH_ERR_INVALID.  The
+ * dummy-wall rows are interpolation constraints (Eq. dummyvel); weighting the
+ * most strongly coupled of them down shortens the inner iteration. */
+sph_status sph_wall_row_scale(sph_neighbors* handle, const sph_visc_params* params, double power,
+                              float* scale, void* stream);
+
 /* Papanastasiou viscosity from the previous velocities (Sec. 2.4, Eq. papa):
  *   grad u_b = sum_a V_a |F_ab| r_ab (x) u_ab;  gdot = sym(grad u);
  *   D = sqrt(2 gdot:gdot);  mu_b = tau0 Ybar(D) + mu0,

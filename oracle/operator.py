@@ -109,6 +109,23 @@ def jacobi_diag(A):
     return A.diagonal().copy()
 
 
+def row_norms2(A):
+    """Squared Euclidean norms of the rows of D^-1 A, D = diag(A): the Jacobi-scaled
+    matrix of App. B, from which a diagonal preconditioner scale is built."""
+    A = sp.csr_matrix(A, dtype=np.float64)
+    B = sp.diags(1.0 / A.diagonal()) @ A
+    return np.asarray(B.multiply(B).sum(axis=1)).ravel()
+
+
+def wall_row_scale(scene, A, power):
+    """The closed-form row scale: row_norms2^-power on wall rows, 1 on fluid rows (the
+    wall rows of a dynamic boundary are identity rows, norm 1, so they keep 1)."""
+    s = np.ones(scene.n)
+    w = np.asarray(scene.ptype) != FLUID
+    s[w] = row_norms2(A)[w] ** (-float(power))
+    return s
+
+
 def apply(A, v):
     """y = A v for an [N, 3] (or [N]) array, in float64."""
     return A @ np.asarray(v, dtype=np.float64)

@@ -34,7 +34,7 @@ EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", 
            "sph_mlp_targets", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train_step", "sph_warm_start",
            "sph_mlp_residual_targets", "sph_mlp_set_mode", "sph_visc_solve_host", "sph_bicgstab_replay",
            "sph_shard_plan", "sph_shard_create", "sph_shard_info", "sph_shard_solve", "sph_shard_destroy",
-           "sph_step"]
+           "sph_step", "sph_set_row_scale", "sph_row_norms", "sph_wall_row_scale"]
 MLP_NPARAMS = 9603
 
 
@@ -151,6 +151,9 @@ def load(path: str = LIB_PATH):
         "sph_shard_destroy": [vp],
         "sph_step": [ctypes.POINTER(sph_state), ctypes.POINTER(sph_step_params), ctypes.POINTER(sph_solve_opts),
                      ctypes.POINTER(vp), ctypes.POINTER(sph_step_report), vp],
+        "sph_set_row_scale": [vp, vp, vp],
+        "sph_row_norms": [vp, ctypes.POINTER(sph_visc_params), vp, vp],
+        "sph_wall_row_scale": [vp, ctypes.POINTER(sph_visc_params), dbl, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -342,6 +345,19 @@ class Neighbors:
         return dict(status=st, iters=rep.iters, refinements=rep.refinements, state=list(rep.state),
                     stalled_any=list(rep.stalled_any), true_rel_res=rep.true_rel_res,
                     true_rel_res_c=list(rep.true_rel_res_c))
+
+    def set_row_scale(self, scale, stream=None):
+        """sph_set_row_scale: scale (device float [n], caller order) multiplies the Jacobi
+        diagonal's inverse in the mixed-precision solves; None clears it."""
+        _check(_lib.sph_set_row_scale(self.handle, None if scale is None else _ptr(scale), _stream(stream)))
+
+    def row_norms(self, params, out, stream=None):
+        """sph_row_norms: squared norms of the rows of D^-1 A (device float [n], caller order)."""
+        _check(_lib.sph_row_norms(self.handle, ctypes.byref(params), _ptr(out), _stream(stream)))
+
+    def wall_row_scale(self, params, power, out, stream=None):
+        """sph_wall_row_scale: norm2^-power on dummy-wall rows, 1 elsewhere (device float [n])."""
+        _check(_lib.sph_wall_row_scale(self.handle, ctypes.byref(params), float(power), _ptr(out), _stream(stream)))
 
     def mu_papanastasiou(self, vel, wall_vel, tau0, mu0, m, mu_out, set_handle=True, stream=None):
         _check(_lib.sph_mu_papanastasiou(self.handle, _ptr(vel), _ptr(wall_vel), float(tau0), float(mu0), float(m),

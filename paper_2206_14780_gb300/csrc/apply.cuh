@@ -48,8 +48,9 @@ __device__ __forceinline__ SliceRange warp_slices(const OpView& op, int64_t gw, 
   return SliceRange{gw, op.nslices, nw};
 }
 
-// Fluid rows: v_b + sum a (v_b - v_a) [times 1/D with Jacobi]; Shepard rows:
-// v_b + sum a v_a; identity rows: v_b.
+// Fluid rows: v_b + sum a (v_b - v_a); Shepard rows: v_b + sum a v_a; identity
+// rows: v_b; with Jacobi each row times its invD (1/D on fluid rows, 1 on wall
+// rows, times the row scale when one is set).
 //
 // PF = false: each group of U entries issues its U coefficient loads, then its U
 // gathers, then the FMAs.  PF = true: the coefficient loads of the next group
@@ -110,12 +111,12 @@ __device__ __forceinline__ float4 apply_row(const OpView& op, const float4* __re
       for (int u = 0; u < U; ++u) e[u] = en[u];
     }
   }
-  if (kd == KIND_FLUID) {
-    const float sc = JACOBI ? op.invD[s] : 1.f;
-    return make_float4((vb.x + ax) * sc, (vb.y + ay) * sc, (vb.z + az) * sc, 0.f);
-  }
-  if (kd == KIND_SHEPARD) return make_float4(vb.x - ax, vb.y - ay, vb.z - az, 0.f);
-  return make_float4(vb.x, vb.y, vb.z, 0.f);
+  // with Jacobi every row is multiplied by its invD (1 on wall rows unless a row
+  // scale is set: x 1.0f leaves them exact)
+  const float sc = JACOBI ? op.invD[s] : 1.f;
+  if (kd == KIND_FLUID) return make_float4((vb.x + ax) * sc, (vb.y + ay) * sc, (vb.z + az) * sc, 0.f);
+  if (kd == KIND_SHEPARD) return make_float4((vb.x - ax) * sc, (vb.y - ay) * sc, (vb.z - az) * sc, 0.f);
+  return make_float4(vb.x * sc, vb.y * sc, vb.z * sc, 0.f);
 }
 
 // the row-loop forms of the solver's apply: 0..3 = (U, PF) in {(8,0), (4,0),

@@ -491,6 +491,7 @@ struct sph_batch {
   std::vector<sph_neighbors*> handles;
   std::vector<sph_visc_params> params;
   std::vector<int64_t> row_off;
+  std::vector<uint64_t> rs_version;   // each handle's row-scale version at creation
   int64_t nrows = 0;
   int32_t ntiles = 0;
   int device = 0, num_sms = 0;
@@ -603,14 +604,20 @@ sph_status sph_batch_create(sph_neighbors* const* handles, const sph_visc_params
       return fail(SPH_ERR_INVALID);
     }
     sph_status e = ensure_operator(H, &params[s], st);
+    if (e == SPH_OK) e = row_scale_refresh(H, st);
     if (e != SPH_OK) return fail(e);
     Bt->handles.push_back(H);
     Bt->params.push_back(params[s]);
     Bt->row_off.push_back(rows);
+    Bt->rs_version.push_back(H->rs_version);
     SceneDesc d{};
     d.op = op_view(H);
     d.op_lo = H->op_lo.p;
     d.D64 = H->D64.p;
+    if (H->row_scaled) {  // the preconditioner's diagonal D / s
+      d.op.invD = H->invD_sc.p;
+      d.D64 = H->D64_sc.p;
+    }
     d.row_off = rows;
     d.n = H->n;
     d.tile_begin = (int32_t)ts.size();
@@ -728,7 +735,8 @@ sph_status sph_batch_solve(sph_batch* Bt, const sph_solve_opts* O, const double*
     }
     sph_neighbors* H = Bt->handles[s];
     // the operator may have been rebuilt since the batch was made
-    if (!H->op_valid || H->op_mu_version != H->mu_version) {
+    if (!H->op_valid || H->op_mu_version != H->mu_version || H->rs_version != Bt->rs_version[s] ||
+        (H->row_scaled && H->rs_op_version != H->op_version)) {
       set_error("sph_batch_solve: scene %d's handle changed after sph_batch_create", s);
       return SPH_ERR_INVALID;
     }

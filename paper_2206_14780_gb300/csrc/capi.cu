@@ -182,6 +182,9 @@ sph_status sph_neighbors_destroy(sph_neighbors* h) {
   h->otf_g.release();
   h->otf_im.release();
   h->otf_rb.release();
+  h->rs_caller.release();
+  h->invD_sc.release();
+  h->D64_sc.release();
   for (auto& e : h->prof_ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : h->sa_ev)
@@ -252,6 +255,10 @@ sph_status sph_visc_solve(sph_neighbors* h, const sph_visc_params* params, const
   }
   if (opts->precision == SPH_PREC_FP64 && (opts->method != SPH_SOLVER_BICGSTAB || !opts->jacobi)) {
     set_error("sph_visc_solve: the float64 solve is the Jacobi-scaled BiCGSTAB (method 0, jacobi 1)");
+    return SPH_ERR_INVALID;
+  }
+  if (opts->precision == SPH_PREC_FP64 && h->row_scaled) {
+    set_error("sph_visc_solve: a row scale applies to the mixed-precision solves; clear it for the float64 solve");
     return SPH_ERR_INVALID;
   }
   if (opts->precision == SPH_PREC_MIXED) return solve_mixed(h, params, opts, b, x, report, as_stream(stream));

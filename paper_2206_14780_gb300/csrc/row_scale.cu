@@ -1,0 +1,146 @@
+// Per-row preconditioner scale on top of the Jacobi diagonal.
+//
+// The solves precondition A x = b from the left by D^-1 (App. B); a row scale s
+// turns that into S D^-1 with S = diag(s), s > 0: the inner iteration then works
+// on (S D^-1 A) d = S D^-1 r, whose solution is the same d, while the stopping
+// test stays on the float64 true residual of A x = b.  This is the diagonal
+// preconditioner-scale alternative to the learned warm start: a scale per
+// particle (the three velocity components share the operator, so a diagonal
+// block is one number) held fixed during a solve.
+//
+// Also here: the squared norms of the rows of D^-1 A, 1 + sum_j (a_j / D)^2 over
+// a fluid row's coefficients (1 + sum_j S_j^2 over a dummy-wall row's Shepard
+// weights, 1 for an identity row), and the closed-form scale that takes them to
+// a power on the dummy-wall rows only.
+#include <cmath>
+
+#include "apply.cuh"
+#include "sph_internal.cuh"
+
+namespace sph {
+namespace {
+
+// out[perm[s]] = squared norm of row s of D^-1 A (mode 0), or the wall scale:
+// 1 on fluid and identity rows, norm2^-power on Shepard rows (mode 1)
+__global__ void k_row_norms(const int64_t* __restrict__ off, const int32_t* __restrict__ cnt,
+                            const int2* __restrict__ ih, const uint8_t* __restrict__ kind,
+                            const float* __restrict__ invD, const int32_t* __restrict__ perm, int64_t n, int mode,
+                            float power, float* __restrict__ out) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = s / kSlice, lane = s % kSlice;
+    const int2* p = ih + off[sl] + lane;
+    const int c = cnt[s];
+    float acc = 0.f;
+    for (int j = 0; j < c; ++j) {
+      const float a = __int_as_float(p[(int64_t)j * kSlice].y);
+      acc = fmaf(a, a, acc);
+    }
+    const float w = invD[s];
+    const float nrm2 = fmaf(w * w, acc, 1.f);
+    float v = nrm2;
+    if (mode == 1) v = kind[s] == KIND_SHEPARD ? powf(nrm2, -power) : 1.f;
+    out[perm[s]] = v;
+  }
+}
+
+// flag[0] = 1 when some s[i] is not a positive finite number
+__global__ void k_rs_check(const float* __restrict__ sc, int64_t n, int32_t* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = sc[i];
+    if (!(v > 0.f) || !isfinite(v)) atomicExch(flag, 1);
+  }
+}
+
+// scaled diagonals of the sorted rows; padding rows keep theirs
+__global__ void k_rs_apply(const float* __restrict__ rs, const int32_t* __restrict__ perm,
+                           const float* __restrict__ invD, const double* __restrict__ D64, int64_t n, int64_t n_pad,
+                           float* __restrict__ invD_sc, double* __restrict__ D64_sc) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+    const float sc = s < n ? rs[perm[s]] : 1.f;
+    invD_sc[s] = invD[s] * sc;
+    D64_sc[s] = D64[s] / (double)sc;
+  }
+}
+
+sph_status row_norms_impl(sph_neighbors* H, const sph_visc_params* P, int mode, double power, float* out,
+                          cudaStream_t st) {
+  SPH_TRY(ensure_operator(H, P, st));
+  SPH_LAUNCH(k_row_norms, grid_for(H, H->n), kBlock, 0, st)(H->op_off.p, H->op_cnt.p, H->op_ih.p, H->op_kind.p,
+                                                             H->invD.p, H->perm.p, H->n, mode, (float)power, out);
+  SPH_TRY_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+}  // namespace
+
+sph_status row_scale_refresh(sph_neighbors* H, cudaStream_t st) {
+  if (!H->row_scaled || H->rs_op_version == H->op_version) return SPH_OK;
+  SPH_TRY(H->invD_sc.alloc(H->n_pad));
+  SPH_TRY(H->D64_sc.alloc(H->n_pad));
+  SPH_LAUNCH(k_rs_apply, grid_for(H, H->n_pad), kBlock, 0, st)(H->rs_caller.p, H->perm.p, H->invD.p, H->D64.p, H->n,
+                                                                H->n_pad, H->invD_sc.p, H->D64_sc.p);
+  SPH_TRY_CUDA(cudaGetLastError());
+  H->rs_op_version = H->op_version;
+  return SPH_OK;
+}
+
+}  // namespace sph
+
+using namespace sph;
+
+extern "C" {
+
+sph_status sph_row_norms(sph_neighbors* h, const sph_visc_params* params, float* norm2, void* stream) {
+  clear_error();
+  if (!h || !params || !norm2) {
+    set_error("sph_row_norms: null argument");
+    return SPH_ERR_INVALID;
+  }
+  return row_norms_impl(h, params, 0, 0.0, norm2, reinterpret_cast<cudaStream_t>(stream));
+}
+
+sph_status sph_wall_row_scale(sph_neighbors* h, const sph_visc_params* params, double power, float* scale,
+                              void* stream) {
+  clear_error();
+  if (!h || !params || !scale) {
+    set_error("sph_wall_row_scale: null argument");
+    return SPH_ERR_INVALID;
+  }
+  if (!std::isfinite(power) || power < 0.0 || power > 64.0) {
+    set_error("sph_wall_row_scale: power %g outside [0, 64]", power);
+    return SPH_ERR_INVALID;
+  }
+  return row_norms_impl(h, params, 1, power, scale, reinterpret_cast<cudaStream_t>(stream));
+}
+
+sph_status sph_set_row_scale(sph_neighbors* h, const float* scale, void* stream) {
+  clear_error();
+  if (!h) {
+    set_error("sph_set_row_scale: null handle");
+    return SPH_ERR_INVALID;
+  }
+  ++h->rs_version;
+  if (!scale) {
+    h->row_scaled = false;
+    return SPH_OK;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  SPH_TRY(h->rs_caller.alloc(h->n));
+  SPH_TRY_CUDA(cudaMemsetAsync(h->flags.p, 0, sizeof(int32_t), st));
+  SPH_LAUNCH(k_rs_check, grid_for(h, h->n), kBlock, 0, st)(scale, h->n, h->flags.p);
+  SPH_TRY_CUDA(cudaGetLastError());
+  int32_t f = 0;
+  SPH_TRY_CUDA(cudaMemcpyAsync(&f, h->flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SPH_TRY_CUDA(cudaStreamSynchronize(st));
+  if (f) {
+    h->row_scaled = false;
+    set_error("sph_set_row_scale: a scale is not a positive finite number");
+    return SPH_ERR_NONFINITE;
+  }
+  SPH_TRY_CUDA(cudaMemcpyAsync(h->rs_caller.p, scale, (size_t)h->n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  h->row_scaled = true;
+  h->rs_op_version = ~0ull;
+  return SPH_OK;
+}
+
+}  // extern "C"

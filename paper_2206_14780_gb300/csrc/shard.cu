@@ -722,6 +722,10 @@ sph_status shard_create(sph_neighbors* H, const sph_visc_params* P, int32_t rank
     set_error("sph_shard_create: need a handle, parameters, an output and 1 <= ranks <= %d", kMaxRanks);
     return SPH_ERR_INVALID;
   }
+  if (H->row_scaled) {
+    set_error("sph_shard_create: the sharded solve uses the Jacobi diagonal alone; clear the row scale first");
+    return SPH_ERR_INVALID;
+  }
   SPH_TRY(ensure_operator(H, P, st));
   sph_shard* Z = new sph_shard();
   Z->ranks = ranks;

@@ -324,13 +324,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_apply_dot_staged(OpView op, const
     }
     if (stop) break;
     float4 o;
+    const float sc = op.invD[s];
     if (kd == KIND_FLUID) {
-      const float sc = op.invD[s];
       o = make_float4((vb.x + ax) * sc, (vb.y + ay) * sc, (vb.z + az) * sc, 0.f);
     } else if (kd == KIND_SHEPARD) {
-      o = make_float4(vb.x - ax, vb.y - ay, vb.z - az, 0.f);
+      o = make_float4((vb.x - ax) * sc, (vb.y - ay) * sc, (vb.z - az) * sc, 0.f);
     } else {
-      o = make_float4(vb.x, vb.y, vb.z, 0.f);
+      o = make_float4(vb.x * sc, vb.y * sc, vb.z * sc, 0.f);
     }
     y[s] = o;
     dots_row<PH>(acc, o, vb, rh, s);
@@ -421,13 +421,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_apply_dot_union(OpView op, const 
         for (int u = 0; u < kUnionU; ++u) e[u] = en[u];
       }
       __syncwarp();
+      const float sc = op.invD[s];
       if (kd == KIND_FLUID) {
-        const float sc = op.invD[s];
         o = make_float4((vb.x + ax) * sc, (vb.y + ay) * sc, (vb.z + az) * sc, 0.f);
       } else if (kd == KIND_SHEPARD) {
-        o = make_float4(vb.x - ax, vb.y - ay, vb.z - az, 0.f);
+        o = make_float4((vb.x - ax) * sc, (vb.y - ay) * sc, (vb.z - az) * sc, 0.f);
       } else {
-        o = make_float4(vb.x, vb.y, vb.z, 0.f);
+        o = make_float4(vb.x * sc, vb.y * sc, vb.z * sc, 0.f);
       }
     }
     y[s] = o;
@@ -863,8 +863,17 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
     H->force_form = O->apply_form - 1;
     H->force_grid = H->num_sms * (occ > 0 ? occ : 1);
   }
+  if (H->row_scaled && !O->jacobi) {
+    set_error("sph_visc_solve: a row scale multiplies the Jacobi diagonal (jacobi = 1)");
+    return SPH_ERR_INVALID;
+  }
+  SPH_TRY(row_scale_refresh(H, st));
   Vecs V{H->v_r.p, H->v_rh.p, H->v_p.p, H->v_Ap.p, H->v_rs.p, H->v_As.p, H->v_d.p};
-  const OpView op = op_view(H);
+  // the preconditioner's diagonal: D, or D / s with a row scale s
+  OpView op = op_view(H);
+  if (H->row_scaled) op.invD = H->invD_sc.p;
+  const float* invD = op.invD;
+  const double* D64 = H->row_scaled ? H->D64_sc.p : H->D64.p;
   SolverScalars* S = H->scal.p;
   unsigned int* C = H->counters.p;
   SPH_TRY_CUDA(cudaMemsetAsync(&S->fault, 0, sizeof(int32_t), st));
@@ -936,12 +945,11 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
     // inner pass: ask it for what the outer loop still needs (with a 4x margin),
     // but never for more than eps_floor (float32 recursions stall below that)
     const double eps = std::fmax(eps_floor, 0.25 * rtol * bnorm / rnorm);
-    const float* invD = H->invD.p;
     if (cg) {
       SPH_LAUNCH(k_cg_init, grid_rows, kBlock, 0, st)(H->r64.p, invD, jacobi, np, V, eps * eps, maxit - total_iters, S,
                                                       H->partials.p, C + CNT_INIT);
     } else {
-      SPH_LAUNCH(k_pass_init, grid_rows, kBlock, 0, st)(H->r64.p, H->D64.p, jacobi, np, V, eps * eps, maxit - total_iters,
+      SPH_LAUNCH(k_pass_init, grid_rows, kBlock, 0, st)(H->r64.p, D64, jacobi, np, V, eps * eps, maxit - total_iters,
                                                         S, H->partials.p, C + CNT_INIT);
     }
     SPH_TRY_CUDA(cudaGetLastError());

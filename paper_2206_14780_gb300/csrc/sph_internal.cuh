@@ -284,6 +284,15 @@ struct sph_neighbors {
 
   // float64 solve vectors r, r0^, p, Ap, r*, Ar* ([n_pad][3] each)
   sph::DBuf<double> w64[7];
+
+  // per-row preconditioner scale (row_scale.cu): s (caller order) multiplies the
+  // Jacobi diagonal's inverse of every row in the mixed-precision solves
+  bool row_scaled = false;
+  sph::DBuf<float> rs_caller;        // [n] s, caller order
+  sph::DBuf<float> invD_sc;          // [n_pad] s / D (sorted)
+  sph::DBuf<double> D64_sc;          // [n_pad] D / s (sorted)
+  uint64_t rs_op_version = ~0ull;    // op_version the scaled diagonals were made for
+  uint64_t rs_version = 0;           // bumped by every sph_set_row_scale
 };
 
 namespace sph {
@@ -325,6 +334,10 @@ void standalone_begin(sph_neighbors* H, cudaStream_t st);
 sph_status standalone_end(sph_neighbors* H, cudaStream_t st, int form);
 struct OpView;
 OpView op_view(const sph_neighbors* H);
+
+// row_scale.cu: the scaled diagonals for the operator of H->op_version (no-op
+// without a row scale)
+sph_status row_scale_refresh(sph_neighbors* H, cudaStream_t st);
 using ApplyDotFn = void (*)(OpView, const float4*, float4*, const float4*, SolverScalars*, double*, unsigned int*);
 ApplyDotFn apply_kernel(int phase, int variant);
 sph_status autotune_apply(sph_neighbors* H, bool merged, unsigned int* counter, cudaStream_t st);

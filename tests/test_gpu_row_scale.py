@@ -1,0 +1,172 @@
+"""The diagonal preconditioner scale on top of Jacobi (S D^-1 from the left): the row
+norms and the closed-form wall scale against the oracle, and scaled solves that keep
+the oracle's solution and true residual."""
+import numpy as np
+import pytest
+
+import scenes
+from oracle import operator as oop, solvers as osv
+from sph_testutil import gpu_solve, lib_build, oracle_system, params_for, rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "couette_dummy": lambda: scenes.couette(0),
+    "couette_dynamic": lambda: scenes.couette(1, boundary=scenes.BC_DYNAMIC),
+    "lava_box_12": lambda: scenes.lava_box(2, n=12),
+    "slope_papanastasiou": lambda: scenes.slope_subset(4, nx=12, ny=8, nz=12),
+}
+
+
+def _dev_f32(torch, n):
+    return torch.empty(n, dtype=torch.float32, device="cuda")
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_row_norms_and_wall_scale_match_oracle(name):
+    torch = torch_cuda()
+    s = CASES[name]()
+    nb, _ = lib_build(s)
+    _, _, A = oracle_system(s)
+    out = _dev_f32(torch, s.n)
+    nb.row_norms(params_for(s), out)
+    want = oop.row_norms2(A)
+    np.testing.assert_allclose(out.cpu().numpy(), want, rtol=2e-6)
+    for power in (0.0, 3.0):
+        nb.wall_row_scale(params_for(s), power, out)
+        np.testing.assert_allclose(out.cpu().numpy(), oop.wall_row_scale(s, A, power), rtol=2e-5)
+    nb.close()
+
+
+def test_unit_scale_leaves_the_solve_bit_identical():
+    """s = 1 multiplies every row's invD by 1.0f: the iterates, and the result, are
+    those of the solve without a scale, bit for bit."""
+    torch = torch_cuda()
+    s = scenes.lava_box(2, n=12)
+    nb, _ = lib_build(s)
+    x0, rep0 = gpu_solve(nb, s)
+    nb.set_row_scale(torch.ones(s.n, dtype=torch.float32, device="cuda"))
+    x1, rep1 = gpu_solve(nb, s)
+    assert rep0["iters"] == rep1["iters"] and rep0["refinements"] == rep1["refinements"]
+    np.testing.assert_array_equal(x0, x1)
+    nb.set_row_scale(None)
+    x2, _ = gpu_solve(nb, s)
+    np.testing.assert_array_equal(x0, x2)
+    nb.close()
+
+
+@pytest.mark.parametrize("name", ["lava_box_12", "couette_dummy", "slope_papanastasiou"])
+def test_wall_scaled_solve_keeps_the_oracle_solution(name):
+    """The scaled system has the solution of A x = b: the 1e-6 solve passes the
+    oracle's residual and a 1e-8 solve lies within 1e-5 of the oracle's solution."""
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    s = CASES[name]()
+    nb, _ = lib_build(s)
+    _, _, A = oracle_system(s)
+    sc = _dev_f32(torch, s.n)
+    nb.wall_row_scale(params_for(s), 3.0, sc)
+    nb.set_row_scale(sc)
+    x, rep = gpu_solve(nb, s)
+    assert rep["status"] == 0, rep
+    res, _ = oop.true_residual(A, x, s.b)
+    assert res <= 1e-6
+    x8, rep8 = gpu_solve(nb, s, binding.solve_opts(rtol=1e-8))
+    assert rep8["status"] == 0
+    assert rel_l2(x8, osv.reference_solution(A, s.b, s.x0)) <= 1e-5
+    nb.close()
+
+
+def test_wall_scale_cuts_iterations_on_a_box():
+    """On a lava box the wall rows' scale shortens the inner iteration (the float64
+    study of the same scale: about a fifth fewer iterations at 15k-90k rows)."""
+    torch = torch_cuda()
+    s = scenes.lava_box(5, n=24)
+    nb, _ = lib_build(s)
+    _, rep0 = gpu_solve(nb, s)
+    sc = _dev_f32(torch, s.n)
+    nb.wall_row_scale(params_for(s), 3.0, sc)
+    nb.set_row_scale(sc)
+    _, rep1 = gpu_solve(nb, s)
+    assert rep0["status"] == 0 and rep1["status"] == 0
+    assert rep1["iters"] < 0.95 * rep0["iters"], (rep0["iters"], rep1["iters"])
+    nb.close()
+
+
+def test_scale_follows_an_operator_rebuild_and_the_cg():
+    """The scale stays with the handle when dt changes (the scaled diagonals are
+    rebuilt for the new operator), and the conjugate gradient takes it too (dynamic
+    walls: S D^-1 stays symmetric positive definite as a preconditioner)."""
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.couette(1, boundary=scenes.BC_DYNAMIC)
+    nb, _ = lib_build(s)
+    sc = torch.from_numpy(np.random.default_rng(3).uniform(0.5, 2.0, s.n).astype(np.float32)).cuda()
+    nb.set_row_scale(sc)
+    for dt in (s.dt, 3 * s.dt):
+        s2 = s.copy()
+        s2.dt = dt
+        _, _, A = oracle_system(s2)
+        for method in (binding.SPH_SOLVER_BICGSTAB, binding.SPH_SOLVER_CG):
+            x, rep = gpu_solve(nb, s2, binding.solve_opts(method=method, rtol=1e-8))
+            assert rep["status"] == 0, (dt, method, rep)
+            assert rel_l2(x, osv.reference_solution(A, s2.b, s2.x0)) <= 1e-5
+    nb.close()
+
+
+def test_bad_scales_and_unsupported_solves_are_refused():
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.couette(0)
+    nb, _ = lib_build(s)
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        v = torch.ones(s.n, dtype=torch.float32, device="cuda")
+        v[s.n // 2] = bad
+        with pytest.raises(RuntimeError):
+            nb.set_row_scale(v)
+    nb.set_row_scale(torch.full((s.n,), 0.5, dtype=torch.float32, device="cuda"))
+    with pytest.raises(RuntimeError):
+        gpu_solve(nb, s, binding.solve_opts(precision=binding.SPH_PREC_FP64))
+    with pytest.raises(RuntimeError):
+        nb.wall_row_scale(params_for(s), -1.0, torch.empty(s.n, dtype=torch.float32, device="cuda"))
+    nb.set_row_scale(None)
+    x, rep = gpu_solve(nb, s, binding.solve_opts(precision=binding.SPH_PREC_FP64))
+    assert rep["status"] == 0
+    nb.close()
+
+
+def test_batched_solve_takes_each_scenes_scale():
+    """The batched solve with the wall scale on some scenes: each scene reaches the
+    oracle's residual and solution; changing a scale after the batch was made is
+    refused."""
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    ss = [scenes.lava_box(2, n=12), scenes.couette(0), scenes.lava_box(7, n=10)]
+    nbs, bs, xs, As = [], [], [], []
+    for k, s in enumerate(ss):
+        nb, _ = lib_build(s)
+        if k != 1:
+            sc = _dev_f32(torch, s.n)
+            nb.wall_row_scale(params_for(s), 3.0, sc)
+            nb.set_row_scale(sc)
+        nbs.append(nb)
+        bs.append(torch.from_numpy(s.b).cuda())
+        xs.append(torch.from_numpy(s.x0).cuda())
+        As.append(oracle_system(s)[2])
+    batch = binding.Batch(nbs, [params_for(s) for s in ss])
+    st, reps = batch.solve(binding.solve_opts(rtol=1e-8), bs, xs)
+    assert st == 0
+    for k, s in enumerate(ss):
+        x = xs[k].cpu().numpy()
+        assert oop.true_residual(As[k], x, s.b)[0] <= 1e-8 * 1.01
+        assert rel_l2(x, osv.reference_solution(As[k], s.b, s.x0)) <= 1e-5
+    nbs[1].set_row_scale(torch.ones(ss[1].n, dtype=torch.float32, device="cuda"))
+    with pytest.raises(RuntimeError):
+        batch.solve(binding.solve_opts(), bs, xs)
+    batch.close()
+    for nb in nbs:
+        nb.close()

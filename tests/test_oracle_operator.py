@@ -138,3 +138,49 @@ def test_rows_apply_matches_assembled():
     rows = [0, 5, 100, s.n - 1, s.n - 40]
     nb = [idx[off[b]:off[b + 1]] for b in rows]
     np.testing.assert_allclose(operator.rows_apply(s, rows, nb, x), (A @ x)[rows], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("boundary", [scenes.BC_DUMMY, scenes.BC_DYNAMIC])
+def test_row_norms_against_rowwise_sums_and_bounds(boundary):
+    """row_norms2 against an explicit row-by-row sum of (A_ij / A_ii)^2, and the bounds
+    the rows' structure fixes: a dummy-wall row with k fluid neighbours carries weights
+    W / S that sum to one, so 1 + 1/k <= norm2 <= 2; dynamic and lone wall rows are
+    identity rows (norm2 = 1); a fluid row's off-diagonal magnitudes sum to D - 1, so
+    (D-1)^2 / (k D^2) <= norm2 - 1 <= (D-1)^2 / D^2 over its k neighbours."""
+    s = scenes.couette(3, nx=8, ny=6, nz=8, boundary=boundary)
+    off, idx = neighbors.build(s.pos, s.lo, s.hi, s.periodic, s.h)
+    A = operator.assemble(s, off, idx).tocsr()
+    rn2 = operator.row_norms2(A)
+    for i in range(0, s.n, 7):
+        lo, hi = A.indptr[i], A.indptr[i + 1]
+        d = A[i, i]
+        want = sum((A.data[j] / d) ** 2 for j in range(lo, hi))
+        assert abs(rn2[i] - want) <= 1e-14 * want
+    fl = s.ptype == scenes.FLUID
+    k = np.diff(A.indptr) - 1                    # off-diagonal entries per row
+    D = A.diagonal()
+    f = fl & (k > 0)
+    assert np.all(rn2[f] - 1 <= (D[f] - 1) ** 2 / D[f] ** 2 * (1 + 1e-12))
+    assert np.all(rn2[f] - 1 >= (D[f] - 1) ** 2 / (k[f] * D[f] ** 2) * (1 - 1e-12))
+    w = ~fl
+    if boundary == scenes.BC_DYNAMIC:
+        np.testing.assert_array_equal(rn2[w], 1.0)
+    else:
+        wk = w & (k > 0)
+        assert wk.sum() > 0
+        assert np.all(rn2[wk] <= 2.0 + 1e-12) and np.all(rn2[wk] >= 1.0 + 1.0 / k[wk] - 1e-12)
+        np.testing.assert_array_equal(rn2[w & (k == 0)], 1.0)
+
+
+def test_wall_row_scale_leaves_fluid_rows_and_falls_with_power():
+    s = scenes.lava_box(2, n=8)
+    off, idx = neighbors.build(s.pos, s.lo, s.hi, s.periodic, s.h)
+    A = operator.assemble(s, off, idx)
+    fl = s.ptype == scenes.FLUID
+    s0 = operator.wall_row_scale(s, A, 0.0)
+    s3 = operator.wall_row_scale(s, A, 3.0)
+    s4 = operator.wall_row_scale(s, A, 4.0)
+    np.testing.assert_array_equal(s0, 1.0)
+    np.testing.assert_array_equal(s3[fl], 1.0)
+    assert np.all(s4[~fl] <= s3[~fl]) and np.all(s3[~fl] <= 1.0) and np.all(s3[~fl] >= 0.125)
+    assert np.any(s3[~fl] < 0.5)
