@@ -514,7 +514,13 @@ def run_sphvisc(args):
         learned["mlp_forward"] = run_mlp_forward(dev)
         learned["mlp_grad"] = run_mlp_grad(dev)
         torch.cuda.empty_cache()
-        learned["precond_scale"] = run_precond_scale(dev)
+        learned["precond_scale"] = ps = run_precond_scale(dev, heads=_scale_heads())
+        # the preconditioner-scale heads against Jacobi alone (same start, v^n + closure)
+        if "learned_vs_plain" in learned:
+            for case in ("box_1157k", "ensemble_64"):
+                for k in ("learned_scale", "wall_p3"):
+                    if k in ps.get(case, {}):
+                        learned["learned_vs_plain"].setdefault(case, {})[f"{k}/jacobi_vn_walls"] = ps[case][k]["vs_jacobi"]
     cpu, oracle_error = None, None
     if oracle is not None:
         rows, err = oracle.result()
@@ -1155,6 +1161,25 @@ def run_learned(weights=None, dev=None, reps=3, mode=None):
     return out
 
 
+def _scale_heads():
+    """The learned wall-row scale (weights/scale_head_mlp.npz) as a head for
+    run_precond_scale: features -> network -> exp(y_0) on wall rows."""
+    import numpy as np
+
+    from paper_2206_14780_gb300 import binding
+
+    path = os.path.join(ROOT, "paper_2206_14780_gb300", "weights", "scale_head_mlp.npz")
+    if not os.path.exists(path):
+        return {}
+    net = binding.Mlp(np.load(path)["params"])
+
+    def learned_scale(nb, p, t, sc):
+        binding.mlp_row_scale(nb, p, net, t["vel"], sc)
+
+    learned_scale.net = net
+    return {"learned_scale": learned_scale}
+
+
 def run_precond_scale(dev=None, reps=3, powers=(2.0, 3.0, 4.0), heads=None):
     """The diagonal preconditioner scale on top of Jacobi (S D^-1 from the left) against
     Jacobi alone, both from v^n with the dummy-wall closure, on the unseen 1.16M-particle
@@ -1504,7 +1529,7 @@ def main():
         out = run_learned(args.weights)
         out["mlp_forward"] = run_mlp_forward(torch.device("cuda", 0))
         out["mlp_grad"] = run_mlp_grad(torch.device("cuda", 0))
-        out["precond_scale"] = run_precond_scale(torch.device("cuda", 0))
+        out["precond_scale"] = run_precond_scale(torch.device("cuda", 0), heads=_scale_heads())
         print(json.dumps(out))
         return
     if args.impl == "reference":

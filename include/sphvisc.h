@@ -623,6 +623,20 @@ sph_status sph_row_norms(sph_neighbors* handle, const sph_visc_params* params, f
 sph_status sph_wall_row_scale(sph_neighbors* handle, const sph_visc_params* params, double power,
                               float* scale, void* stream);
 
+/* The learned scale: the network mlp (the warm start's 16-64-64-64-3 architecture,
+ * trained for this use) on the features of sph_mlp_features for velocities vel
+ * (device [n][4] float); scale (device [n] float, caller order) = exp(y_0),
+ * y_0 clamped to [-8, 2], on wall rows and 1 on fluid rows, ready for
+ * sph_set_row_scale.  Wendland kernel only (SPH_ERR_INVALID otherwise). */
+sph_status sph_mlp_row_scale(sph_neighbors* handle, const sph_visc_params* params, const sph_mlp* mlp,
+                             const float* vel, float* scale, void* stream);
+
+/* Training targets of the learned scale: targets (device [n][4] float, caller
+ * order) = (log s, 0, 0, 0) with s the closed-form wall scale of
+ * sph_wall_row_scale for power, and mask (device [n] u8) = 1 on wall rows. */
+sph_status sph_mlp_scale_targets(sph_neighbors* handle, const sph_visc_params* params, double power,
+                                 float* targets, uint8_t* mask, void* stream);
+
 /* Papanastasiou viscosity from the previous velocities (Sec. 2.4, Eq. papa):
  *   grad u_b = sum_a V_a |F_ab| r_ab (x) u_ab;  gdot = sym(grad u);
  *   D = sqrt(2 gdot:gdot);  mu_b = tau0 Ybar(D) + mu0,

@@ -34,7 +34,8 @@ EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", 
            "sph_mlp_targets", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train_step", "sph_warm_start",
            "sph_mlp_residual_targets", "sph_mlp_set_mode", "sph_visc_solve_host", "sph_bicgstab_replay",
            "sph_shard_plan", "sph_shard_create", "sph_shard_info", "sph_shard_solve", "sph_shard_destroy",
-           "sph_step", "sph_set_row_scale", "sph_row_norms", "sph_wall_row_scale"]
+           "sph_step", "sph_set_row_scale", "sph_row_norms", "sph_wall_row_scale",
+           "sph_mlp_row_scale", "sph_mlp_scale_targets"]
 MLP_NPARAMS = 9603
 
 
@@ -154,6 +155,8 @@ def load(path: str = LIB_PATH):
         "sph_set_row_scale": [vp, vp, vp],
         "sph_row_norms": [vp, ctypes.POINTER(sph_visc_params), vp, vp],
         "sph_wall_row_scale": [vp, ctypes.POINTER(sph_visc_params), dbl, vp, vp],
+        "sph_mlp_row_scale": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp, vp],
+        "sph_mlp_scale_targets": [vp, ctypes.POINTER(sph_visc_params), dbl, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -543,6 +546,18 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def mlp_row_scale(nb, params, mlp, vel, scale, stream=None):
+    """sph_mlp_row_scale: the learned wall-row scale (device float [n], caller order)."""
+    _check(_lib.sph_mlp_row_scale(nb.handle, ctypes.byref(params), mlp.handle, _ptr(vel), _ptr(scale),
+                                  _stream(stream)))
+
+
+def mlp_scale_targets(nb, params, power, targets, mask, stream=None):
+    """sph_mlp_scale_targets: (log s, 0, 0, 0) of the closed-form wall scale, wall-row mask."""
+    _check(_lib.sph_mlp_scale_targets(nb.handle, ctypes.byref(params), float(power), _ptr(targets), _ptr(mask),
+                                      _stream(stream)))
 
 
 def mlp_features(nb, params, vel, feats, stream=None):

@@ -10,8 +10,12 @@
 //
 // Also here: the squared norms of the rows of D^-1 A, 1 + sum_j (a_j / D)^2 over
 // a fluid row's coefficients (1 + sum_j S_j^2 over a dummy-wall row's Shepard
-// weights, 1 for an identity row), and the closed-form scale that takes them to
-// a power on the dummy-wall rows only.
+// weights, 1 for an identity row); the closed-form scale that takes them to a
+// power on the dummy-wall rows only; and the learned scale, the warm-start
+// network's architecture evaluated on the same 16 features, whose first output is
+// the log of a wall row's scale (trained on the closed form's logs).
+#include <cuda_bf16.h>
+
 #include <cmath>
 
 #include "apply.cuh"
@@ -20,6 +24,23 @@
 namespace sph {
 namespace {
 
+// learned scales are exp(y) with y clamped to this range
+constexpr float kLogScaleMin = -8.f, kLogScaleMax = 2.f;
+
+// squared norm of sorted row s of D^-1 A from the stored float32 coefficients
+__device__ __forceinline__ float row_norm2(const int64_t* __restrict__ off, const int32_t* __restrict__ cnt,
+                                           const int2* __restrict__ ih, const float* __restrict__ invD, int64_t s) {
+  const int2* p = ih + off[s / kSlice] + s % kSlice;
+  const int c = cnt[s];
+  float acc = 0.f;
+  for (int j = 0; j < c; ++j) {
+    const float a = __int_as_float(p[(int64_t)j * kSlice].y);
+    acc = fmaf(a, a, acc);
+  }
+  const float w = invD[s];
+  return fmaf(w * w, acc, 1.f);
+}
+
 // out[perm[s]] = squared norm of row s of D^-1 A (mode 0), or the wall scale:
 // 1 on fluid and identity rows, norm2^-power on Shepard rows (mode 1)
 __global__ void k_row_norms(const int64_t* __restrict__ off, const int32_t* __restrict__ cnt,
@@ -27,19 +48,35 @@ __global__ void k_row_norms(const int64_t* __restrict__ off, const int32_t* __re
                             const float* __restrict__ invD, const int32_t* __restrict__ perm, int64_t n, int mode,
                             float power, float* __restrict__ out) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t sl = s / kSlice, lane = s % kSlice;
-    const int2* p = ih + off[sl] + lane;
-    const int c = cnt[s];
-    float acc = 0.f;
-    for (int j = 0; j < c; ++j) {
-      const float a = __int_as_float(p[(int64_t)j * kSlice].y);
-      acc = fmaf(a, a, acc);
-    }
-    const float w = invD[s];
-    const float nrm2 = fmaf(w * w, acc, 1.f);
+    const float nrm2 = row_norm2(off, cnt, ih, invD, s);
     float v = nrm2;
     if (mode == 1) v = kind[s] == KIND_SHEPARD ? powf(nrm2, -power) : 1.f;
     out[perm[s]] = v;
+  }
+}
+
+// training targets of the learned scale: (log of the closed-form wall scale, 0, 0, 0)
+// and the mask of the wall rows (caller order)
+__global__ void k_scale_targets(const int64_t* __restrict__ off, const int32_t* __restrict__ cnt,
+                                const int2* __restrict__ ih, const uint8_t* __restrict__ kind,
+                                const float* __restrict__ invD, const uint8_t* __restrict__ type,
+                                const int32_t* __restrict__ perm, int64_t n, float power, float4* __restrict__ tgt,
+                                uint8_t* __restrict__ mask) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const float t = kind[s] == KIND_SHEPARD ? -power * logf(row_norm2(off, cnt, ih, invD, s)) : 0.f;
+    const int64_t i = perm[s];
+    tgt[i] = make_float4(t, 0.f, 0.f, 0.f);
+    mask[i] = type[s] == SPH_FLUID ? 0 : 1;
+  }
+}
+
+// the learned scale from the network's outputs y (caller order): exp of the
+// clamped first output on wall rows, 1 on fluid rows
+__global__ void k_scale_from_net(const float4* __restrict__ y, const uint8_t* __restrict__ type,
+                                 const int32_t* __restrict__ perm, int64_t n, float* __restrict__ out) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = perm[s];
+    out[i] = type[s] == SPH_FLUID ? 1.f : expf(fminf(fmaxf(y[i].x, kLogScaleMin), kLogScaleMax));
   }
 }
 
@@ -72,6 +109,11 @@ sph_status row_norms_impl(sph_neighbors* H, const sph_visc_params* P, int mode, 
 }
 
 }  // namespace
+
+sph_status features_impl(sph_neighbors* H, const sph_visc_params* P, const float* vel, __nv_bfloat16* feats,
+                         cudaStream_t st);
+sph_status mlp_forward_launch(const sph_mlp* M, const __nv_bfloat16* feats, int64_t m, float4* out, int num_sms,
+                              cudaStream_t st);
 
 sph_status row_scale_refresh(sph_neighbors* H, cudaStream_t st) {
   if (!H->row_scaled || H->rs_op_version == H->op_version) return SPH_OK;
@@ -140,6 +182,49 @@ sph_status sph_set_row_scale(sph_neighbors* h, const float* scale, void* stream)
   SPH_TRY_CUDA(cudaMemcpyAsync(h->rs_caller.p, scale, (size_t)h->n * sizeof(float), cudaMemcpyDeviceToDevice, st));
   h->row_scaled = true;
   h->rs_op_version = ~0ull;
+  return SPH_OK;
+}
+
+sph_status sph_mlp_scale_targets(sph_neighbors* h, const sph_visc_params* params, double power, float* targets,
+                                 uint8_t* mask, void* stream) {
+  clear_error();
+  if (!h || !params || !targets || !mask) {
+    set_error("sph_mlp_scale_targets: null argument");
+    return SPH_ERR_INVALID;
+  }
+  if (!std::isfinite(power) || power < 0.0 || power > 64.0) {
+    set_error("sph_mlp_scale_targets: power %g outside [0, 64]", power);
+    return SPH_ERR_INVALID;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  SPH_TRY(ensure_operator(h, params, st));
+  SPH_LAUNCH(k_scale_targets, grid_for(h, h->n), kBlock, 0, st)(h->op_off.p, h->op_cnt.p, h->op_ih.p, h->op_kind.p,
+                                                                 h->invD.p, h->type_s.p, h->perm.p, h->n, (float)power,
+                                                                 reinterpret_cast<float4*>(targets), mask);
+  SPH_TRY_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+sph_status sph_mlp_row_scale(sph_neighbors* h, const sph_visc_params* params, const sph_mlp* mlp, const float* vel,
+                             float* scale, void* stream) {
+  clear_error();
+  if (!h || !params || !mlp || !vel || !scale) {
+    set_error("sph_mlp_row_scale: null argument");
+    return SPH_ERR_INVALID;
+  }
+  if (h->kernel != SPH_KERNEL_WENDLAND) {
+    set_error("sph_mlp_row_scale: the network's features are written for the Wendland kernel");
+    return SPH_ERR_INVALID;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  SPH_TRY(h->feat_out.alloc(h->n * 8));      // bf16 features [n][16]
+  SPH_TRY(h->feat_delta.alloc(h->n));        // float4 network outputs
+  __nv_bfloat16* f = reinterpret_cast<__nv_bfloat16*>(h->feat_out.p);
+  SPH_TRY(features_impl(h, params, vel, f, st));
+  SPH_TRY(mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st));
+  SPH_LAUNCH(k_scale_from_net, grid_for(h, h->n), kBlock, 0, st)(h->feat_delta.p, h->type_s.p, h->perm.p, h->n,
+                                                                  scale);
+  SPH_TRY_CUDA(cudaGetLastError());
   return SPH_OK;
 }
 

@@ -170,3 +170,91 @@ def test_batched_solve_takes_each_scenes_scale():
     batch.close()
     for nb in nbs:
         nb.close()
+
+
+def test_scale_targets_match_the_oracle_closed_form():
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.lava_box(3, n=10)
+    nb, _ = lib_build(s)
+    _, _, A = oracle_system(s)
+    tgt = torch.empty((s.n, 4), dtype=torch.float32, device="cuda")
+    mask = torch.empty(s.n, dtype=torch.uint8, device="cuda")
+    binding.mlp_scale_targets(nb, params_for(s), 4.0, tgt, mask)
+    t = tgt.cpu().numpy()
+    np.testing.assert_allclose(t[:, 0], np.log(oop.wall_row_scale(s, A, 4.0)), rtol=0, atol=2e-5)
+    np.testing.assert_array_equal(t[:, 1:], 0.0)
+    np.testing.assert_array_equal(mask.cpu().numpy(), (s.ptype != scenes.FLUID).astype(np.uint8))
+    nb.close()
+
+
+def _scale_net():
+    import os
+
+    from paper_2206_14780_gb300 import binding
+
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2206_14780_gb300",
+                        "weights", "scale_head_mlp.npz")
+    z = np.load(path)
+    return binding.Mlp(z["params"]), z["params"]
+
+
+def test_learned_scale_is_the_networks_first_output_on_wall_rows():
+    """sph_mlp_row_scale = exp(y_0) of the network on the handle's features on wall
+    rows, 1 on fluid rows; and against the oracle's float64 features and network with
+    the same bf16 rounding points (feature roundings may flip, so loosely)."""
+    torch = torch_cuda()
+    from oracle import features as ofeat, mlp as omlp, neighbors as onb
+    from paper_2206_14780_gb300 import binding
+
+    net, theta = _scale_net()
+    s = scenes.lava_box(4, n=12)
+    nb, _ = lib_build(s)
+    p = params_for(s)
+    vel = torch.from_numpy(s.vel).cuda()
+    sc = torch.empty(s.n, dtype=torch.float32, device="cuda")
+    binding.mlp_row_scale(nb, p, net, vel, sc)
+    f = torch.empty((s.n, 16), dtype=torch.int16, device="cuda")
+    binding.mlp_features(nb, p, vel, f)
+    y = torch.empty((s.n, 4), dtype=torch.float32, device="cuda")
+    net.forward(f, y)
+    wall = s.ptype != scenes.FLUID
+    got = sc.cpu().numpy()
+    np.testing.assert_array_equal(got[~wall], 1.0)
+    want = np.exp(np.clip(y.cpu().numpy()[:, 0].astype(np.float64), -8.0, 2.0))
+    np.testing.assert_allclose(got[wall], want[wall], rtol=1e-6)
+    off, idx = onb.build(s.pos, s.lo, s.hi, s.periodic, s.h)
+    Fr, _ = ofeat.features(s, off, idx, oop.assemble(s, off, idx))
+    yr, _ = omlp.forward(omlp.unflatten(theta.astype(np.float64)), omlp.bf16_round(Fr), bf16=True)
+    d = np.abs(np.log(got[wall]) - np.clip(yr[wall, 0], -8.0, 2.0))
+    assert np.median(d) <= 0.01 and d.max() <= 0.15, (np.median(d), d.max())
+    nb.close()
+
+
+def test_learned_scale_cuts_iterations_on_an_unseen_full_size_box():
+    """The committed head on a 1.16M-particle lava box it never saw (seed 11): fewer
+    iterations than Jacobi alone from the same start (v^n with the wall closure)."""
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    net, _ = _scale_net()
+    s = scenes.lava_box(11, n=100)
+    t = binding.scene_tensors(s, torch.device("cuda", 0))
+    vel = torch.from_numpy(s.vel).cuda()
+    nb = binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
+    p = params_for(s)
+    b = torch.from_numpy(s.b).cuda()
+    its = {}
+    for name in ("jacobi", "learned"):
+        if name == "learned":
+            sc = torch.empty(s.n, dtype=torch.float32, device="cuda")
+            binding.mlp_row_scale(nb, p, net, vel, sc)
+            nb.set_row_scale(sc)
+        x = torch.empty_like(b)
+        binding.warm_start(nb, p, None, vel, t["ptype"], b, x)
+        rep = nb.solve(p, binding.solve_opts(), b, x)
+        assert rep["status"] == 0 and rep["true_rel_res"] <= 1e-6
+        its[name] = rep["iters"]
+    assert its["learned"] < 0.9 * its["jacobi"], its
+    nb.close()
