@@ -745,21 +745,28 @@ def run_shard(dev, n=60, ranks=(1, 2, 4)):
         w0 = time.perf_counter()
         sh = binding.Shard(nb, p, k)
         create_s = time.perf_counter() - w0
-        x = x0.clone()
-        sh.solve(binding.solve_opts(), b, x)
-        x = x0.clone()
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        rep = sh.solve(binding.solve_opts(), b, x)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
+        row = {}
+        for striped in (False, True):               # striping: exchange overlapped with the interior slices
+            sh.set_striping(striped)
+            x = x0.clone()
+            sh.solve(binding.solve_opts(), b, x)
+            x = x0.clone()
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            rep = sh.solve(binding.solve_opts(), b, x)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if x_one is None:
+                x_one = x.clone()
+            key = "striped" if striped else "unstriped"
+            row[f"ms_per_solve_{key}"] = e0.elapsed_time(e1)
+            row[f"bit_identical_to_k1_{key}"] = bool(torch.equal(x, x_one))
         info = sh.info()
         sh.close()
-        if x_one is None:
-            x_one = x.clone()
-        out[f"k{k}"] = dict(ms_per_solve=e0.elapsed_time(e1), iters=rep["iters"], true_rel_res=rep["true_rel_res"],
-                            halo_rows=info["halo"], layers=info["layers"], create_s=create_s,
-                            bit_identical_to_k1=bool(torch.equal(x, x_one)))
+        out[f"k{k}"] = dict(ms_per_solve=row["ms_per_solve_striped"], iters=rep["iters"],
+                            true_rel_res=rep["true_rel_res"], halo_rows=info["halo"], layers=info["layers"],
+                            create_s=create_s, bit_identical_to_k1=row["bit_identical_to_k1_striped"] and
+                            row["bit_identical_to_k1_unstriped"], **row)
     x = x0.clone()
     nb.solve(p, binding.solve_opts(), b, x)
     x = x0.clone()

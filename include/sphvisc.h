@@ -496,6 +496,18 @@ sph_status sph_shard_info(const sph_shard* shard, int32_t* axis, int32_t* layers
 sph_status sph_shard_solve(sph_shard* shard, const sph_solve_opts* opts, const double* b, double* x,
                            sph_solve_report* report, void* stream);
 
+/* Striping (off by default; the overlap of transfers with computation that Sec. 7.2
+ * and the conclusions name as the remedy for the exchange overhead): per apply,
+ * the halo exchange runs on a stream of the shard's own while the interior slices
+ * (32-row groups none of whose rows references a halo row) are applied on the
+ * solve's stream; the edge slices follow when the exchange is done.  Each slice's
+ * result and dots are those of the unstriped order, so the iterates are
+ * bit-identical either way.  With every sub-domain on one GPU the exchange is a
+ * small gather with nothing to hide, and the split launches and cross-stream
+ * events make the solve slower; the overlap pays where the exchange is a
+ * transfer between devices.  on: 0 or 1, else SPH_ERR_INVALID. */
+sph_status sph_shard_set_striping(sph_shard* shard, int32_t on);
+
 sph_status sph_shard_destroy(sph_shard* shard);
 
 /* ---- Learned warm start ---------------------------------------------------

@@ -35,7 +35,8 @@ EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", 
            "sph_mlp_residual_targets", "sph_mlp_set_mode", "sph_visc_solve_host", "sph_bicgstab_replay",
            "sph_shard_plan", "sph_shard_create", "sph_shard_info", "sph_shard_solve", "sph_shard_destroy",
            "sph_step", "sph_set_row_scale", "sph_row_norms", "sph_wall_row_scale",
-           "sph_mlp_row_scale", "sph_mlp_scale_targets"]
+           "sph_mlp_row_scale", "sph_mlp_scale_targets",
+           "sph_shard_set_striping"]
 MLP_NPARAMS = 9603
 
 
@@ -150,6 +151,7 @@ def load(path: str = LIB_PATH):
         "sph_shard_info": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), vp, vp, ctypes.POINTER(i64)],
         "sph_shard_solve": [vp, ctypes.POINTER(sph_solve_opts), vp, vp, ctypes.POINTER(sph_solve_report), vp],
         "sph_shard_destroy": [vp],
+        "sph_shard_set_striping": [vp, i32],
         "sph_step": [ctypes.POINTER(sph_state), ctypes.POINTER(sph_step_params), ctypes.POINTER(sph_solve_opts),
                      ctypes.POINTER(vp), ctypes.POINTER(sph_step_report), vp],
         "sph_set_row_scale": [vp, vp, vp],
@@ -245,6 +247,10 @@ class Shard:
                                    owned.ctypes.data_as(ctypes.c_void_p), halo.ctypes.data_as(ctypes.c_void_p),
                                    ctypes.byref(ex)))
         return dict(axis=ax.value, layers=nl.value, owned=owned.tolist(), halo=halo.tolist(), exchanged=ex.value)
+
+    def set_striping(self, on):
+        """sph_shard_set_striping: overlap each halo exchange with the interior slices' apply."""
+        _check(_lib.sph_shard_set_striping(self.handle, int(bool(on))))
 
     def solve(self, opts, b, x, stream=None):
         rep = sph_solve_report()

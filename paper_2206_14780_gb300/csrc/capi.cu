@@ -305,6 +305,11 @@ sph_status sph_shard_info(const sph_shard* shard, int32_t* axis, int32_t* layers
   return shard_info(shard, axis, layers, owned, halo, exchanged);
 }
 
+sph_status sph_shard_set_striping(sph_shard* shard, int32_t on) {
+  clear_error();
+  return shard_set_striping(shard, on);
+}
+
 sph_status sph_shard_solve(sph_shard* shard, const sph_solve_opts* opts, const double* b, double* x,
                            sph_solve_report* report, void* stream) {
   clear_error();

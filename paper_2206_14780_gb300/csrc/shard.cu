@@ -70,6 +70,8 @@ struct Rank {
   DBuf<float> invD;         // [n_local]
   DBuf<double> D64;         // [n_local]
   DBuf<int32_t> caller;     // [n_owned]: caller index of an owned row, -1 for padding
+  DBuf<int32_t> slices;     // [nslices] interior slices (no halo column) first, then edge slices
+  int64_t n_interior = 0;   // interior slices
   DBuf<float4> r, rh, p, Ap, rs, As, d, x2;   // x2: [2 n_local]
   DBuf<double> x64, b64, r64;                 // [n_local][3]
   OpView view() const {
@@ -230,14 +232,17 @@ __global__ void k_sh_exchange(int64_t m, const int32_t* __restrict__ dst_rank, c
 }
 
 // y = D^-1 A v with the phase's dots per slice: PH 0: r0^.Ap (3); PH 1: r*.Ar*, Ar*.Ar* (6)
+// over the slices slist[k0 .. k1) (slist null: slices k0 .. k1)
 template <int PH>
 __global__ void __launch_bounds__(kBlock) k_sh_apply(OpView op, const float4* __restrict__ v, float4* __restrict__ y,
                                                      const float4* __restrict__ rh, const SolverScalars* __restrict__ S,
-                                                     double* __restrict__ slice_part) {
+                                                     double* __restrict__ slice_part,
+                                                     const int32_t* __restrict__ slist, int64_t k0, int64_t k1) {
   if (S->done) return;
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sl < op.nslices; sl += nw) {
+  for (int64_t k = k0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); k < k1; k += nw) {
+    const int64_t sl = slist ? slist[k] : k;
     const int64_t s = sl * kSlice + lane;
     float4 vb;
     const float4 o = apply_row<4, true, true>(op, v, sl, lane, vb);
@@ -461,6 +466,10 @@ struct sph_shard {
   sph::DBuf<float4*> ptr_tab;            // [8][ranks] per-vector pointer tables
   std::vector<int64_t> halo_rows;
   sph::SolverScalars* host_scal = nullptr;
+  // striping: the halo exchange on its own stream while the interior slices compute
+  bool striped = false;
+  cudaStream_t xstream = nullptr;
+  cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
 };
 
 namespace sph {
@@ -479,6 +488,7 @@ sph_status shard_release(sph_shard* Z) {
     R.invD.release();
     R.D64.release();
     R.caller.release();
+    R.slices.release();
     for (DBuf<float4>* v : {&R.r, &R.rh, &R.p, &R.Ap, &R.rs, &R.As, &R.d, &R.x2}) v->release();
     R.x64.release();
     R.b64.release();
@@ -496,6 +506,11 @@ sph_status shard_release(sph_shard* Z) {
   Z->ptr_tab.release();
   if (Z->host_scal) cudaFreeHost(Z->host_scal);
   Z->host_scal = nullptr;
+  if (Z->ev_ready) cudaEventDestroy(Z->ev_ready);
+  if (Z->ev_done) cudaEventDestroy(Z->ev_done);
+  if (Z->xstream) cudaStreamDestroy(Z->xstream);
+  Z->ev_ready = Z->ev_done = nullptr;
+  Z->xstream = nullptr;
   return SPH_OK;
 }
 
@@ -638,6 +653,17 @@ sph_status shard_build(sph_shard* Z, cudaStream_t st) {
     SPH_TRY(upload(K.invD, linvD, st));
     SPH_TRY(upload(K.D64, lD64, st));
     SPH_TRY(upload(K.caller, lcaller, st));
+    // slices whose rows reference no halo row can be applied before the exchange
+    std::vector<int32_t> inner, edge;
+    for (int64_t sl = 0; sl < K.nslices; ++sl) {
+      bool halo_ref = false;
+      for (int64_t e = loff[sl]; e < loff[sl + 1] && !halo_ref; ++e) halo_ref = lih[e].x >= K.n_owned;
+      (halo_ref ? edge : inner).push_back((int32_t)sl);
+    }
+    K.n_interior = (int64_t)inner.size();
+    inner.insert(inner.end(), edge.begin(), edge.end());
+    if (inner.empty()) inner.push_back(0);
+    SPH_TRY(upload(K.slices, inner, st));
     for (DBuf<float4>* v : {&K.r, &K.rh, &K.p, &K.Ap, &K.rs, &K.As, &K.d}) {
       SPH_TRY(v->alloc(K.n_local));
       SPH_TRY_CUDA(cudaMemsetAsync(v->p, 0, K.n_local * sizeof(float4), st));
@@ -700,6 +726,38 @@ Vec4 vecs(Rank& R) { return Vec4{R.r.p, R.rh.p, R.p.p, R.Ap.p, R.rs.p, R.As.p, R
 
 double* part_of(sph_shard* Z, const Rank& R) { return Z->slice_part.p + R.slice0 * kMaxDots; }
 
+// the halo exchange of p (PH 0) or r* (PH 1) and every rank's apply of it with the
+// phase's per-slice dots.  Striped (Sec. 7.1's overlap of transfers with computation):
+// the exchange runs on its own stream while the interior slices, which reference
+// no halo row, are applied; the edge slices follow once it is done.  Each slice's
+// result and dots are the same either way, so the iterates do not change.
+template <int PH>
+sph_status apply_phase(sph_shard* Z, cudaStream_t st) {
+  const int tab = PH == 0 ? TAB_P : TAB_RS;
+  auto launch = [&](int q, const int32_t* slist, int64_t k0, int64_t k1) {
+    Rank& R = Z->rk[q];
+    SPH_LAUNCH(k_sh_apply<PH>, rows_grid(Z->H, R.n_owned), kBlock, 0, st)(
+        R.view(), PH == 0 ? R.p.p : R.rs.p, PH == 0 ? R.Ap.p : R.As.p, R.rh.p, Z->scal.p + q, part_of(Z, R), slist,
+        k0, k1);
+  };
+  if (!Z->striped || Z->n_exchange == 0) {
+    SPH_TRY(exchange(Z, tab, 1, st));
+    for (int q = 0; q < Z->ranks; ++q) launch(q, nullptr, 0, Z->rk[q].nslices);
+    return SPH_OK;
+  }
+  SPH_TRY_CUDA(cudaEventRecord(Z->ev_ready, st));
+  SPH_TRY_CUDA(cudaStreamWaitEvent(Z->xstream, Z->ev_ready, 0));
+  SPH_TRY(exchange(Z, tab, 1, Z->xstream));
+  SPH_TRY_CUDA(cudaEventRecord(Z->ev_done, Z->xstream));
+  for (int q = 0; q < Z->ranks; ++q)
+    if (Z->rk[q].n_interior > 0) launch(q, Z->rk[q].slices.p, 0, Z->rk[q].n_interior);
+  SPH_TRY_CUDA(cudaStreamWaitEvent(st, Z->ev_done, 0));
+  for (int q = 0; q < Z->ranks; ++q)
+    if (Z->rk[q].n_interior < Z->rk[q].nslices) launch(q, Z->rk[q].slices.p, Z->rk[q].n_interior, Z->rk[q].nslices);
+  SPH_TRY_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
 // x64 (+ d when add), its hi/lo split, the split's halo exchange, r64 = b - A x and |r64|^2 per component
 sph_status shard_residual(sph_shard* Z, bool add, cudaStream_t st, double rr[3]) {
   for (Rank& R : Z->rk)
@@ -732,7 +790,13 @@ sph_status shard_create(sph_neighbors* H, const sph_visc_params* P, int32_t rank
   Z->H = H;
   Z->n = H->n;
   Z->device = H->device;
-  const sph_status s = shard_build(Z, st);
+  sph_status s = shard_build(Z, st);
+  if (s == SPH_OK && (cudaStreamCreateWithFlags(&Z->xstream, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&Z->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&Z->ev_done, cudaEventDisableTiming) != cudaSuccess)) {
+    set_error("sph_shard_create: could not create the exchange stream and its events");
+    s = SPH_ERR_CUDA;
+  }
   if (s != SPH_OK) {
     shard_release(Z);
     delete Z;
@@ -746,6 +810,15 @@ sph_status shard_destroy(sph_shard* Z) {
   if (!Z) return SPH_OK;
   shard_release(Z);
   delete Z;
+  return SPH_OK;
+}
+
+sph_status shard_set_striping(sph_shard* Z, int32_t on) {
+  if (!Z || (on != 0 && on != 1)) {
+    set_error("sph_shard_set_striping: null shard or a flag other than 0 / 1");
+    return SPH_ERR_INVALID;
+  }
+  Z->striped = on != 0;
   return SPH_OK;
 }
 
@@ -826,23 +899,13 @@ sph_status shard_solve(sph_shard* Z, const sph_solve_opts* O, const double* b, d
           Rank& R = Z->rk[q];
           SPH_LAUNCH(k_sh_p_update, rows_grid(H, R.n_owned), kBlock, 0, st)(R.n_owned, vecs(R), Z->scal.p + q);
         }
-        SPH_TRY(exchange(Z, TAB_P, 1, st));
-        for (int q = 0; q < Z->ranks; ++q) {
-          Rank& R = Z->rk[q];
-          SPH_LAUNCH(k_sh_apply<0>, rows_grid(H, R.n_owned), kBlock, 0, st)(R.view(), R.p.p, R.Ap.p, R.rh.p,
-                                                                            Z->scal.p + q, part_of(Z, R));
-        }
+        SPH_TRY(apply_phase<0>(Z, st));
         SPH_TRY((reduce_all<3, CMB_DELTA>(Z, st)));
         for (int q = 0; q < Z->ranks; ++q) {
           Rank& R = Z->rk[q];
           SPH_LAUNCH(k_sh_rstar, rows_grid(H, R.n_owned), kBlock, 0, st)(R.n_owned, vecs(R), Z->scal.p + q);
         }
-        SPH_TRY(exchange(Z, TAB_RS, 1, st));
-        for (int q = 0; q < Z->ranks; ++q) {
-          Rank& R = Z->rk[q];
-          SPH_LAUNCH(k_sh_apply<1>, rows_grid(H, R.n_owned), kBlock, 0, st)(R.view(), R.rs.p, R.As.p, R.rh.p,
-                                                                            Z->scal.p + q, part_of(Z, R));
-        }
+        SPH_TRY(apply_phase<1>(Z, st));
         SPH_TRY((reduce_all<6, CMB_OMEGA>(Z, st)));
         for (int q = 0; q < Z->ranks; ++q) {
           Rank& R = Z->rk[q];

@@ -358,6 +358,7 @@ sph_status shard_plan(int64_t n, const int32_t* layer, int32_t nlayers, int32_t 
                       int32_t* rank_first_layer, int64_t* layer_first_virt);
 sph_status shard_create(sph_neighbors* H, const sph_visc_params* P, int32_t ranks, sph_shard** out, cudaStream_t st);
 sph_status shard_destroy(sph_shard* Z);
+sph_status shard_set_striping(sph_shard* Z, int32_t on);
 sph_status shard_info(const sph_shard* Z, int32_t* axis, int32_t* layers, int64_t* owned, int64_t* halo,
                       int64_t* exchanged);
 sph_status shard_solve(sph_shard* Z, const sph_solve_opts* O, const double* b, double* x, sph_solve_report* R,

@@ -24,11 +24,12 @@ def layers_of(nb, s):
     return nl
 
 
-def shard_solve(nb, s, ranks, opts=None, b=None, x0=None):
+def shard_solve(nb, s, ranks, opts=None, b=None, x0=None, striped=True):
     torch = torch_cuda()
     from paper_2206_14780_gb300 import binding
 
     sh = binding.Shard(nb, params_for(s), ranks)
+    sh.set_striping(striped)
     bt = torch.from_numpy(np.ascontiguousarray(s.b if b is None else b, np.float64)).cuda()
     xt = torch.from_numpy(np.ascontiguousarray(s.x0 if x0 is None else x0, np.float64)).cuda()
     rep = sh.solve(opts or binding.solve_opts(), bt, xt)
@@ -55,13 +56,15 @@ def test_iterates_do_not_depend_on_the_number_of_subdomains(name):
     for k in (1, 2, 3, 4):
         if k > nl:
             continue
-        x, rep, info = shard_solve(nb, s, k)
-        assert rep["status"] == 0, (k, rep)
-        runs[k] = (x, rep, info)
-    x1, r1, i1 = runs[1]
+        for striped in (True, False):
+            x, rep, info = shard_solve(nb, s, k, striped=striped)
+            assert rep["status"] == 0, (k, striped, rep)
+            runs[(k, striped)] = (x, rep, info)
+    x1, r1, i1 = runs[(1, True)]
     assert i1["halo"] == [0] and i1["exchanged"] == 0
-    for k, (x, rep, info) in runs.items():
-        np.testing.assert_array_equal(x, x1, err_msg=f"{name}: {k} sub-domains")
+    # striping (the exchange overlapped with the interior slices) changes no bit either
+    for (k, striped), (x, rep, info) in runs.items():
+        np.testing.assert_array_equal(x, x1, err_msg=f"{name}: {k} sub-domains, striped {striped}")
         assert rep["iters"] == r1["iters"] and rep["refinements"] == r1["refinements"]
         assert rep["true_rel_res"] == r1["true_rel_res"]
         if k > 1:
