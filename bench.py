@@ -518,7 +518,7 @@ def run_sphvisc(args):
         # the preconditioner-scale heads against Jacobi alone (same start, v^n + closure)
         if "learned_vs_plain" in learned:
             for case in ("box_1157k", "ensemble_64"):
-                for k in ("learned_scale", "wall_p3"):
+                for k in ("learned_scale", "wall_p3", "wall_c0.125"):
                     if k in ps.get(case, {}):
                         learned["learned_vs_plain"].setdefault(case, {})[f"{k}/jacobi_vn_walls"] = ps[case][k]["vs_jacobi"]
     cpu, oracle_error = None, None
@@ -1181,19 +1181,21 @@ def _scale_heads():
     net = binding.Mlp(np.load(path)["params"])
 
     def learned_scale(nb, p, t, sc):
-        binding.mlp_row_scale(nb, p, net, t["vel"], sc)
+        binding.mlp_row_scale(nb, p, net, t["vel"], None)      # installed on the handle directly
+        return "installed"
 
     learned_scale.net = net
     return {"learned_scale": learned_scale}
 
 
-def run_precond_scale(dev=None, reps=3, powers=(2.0, 3.0, 4.0), heads=None):
+def run_precond_scale(dev=None, reps=3, fixed=((1.0, 3.0), (0.25, 0.0), (0.125, 0.0)), heads=None):
     """The diagonal preconditioner scale on top of Jacobi (S D^-1 from the left) against
     Jacobi alone, both from v^n with the dummy-wall closure, on the unseen 1.16M-particle
     boxes (seeds 1-3, single solves) and the unseen 64-scene ensemble (seed 1, batched
-    solve).  Scales: the closed form norm2^-p on the dummy-wall rows (sph_wall_row_scale)
-    for each p, and optional learned heads (name -> callable(nb, p, t, out) filling the
-    scale).  ms = the scale's own kernels + the solve."""
+    solve).  Scales: the closed forms factor norm2^-power on the dummy-wall rows
+    (sph_wall_row_scale) for each (factor, power) in fixed, and optional learned heads
+    (name -> callable(nb, p, t, out) filling the scale).  ms = the scale's own kernels +
+    the solve."""
     import numpy as np
     import torch
 
@@ -1209,8 +1211,9 @@ def run_precond_scale(dev=None, reps=3, powers=(2.0, 3.0, 4.0), heads=None):
 
     def scalers():
         out = {"jacobi": None}
-        for pw in powers:
-            out[f"wall_p{pw:g}"] = (lambda pw_: lambda nb, p, t, sc: nb.wall_row_scale(p, pw_, sc))(pw)
+        for f, pw in fixed:
+            key = f"wall_p{pw:g}" if f == 1.0 else (f"wall_c{f:g}" if pw == 0.0 else f"wall_c{f:g}_p{pw:g}")
+            out[key] = (lambda f_, pw_: lambda nb, p, t, sc: nb.wall_row_scale(p, f_, pw_, sc))(f, pw)
         out.update(heads)
         return out
 
@@ -1232,8 +1235,7 @@ def run_precond_scale(dev=None, reps=3, powers=(2.0, 3.0, 4.0), heads=None):
                 ev4[0].record(stream)
                 if fill_scale is None:
                     nb.set_row_scale(None)
-                else:
-                    fill_scale(nb, p, t, sc)
+                elif fill_scale(nb, p, t, sc) != "installed":
                     nb.set_row_scale(sc)
                 ev4[1].record(stream)
                 binding.warm_start(nb, p, None, t["vel"], t["ptype"], b, x)
@@ -1286,8 +1288,7 @@ def run_precond_scale(dev=None, reps=3, powers=(2.0, 3.0, 4.0), heads=None):
         for k in range(len(ens)):
             if fill_scale is None:
                 nbs[k].set_row_scale(None)
-            else:
-                fill_scale(nbs[k], ps[k], ts[k], scs[k])
+            elif fill_scale(nbs[k], ps[k], ts[k], scs[k]) != "installed":
                 nbs[k].set_row_scale(scs[k])
         ev[1].record(stream)
         torch.cuda.synchronize(dev)

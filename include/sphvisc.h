@@ -530,7 +530,8 @@ sph_status sph_mlp_destroy(sph_mlp* mlp);
 /* Features (device, [n][16] bf16 bits, caller order) of the particles of
  * `handle` for velocities vel (device, [n][4] float): v/U, the Jacobi-scaled
  * explicit viscous increment D^-1 (v - A v) / U and its second application,
- * log10(mu)/5, log10(1 + dt sum c)/4, nearest wall neighbour / 2h, the Shepard
+ * log10(mu)/5, log10(1 + dt sum c)/4 (on a wall row: of the mean over its fluid
+ * neighbours), nearest wall neighbour / 2h, the Shepard
  * sum of W V, neighbour count / 80, |v| relative to the neighbourhood RMS, and
  * the wall flag.  scale_out (host, may be NULL): U = RMS |v| over the fluid. */
 sph_status sph_mlp_features(sph_neighbors* handle, const sph_visc_params* params, const float* vel,
@@ -628,26 +629,31 @@ sph_status sph_set_row_scale(sph_neighbors* handle, const float* scale, void* st
 sph_status sph_row_norms(sph_neighbors* handle, const sph_visc_params* params, float* norm2, void* stream);
 
 /* The closed-form wall scale: scale (device [n] float, caller order) =
- * norm2^-power on dummy-wall (Shepard) rows and 1 on fluid and identity rows,
- * norm2 as in sph_row_norms; 0 <= power <= 64, else SPH_ERR_INVALID.  The
- * dummy-wall rows are interpolation constraints (Eq. dummyvel); weighting the
- * most strongly coupled of them down shortens the inner iteration. */
-sph_status sph_wall_row_scale(sph_neighbors* handle, const sph_visc_params* params, double power,
-                              float* scale, void* stream);
+ * factor norm2^-power on dummy-wall (Shepard) rows and 1 on fluid and identity
+ * rows, norm2 as in sph_row_norms; 1e-6 <= factor <= 1e6 and 0 <= power <= 64,
+ * else SPH_ERR_INVALID.  The dummy-wall rows are interpolation constraints
+ * (Eq. dummyvel); weighting them down against the Jacobi-scaled fluid rows
+ * shortens the inner iteration on stiff systems. */
+sph_status sph_wall_row_scale(sph_neighbors* handle, const sph_visc_params* params, double factor,
+                              double power, float* scale, void* stream);
 
 /* The learned scale: the network mlp (the warm start's 16-64-64-64-3 architecture,
  * trained for this use) on the features of sph_mlp_features for velocities vel
  * (device [n][4] float); scale (device [n] float, caller order) = exp(y_0),
  * y_0 clamped to [-8, 2], on wall rows and 1 on fluid rows, ready for
- * sph_set_row_scale.  Wendland kernel only (SPH_ERR_INVALID otherwise). */
+ * sph_set_row_scale.  scale may be NULL: the learned scale then becomes the
+ * handle's row scale directly, as sph_set_row_scale would make it, without the
+ * check and the synchronisation (its values are positive and finite by
+ * construction).  Wendland kernel only (SPH_ERR_INVALID otherwise). */
 sph_status sph_mlp_row_scale(sph_neighbors* handle, const sph_visc_params* params, const sph_mlp* mlp,
                              const float* vel, float* scale, void* stream);
 
 /* Training targets of the learned scale: targets (device [n][4] float, caller
  * order) = (log s, 0, 0, 0) with s the closed-form wall scale of
- * sph_wall_row_scale for power, and mask (device [n] u8) = 1 on wall rows. */
-sph_status sph_mlp_scale_targets(sph_neighbors* handle, const sph_visc_params* params, double power,
-                                 float* targets, uint8_t* mask, void* stream);
+ * sph_wall_row_scale for factor and power, and mask (device [n] u8) = 1 on wall
+ * rows. */
+sph_status sph_mlp_scale_targets(sph_neighbors* handle, const sph_visc_params* params, double factor,
+                                 double power, float* targets, uint8_t* mask, void* stream);
 
 /* Papanastasiou viscosity from the previous velocities (Sec. 2.4, Eq. papa):
  *   grad u_b = sum_a V_a |F_ab| r_ab (x) u_ab;  gdot = sym(grad u);

@@ -7,7 +7,8 @@ feature set is this project's choice, listed in the library header):
   3-5  e1 / U, e1 = D^-1 (v - A v)   on fluid rows (A = A(dt), D its diagonal)
   6-8  e2 / U, e2 = D^-1 (e1 - A e1) on fluid rows
   9    log10(mu) / 5
-  10   log10(D) / 4
+  10   log10(D) / 4; on a wall row (D = 1) log10 of the mean D of its fluid neighbours / 4
+       (0 without one)
   11   min over wall neighbours of r / (2h), 1 without one
   12   W(0) V_b + sum over fluid neighbours of W_ba V_a
   13   neighbour count / 80
@@ -47,6 +48,8 @@ def features(scene, offsets, idx, A, vel=None):
         F[b, 11] = min(1.0, (r[wall] / (2 * h)).min()) if wall.any() else 1.0
         F[b, 12] = kernel.W(0.0, h) * V[b] + (kernel.W(r[~wall], h) * V[nb[~wall]]).sum()
         F[b, 13] = len(nb) / 80.0
+        if not fl[b]:
+            F[b, 10] = np.log10(D[nb[~wall]].mean()) / 4.0 if (~wall).any() else 0.0
         vn = np.linalg.norm(v[b])
         rms = np.sqrt((v[nb] ** 2).sum(axis=1).mean()) if len(nb) else 0.0
         F[b, 14] = vn / (vn + rms) if vn + rms > 0 else 0.0

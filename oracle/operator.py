@@ -117,12 +117,14 @@ def row_norms2(A):
     return np.asarray(B.multiply(B).sum(axis=1)).ravel()
 
 
-def wall_row_scale(scene, A, power):
-    """The closed-form row scale: row_norms2^-power on wall rows, 1 on fluid rows (the
-    wall rows of a dynamic boundary are identity rows, norm 1, so they keep 1)."""
+def wall_row_scale(scene, A, power, factor=1.0):
+    """The closed-form row scale: factor row_norms2^-power on the wall rows that carry
+    Shepard weights (a fluid neighbour), 1 on fluid rows and on identity rows (lone dummy
+    walls and every wall row of a dynamic boundary)."""
+    A = sp.csr_matrix(A)
     s = np.ones(scene.n)
-    w = np.asarray(scene.ptype) != FLUID
-    s[w] = row_norms2(A)[w] ** (-float(power))
+    w = (np.asarray(scene.ptype) != FLUID) & (np.diff(A.indptr) > 1)
+    s[w] = float(factor) * row_norms2(A)[w] ** (-float(power))
     return s
 
 

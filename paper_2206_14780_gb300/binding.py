@@ -156,9 +156,9 @@ def load(path: str = LIB_PATH):
                      ctypes.POINTER(vp), ctypes.POINTER(sph_step_report), vp],
         "sph_set_row_scale": [vp, vp, vp],
         "sph_row_norms": [vp, ctypes.POINTER(sph_visc_params), vp, vp],
-        "sph_wall_row_scale": [vp, ctypes.POINTER(sph_visc_params), dbl, vp, vp],
+        "sph_wall_row_scale": [vp, ctypes.POINTER(sph_visc_params), dbl, dbl, vp, vp],
         "sph_mlp_row_scale": [vp, ctypes.POINTER(sph_visc_params), vp, vp, vp, vp],
-        "sph_mlp_scale_targets": [vp, ctypes.POINTER(sph_visc_params), dbl, vp, vp, vp],
+        "sph_mlp_scale_targets": [vp, ctypes.POINTER(sph_visc_params), dbl, dbl, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -364,9 +364,10 @@ class Neighbors:
         """sph_row_norms: squared norms of the rows of D^-1 A (device float [n], caller order)."""
         _check(_lib.sph_row_norms(self.handle, ctypes.byref(params), _ptr(out), _stream(stream)))
 
-    def wall_row_scale(self, params, power, out, stream=None):
-        """sph_wall_row_scale: norm2^-power on dummy-wall rows, 1 elsewhere (device float [n])."""
-        _check(_lib.sph_wall_row_scale(self.handle, ctypes.byref(params), float(power), _ptr(out), _stream(stream)))
+    def wall_row_scale(self, params, factor, power, out, stream=None):
+        """sph_wall_row_scale: factor norm2^-power on dummy-wall rows, 1 elsewhere (device float [n])."""
+        _check(_lib.sph_wall_row_scale(self.handle, ctypes.byref(params), float(factor), float(power), _ptr(out),
+                                       _stream(stream)))
 
     def mu_papanastasiou(self, vel, wall_vel, tau0, mu0, m, mu_out, set_handle=True, stream=None):
         _check(_lib.sph_mu_papanastasiou(self.handle, _ptr(vel), _ptr(wall_vel), float(tau0), float(mu0), float(m),
@@ -555,15 +556,16 @@ class Mlp:
 
 
 def mlp_row_scale(nb, params, mlp, vel, scale, stream=None):
-    """sph_mlp_row_scale: the learned wall-row scale (device float [n], caller order)."""
+    """sph_mlp_row_scale: the learned wall-row scale (device float [n], caller order), or
+    with scale None installed as the handle's row scale directly."""
     _check(_lib.sph_mlp_row_scale(nb.handle, ctypes.byref(params), mlp.handle, _ptr(vel), _ptr(scale),
                                   _stream(stream)))
 
 
-def mlp_scale_targets(nb, params, power, targets, mask, stream=None):
+def mlp_scale_targets(nb, params, factor, power, targets, mask, stream=None):
     """sph_mlp_scale_targets: (log s, 0, 0, 0) of the closed-form wall scale, wall-row mask."""
-    _check(_lib.sph_mlp_scale_targets(nb.handle, ctypes.byref(params), float(power), _ptr(targets), _ptr(mask),
-                                      _stream(stream)))
+    _check(_lib.sph_mlp_scale_targets(nb.handle, ctypes.byref(params), float(factor), float(power), _ptr(targets),
+                                      _ptr(mask), _stream(stream)))
 
 
 def mlp_features(nb, params, vel, feats, stream=None):

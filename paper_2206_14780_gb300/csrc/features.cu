@@ -224,6 +224,8 @@ __global__ void __launch_bounds__(kBlock) k_features(const float4* __restrict__ 
     const int c = cnt[s];
     const int64_t base = slice_off[s / kSlice] + (s % kSlice);
     float dmin = 1.f, shep = g.w_scale * (pb.w / rho[s]), v2 = 0.f;
+    double dsum = 0.0;   // D over the fluid neighbours (feature 10 of a wall row)
+    int nfl = 0;
     for (int j = 0; j < c; ++j) {
       const int32_t t = nbr[base + (int64_t)j * kSlice];
       const float4 pa = pos[t];
@@ -237,6 +239,8 @@ __global__ void __launch_bounds__(kBlock) k_features(const float4* __restrict__ 
         const float tq = fmaxf(1.f - 0.5f * q, 0.f);
         const float t2 = tq * tq;
         shep += g.w_scale * t2 * t2 * (2.f * q + 1.f) * (pa.w / rho[t]);
+        dsum += D64[t];
+        ++nfl;
       } else {
         dmin = fminf(dmin, r * g.inv_2h);
       }
@@ -258,7 +262,9 @@ __global__ void __launch_bounds__(kBlock) k_features(const float4* __restrict__ 
     f[7] = fluid ? b.y * iU : 0.f;
     f[8] = fluid ? b.z * iU : 0.f;
     f[9] = log10f(mu[s]) * 0.2f;
-    f[10] = (float)(log10(D64[s]) * 0.25);
+    // log10 D / 4; on a wall row (D = 1) the mean D of its fluid neighbours, the
+    // stiffness its row couples to
+    f[10] = (float)(log10(fluid ? D64[s] : (nfl > 0 ? dsum / nfl : 1.0)) * 0.25);
     f[11] = dmin;
     f[12] = shep;
     f[13] = (float)c * (1.f / 80.f);

@@ -10,10 +10,10 @@
 //
 // Also here: the squared norms of the rows of D^-1 A, 1 + sum_j (a_j / D)^2 over
 // a fluid row's coefficients (1 + sum_j S_j^2 over a dummy-wall row's Shepard
-// weights, 1 for an identity row); the closed-form scale that takes them to a
-// power on the dummy-wall rows only; and the learned scale, the warm-start
-// network's architecture evaluated on the same 16 features, whose first output is
-// the log of a wall row's scale (trained on the closed form's logs).
+// weights, 1 for an identity row); the closed-form scale factor norm2^-power on
+// the dummy-wall rows only; and the learned scale, the warm-start network's
+// architecture evaluated on the same 16 features, whose first output is the log of
+// a wall row's scale.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -42,15 +42,19 @@ __device__ __forceinline__ float row_norm2(const int64_t* __restrict__ off, cons
 }
 
 // out[perm[s]] = squared norm of row s of D^-1 A (mode 0), or the wall scale:
-// 1 on fluid and identity rows, norm2^-power on Shepard rows (mode 1)
+// 1 on fluid and identity rows, factor norm2^-power on Shepard rows (mode 1)
 __global__ void k_row_norms(const int64_t* __restrict__ off, const int32_t* __restrict__ cnt,
                             const int2* __restrict__ ih, const uint8_t* __restrict__ kind,
                             const float* __restrict__ invD, const int32_t* __restrict__ perm, int64_t n, int mode,
-                            float power, float* __restrict__ out) {
+                            float factor, float power, float* __restrict__ out) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-    const float nrm2 = row_norm2(off, cnt, ih, invD, s);
-    float v = nrm2;
-    if (mode == 1) v = kind[s] == KIND_SHEPARD ? powf(nrm2, -power) : 1.f;
+    float v;
+    if (mode == 0) {
+      v = row_norm2(off, cnt, ih, invD, s);
+    } else {
+      v = kind[s] == KIND_SHEPARD ? (power != 0.f ? factor * powf(row_norm2(off, cnt, ih, invD, s), -power) : factor)
+                                  : 1.f;
+    }
     out[perm[s]] = v;
   }
 }
@@ -60,10 +64,12 @@ __global__ void k_row_norms(const int64_t* __restrict__ off, const int32_t* __re
 __global__ void k_scale_targets(const int64_t* __restrict__ off, const int32_t* __restrict__ cnt,
                                 const int2* __restrict__ ih, const uint8_t* __restrict__ kind,
                                 const float* __restrict__ invD, const uint8_t* __restrict__ type,
-                                const int32_t* __restrict__ perm, int64_t n, float power, float4* __restrict__ tgt,
-                                uint8_t* __restrict__ mask) {
+                                const int32_t* __restrict__ perm, int64_t n, float log_factor, float power,
+                                float4* __restrict__ tgt, uint8_t* __restrict__ mask) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-    const float t = kind[s] == KIND_SHEPARD ? -power * logf(row_norm2(off, cnt, ih, invD, s)) : 0.f;
+    const float t = kind[s] == KIND_SHEPARD
+                        ? log_factor - (power != 0.f ? power * logf(row_norm2(off, cnt, ih, invD, s)) : 0.f)
+                        : 0.f;
     const int64_t i = perm[s];
     tgt[i] = make_float4(t, 0.f, 0.f, 0.f);
     mask[i] = type[s] == SPH_FLUID ? 0 : 1;
@@ -99,11 +105,12 @@ __global__ void k_rs_apply(const float* __restrict__ rs, const int32_t* __restri
   }
 }
 
-sph_status row_norms_impl(sph_neighbors* H, const sph_visc_params* P, int mode, double power, float* out,
-                          cudaStream_t st) {
+sph_status row_norms_impl(sph_neighbors* H, const sph_visc_params* P, int mode, double factor, double power,
+                          float* out, cudaStream_t st) {
   SPH_TRY(ensure_operator(H, P, st));
   SPH_LAUNCH(k_row_norms, grid_for(H, H->n), kBlock, 0, st)(H->op_off.p, H->op_cnt.p, H->op_ih.p, H->op_kind.p,
-                                                             H->invD.p, H->perm.p, H->n, mode, (float)power, out);
+                                                             H->invD.p, H->perm.p, H->n, mode, (float)factor,
+                                                             (float)power, out);
   SPH_TRY_CUDA(cudaGetLastError());
   return SPH_OK;
 }
@@ -138,21 +145,27 @@ sph_status sph_row_norms(sph_neighbors* h, const sph_visc_params* params, float*
     set_error("sph_row_norms: null argument");
     return SPH_ERR_INVALID;
   }
-  return row_norms_impl(h, params, 0, 0.0, norm2, reinterpret_cast<cudaStream_t>(stream));
+  return row_norms_impl(h, params, 0, 1.0, 0.0, norm2, reinterpret_cast<cudaStream_t>(stream));
 }
 
-sph_status sph_wall_row_scale(sph_neighbors* h, const sph_visc_params* params, double power, float* scale,
-                              void* stream) {
+static bool scale_args_ok(const char* fn, double factor, double power) {
+  if (!std::isfinite(power) || power < 0.0 || power > 64.0 || !std::isfinite(factor) || !(factor >= 1e-6) ||
+      factor > 1e6) {
+    set_error("%s: factor %g outside [1e-6, 1e6] or power %g outside [0, 64]", fn, factor, power);
+    return false;
+  }
+  return true;
+}
+
+sph_status sph_wall_row_scale(sph_neighbors* h, const sph_visc_params* params, double factor, double power,
+                              float* scale, void* stream) {
   clear_error();
   if (!h || !params || !scale) {
     set_error("sph_wall_row_scale: null argument");
     return SPH_ERR_INVALID;
   }
-  if (!std::isfinite(power) || power < 0.0 || power > 64.0) {
-    set_error("sph_wall_row_scale: power %g outside [0, 64]", power);
-    return SPH_ERR_INVALID;
-  }
-  return row_norms_impl(h, params, 1, power, scale, reinterpret_cast<cudaStream_t>(stream));
+  if (!scale_args_ok("sph_wall_row_scale", factor, power)) return SPH_ERR_INVALID;
+  return row_norms_impl(h, params, 1, factor, power, scale, reinterpret_cast<cudaStream_t>(stream));
 }
 
 sph_status sph_set_row_scale(sph_neighbors* h, const float* scale, void* stream) {
@@ -185,21 +198,19 @@ sph_status sph_set_row_scale(sph_neighbors* h, const float* scale, void* stream)
   return SPH_OK;
 }
 
-sph_status sph_mlp_scale_targets(sph_neighbors* h, const sph_visc_params* params, double power, float* targets,
-                                 uint8_t* mask, void* stream) {
+sph_status sph_mlp_scale_targets(sph_neighbors* h, const sph_visc_params* params, double factor, double power,
+                                 float* targets, uint8_t* mask, void* stream) {
   clear_error();
   if (!h || !params || !targets || !mask) {
     set_error("sph_mlp_scale_targets: null argument");
     return SPH_ERR_INVALID;
   }
-  if (!std::isfinite(power) || power < 0.0 || power > 64.0) {
-    set_error("sph_mlp_scale_targets: power %g outside [0, 64]", power);
-    return SPH_ERR_INVALID;
-  }
+  if (!scale_args_ok("sph_mlp_scale_targets", factor, power)) return SPH_ERR_INVALID;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   SPH_TRY(ensure_operator(h, params, st));
   SPH_LAUNCH(k_scale_targets, grid_for(h, h->n), kBlock, 0, st)(h->op_off.p, h->op_cnt.p, h->op_ih.p, h->op_kind.p,
-                                                                 h->invD.p, h->type_s.p, h->perm.p, h->n, (float)power,
+                                                                 h->invD.p, h->type_s.p, h->perm.p, h->n,
+                                                                 (float)std::log(factor), (float)power,
                                                                  reinterpret_cast<float4*>(targets), mask);
   SPH_TRY_CUDA(cudaGetLastError());
   return SPH_OK;
@@ -208,7 +219,7 @@ sph_status sph_mlp_scale_targets(sph_neighbors* h, const sph_visc_params* params
 sph_status sph_mlp_row_scale(sph_neighbors* h, const sph_visc_params* params, const sph_mlp* mlp, const float* vel,
                              float* scale, void* stream) {
   clear_error();
-  if (!h || !params || !mlp || !vel || !scale) {
+  if (!h || !params || !mlp || !vel) {
     set_error("sph_mlp_row_scale: null argument");
     return SPH_ERR_INVALID;
   }
@@ -222,9 +233,21 @@ sph_status sph_mlp_row_scale(sph_neighbors* h, const sph_visc_params* params, co
   __nv_bfloat16* f = reinterpret_cast<__nv_bfloat16*>(h->feat_out.p);
   SPH_TRY(features_impl(h, params, vel, f, st));
   SPH_TRY(mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st));
-  SPH_LAUNCH(k_scale_from_net, grid_for(h, h->n), kBlock, 0, st)(h->feat_delta.p, h->type_s.p, h->perm.p, h->n,
-                                                                  scale);
+  // without an output array the scale goes straight into the handle: exp of a clamped
+  // value (NaN clamps to the lower bound) is positive and finite, so unlike
+  // sph_set_row_scale nothing needs checking and nothing synchronises
+  float* out = scale;
+  if (!out) {
+    SPH_TRY(h->rs_caller.alloc(h->n));
+    out = h->rs_caller.p;
+  }
+  SPH_LAUNCH(k_scale_from_net, grid_for(h, h->n), kBlock, 0, st)(h->feat_delta.p, h->type_s.p, h->perm.p, h->n, out);
   SPH_TRY_CUDA(cudaGetLastError());
+  if (!scale) {
+    ++h->rs_version;
+    h->row_scaled = true;
+    h->rs_op_version = ~0ull;
+  }
   return SPH_OK;
 }
 

@@ -32,9 +32,9 @@ def test_row_norms_and_wall_scale_match_oracle(name):
     nb.row_norms(params_for(s), out)
     want = oop.row_norms2(A)
     np.testing.assert_allclose(out.cpu().numpy(), want, rtol=2e-6)
-    for power in (0.0, 3.0):
-        nb.wall_row_scale(params_for(s), power, out)
-        np.testing.assert_allclose(out.cpu().numpy(), oop.wall_row_scale(s, A, power), rtol=2e-5)
+    for factor, power in ((1.0, 0.0), (1.0, 3.0), (0.125, 0.0), (0.5, 2.0)):
+        nb.wall_row_scale(params_for(s), factor, power, out)
+        np.testing.assert_allclose(out.cpu().numpy(), oop.wall_row_scale(s, A, power, factor), rtol=2e-5)
     nb.close()
 
 
@@ -66,7 +66,7 @@ def test_wall_scaled_solve_keeps_the_oracle_solution(name):
     nb, _ = lib_build(s)
     _, _, A = oracle_system(s)
     sc = _dev_f32(torch, s.n)
-    nb.wall_row_scale(params_for(s), 3.0, sc)
+    nb.wall_row_scale(params_for(s), 1.0, 3.0, sc)
     nb.set_row_scale(sc)
     x, rep = gpu_solve(nb, s)
     assert rep["status"] == 0, rep
@@ -78,15 +78,17 @@ def test_wall_scaled_solve_keeps_the_oracle_solution(name):
     nb.close()
 
 
-def test_wall_scale_cuts_iterations_on_a_box():
-    """On a lava box the wall rows' scale shortens the inner iteration (the float64
-    study of the same scale: about a fifth fewer iterations at 15k-90k rows)."""
+@pytest.mark.parametrize("factor,power", [(1.0, 3.0), (0.125, 0.0)])
+def test_wall_scale_cuts_iterations_on_a_box(factor, power):
+    """On a stiff lava box weighting the wall rows down shortens the inner iteration
+    (the float64 study: about a fifth fewer iterations with norm2^-3, about a third with
+    a constant 1/8, at 15k-90k rows)."""
     torch = torch_cuda()
     s = scenes.lava_box(5, n=24)
     nb, _ = lib_build(s)
     _, rep0 = gpu_solve(nb, s)
     sc = _dev_f32(torch, s.n)
-    nb.wall_row_scale(params_for(s), 3.0, sc)
+    nb.wall_row_scale(params_for(s), factor, power, sc)
     nb.set_row_scale(sc)
     _, rep1 = gpu_solve(nb, s)
     assert rep0["status"] == 0 and rep1["status"] == 0
@@ -130,8 +132,9 @@ def test_bad_scales_and_unsupported_solves_are_refused():
     nb.set_row_scale(torch.full((s.n,), 0.5, dtype=torch.float32, device="cuda"))
     with pytest.raises(RuntimeError):
         gpu_solve(nb, s, binding.solve_opts(precision=binding.SPH_PREC_FP64))
-    with pytest.raises(RuntimeError):
-        nb.wall_row_scale(params_for(s), -1.0, torch.empty(s.n, dtype=torch.float32, device="cuda"))
+    for factor, power in ((1.0, -1.0), (0.0, 1.0), (float("nan"), 0.0)):
+        with pytest.raises(RuntimeError):
+            nb.wall_row_scale(params_for(s), factor, power, torch.empty(s.n, dtype=torch.float32, device="cuda"))
     nb.set_row_scale(None)
     x, rep = gpu_solve(nb, s, binding.solve_opts(precision=binding.SPH_PREC_FP64))
     assert rep["status"] == 0
@@ -151,7 +154,7 @@ def test_batched_solve_takes_each_scenes_scale():
         nb, _ = lib_build(s)
         if k != 1:
             sc = _dev_f32(torch, s.n)
-            nb.wall_row_scale(params_for(s), 3.0, sc)
+            nb.wall_row_scale(params_for(s), 1.0, 3.0, sc)
             nb.set_row_scale(sc)
         nbs.append(nb)
         bs.append(torch.from_numpy(s.b).cuda())
@@ -181,9 +184,10 @@ def test_scale_targets_match_the_oracle_closed_form():
     _, _, A = oracle_system(s)
     tgt = torch.empty((s.n, 4), dtype=torch.float32, device="cuda")
     mask = torch.empty(s.n, dtype=torch.uint8, device="cuda")
-    binding.mlp_scale_targets(nb, params_for(s), 4.0, tgt, mask)
-    t = tgt.cpu().numpy()
-    np.testing.assert_allclose(t[:, 0], np.log(oop.wall_row_scale(s, A, 4.0)), rtol=0, atol=2e-5)
+    for factor, power in ((1.0, 4.0), (0.125, 0.0), (0.25, 1.5)):
+        binding.mlp_scale_targets(nb, params_for(s), factor, power, tgt, mask)
+        t = tgt.cpu().numpy()
+        np.testing.assert_allclose(t[:, 0], np.log(oop.wall_row_scale(s, A, power, factor)), rtol=0, atol=2e-5)
     np.testing.assert_array_equal(t[:, 1:], 0.0)
     np.testing.assert_array_equal(mask.cpu().numpy(), (s.ptype != scenes.FLUID).astype(np.uint8))
     nb.close()
@@ -234,7 +238,9 @@ def test_learned_scale_is_the_networks_first_output_on_wall_rows():
 
 def test_learned_scale_cuts_iterations_on_an_unseen_full_size_box():
     """The committed head on a 1.16M-particle lava box it never saw (seed 11): fewer
-    iterations than Jacobi alone from the same start (v^n with the wall closure)."""
+    iterations than Jacobi alone and than the closed-form norm2^-3 scale, from the same
+    start (v^n with the wall closure); installing the scale directly (no output array)
+    gives the same solve bit for bit."""
     torch = torch_cuda()
     from paper_2206_14780_gb300 import binding
 
@@ -245,16 +251,26 @@ def test_learned_scale_cuts_iterations_on_an_unseen_full_size_box():
     nb = binding.build_neighbors(t["pos"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
     p = params_for(s)
     b = torch.from_numpy(s.b).cuda()
-    its = {}
-    for name in ("jacobi", "learned"):
-        if name == "learned":
-            sc = torch.empty(s.n, dtype=torch.float32, device="cuda")
+    its, xs = {}, {}
+    for name in ("jacobi", "wall_p3", "learned", "learned_installed"):
+        sc = torch.empty(s.n, dtype=torch.float32, device="cuda")
+        if name == "jacobi":
+            nb.set_row_scale(None)
+        elif name == "wall_p3":
+            nb.wall_row_scale(p, 1.0, 3.0, sc)
+            nb.set_row_scale(sc)
+        elif name == "learned":
             binding.mlp_row_scale(nb, p, net, vel, sc)
             nb.set_row_scale(sc)
+        else:
+            nb.set_row_scale(None)
+            binding.mlp_row_scale(nb, p, net, vel, None)
         x = torch.empty_like(b)
         binding.warm_start(nb, p, None, vel, t["ptype"], b, x)
         rep = nb.solve(p, binding.solve_opts(), b, x)
         assert rep["status"] == 0 and rep["true_rel_res"] <= 1e-6
         its[name] = rep["iters"]
-    assert its["learned"] < 0.9 * its["jacobi"], its
+        xs[name] = x
+    assert its["learned"] < 0.8 * its["jacobi"] and its["learned"] < its["wall_p3"], its
+    assert its["learned_installed"] == its["learned"] and torch.equal(xs["learned_installed"], xs["learned"])
     nb.close()

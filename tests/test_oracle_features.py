@@ -94,3 +94,23 @@ def test_velocity_features_are_scale_free():
     F2, U2 = ofeat.features(s, off, idx, A, vel=v2.astype(np.float32))
     assert abs(U2 - 16.0 * U1) <= 1e-12 * U2
     np.testing.assert_allclose(F2, F1, rtol=1e-6, atol=1e-12)
+
+
+def test_wall_rows_carry_the_stiffness_of_their_fluid_neighbours():
+    """Feature 10 of a wall row is log10 of the mean diagonal D of its fluid neighbours / 4.
+    In a Couette channel on a lattice whose dummy walls continue the lattice, every fluid
+    particle sees the full lattice neighbourhood, so every fluid D is the lattice sum
+    1 + dt sum c; wall rows within 2h of the fluid then carry log10 of that same D / 4 and
+    the deeper ones 0."""
+    s = scenes.couette(0, noise=0.0)
+    off, idx, A = _build(s)
+    F, _ = ofeat.features(s, off, idx, A)
+    _, D, _, _ = _lattice_sums(s, np.zeros(3))
+    fl = s.ptype == scenes.FLUID
+    np.testing.assert_allclose(A.diagonal()[fl], D, rtol=1e-6)
+    np.testing.assert_allclose(F[fl, 10], np.log10(D) / 4.0, rtol=1e-6)
+    k = np.diff(A.tocsr().indptr) - 1
+    near = (~fl) & (k > 0)
+    assert near.sum() > 0 and (~fl & (k == 0)).sum() > 0
+    np.testing.assert_allclose(F[near, 10], np.log10(D) / 4.0, rtol=1e-6)
+    np.testing.assert_array_equal(F[(~fl) & (k == 0), 10], 0.0)

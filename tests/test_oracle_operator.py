@@ -184,3 +184,10 @@ def test_wall_row_scale_leaves_fluid_rows_and_falls_with_power():
     np.testing.assert_array_equal(s3[fl], 1.0)
     assert np.all(s4[~fl] <= s3[~fl]) and np.all(s3[~fl] <= 1.0) and np.all(s3[~fl] >= 0.125)
     assert np.any(s3[~fl] < 0.5)
+    # a constant factor on the Shepard rows only: lone walls (identity rows) keep 1
+    k = np.diff(A.tocsr().indptr) - 1
+    c = operator.wall_row_scale(s, A, 0.0, factor=0.25)
+    np.testing.assert_array_equal(c[fl], 1.0)
+    np.testing.assert_array_equal(c[(~fl) & (k > 0)], 0.25)
+    np.testing.assert_array_equal(c[(~fl) & (k == 0)], 1.0)
+    assert ((~fl) & (k == 0)).sum() > 0
