@@ -214,11 +214,17 @@ __global__ void __launch_bounds__(kBlock) k_features(const float4* __restrict__ 
                                                      const int32_t* __restrict__ nbr, const int32_t* __restrict__ perm,
                                                      const float4* __restrict__ v, const float4* __restrict__ e1,
                                                      const float4* __restrict__ e2, int64_t n, FeatGeom g,
-                                                     const double* __restrict__ scale,
+                                                     const double* __restrict__ scale, int walls_only,
                                                      __nv_bfloat16* __restrict__ feats) {
   const float U = (float)sqrt(scale[0] / fmax(scale[1], 1.0));
   const float iU = U > 0.f ? 1.f / U : 0.f;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    if (walls_only && type[s] == SPH_FLUID) {   // zeros: the caller reads the wall rows only
+      uint4* out = reinterpret_cast<uint4*>(feats + (int64_t)perm[s] * 16);
+      out[0] = make_uint4(0u, 0u, 0u, 0u);
+      out[1] = make_uint4(0u, 0u, 0u, 0u);
+      continue;
+    }
     const float4 pb = pos[s];
     const float4 vb = v[s];
     const int c = cnt[s];
@@ -397,9 +403,11 @@ __global__ void k_resid_targets(const float4* __restrict__ y, const float4* __re
 }  // namespace
 
 // features of the particle set on handle H for velocities vel (caller order);
-// leaves the scale sums (|v|^2, count) in H->feat_scale (device)
+// leaves the scale sums (|v|^2, count) in H->feat_scale (device).  walls_only:
+// the wall rows' features alone (fluid rows zero); a wall row's Neumann
+// increments are zero by definition, so the two operator applies are skipped
 sph_status features_impl(sph_neighbors* H, const sph_visc_params* P, const float* vel, __nv_bfloat16* feats,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool walls_only) {
   SPH_TRY(ensure_operator(H, P, st));
   SPH_TRY(ensure_workspace(H));
   SPH_TRY(H->feat_tmp.alloc(4 * H->n_pad));
@@ -411,10 +419,12 @@ sph_status features_impl(sph_neighbors* H, const sph_visc_params* P, const float
   float4* e2 = vs + 3 * np;
   const int grid = grid_for(H, np);
   SPH_LAUNCH(k_feat_gather, grid, kBlock, 0, st)(reinterpret_cast<const float4*>(vel), H->perm.p, H->n, np, vs);
-  launch_apply_f32(H, vs, y, false, st);
-  SPH_LAUNCH(k_feat_incr, grid, kBlock, 0, st)(vs, y, H->invD.p, H->type_s.p, H->n, np, e1);
-  launch_apply_f32(H, e1, y, false, st);
-  SPH_LAUNCH(k_feat_incr, grid, kBlock, 0, st)(e1, y, H->invD.p, H->type_s.p, H->n, np, e2);
+  if (!walls_only) {
+    launch_apply_f32(H, vs, y, false, st);
+    SPH_LAUNCH(k_feat_incr, grid, kBlock, 0, st)(vs, y, H->invD.p, H->type_s.p, H->n, np, e1);
+    launch_apply_f32(H, e1, y, false, st);
+    SPH_LAUNCH(k_feat_incr, grid, kBlock, 0, st)(e1, y, H->invD.p, H->type_s.p, H->n, np, e2);
+  }
   int rg = grid < H->red_grid ? grid : H->red_grid;
   SPH_LAUNCH(k_feat_scale, rg, kBlock, 0, st)(vs, H->type_s.p, H->n, H->partials.p, H->counters.p + 7,
                                               H->feat_scale.p);
@@ -430,7 +440,7 @@ sph_status features_impl(sph_neighbors* H, const sph_visc_params* P, const float
   g.w_scale = (float)(21.0 / (16.0 * M_PI) / (h * h * h));
   SPH_LAUNCH(k_features, grid_for(H, H->n), kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->type_s.p, H->D64.p,
                                                            H->cnt.p, H->slice_off.p, H->nbr.p, H->perm.p, vs, e1, e2,
-                                                           H->n, g, H->feat_scale.p, feats);
+                                                           H->n, g, H->feat_scale.p, walls_only ? 1 : 0, feats);
   SPH_TRY_CUDA(cudaGetLastError());
   return SPH_OK;
 }
@@ -495,7 +505,7 @@ sph_status sph_mlp_features(sph_neighbors* h, const sph_visc_params* params, con
     return SPH_ERR_INVALID;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  SPH_TRY(features_impl(h, params, vel, reinterpret_cast<__nv_bfloat16*>(feats), st));
+  SPH_TRY(features_impl(h, params, vel, reinterpret_cast<__nv_bfloat16*>(feats), st, false));
   if (scale_out) {
     double sc[2];
     SPH_TRY_CUDA(cudaMemcpyAsync(sc, h->feat_scale.p, sizeof(sc), cudaMemcpyDeviceToHost, st));
@@ -555,7 +565,7 @@ sph_status sph_warm_start(sph_neighbors* h, const sph_visc_params* params, const
     SPH_TRY(h->feat_out.alloc(h->n * 8));      // bf16 features [n][16]
     SPH_TRY(h->feat_delta.alloc(h->n));        // float4 network outputs
     __nv_bfloat16* f = reinterpret_cast<__nv_bfloat16*>(h->feat_out.p);
-    SPH_TRY(features_impl(h, params, vel, f, st));
+    SPH_TRY(features_impl(h, params, vel, f, st, false));
     SPH_TRY(mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st));
     delta = h->feat_delta.p;
     if (mlp_mode(mlp) & SPH_MLP_HIGHPASS) {
@@ -597,7 +607,7 @@ sph_status sph_mlp_residual_targets(sph_neighbors* h, const sph_visc_params* par
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   __nv_bfloat16* f = reinterpret_cast<__nv_bfloat16*>(feats);
-  SPH_TRY(features_impl(h, params, vel, f, st));
+  SPH_TRY(features_impl(h, params, vel, f, st, false));
   SPH_TRY(h->feat_delta.alloc(h->n));
   SPH_TRY(h->x64.alloc(3 * h->n_pad));
   SPH_TRY(h->r64.alloc(3 * h->n_pad));

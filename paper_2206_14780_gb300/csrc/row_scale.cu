@@ -118,7 +118,7 @@ sph_status row_norms_impl(sph_neighbors* H, const sph_visc_params* P, int mode, 
 }  // namespace
 
 sph_status features_impl(sph_neighbors* H, const sph_visc_params* P, const float* vel, __nv_bfloat16* feats,
-                         cudaStream_t st);
+                         cudaStream_t st, bool walls_only);
 sph_status mlp_forward_launch(const sph_mlp* M, const __nv_bfloat16* feats, int64_t m, float4* out, int num_sms,
                               cudaStream_t st);
 
@@ -231,7 +231,7 @@ sph_status sph_mlp_row_scale(sph_neighbors* h, const sph_visc_params* params, co
   SPH_TRY(h->feat_out.alloc(h->n * 8));      // bf16 features [n][16]
   SPH_TRY(h->feat_delta.alloc(h->n));        // float4 network outputs
   __nv_bfloat16* f = reinterpret_cast<__nv_bfloat16*>(h->feat_out.p);
-  SPH_TRY(features_impl(h, params, vel, f, st));
+  SPH_TRY(features_impl(h, params, vel, f, st, true));   // only the wall rows' scales are used
   SPH_TRY(mlp_forward_launch(mlp, f, h->n, h->feat_delta.p, h->num_sms, st));
   // without an output array the scale goes straight into the handle: exp of a clamped
   // value (NaN clamps to the lower bound) is positive and finite, so unlike
