@@ -521,6 +521,9 @@ def run_sphvisc(args):
                 for k in ("learned_scale", "wall_p3", "wall_c0.125"):
                     if k in ps.get(case, {}):
                         learned["learned_vs_plain"].setdefault(case, {})[f"{k}/jacobi_vn_walls"] = ps[case][k]["vs_jacobi"]
+                        if "vs_sequential_plain" in ps[case][k]:
+                            learned["learned_vs_plain"][case][f"{k}_batched/sequential_plain"] = \
+                                ps[case][k]["vs_sequential_plain"]
     cpu, oracle_error = None, None
     if oracle is not None:
         rows, err = oracle.result()
@@ -1316,6 +1319,28 @@ def run_precond_scale(dev=None, reps=3, fixed=((1.0, 3.0), (0.25, 0.0), (0.125, 
     for k in names:
         eres[k]["vs_jacobi"] = dict(iters=eres[k]["iters_sum"] / eres["jacobi"]["iters_sum"],
                                     ms=eres[k]["ms"] / eres["jacobi"]["ms"])
+    # the plain GPU BiCGSTAB on the same scenes one by one (Jacobi, no batching): what the
+    # learned and batched form is measured against
+    for k in range(len(ens)):
+        nbs[k].set_row_scale(None)
+        binding.warm_start(nbs[k], ps[k], None, ts[k]["vel"], ts[k]["ptype"], bs[k], xs[k])
+        nbs[k].solve(ps[k], opts, bs[k], xs[k])          # warm-up
+    for k in range(len(ens)):
+        binding.warm_start(nbs[k], ps[k], None, ts[k]["vel"], ts[k]["ptype"], bs[k], xs[k])
+    seq_its, seq_res = 0, 0.0
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    for k in range(len(ens)):
+        rep = nbs[k].solve(ps[k], opts, bs[k], xs[k])
+        seq_its += rep["iters"]
+        seq_res = max(seq_res, rep["true_rel_res"])
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    seq_ms = ev[0].elapsed_time(ev[1])
+    eres["jacobi_sequential"] = dict(iters_sum=seq_its, ms=seq_ms, max_true_rel_res=seq_res,
+                                     note="the 64 single-scene solves one after another (solves timed, as batched)")
+    for k in names:
+        eres[k]["vs_sequential_plain"] = dict(iters=eres[k]["iters_sum"] / seq_its, ms=eres[k]["ms"] / seq_ms)
     out["ensemble_64"] = dict(workload=f"64 scenes, seed 1, {sum(sc_.n for sc_ in ens)} particles, batched solve",
                               **eres)
     for nb_ in nbs:
