@@ -19,7 +19,7 @@ def _lattice_offsets(radius):
 
 
 def test_lattice_count_is_80():
-    # h = 1.3 dx, support 2.6 dx: the paper says "around 80"; the exact lattice count is 80
+    # h = 1.3 dx, support 2.6 dx: the paper gives about 80 neighbours; the exact lattice count is 80
     assert len(_lattice_offsets(2.6)) == 80
     s = scenes.periodic_lattice(8)
     off, idx = neighbors.bruteforce(s.pos, s.lo, s.hi, s.periodic, s.h)
@@ -28,7 +28,7 @@ def test_lattice_count_is_80():
 
 
 def test_gaussian_lattice_count_is_250():
-    # truncated Gaussian, support 3h = 3.9 dx: the paper says "around 250"; the exact
+    # truncated Gaussian, support 3h = 3.9 dx: the paper gives about 250 neighbours; the exact
     # lattice count is 250, and brute force and the k-d tree find it on every particle
     assert len(_lattice_offsets(3.9)) == 250
     s = scenes.periodic_lattice(12, kernel=scenes.KERNEL_GAUSSIAN)
