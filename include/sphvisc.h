@@ -614,7 +614,9 @@ sph_status sph_warm_start(sph_neighbors* handle, const sph_visc_params* params, 
  * inner BiCGSTAB or CG works on (S D^-1 A) d = S D^-1 r, with the same solution,
  * and the stop stays on the float64 true residual of A x = b.  scale: (device)
  * [n] float, caller order, copied; NULL clears it.  The scale stays with the
- * handle across operator rebuilds until cleared.  Values that are not positive
+ * handle across operator rebuilds and neighbour rebuilds of the same particles
+ * until cleared; a neighbour rebuild with another particle count clears it.
+ * Values that are not positive
  * finite numbers: SPH_ERR_NONFINITE (synchronises to check).  The batched solve
  * takes each handle's scale as it stands at sph_batch_create (setting or clearing
  * one afterwards makes sph_batch_solve return SPH_ERR_INVALID); the float64 and

@@ -458,6 +458,10 @@ sph_status build_neighbors(const sph_scene* sc, int32_t maxnb, sph_neighbors** o
   TRYF_CUDA(cudaGetDevice(&H->device));
   TRYF_CUDA(cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, H->device));
   const int64_t n = sc->n;
+  if (H->row_scaled && H->n != n) {   // a caller-order row scale no longer fits
+    H->row_scaled = false;
+    ++H->rs_version;
+  }
   H->n = n;
   H->n_pad = (n + kSlice - 1) / kSlice * kSlice;
   H->nslices = H->n_pad / kSlice;

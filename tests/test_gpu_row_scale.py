@@ -274,3 +274,33 @@ def test_learned_scale_cuts_iterations_on_an_unseen_full_size_box():
     assert its["learned"] < 0.8 * its["jacobi"] and its["learned"] < its["wall_p3"], its
     assert its["learned_installed"] == its["learned"] and torch.equal(xs["learned_installed"], xs["learned"])
     nb.close()
+
+
+def test_rebuild_keeps_the_scale_for_the_same_particles_and_drops_it_otherwise():
+    """A neighbour rebuild of the same particles (moved) keeps the caller-order scale and
+    the solve still meets the oracle; a rebuild with another particle count clears it
+    (the float64 solve, which refuses a scaled handle, then runs)."""
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    s = scenes.lava_box(2, n=10)
+    nb, t = lib_build(s)
+    sc = _dev_f32(torch, s.n)
+    nb.wall_row_scale(params_for(s), 0.125, 0.0, sc)
+    nb.set_row_scale(sc)
+    s2 = s.copy()
+    s2.pos = s.pos.copy()
+    s2.pos[s2.ptype == scenes.FLUID, :3] += np.float32(0.05 * s.dx)   # fluid shifted, same particles
+    pos2 = torch.from_numpy(s2.pos).cuda()
+    nb.rebuild(pos2, t["rho"], t["mu"], t["ptype"], s2.lo, s2.hi, s2.periodic, s2.h)
+    with pytest.raises(RuntimeError):                   # still scaled
+        gpu_solve(nb, s2, binding.solve_opts(precision=binding.SPH_PREC_FP64))
+    _, _, A2 = oracle_system(s2)
+    x, rep = gpu_solve(nb, s2, binding.solve_opts(rtol=1e-8))
+    assert rep["status"] == 0 and rel_l2(x, osv.reference_solution(A2, s2.b, s2.x0)) <= 1e-5
+    s3 = scenes.lava_box(3, n=9)
+    t3 = binding.scene_tensors(s3, torch.device("cuda", 0))
+    nb.rebuild(t3["pos"], t3["rho"], t3["mu"], t3["ptype"], s3.lo, s3.hi, s3.periodic, s3.h)
+    x3, rep3 = gpu_solve(nb, s3, binding.solve_opts(precision=binding.SPH_PREC_FP64))
+    assert rep3["status"] == 0
+    nb.close()
