@@ -470,7 +470,7 @@ def run_sphvisc(args):
                     apply_variant=prof["apply_variant"], apply_grid=prof["apply_grid"],
                     autotune_us=prof["tune_us"][:2],
                     algorithmic_bytes_per_launch=prof["apply_bytes"],
-                    timing="CUDA events on the solve stream around both applies of every 4th BiCGSTAB "
+                    timing="CUDA events on the solve stream around both applies of every 8th BiCGSTAB "
                            "iteration inside the timed region (launches after convergence excluded)")
     apply_forms = None
     channel = None

@@ -671,7 +671,7 @@ sph_status sph_mu_papanastasiou(sph_neighbors* handle, const float* vel, const f
 
 /* Instrumentation (tracing): launch counts and the device time of the operator
  * apply inside solves, measured with CUDA events recorded on the solve's own
- * stream around the two apply launches of every fourth BiCGSTAB iteration (a
+ * stream around the two apply launches of every eighth BiCGSTAB iteration (a
  * sample, so that the event records do not slow the loop they time).  Off by
  * default; enabling it adds two event records per sampled apply. */
 typedef struct {

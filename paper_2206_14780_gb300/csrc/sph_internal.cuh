@@ -382,7 +382,7 @@ sph_status bicgstab_replay(const double* gamma0, double eps, int32_t maxit, int3
 // when profiling is on (sampling keeps the event records from slowing the
 // loop they time); prof_flush folds the recorded pairs of launches that did
 // work into prof_ms (call only after a stream synchronisation)
-constexpr int kProfStride = 4;
+constexpr int kProfStride = 8;
 void prof_begin(sph_neighbors* H, cudaStream_t st, int phase = 0);
 void prof_end(sph_neighbors* H, cudaStream_t st);
 void prof_flush(sph_neighbors* H, int valid_launches);
