@@ -13,8 +13,9 @@ Everything here is plain, slow and in float64, written from the paper:
                  candidate search filtered by the same predicate
 * ``operator``   K_ab and the viscous matrix A(dt) for dummy and dynamic walls
                  (Eqs. kab, diag, offdiag, implicit-system-dyn-full,
-                 implicit-system-dummy-full), its Jacobi diagonal, A v and the
-                 true residual
+                 implicit-system-dummy-full), its Jacobi diagonal, A v, the
+                 true residual, the row norms of D^-1 A and the closed-form wall-row
+                 scale of the diagonal preconditioner-scale head
 * ``solvers``    textbook BiCGSTAB, the paper's restructured BiCGSTAB with its
                  per-component state machine (Sec. 4.2), the rotated CG (Sec. 4.1),
                  dense LU and a hand-written Gaussian elimination
@@ -22,7 +23,8 @@ Everything here is plain, slow and in float64, written from the paper:
                  Papanastasiou viscosity with the truncated series (Sec. 2.4)
 * ``mlp``        the warm-start network (forward, loss, backward) in float64,
                  optionally with the bf16 rounding points of the GPU kernels
-* ``features``   the sixteen per-particle inputs of that network
+* ``features``   the sixteen per-particle inputs of that network (shared by the
+                 warm start and the preconditioner-scale head)
 * ``warmstart``  x0 = v + U y with the dummy-wall closure (Eq. dummyvel), the
                  residual training loss and its MSE pseudo-targets
 * ``step``       one semi-implicit predictor/corrector step (Sec. 3.3): Cole's

@@ -10,7 +10,7 @@
 //
 // Also here: the squared norms of the rows of D^-1 A, 1 + sum_j (a_j / D)^2 over
 // a fluid row's coefficients (1 + sum_j S_j^2 over a dummy-wall row's Shepard
-// weights, 1 for an identity row); the closed-form scale factor norm2^-power on
+// weights, 1 for an identity row); the closed-form scale, factor x norm2^-power on
 // the dummy-wall rows only; and the learned scale, the warm-start network's
 // architecture evaluated on the same 16 features, whose first output is the log of
 // a wall row's scale.
