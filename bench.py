@@ -664,19 +664,44 @@ def run_gaussian(dev, n=100, reps=3):
     reps_ = [step() for _ in range(reps)]
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    step_ms = e0.elapsed_time(e1) / reps
     prof = nb.profile_read(reset=True)
     nb.profile(False)
     _, nnz, maxc = nb.info()
+    # the same solve with the closed-form wall-row scale of the preconditioner (constant
+    # 1/8 on the dummy-wall rows), from the same start
+    sc = torch.empty(s.n, dtype=torch.float32, device=dev)
+    nb.wall_row_scale(p, 0.125, 0.0, sc)
+    nb.set_row_scale(sc)
+    binding.warm_start(nb, p, None, t["vel"], t["ptype"], b, x)
+    nb.solve(p, opts, b, x)
+    binding.warm_start(nb, p, None, t["vel"], t["ptype"], b, x)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    rep_sc = nb.solve(p, opts, b, x)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    wall_scaled = dict(iters=rep_sc["iters"], solve_ms=e0.elapsed_time(e1), true_rel_res=rep_sc["true_rel_res"])
+    nb.set_row_scale(None)
+    binding.warm_start(nb, p, None, t["vel"], t["ptype"], b, x)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    rep_pl = nb.solve(p, opts, b, x)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    wall_scaled["jacobi_solve_ms"] = e0.elapsed_time(e1)
+    wall_scaled["jacobi_iters"] = rep_pl["iters"]
     nb.close()
     us = 1e3 * prof["apply_ms"] / max(1, prof["apply_launches"])
     hbm, kind = read_peaks()
     gbs = prof["apply_bytes"] / (us * 1e-6) / 1e9 if prof["apply_launches"] else None
     return dict(workload=f"lava box {n}^3 fluid, truncated Gaussian (k = 3, h = 1.3 dx), 4 dummy layers "
                          f"(N={s.n})", particles=s.n, neighbour_pairs=int(nnz), max_neighbours=int(maxc),
-                ms_per_step=e0.elapsed_time(e1) / reps, iters=[r["iters"] for r in reps_],
+                ms_per_step=step_ms, iters=[r["iters"] for r in reps_],
                 passes=reps_[0]["refinements"], max_true_rel_res=max(r["true_rel_res"] for r in reps_),
                 apply_us=us, apply_algorithmic_bytes=prof["apply_bytes"], apply_gbs=gbs,
-                apply_frac_of_hbm=(gbs / hbm) if gbs else None, peak_source=kind)
+                apply_frac_of_hbm=(gbs / hbm) if gbs else None, peak_source=kind,
+                wall_scale_c0_125=wall_scaled)
 
 
 # ------------------------------------------------- CG and sharded solve -------
