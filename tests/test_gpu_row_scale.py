@@ -304,3 +304,26 @@ def test_rebuild_keeps_the_scale_for_the_same_particles_and_drops_it_otherwise()
     x3, rep3 = gpu_solve(nb, s3, binding.solve_opts(precision=binding.SPH_PREC_FP64))
     assert rep3["status"] == 0
     nb.close()
+
+
+def test_learned_scale_entry_points_refuse_bad_arguments():
+    """The learned scale needs the Wendland kernel its features are written for; the
+    target builder checks factor and power like the closed form does."""
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    net, _ = _scale_net()
+    g = scenes.periodic_lattice(12, jitter=0.05, seed=2, kernel=scenes.KERNEL_GAUSSIAN)
+    nb, t = lib_build(g, max_neighbors=512)
+    with pytest.raises(RuntimeError):
+        binding.mlp_row_scale(nb, params_for(g), net, torch.from_numpy(g.vel).cuda(),
+                              torch.empty(g.n, dtype=torch.float32, device="cuda"))
+    nb.close()
+    s = scenes.couette(0)
+    nb, _ = lib_build(s)
+    tgt = torch.empty((s.n, 4), dtype=torch.float32, device="cuda")
+    mask = torch.empty(s.n, dtype=torch.uint8, device="cuda")
+    for factor, power in ((0.0, 1.0), (1.0, 65.0), (float("inf"), 0.0)):
+        with pytest.raises(RuntimeError):
+            binding.mlp_scale_targets(nb, params_for(s), factor, power, tgt, mask)
+    nb.close()

@@ -125,3 +125,19 @@ def test_shard_rejects_other_solver_options_and_a_changed_operator():
     sh.close()
     with pytest.raises(binding.SphError):
         binding.Shard(nb, params_for(s), 65)
+
+
+def test_striping_switch_takes_only_zero_or_one():
+    import ctypes
+
+    from paper_2206_14780_gb300 import binding
+
+    s = SHARD_SCENES["couette_dummy"]()
+    nb, _ = lib_build(s)
+    sh = binding.Shard(nb, params_for(s), 2)
+    lib = binding.load()
+    assert lib.sph_shard_set_striping(sh.handle, 2) == 1
+    assert lib.sph_shard_set_striping(sh.handle, 1) == 0
+    assert lib.sph_shard_set_striping(None, 1) == 1
+    sh.close()
+    nb.close()
