@@ -493,6 +493,18 @@ def run_sphvisc(args):
     sequence = None
     if not args.no_sequence and world == 1:
         sequence = run_sequence(nb, s, b, t, args.sequence_steps, dev)
+        heads = _scale_heads()
+        if "learned_scale" in heads:
+            # the same sequence with the learned wall-row scale, computed once from v^0
+            # (positions, and so the operator, stay frozen over the sequence)
+            torch.cuda.synchronize(dev)
+            w0_ = time.perf_counter()
+            heads["learned_scale"](nb, binding.visc_params(s.dt, s.boundary, s.mean), t, None)
+            torch.cuda.synchronize(dev)
+            scale_ms = 1e3 * (time.perf_counter() - w0_)
+            sequence["learned_scale"] = run_sequence(nb, s, b, t, args.sequence_steps, dev)
+            sequence["learned_scale"]["scale_setup_ms"] = scale_ms
+            nb.set_row_scale(None)
     ensemble = None
     if not args.no_ensemble and world == 1:
         nb.close()
