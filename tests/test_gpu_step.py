@@ -169,3 +169,35 @@ def test_picard_step_matches_oracle():
     err = np.linalg.norm(u[fl] - info["u_new"][fl]) / np.linalg.norm(info["u_new"][fl])
     assert err < 1e-5, err
     np.testing.assert_allclose(t["mu"].cpu().numpy()[fl], new.mu[fl], rtol=1e-4)
+
+
+def test_step_with_a_row_scale_keeps_the_oracles_step():
+    """A preconditioner row scale on the stepper's handle (kept across the step's
+    neighbour and operator rebuilds) changes how the two solves converge, not what they
+    converge to: the second step still matches the oracle's step from the first step's
+    state."""
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    make, prm = STEP_CASES["couette_dummy"]
+    s = make()
+    st, t = _stepper(s)
+    opts = binding.solve_opts(rtol=1e-10, eps_inner=1e-3)
+    assert st.step(_params(s, prm), opts)["status"] == 0
+    s1 = s.copy()
+    s1.pos = t["pos"].cpu().numpy()
+    s1.vel = t["vel"].cpu().numpy()
+    s1.rho = t["rho"].cpu().numpy()
+    s1.mu = t["mu"].cpu().numpy()
+    sc = torch.from_numpy(np.random.default_rng(5).uniform(0.1, 1.0, s.n).astype(np.float32)).cuda()
+    lib = binding.load()
+    assert lib.sph_set_row_scale(st.handle, sc.data_ptr(), None) == 0
+    rep = st.step(_params(s1, prm), opts)
+    st.close()
+    assert rep["status"] == 0, rep
+    new, info = ostep.step(s1, prm)
+    fl = s.ptype == scenes.FLUID
+    u = t["vel"].cpu().numpy()[:, :3].astype(np.float64)
+    err_u = np.linalg.norm(u[fl] - info["u_new"][fl]) / np.linalg.norm(info["u_new"][fl])
+    assert err_u < 1e-5, err_u
+    np.testing.assert_allclose(t["rho"].cpu().numpy().astype(np.float64), new.rho.astype(np.float64), rtol=2e-6)
