@@ -531,9 +531,10 @@ sph_status sph_mlp_destroy(sph_mlp* mlp);
  * `handle` for velocities vel (device, [n][4] float): v/U, the Jacobi-scaled
  * explicit viscous increment D^-1 (v - A v) / U and its second application,
  * log10(mu)/5, log10(1 + dt sum c)/4 (on a wall row: of the mean over its fluid
- * neighbours), nearest wall neighbour / 2h, the Shepard
- * sum of W V, neighbour count / 80, |v| relative to the neighbourhood RMS, and
- * the wall flag.  scale_out (host, may be NULL): U = RMS |v| over the fluid. */
+ * neighbours), nearest wall neighbour / 2h (at most 1), the Shepard sum of W V
+ * (W of the handle's kernel), neighbour count / 80, |v| relative to the
+ * neighbourhood RMS, and the wall flag.  scale_out (host, may be NULL): U = RMS |v|
+ * over the fluid. */
 sph_status sph_mlp_features(sph_neighbors* handle, const sph_visc_params* params, const float* vel,
                             uint16_t* feats, double* scale_out, void* stream);
 
@@ -646,7 +647,7 @@ sph_status sph_wall_row_scale(sph_neighbors* handle, const sph_visc_params* para
  * sph_set_row_scale.  scale may be NULL: the learned scale then becomes the
  * handle's row scale directly, as sph_set_row_scale would make it, without the
  * check and the synchronisation (its values are positive and finite by
- * construction).  Wendland kernel only (SPH_ERR_INVALID otherwise). */
+ * construction).  Either kernel (the Shepard feature uses the handle's W). */
 sph_status sph_mlp_row_scale(sph_neighbors* handle, const sph_visc_params* params, const sph_mlp* mlp,
                              const float* vel, float* scale, void* stream);
 

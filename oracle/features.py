@@ -10,7 +10,7 @@ feature set is this project's choice, listed in the library header):
   10   log10(D) / 4; on a wall row (D = 1) log10 of the mean D of its fluid neighbours / 4
        (0 without one)
   11   min over wall neighbours of r / (2h), 1 without one
-  12   W(0) V_b + sum over fluid neighbours of W_ba V_a
+  12   W(0) V_b + sum over fluid neighbours of W_ba V_a (W of the scene's kernel)
   13   neighbour count / 80
   14   |v_b| / (|v_b| + sqrt(mean over neighbours of |v_a|^2))
   15   1 for wall particles
@@ -38,6 +38,7 @@ def features(scene, offsets, idx, A, vel=None):
     F[:, 9] = np.log10(np.asarray(scene.mu, np.float32).astype(np.float64)) / 5.0
     F[:, 10] = np.log10(D) / 4.0
     h = float(np.float32(scene.h))
+    kid = getattr(scene, "kernel", kernel.WENDLAND)
     m = np.asarray(scene.pos, np.float32)[:, 3].astype(np.float64)
     rho = np.asarray(scene.rho, np.float32).astype(np.float64)
     V = m / rho
@@ -46,7 +47,7 @@ def features(scene, offsets, idx, A, vel=None):
         r = np.sqrt(neighbors.pair_r2(scene.pos, nb, np.full(nb.shape, b), scene.lo, scene.hi, scene.periodic))
         wall = ~fl[nb]
         F[b, 11] = min(1.0, (r[wall] / (2 * h)).min()) if wall.any() else 1.0
-        F[b, 12] = kernel.W(0.0, h) * V[b] + (kernel.W(r[~wall], h) * V[nb[~wall]]).sum()
+        F[b, 12] = kernel.W(0.0, h, kid) * V[b] + (kernel.W(r[~wall], h, kid) * V[nb[~wall]]).sum()
         F[b, 13] = len(nb) / 80.0
         if not fl[b]:
             F[b, 10] = np.log10(D[nb[~wall]].mean()) / 4.0 if (~wall).any() else 0.0

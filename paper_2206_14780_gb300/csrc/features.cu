@@ -203,8 +203,18 @@ __global__ void __launch_bounds__(kBlock) k_highpass_T(const float4* __restrict_
 struct FeatGeom {
   float L[3], invL[3];
   int periodic[3];
-  float inv_h, inv_2h, w_scale;  // w_scale = 21/(16 pi) / h^3
+  float inv_h, inv_2h, w_scale;  // Wendland: w_scale = 21/(16 pi) / h^3
+  int gauss;                     // truncated Gaussian: W = w_scale (e^{-q^2} - g_tail), w_scale = 1/(w_G h^3)
+  float g_tail;
 };
+
+// W(r) of the handle's kernel for q = r / h inside the support
+__device__ __forceinline__ float feat_w(const FeatGeom& g, float q) {
+  if (g.gauss) return g.w_scale * (__expf(-q * q) - g.g_tail);
+  const float tq = fmaxf(1.f - 0.5f * q, 0.f);
+  const float t2 = tq * tq;
+  return g.w_scale * t2 * t2 * (2.f * q + 1.f);
+}
 
 __global__ void __launch_bounds__(kBlock) k_features(const float4* __restrict__ pos, const float* __restrict__ rho,
                                                      const float* __restrict__ mu, const uint8_t* __restrict__ type,
@@ -229,7 +239,7 @@ __global__ void __launch_bounds__(kBlock) k_features(const float4* __restrict__ 
     const float4 vb = v[s];
     const int c = cnt[s];
     const int64_t base = slice_off[s / kSlice] + (s % kSlice);
-    float dmin = 1.f, shep = g.w_scale * (pb.w / rho[s]), v2 = 0.f;
+    float dmin = 1.f, shep = feat_w(g, 0.f) * (pb.w / rho[s]), v2 = 0.f;
     double dsum = 0.0;   // D over the fluid neighbours (feature 10 of a wall row)
     int nfl = 0;
     for (int j = 0; j < c; ++j) {
@@ -241,10 +251,7 @@ __global__ void __launch_bounds__(kBlock) k_features(const float4* __restrict__ 
         if (g.periodic[ax]) d[ax] -= g.L[ax] * rintf(d[ax] * g.invL[ax]);
       const float r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
       if (type[t] == SPH_FLUID) {
-        const float q = r * g.inv_h;
-        const float tq = fmaxf(1.f - 0.5f * q, 0.f);
-        const float t2 = tq * tq;
-        shep += g.w_scale * t2 * t2 * (2.f * q + 1.f) * (pa.w / rho[t]);
+        shep += feat_w(g, r * g.inv_h) * (pa.w / rho[t]);
         dsum += D64[t];
         ++nfl;
       } else {
@@ -437,7 +444,9 @@ sph_status features_impl(sph_neighbors* H, const sph_visc_params* P, const float
   const double h = (double)H->h;
   g.inv_h = (float)(1.0 / h);
   g.inv_2h = (float)(0.5 / h);
-  g.w_scale = (float)(21.0 / (16.0 * M_PI) / (h * h * h));
+  g.gauss = H->kernel == SPH_KERNEL_GAUSSIAN ? 1 : 0;
+  g.w_scale = (float)(g.gauss ? 1.0 / (gauss_norm() * h * h * h) : 21.0 / (16.0 * M_PI) / (h * h * h));
+  g.g_tail = (float)std::exp(-kGaussK * kGaussK);
   SPH_LAUNCH(k_features, grid_for(H, H->n), kBlock, 0, st)(H->pos_s.p, H->rho_s.p, H->mu_s.p, H->type_s.p, H->D64.p,
                                                            H->cnt.p, H->slice_off.p, H->nbr.p, H->perm.p, vs, e1, e2,
                                                            H->n, g, H->feat_scale.p, walls_only ? 1 : 0, feats);
@@ -500,10 +509,7 @@ sph_status sph_mlp_features(sph_neighbors* h, const sph_visc_params* params, con
     set_error("sph_mlp_features: null argument");
     return SPH_ERR_INVALID;
   }
-  if (h->kernel != SPH_KERNEL_WENDLAND) {
-    set_error("sph_mlp_features: the network's features are written for the Wendland kernel");
-    return SPH_ERR_INVALID;
-  }
+
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   SPH_TRY(features_impl(h, params, vel, reinterpret_cast<__nv_bfloat16*>(feats), st, false));
   if (scale_out) {
@@ -558,7 +564,7 @@ sph_status sph_warm_start(sph_neighbors* h, const sph_visc_params* params, const
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const float4* delta = nullptr;
   if (mlp && h->kernel != SPH_KERNEL_WENDLAND) {
-    set_error("sph_warm_start: the network's features are written for the Wendland kernel (pass no network)");
+    set_error("sph_warm_start: the warm-start network takes Wendland-kernel scenes (pass no network)");
     return SPH_ERR_INVALID;
   }
   if (mlp) {
@@ -602,7 +608,7 @@ sph_status sph_mlp_residual_targets(sph_neighbors* h, const sph_visc_params* par
     return SPH_ERR_INVALID;
   }
   if (h->kernel != SPH_KERNEL_WENDLAND) {
-    set_error("sph_mlp_residual_targets: the network's features are written for the Wendland kernel");
+    set_error("sph_mlp_residual_targets: the warm-start network takes Wendland-kernel scenes");
     return SPH_ERR_INVALID;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -223,10 +223,6 @@ sph_status sph_mlp_row_scale(sph_neighbors* h, const sph_visc_params* params, co
     set_error("sph_mlp_row_scale: null argument");
     return SPH_ERR_INVALID;
   }
-  if (h->kernel != SPH_KERNEL_WENDLAND) {
-    set_error("sph_mlp_row_scale: the network's features are written for the Wendland kernel");
-    return SPH_ERR_INVALID;
-  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   SPH_TRY(h->feat_out.alloc(h->n * 8));      // bf16 features [n][16]
   SPH_TRY(h->feat_delta.alloc(h->n));        // float4 network outputs

@@ -52,19 +52,25 @@ class Family:
         from paper_2206_14780_gb300 import binding
 
         self.kind = kind
+        gauss = kind.endswith("_gauss")      # the truncated Gaussian kernel (4 dummy layers)
+        kind = kind[:-6] if gauss else kind
         big = kind.endswith("_big")
         kind = kind[:-4] if big else kind
         self.kind = kind
+        kw = dict(kernel=scenes.KERNEL_GAUSSIAN, layers=4) if gauss else {}
         if kind == "couette":
-            self.scene = scenes.couette(seed, nx=40, ny=20, nz=40) if big else scenes.couette(seed)
+            if gauss:
+                self.scene = scenes.couette(seed, nx=40 if big else 20, ny=20 if big else 10, nz=40 if big else 16, **kw)
+            else:
+                self.scene = scenes.couette(seed, nx=40, ny=20, nz=40) if big else scenes.couette(seed)
         elif kind == "slope":
             self.scene = scenes.slope(seed, nx=32, ny=20, nz=32) if big else scenes.slope(seed, nx=16, ny=10, nz=16)
         else:
-            self.scene = scenes.lava_box(seed, n=32 if big else 16)
+            self.scene = scenes.lava_box(seed, n=32 if big else 16, **kw)
         s = self.scene
         self.t = binding.scene_tensors(s, dev)
         self.nb = binding.build_neighbors(self.t["pos"], self.t["rho"], self.t["mu"], self.t["ptype"], s.lo, s.hi,
-                                          s.periodic, s.h)
+                                          s.periodic, s.h, max_neighbors=512 if gauss else 128, kernel=s.kernel)
         self.dev = dev
         self.fl = np.flatnonzero(s.ptype == scenes.FLUID)
         self.fl_t = torch.from_numpy(self.fl).to(dev)

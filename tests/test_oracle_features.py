@@ -114,3 +114,18 @@ def test_wall_rows_carry_the_stiffness_of_their_fluid_neighbours():
     assert near.sum() > 0 and (~fl & (k == 0)).sum() > 0
     np.testing.assert_allclose(F[near, 10], np.log10(D) / 4.0, rtol=1e-6)
     np.testing.assert_array_equal(F[(~fl) & (k == 0), 10], 0.0)
+
+
+@pytest.mark.parametrize("kern,tol", [(scenes.KERNEL_GAUSSIAN, 2e-4), (scenes.KERNEL_WENDLAND, 2e-2)])
+def test_shepard_feature_is_a_partition_of_unity_on_a_lattice(kern, tol):
+    """Feature 12 (W(0) V_b + sum W_ba V_a with the scene's own kernel) on a perfect periodic
+    lattice is the lattice quadrature of the kernel's unit integral: 1 up to the
+    quadrature error, at h = 1.3 dx about 1e-4 for the truncated Gaussian (a smooth
+    Gaussian would sum to 1 within exp(-pi^2 h^2 / dx^2) ~ 1e-7, but the truncation at 3h
+    leaves a slope jump of 6 e^-9 ~ 7e-4 at the support edge) and about 1% for the
+    Wendland kernel; a Shepard sum written with the wrong kernel misses by far more."""
+    s = scenes.periodic_lattice(12, kernel=kern)
+    off, idx = onb.build(s.pos, s.lo, s.hi, s.periodic, s.h, kernel_id=kern)
+    A = oop.assemble(s, off, idx)
+    F, _ = ofeat.features(s, off, idx, A)
+    np.testing.assert_allclose(F[:, 12], 1.0, rtol=0, atol=tol)
