@@ -35,9 +35,11 @@ if ROOT not in sys.path:
 from paper_2206_14780_gb300.train_warmstart import Family, _init_params  # noqa: E402
 
 DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "scale_head_mlp.npz")
-# training geometries: (family, seed); sizes from 3.2k to 40k particles
+# training geometries: (family, seed); sizes from 3.2k to 45k particles; _gauss: the truncated
+# Gaussian kernel with 4 dummy layers
 GEOMETRIES = [("couette", 0), ("couette", 1), ("couette_big", 2), ("box", 3), ("box", 4), ("box_big", 5),
-              ("box_big", 6), ("slope", 7), ("slope_big", 8)]
+              ("box_big", 6), ("slope", 7), ("slope_big", 8), ("couette_gauss", 9), ("box_gauss", 10),
+              ("box_big_gauss", 11)]
 
 
 def _closure_x0(fam, p, vt, bt):
@@ -134,7 +136,8 @@ def evaluate(net, n, seed, dev, fixed=((1.0, 3.0), (0.125, 0.0))):
     from paper_2206_14780_gb300 import binding
 
     rng = np.random.default_rng(seed)
-    fams = [Family(k, 100 + j + seed, dev) for j, k in enumerate(["couette", "box_big", "slope_big", "box"])]
+    fams = [Family(k, 100 + j + seed, dev) for j, k in enumerate(["couette", "box_big", "slope_big", "box",
+                                                                   "box_gauss"])]
     opts = binding.solve_opts()
     keys = ["jacobi"] + [f"c{f:g}_p{pw:g}" for f, pw in fixed] + ["learned"]
     its = {k: [] for k in keys}

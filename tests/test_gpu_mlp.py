@@ -122,18 +122,19 @@ def test_training_reduces_loss():
 
 
 @pytest.mark.parametrize("make", [lambda: scenes.couette(2), lambda: scenes.lava_box(3, n=10),
-                                  lambda: scenes.slope_subset(1, nx=12, ny=8, nz=12)])
+                                  lambda: scenes.slope_subset(1, nx=12, ny=8, nz=12),
+                                  lambda: scenes.lava_box(4, n=10, layers=4, kernel=scenes.KERNEL_GAUSSIAN)])
 def test_features_match_oracle(make):
     torch = torch_cuda()
     from paper_2206_14780_gb300 import binding
 
     s = make()
-    nb, t = lib_build(s)
+    nb, t = lib_build(s, max_neighbors=512 if s.kernel == scenes.KERNEL_GAUSSIAN else 128)
     vel = torch.from_numpy(s.vel).cuda()
     f = torch.empty((s.n, 16), dtype=torch.int16, device="cuda")
     U = binding.mlp_features(nb, params_for(s), vel, f)
     F = f.view(torch.bfloat16).float().cpu().numpy().astype(np.float64)
-    off, idx = onb.build(s.pos, s.lo, s.hi, s.periodic, s.h)
+    off, idx = onb.build(s.pos, s.lo, s.hi, s.periodic, s.h, kernel_id=s.kernel)
     A = oop.assemble(s, off, idx)
     Fr, Ur = ofeat.features(s, off, idx, A)
     assert abs(U - Ur) <= 1e-6 * Ur

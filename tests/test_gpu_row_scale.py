@@ -306,18 +306,21 @@ def test_rebuild_keeps_the_scale_for_the_same_particles_and_drops_it_otherwise()
     nb.close()
 
 
-def test_learned_scale_entry_points_refuse_bad_arguments():
-    """The learned scale needs the Wendland kernel its features are written for; the
-    target builder checks factor and power like the closed form does."""
+def test_learned_scale_entry_points_take_either_kernel_and_refuse_bad_arguments():
+    """The learned scale runs on a truncated-Gaussian handle too (its features use the
+    handle's kernel): positive finite scales, 1 on fluid rows; the target builder checks
+    factor and power like the closed form does."""
     torch = torch_cuda()
     from paper_2206_14780_gb300 import binding
 
     net, _ = _scale_net()
-    g = scenes.periodic_lattice(12, jitter=0.05, seed=2, kernel=scenes.KERNEL_GAUSSIAN)
+    g = scenes.lava_box(3, n=10, layers=4, kernel=scenes.KERNEL_GAUSSIAN)
     nb, t = lib_build(g, max_neighbors=512)
-    with pytest.raises(RuntimeError):
-        binding.mlp_row_scale(nb, params_for(g), net, torch.from_numpy(g.vel).cuda(),
-                              torch.empty(g.n, dtype=torch.float32, device="cuda"))
+    sc = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    binding.mlp_row_scale(nb, params_for(g), net, torch.from_numpy(g.vel).cuda(), sc)
+    v = sc.cpu().numpy()
+    assert np.all(np.isfinite(v)) and np.all(v > 0)
+    np.testing.assert_array_equal(v[g.ptype == scenes.FLUID], 1.0)
     nb.close()
     s = scenes.couette(0)
     nb, _ = lib_build(s)
