@@ -88,6 +88,14 @@ def test_gaussian_rejections_and_capacity():
     y = torch.empty_like(v)
     with pytest.raises(binding.SphError):
         nb.apply_otf(params_for(s), v, y)
-    feats = torch.empty((s.n, 16), dtype=torch.int16, device="cuda")
+    # the warm-start network takes Wendland scenes only (its features run on either kernel)
+    import numpy as np
+
+    net = binding.Mlp(np.zeros(binding.MLP_NPARAMS, np.float32))
+    b = torch.zeros((s.n, 3), dtype=torch.float64, device="cuda")
+    x0 = torch.empty_like(b)
     with pytest.raises(binding.SphError):
-        binding.mlp_features(nb, params_for(s), v, feats)
+        binding.warm_start(nb, params_for(s), net, v, t["ptype"], b, x0)
+    feats = torch.empty((s.n, 16), dtype=torch.int16, device="cuda")
+    binding.mlp_features(nb, params_for(s), v, feats)
+    net.close()
