@@ -201,3 +201,41 @@ def test_step_with_a_row_scale_keeps_the_oracles_step():
     err_u = np.linalg.norm(u[fl] - info["u_new"][fl]) / np.linalg.norm(info["u_new"][fl])
     assert err_u < 1e-5, err_u
     np.testing.assert_allclose(t["rho"].cpu().numpy().astype(np.float64), new.rho.astype(np.float64), rtol=2e-6)
+
+
+@pytest.mark.slow
+def test_papanastasiou_poiseuille_flow_reaches_the_bingham_profile():
+    """The plane Poiseuille flow of a Papanastasiou fluid of Sec. 5.4 (Wendland, dummy
+    walls, dp = 1/16, mu0 = 0.1 Pa s, tau0 = 0.0125 Pa, m = 1000 s), the viscosity
+    recomputed from the velocities every step, from rest to t = 10 s: its l1 and l2
+    errors against the non-regularised Bingham profile (plug |z| < tau0 / (rho0 g) at
+    u_p = 1.5625e-2 m/s) within twice the paper's table for this configuration, the
+    flow one-directional and the plug the fastest part of the profile."""
+    from paper_2206_14780_gb300 import binding
+
+    gold = dict(l.split() for l in open(os.path.join(GOLDEN, "poiseuille_papanastasiou_wendland_dummy_dp16.txt"))
+                if l.strip() and not l.startswith("#"))
+    gold = {k: float(v) for k, v in gold.items()}
+    dx, g, mu0, tau0, m, L = 1.0 / 16, 0.05, 0.1, 0.0125, 1000.0, 1.0
+    s = scenes.couette(0, nx=8, ny=16, nz=8, dx=dx, rho0=1.0, nu=mu0, dt=1e-2, U=0.0, noise=0.0)
+    s.vel[:] = 0.0
+    st, t = _stepper(s)
+    dt = 2.5e-3
+    prm = binding.step_params(dt, 1.0, 6.32, 7.0, (g, 0.0, 0.0), s.boundary, s.mean, rheology=(tau0, mu0, m))
+    opts = binding.solve_opts(rtol=1e-8)
+    for _ in range(int(round(10.0 / dt))):
+        assert st.step(prm, opts)["status"] == 0
+    st.close()
+    fl = s.ptype == scenes.FLUID
+    z = t["pos"].cpu().numpy()[fl, 1].astype(np.float64) - 0.5 * L
+    u = t["vel"].cpu().numpy()[fl, 0].astype(np.float64)
+    zp = tau0 / g
+    u_plug = (0.5 * L - zp) * (g * 0.5 * L - tau0) / (2.0 * mu0)
+    assert abs(u_plug - 1.5625e-2) < 1e-12
+    az = np.abs(z)
+    exact = np.where(az >= zp, 0.5 * g / mu0 * (0.25 * L * L - z * z) - tau0 / mu0 * (0.5 * L - az), u_plug)
+    e = u - exact
+    l1, l2 = np.abs(e).mean(), np.sqrt((e * e).mean())
+    assert l1 < 2.0 * gold["l1"] and l2 < 2.0 * gold["l2"], (l1, l2, gold)
+    assert np.abs(t["vel"].cpu().numpy()[fl, 1:3]).max() < 5e-3 * u_plug
+    assert u[az < 0.5 * zp].min() > u[az > 0.5 * L - 2 * dx].max()
