@@ -485,7 +485,6 @@ def run_sphvisc(args):
     poiseuille = None
     if world == 1 and not args.no_poiseuille:
         poiseuille = run_poiseuille(dev)
-        poiseuille["papanastasiou"] = run_poiseuille_papanastasiou(dev)
     cg = shard = None
     if world == 1 and not args.no_cg:
         cg = run_cg(dev)
@@ -865,31 +864,55 @@ def run_shard(dev, n=60, ranks=(1, 2, 4)):
 
 # ------------------------------------------------------ Poiseuille flow -------
 
-POISEUILLE_PAPER = {"l1": 1.227e-3, "l2": 1.282e-3, "l1_102": 3.916e-4, "l2_102": 3.929e-4}
-POISEUILLE_PAPA_PAPER = {"l1": 4.724e-3, "l2": 4.815e-3}
+# the paper's numbers at dp = 1/16 (Sec. 5.3, Table tab:newton-error and Table tab:newton-times;
+# Sec. 5.4, Table tab:papa-error and Table tab:papa-times): the l1 and l2 errors of the steady
+# profile (and, for Wendland, against 102% of it) and the semi-implicit runtime in seconds of the
+# whole run to t = 10 s on the paper's machine
+POISEUILLE_PAPER = {
+    "newton_wendland_dummy": {"l1": 1.227e-3, "l2": 1.282e-3, "l1_102": 3.916e-4, "l2_102": 3.929e-4,
+                              "runtime_s": 33.0},
+    "newton_wendland_dynamic": {"l1": 1.210e-3, "l2": 1.325e-3, "l1_102": 4.288e-4, "l2_102": 4.576e-4,
+                                "runtime_s": 24.0},
+    "newton_gaussian_dummy": {"l1": 3.615e-4, "l2": 3.713e-4, "runtime_s": 68.0},
+    "newton_gaussian_dynamic": {"l1": 2.083e-3, "l2": 2.153e-3, "runtime_s": 46.0},
+    "papanastasiou_wendland_dummy": {"l1": 4.724e-3, "l2": 4.815e-3, "runtime_s": 95.0},
+    "papanastasiou_wendland_dynamic": {"l1": 3.009e-3, "l2": 3.232e-3, "runtime_s": 74.0},
+    "papanastasiou_gaussian_dummy": {"l1": 7.027e-3, "l2": 7.227e-3, "runtime_s": 180.0},
+    "papanastasiou_gaussian_dynamic": {"l1": 4.569e-3, "l2": 4.769e-3, "runtime_s": 130.0},
+}
 
 
-def run_poiseuille_papanastasiou(dev, t_end=10.0, dt=2.5e-3):
-    """The plane Poiseuille flow of a Papanastasiou fluid (Sec. 5.4) with the full
-    semi-implicit step: Wendland h = 1.3 dp, dummy walls, dp = 1/16, mu0 = 0.1 Pa s,
-    tau0 = 0.0125 Pa, m = 1000 s, the rest as the Newtonian case, viscosity recomputed
-    from the velocities each step.  The l1 and l2 errors of the steady profile against
-    the non-regularised Bingham solution, next to the paper's table (Sec. 5.4, Wendland,
-    dummy, 1/16)."""
+def run_poiseuille_case(dev, case, t_end=10.0):
+    """One plane Poiseuille flow of Sec. 5 with the full semi-implicit step (sph_step),
+    from rest to the viscous relaxation time t = 10 s: L = 1 m, g = 0.05 m/s^2,
+    rho0 = 1 kg/m^3, c0 = 6.32 m/s, h = 1.3 dp, dp = 1/16, dt = 0.3 h / c0 (the
+    sound-speed limit of Tables tab:newton-times and tab:papa-times), the wall layout of
+    Sec. 5.2 for the boundary model.  Newtonian: mu = 0.1 Pa s, profile
+    u(z) = rho0 g / (2 mu) (L^2/4 - z^2).  Papanastasiou (Sec. 5.4): mu0 = 0.1 Pa s,
+    tau0 = 0.0125 Pa, m = 1000 s, the viscosity recomputed from the velocities each
+    step, compared with the non-regularised Bingham profile (plug |z| < tau0 / (rho0 g)).
+    The l1 and l2 errors and the device time of the whole run, beside the paper's."""
     import numpy as np
     import torch
 
     import scenes
     from paper_2206_14780_gb300 import binding
 
-    dx, g, mu0, tau0, m, L = 1.0 / 16, 0.05, 0.1, 0.0125, 1000.0, 1.0
-    s = scenes.couette(0, nx=8, ny=16, nz=8, dx=dx, rho0=1.0, nu=mu0, dt=dt, U=0.0, noise=0.0)
-    s.vel[:] = 0.0
+    rheo, kname, bname = case.split("_")
+    kern = scenes.KERNEL_GAUSSIAN if kname == "gaussian" else scenes.KERNEL_WENDLAND
+    bc = scenes.BC_DYNAMIC if bname == "dynamic" else scenes.BC_DUMMY
+    g, mu0, tau0, m, c0 = 0.05, 0.1, 0.0125, 1000.0, 6.32
+    s = scenes.poiseuille(bc, kern)
+    L = s.meta["L"]
+    dt = 0.3 * s.h / c0
+    steps = int(np.ceil(t_end / dt))
     t = {k: torch.from_numpy(getattr(s, k).copy()).to(dev) for k in ("pos", "vel", "rho", "mu", "ptype")}
-    st = binding.Stepper(t["pos"], t["vel"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
-    prm = binding.step_params(dt, 1.0, 6.32, 7.0, (g, 0.0, 0.0), s.boundary, s.mean, rheology=(tau0, mu0, m))
+    st = binding.Stepper(t["pos"], t["vel"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h,
+                         kernel=kern)
+    prm = binding.step_params(dt, 1.0, c0, 7.0, (g, 0.0, 0.0), s.boundary, s.mean,
+                              max_neighbors=512 if kern == scenes.KERNEL_GAUSSIAN else 128,
+                              rheology=(tau0, mu0, m) if rheo == "papanastasiou" else None)
     opts = binding.solve_opts(rtol=1e-8)
-    steps = int(round(t_end / dt))
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
@@ -902,64 +925,31 @@ def run_poiseuille_papanastasiou(dev, t_end=10.0, dt=2.5e-3):
     torch.cuda.synchronize(dev)
     st.close()
     fl = s.ptype == scenes.FLUID
-    z = t["pos"].cpu().numpy()[fl, 1].astype(np.float64) - 0.5 * L
+    z = t["pos"].cpu().numpy()[fl, 1].astype(np.float64) - s.meta["centre"]
     u = t["vel"].cpu().numpy()[fl, 0].astype(np.float64)
-    zp = tau0 / g
-    u_plug = (0.5 * L - zp) * (g * 0.5 * L - tau0) / (2.0 * mu0)
-    az = np.abs(z)
-    exact = np.where(az >= zp, 0.5 * g / mu0 * (0.25 * L * L - z * z) - tau0 / mu0 * (0.5 * L - az), u_plug)
-    e = u - exact
-    return dict(workload=f"plane Poiseuille, Papanastasiou, dp = 1/16, {int(fl.sum())} fluid + {int((~fl).sum())} "
-                         f"dummy wall particles, {steps} steps of dt = {dt} to t = {t_end} s", steps=steps,
-                ms_per_step=e0.elapsed_time(e1) / steps, iterations_per_step=its / steps, u_max=float(u.max()),
-                u_plug_bingham=u_plug, paper=POISEUILLE_PAPA_PAPER, l1=float(np.abs(e).mean()),
-                l2=float(np.sqrt((e * e).mean())))
-
-
-def run_poiseuille(dev, t_end=10.0, dt=2.5e-3):
-    """The plane Poiseuille flow of Sec. 5 with the full semi-implicit step (sph_step):
-    Newtonian, Wendland h = 1.3 dp, dummy walls, dp = 1/16, L = 1 m, g = 0.05 m/s^2,
-    mu = 0.1 Pa s, rho0 = 1 kg/m^3, c0 = 6.32 m/s, from rest to t = 10 s.  The l1 and l2
-    errors of the steady profile against u(z) = rho0 g / (2 mu) (L^2/4 - z^2) and
-    against 102% of it, next to the paper's table (Sec. 5.3, Wendland, dummy, 1/16)."""
-    import numpy as np
-    import torch
-
-    import scenes
-    from paper_2206_14780_gb300 import binding
-
-    dx, g, mu, L = 1.0 / 16, 0.05, 0.1, 1.0
-    s = scenes.couette(0, nx=8, ny=16, nz=8, dx=dx, rho0=1.0, nu=mu, dt=dt, U=0.0, noise=0.0)
-    s.vel[:] = 0.0
-    t = {k: torch.from_numpy(getattr(s, k).copy()).to(dev) for k in ("pos", "vel", "rho", "mu", "ptype")}
-    st = binding.Stepper(t["pos"], t["vel"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h)
-    prm = binding.step_params(dt, 1.0, 6.32, 7.0, (g, 0.0, 0.0), s.boundary, s.mean)
-    opts = binding.solve_opts(rtol=1e-8)
-    steps = int(round(t_end / dt))
-    stream = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    its = 0
-    for _ in range(steps):
-        rep = st.step(prm, opts)
-        its += rep["half"]["iters"] + rep["full"]["iters"]
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    st.close()
-    fl = s.ptype == scenes.FLUID
-    z = t["pos"].cpu().numpy()[fl, 1].astype(np.float64) - 0.5 * L
-    u = t["vel"].cpu().numpy()[fl, 0].astype(np.float64)
-    exact = 0.5 * g / mu * (0.25 * L * L - z * z)
-    out = dict(workload=f"plane Poiseuille, dp = 1/16, {int(fl.sum())} fluid + {int((~fl).sum())} dummy wall particles, "
-                        f"{steps} steps of dt = {dt} to t = {t_end} s", steps=steps,
-               ms_per_step=e0.elapsed_time(e1) / steps, iterations_per_step=its / steps,
-               u_max=float(u.max()), u_max_exact=float(exact.max()), paper=POISEUILLE_PAPER)
+    exact = 0.5 * g / mu0 * (0.25 * L * L - z * z)
+    if rheo == "papanastasiou":
+        zp = tau0 / g
+        az = np.abs(z)
+        u_plug = (0.5 * L - zp) * (g * 0.5 * L - tau0) / (2.0 * mu0)
+        exact = np.where(az >= zp, exact - tau0 / mu0 * (0.5 * L - az), u_plug)
+    paper = POISEUILLE_PAPER[case]
+    out = dict(workload=f"{int(fl.sum())} fluid + {int((~fl).sum())} {bname} wall particles, {steps} steps of "
+                        f"dt = {dt:.4g} s to t = {t_end} s", steps=steps, dt=dt,
+               run_s=e0.elapsed_time(e1) / 1e3, ms_per_step=e0.elapsed_time(e1) / steps,
+               iterations_per_step=its / steps, u_max=float(u.max()), u_max_exact=float(exact.max()), paper=paper)
     for f, k1, k2 in ((1.0, "l1", "l2"), (1.02, "l1_102", "l2_102")):
+        if k1 not in paper:
+            continue
         e = u - f * exact
         out[k1] = float(np.abs(e).mean())
         out[k2] = float(np.sqrt((e * e).mean()))
     return out
+
+
+def run_poiseuille(dev):
+    """Every dp = 1/16 configuration of POISEUILLE_PAPER, one full run each."""
+    return {case: run_poiseuille_case(dev, case) for case in POISEUILLE_PAPER}
 
 
 # --------------------------------------------------------- network forward ----

@@ -207,6 +207,30 @@ def couette(seed: int = 0, nx: int = 20, ny: int = 10, nz: int = 10, dx: float =
                      v, boundary=boundary, meta=dict(seed=seed, U=U, H=H, nu=nu), kernel=kernel)
 
 
+def poiseuille(boundary: int = BC_DUMMY, kernel: int = KERNEL_WENDLAND, inv_dp: int = 16,
+               L: float = 1.0, mu: float = 0.1, dt: float = 1e-2) -> Scene:
+    """Plane Poiseuille channel of width L at rest, laid out as Sec. 5.2 does for each
+    boundary model (rho0 = 1 kg/m^3).
+
+    Dummy walls: the analytical walls lie half a spacing outside the fluid, so
+    1/dp fluid layers fill the channel.  Dynamic walls: the first wall layer sits on
+    the analytical wall, so 1/dp - 1 fluid layers sit between the two first wall
+    layers, one of them on the centre line.  Wendland takes 3 wall layers, the
+    truncated Gaussian 4.  meta: L and "centre" (the y of the centre line; the
+    analytical profile is a function of y - centre).  The periodic x and z extent
+    (8 spacings for Wendland, 12 for the Gaussian) is twice the kernel's support.
+    """
+    dx = L / inv_dp
+    gauss = kernel == KERNEL_GAUSSIAN
+    ny = inv_dp if boundary == BC_DUMMY else inv_dp - 1
+    nxz = 12 if gauss else 8
+    s = couette(0, nx=nxz, ny=ny, nz=nxz, dx=dx, rho0=1.0, nu=mu, dt=dt, U=0.0, noise=0.0,
+                layers=4 if gauss else 3, boundary=boundary, kernel=kernel)
+    s.name = "poiseuille"
+    s.meta.update(L=L, centre=0.5 * ny * dx)
+    return s
+
+
 def lava_box(seed: int = 0, n: int = 100, dx: float = 0.005, rho0: float = 1000.0, nu: float = 10.0,
              dt: float = 5e-4, sigma: float = 0.1, jitter: float = 0.1, layers: int = 3,
              boundary: int = BC_DUMMY, kernel: int = KERNEL_WENDLAND) -> Scene:

@@ -1,6 +1,7 @@
 """The semi-implicit predictor/corrector step (paper Sec. 3.3) on the GPU: one step against
-the oracle's step, and the plane Poiseuille flow run to steady state against the
-analytic profile and the paper's error table."""
+the oracle's step, and the plane Poiseuille flows of Sec. 5 (Newtonian and Papanastasiou,
+both kernels, both boundary models) run to steady state against the analytic profiles and
+the paper's error tables."""
 import os
 
 import numpy as np
@@ -106,45 +107,6 @@ def test_fluid_at_rest_stays_at_rest_on_the_gpu():
     np.testing.assert_array_equal(t["vel"].cpu().numpy()[s.ptype == scenes.FLUID], 0.0)
 
 
-@pytest.mark.slow
-def test_poiseuille_flow_reaches_the_analytic_profile():
-    """The plane Poiseuille flow of Sec. 5 (Newtonian, Wendland h = 1.3 dp, dummy walls,
-    dp = 1/16): L = 1 m, g = 0.05 m/s^2, mu = 0.1 Pa s, rho0 = 1 kg/m^3, c0 = 6.32 m/s,
-    from rest to t = 10 s (the viscous relaxation time) with the full step.  The
-    steady profile is u(z) = rho0 g / (2 mu) (L^2/4 - z^2) (u_max = 6.25e-2 m/s); its l1
-    and l2 errors are compared with the paper's table for this configuration."""
-    from paper_2206_14780_gb300 import binding
-
-    gold = dict(l.split() for l in open(os.path.join(GOLDEN, "poiseuille_newton_wendland_dummy_dp16.txt"))
-                if l.strip() and not l.startswith("#"))
-    gold = {k: float(v) for k, v in gold.items()}
-    dx, g, mu, L = 1.0 / 16, 0.05, 0.1, 1.0
-    s = scenes.couette(0, nx=8, ny=16, nz=8, dx=dx, rho0=1.0, nu=mu, dt=1e-2, U=0.0, noise=0.0)
-    s.vel[:] = 0.0
-    st, t = _stepper(s)
-    dt = 2.5e-3
-    prm = binding.step_params(dt, 1.0, 6.32, 7.0, (g, 0.0, 0.0), s.boundary, s.mean)
-    opts = binding.solve_opts(rtol=1e-8)
-    for _ in range(int(round(10.0 / dt))):
-        rep = st.step(prm, opts)
-        assert rep["status"] == 0
-    st.close()
-    fl = s.ptype == scenes.FLUID
-    pos = t["pos"].cpu().numpy()[fl].astype(np.float64)
-    u = t["vel"].cpu().numpy()[fl, 0].astype(np.float64)
-    z = pos[:, 1] - 0.5 * L
-    exact = 0.5 * g / mu * (0.25 * L * L - z * z)
-    e = u - exact
-    l1, l2 = np.abs(e).mean(), np.sqrt((e * e).mean())
-    assert np.abs(e).max() < 0.05 * exact.max()
-    assert l1 < 2.0 * gold["l1"] and l2 < 2.0 * gold["l2"], (l1, l2, gold)
-    # the flow stays one-directional (the weakly compressible fluid keeps acoustic
-    # noise of ~1e-3 u_max across the channel) and the density near rest
-    assert np.abs(t["vel"].cpu().numpy()[fl, 1:3]).max() < 5e-3 * exact.max()
-    rho = t["rho"].cpu().numpy()[fl]
-    assert np.abs(rho - 1.0).max() < 1e-3
-
-
 def test_picard_step_matches_oracle():
     """The non-linear form (Sec. 8): four fixed-point passes of the corrector's system
     with the viscosity recomputed from the new velocities, on the GPU and in the
@@ -203,39 +165,67 @@ def test_step_with_a_row_scale_keeps_the_oracles_step():
     np.testing.assert_allclose(t["rho"].cpu().numpy().astype(np.float64), new.rho.astype(np.float64), rtol=2e-6)
 
 
+POISEUILLE_CASES = ["newton_wendland_dummy", "newton_wendland_dynamic", "newton_gaussian_dummy",
+                    "newton_gaussian_dynamic", "papanastasiou_wendland_dummy", "papanastasiou_wendland_dynamic",
+                    "papanastasiou_gaussian_dummy", "papanastasiou_gaussian_dynamic"]
+
+
 @pytest.mark.slow
-def test_papanastasiou_poiseuille_flow_reaches_the_bingham_profile():
-    """The plane Poiseuille flow of a Papanastasiou fluid of Sec. 5.4 (Wendland, dummy
-    walls, dp = 1/16, mu0 = 0.1 Pa s, tau0 = 0.0125 Pa, m = 1000 s), the viscosity
-    recomputed from the velocities every step, from rest to t = 10 s: its l1 and l2
-    errors against the non-regularised Bingham profile (plug |z| < tau0 / (rho0 g) at
-    u_p = 1.5625e-2 m/s) within twice the paper's table for this configuration, the
-    flow one-directional and the plug the fastest part of the profile."""
+@pytest.mark.parametrize("case", POISEUILLE_CASES)
+def test_poiseuille_flow_matches_the_paper_error_table(case):
+    """The plane Poiseuille flows of Sec. 5 at dp = 1/16 with the full step, from rest to
+    the viscous relaxation time t = 10 s: L = 1 m, g = 0.05 m/s^2, rho0 = 1 kg/m^3,
+    c0 = 6.32 m/s, h = 1.3 dp, dt = 0.3 h / c0, each boundary model with its wall layout
+    of Sec. 5.2.  Newtonian (mu = 0.1 Pa s): the steady profile
+    u(z) = rho0 g / (2 mu) (L^2/4 - z^2) (u_max = 6.25e-2 m/s), its l1 and l2 errors within
+    20% of the paper's Table tab:newton-error (and of the 102% columns where the table has
+    them).  Papanastasiou (Sec. 5.4: mu0 = 0.1 Pa s, tau0 = 0.0125 Pa, m = 1000 s, the
+    viscosity recomputed from the velocities each step): the errors against the
+    non-regularised Bingham profile (plug |z| < tau0 / (rho0 g) at u_p = 1.5625e-2 m/s)
+    no larger than the paper's Table tab:papa-error, the plug the fastest part of the
+    profile.  Both: the flow one-directional, the density near rest."""
     from paper_2206_14780_gb300 import binding
 
-    gold = dict(l.split() for l in open(os.path.join(GOLDEN, "poiseuille_papanastasiou_wendland_dummy_dp16.txt"))
+    rheo, kname, bname = case.split("_")
+    gold = dict(l.split() for l in open(os.path.join(GOLDEN, f"poiseuille_{case}_dp16.txt"))
                 if l.strip() and not l.startswith("#"))
     gold = {k: float(v) for k, v in gold.items()}
-    dx, g, mu0, tau0, m, L = 1.0 / 16, 0.05, 0.1, 0.0125, 1000.0, 1.0
-    s = scenes.couette(0, nx=8, ny=16, nz=8, dx=dx, rho0=1.0, nu=mu0, dt=1e-2, U=0.0, noise=0.0)
-    s.vel[:] = 0.0
+    kern = scenes.KERNEL_GAUSSIAN if kname == "gaussian" else scenes.KERNEL_WENDLAND
+    s = scenes.poiseuille(scenes.BC_DYNAMIC if bname == "dynamic" else scenes.BC_DUMMY, kern)
+    g, mu0, tau0, m, c0, L = 0.05, 0.1, 0.0125, 1000.0, 6.32, s.meta["L"]
     st, t = _stepper(s)
-    dt = 2.5e-3
-    prm = binding.step_params(dt, 1.0, 6.32, 7.0, (g, 0.0, 0.0), s.boundary, s.mean, rheology=(tau0, mu0, m))
+    dt = 0.3 * s.h / c0
+    prm = binding.step_params(dt, 1.0, c0, 7.0, (g, 0.0, 0.0), s.boundary, s.mean,
+                              max_neighbors=512 if kern == scenes.KERNEL_GAUSSIAN else 128,
+                              rheology=(tau0, mu0, m) if rheo == "papanastasiou" else None)
     opts = binding.solve_opts(rtol=1e-8)
-    for _ in range(int(round(10.0 / dt))):
-        assert st.step(prm, opts)["status"] == 0
+    for _ in range(int(np.ceil(10.0 / dt))):
+        rep = st.step(prm, opts)
+        assert rep["status"] == 0, rep
     st.close()
     fl = s.ptype == scenes.FLUID
-    z = t["pos"].cpu().numpy()[fl, 1].astype(np.float64) - 0.5 * L
+    z = t["pos"].cpu().numpy()[fl, 1].astype(np.float64) - s.meta["centre"]
     u = t["vel"].cpu().numpy()[fl, 0].astype(np.float64)
-    zp = tau0 / g
-    u_plug = (0.5 * L - zp) * (g * 0.5 * L - tau0) / (2.0 * mu0)
-    assert abs(u_plug - 1.5625e-2) < 1e-12
-    az = np.abs(z)
-    exact = np.where(az >= zp, 0.5 * g / mu0 * (0.25 * L * L - z * z) - tau0 / mu0 * (0.5 * L - az), u_plug)
+    exact = 0.5 * g / mu0 * (0.25 * L * L - z * z)
+    if rheo == "papanastasiou":
+        zp = tau0 / g
+        u_plug = (0.5 * L - zp) * (g * 0.5 * L - tau0) / (2.0 * mu0)
+        assert abs(u_plug - 1.5625e-2) < 1e-12
+        az = np.abs(z)
+        exact = np.where(az >= zp, exact - tau0 / mu0 * (0.5 * L - az), u_plug)
     e = u - exact
     l1, l2 = np.abs(e).mean(), np.sqrt((e * e).mean())
-    assert l1 < 2.0 * gold["l1"] and l2 < 2.0 * gold["l2"], (l1, l2, gold)
-    assert np.abs(t["vel"].cpu().numpy()[fl, 1:3]).max() < 5e-3 * u_plug
-    assert u[az < 0.5 * zp].min() > u[az > 0.5 * L - 2 * dx].max()
+    if rheo == "papanastasiou":
+        assert l1 <= gold["l1"] and l2 <= gold["l2"], (l1, l2, gold)
+        assert u[az < 0.5 * zp].min() > u[az > 0.5 * L - 2 * s.dx].max()
+    else:
+        assert abs(exact.max() - 6.25e-2) < 2e-3
+        assert abs(l1 / gold["l1"] - 1) < 0.2 and abs(l2 / gold["l2"] - 1) < 0.2, (l1, l2, gold)
+        if "l1_102" in gold:
+            e = u - 1.02 * exact
+            l1, l2 = np.abs(e).mean(), np.sqrt((e * e).mean())
+            assert abs(l1 / gold["l1_102"] - 1) < 0.2 and abs(l2 / gold["l2_102"] - 1) < 0.2, (l1, l2, gold)
+    # the flow stays one-directional (the weakly compressible fluid keeps acoustic
+    # noise of ~1e-3 u_max across the channel) and the density near rest
+    assert np.abs(t["vel"].cpu().numpy()[fl, 1:3]).max() < 5e-3 * exact.max()
+    assert np.abs(t["rho"].cpu().numpy()[fl] - 1.0).max() < 1e-3
