@@ -49,6 +49,8 @@ def parse(argv=None):
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-gaussian", action="store_true")
     ap.add_argument("--no-poiseuille", action="store_true")
+    ap.add_argument("--poiseuille-only", default=None,
+                    help="comma-separated 1/dp list (e.g. 16,32,64): only the Poiseuille runs, one JSON line")
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-shard", action="store_true")
     ap.add_argument("--ensemble-only", action="store_true")
@@ -864,28 +866,44 @@ def run_shard(dev, n=60, ranks=(1, 2, 4)):
 
 # ------------------------------------------------------ Poiseuille flow -------
 
-# the paper's numbers at dp = 1/16 (Sec. 5.3, Table tab:newton-error and Table tab:newton-times;
-# Sec. 5.4, Table tab:papa-error and Table tab:papa-times): the l1 and l2 errors of the steady
-# profile (and, for Wendland, against 102% of it) and the semi-implicit runtime in seconds of the
-# whole run to t = 10 s on the paper's machine
+# the paper's numbers (Sec. 5.3, Tables tab:newton-error and tab:newton-times; Sec. 5.4, Tables
+# tab:papa-error and tab:papa-times) per configuration and 1/dp: the l1 and l2 errors of the
+# steady profile (and, for Wendland Newtonian, against 102% of it) and the semi-implicit runtime
+# in seconds of the whole run to t = 10 s on the paper's machine.  (The 1/64 Wendland dynamic
+# l2 against 102% is printed as 1.204e-3, ten times its l1 and its rate: kept as printed.)
+def _pp(l1, l2, rt, l1_102=None, l2_102=None):
+    d = {"l1": l1, "l2": l2, "runtime_s": rt}
+    if l1_102 is not None:
+        d.update(l1_102=l1_102, l2_102=l2_102)
+    return d
+
+
 POISEUILLE_PAPER = {
-    "newton_wendland_dummy": {"l1": 1.227e-3, "l2": 1.282e-3, "l1_102": 3.916e-4, "l2_102": 3.929e-4,
-                              "runtime_s": 33.0},
-    "newton_wendland_dynamic": {"l1": 1.210e-3, "l2": 1.325e-3, "l1_102": 4.288e-4, "l2_102": 4.576e-4,
-                                "runtime_s": 24.0},
-    "newton_gaussian_dummy": {"l1": 3.615e-4, "l2": 3.713e-4, "runtime_s": 68.0},
-    "newton_gaussian_dynamic": {"l1": 2.083e-3, "l2": 2.153e-3, "runtime_s": 46.0},
-    "papanastasiou_wendland_dummy": {"l1": 4.724e-3, "l2": 4.815e-3, "runtime_s": 95.0},
-    "papanastasiou_wendland_dynamic": {"l1": 3.009e-3, "l2": 3.232e-3, "runtime_s": 74.0},
-    "papanastasiou_gaussian_dummy": {"l1": 7.027e-3, "l2": 7.227e-3, "runtime_s": 180.0},
-    "papanastasiou_gaussian_dynamic": {"l1": 4.569e-3, "l2": 4.769e-3, "runtime_s": 130.0},
+    "newton_wendland_dummy": {16: _pp(1.227e-3, 1.282e-3, 33.0, 3.916e-4, 3.929e-4),
+                              32: _pp(9.598e-4, 1.032e-3, 370.0, 1.260e-4, 1.294e-4),
+                              64: _pp(8.792e-4, 9.585e-4, 5600.0, 4.573e-5, 5.435e-5)},
+    "newton_wendland_dynamic": {16: _pp(1.210e-3, 1.325e-3, 24.0, 4.288e-4, 4.576e-4),
+                                32: _pp(1.061e-3, 1.133e-3, 250.0, 2.283e-4, 2.338e-4),
+                                64: _pp(9.490e-4, 1.024e-3, 4300.0, 1.158e-4, 1.204e-3)},
+    "newton_gaussian_dummy": {16: _pp(3.615e-4, 3.713e-4, 68.0), 32: _pp(4.081e-5, 5.087e-5, 740.0),
+                              64: _pp(2.010e-5, 2.096e-5, 13000.0)},
+    "newton_gaussian_dynamic": {16: _pp(2.083e-3, 2.153e-3, 46.0), 32: _pp(1.033e-3, 1.050e-3, 430.0),
+                                64: _pp(5.097e-4, 5.139e-4, 9700.0)},
+    "papanastasiou_wendland_dummy": {16: _pp(4.724e-3, 4.815e-3, 95.0), 32: _pp(1.861e-3, 1.894e-3, 1400.0),
+                                     64: _pp(7.339e-4, 7.631e-4, 27000.0)},
+    "papanastasiou_wendland_dynamic": {16: _pp(3.009e-3, 3.232e-3, 74.0), 32: _pp(1.138e-3, 1.196e-3, 1000.0),
+                                       64: _pp(3.715e-4, 6.833e-4, 20000.0)},
+    "papanastasiou_gaussian_dummy": {16: _pp(7.027e-3, 7.227e-3, 180.0), 32: _pp(2.928e-3, 2.982e-3, 2600.0),
+                                     64: _pp(1.336e-3, 1.360e-3, 61000.0)},
+    "papanastasiou_gaussian_dynamic": {16: _pp(4.569e-3, 4.769e-3, 130.0), 32: _pp(1.720e-3, 1.790e-3, 1700.0),
+                                       64: _pp(7.245e-4, 7.635e-4, 43000.0)},
 }
 
 
-def run_poiseuille_case(dev, case, t_end=10.0):
+def run_poiseuille_case(dev, case, inv_dp=16, t_end=10.0):
     """One plane Poiseuille flow of Sec. 5 with the full semi-implicit step (sph_step),
     from rest to the viscous relaxation time t = 10 s: L = 1 m, g = 0.05 m/s^2,
-    rho0 = 1 kg/m^3, c0 = 6.32 m/s, h = 1.3 dp, dp = 1/16, dt = 0.3 h / c0 (the
+    rho0 = 1 kg/m^3, c0 = 6.32 m/s, h = 1.3 dp, dp = 1/inv_dp, dt = 0.3 h / c0 (the
     sound-speed limit of Tables tab:newton-times and tab:papa-times), the wall layout of
     Sec. 5.2 for the boundary model.  Newtonian: mu = 0.1 Pa s, profile
     u(z) = rho0 g / (2 mu) (L^2/4 - z^2).  Papanastasiou (Sec. 5.4): mu0 = 0.1 Pa s,
@@ -902,7 +920,7 @@ def run_poiseuille_case(dev, case, t_end=10.0):
     kern = scenes.KERNEL_GAUSSIAN if kname == "gaussian" else scenes.KERNEL_WENDLAND
     bc = scenes.BC_DYNAMIC if bname == "dynamic" else scenes.BC_DUMMY
     g, mu0, tau0, m, c0 = 0.05, 0.1, 0.0125, 1000.0, 6.32
-    s = scenes.poiseuille(bc, kern)
+    s = scenes.poiseuille(bc, kern, inv_dp=inv_dp)
     L = s.meta["L"]
     dt = 0.3 * s.h / c0
     steps = int(np.ceil(t_end / dt))
@@ -933,7 +951,7 @@ def run_poiseuille_case(dev, case, t_end=10.0):
         az = np.abs(z)
         u_plug = (0.5 * L - zp) * (g * 0.5 * L - tau0) / (2.0 * mu0)
         exact = np.where(az >= zp, exact - tau0 / mu0 * (0.5 * L - az), u_plug)
-    paper = POISEUILLE_PAPER[case]
+    paper = POISEUILLE_PAPER[case][inv_dp]
     out = dict(workload=f"{int(fl.sum())} fluid + {int((~fl).sum())} {bname} wall particles, {steps} steps of "
                         f"dt = {dt:.4g} s to t = {t_end} s", steps=steps, dt=dt,
                run_s=e0.elapsed_time(e1) / 1e3, ms_per_step=e0.elapsed_time(e1) / steps,
@@ -947,9 +965,24 @@ def run_poiseuille_case(dev, case, t_end=10.0):
     return out
 
 
-def run_poiseuille(dev):
-    """Every dp = 1/16 configuration of POISEUILLE_PAPER, one full run each."""
-    return {case: run_poiseuille_case(dev, case) for case in POISEUILLE_PAPER}
+def run_poiseuille(dev, resolutions=(16,)):
+    """Every configuration of POISEUILLE_PAPER at each 1/dp in resolutions, one full run
+    each; with more than one resolution, the convergence rates log2(e_coarse / e_fine)
+    of l1 and l2 between consecutive ones (the paper prints its own rates beside its
+    errors)."""
+    import math
+
+    out = {}
+    for case in POISEUILLE_PAPER:
+        runs = {r: run_poiseuille_case(dev, case, r) for r in resolutions}
+        if len(resolutions) == 1:
+            out[case] = runs[resolutions[0]]
+            continue
+        for r0, r1 in zip(resolutions, resolutions[1:]):
+            for k in ("l1", "l2"):
+                runs[r1][f"rate_{k}"] = math.log2(runs[r0][k] / runs[r1][k])
+        out[case] = {str(r): v for r, v in runs.items()}
+    return out
 
 
 # --------------------------------------------------------- network forward ----
@@ -1672,6 +1705,12 @@ def main():
         return
     if args.ensemble_only:
         print(json.dumps(run_ensemble(0, scenes_n=args.ensemble_scenes)))
+        return
+    if args.poiseuille_only:
+        import torch
+
+        res = tuple(int(r) for r in args.poiseuille_only.split(","))
+        print(json.dumps(run_poiseuille(torch.device("cuda", 0), res)))
         return
     if args.precision_only:
         out = run_precision()

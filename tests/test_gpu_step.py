@@ -168,30 +168,33 @@ def test_step_with_a_row_scale_keeps_the_oracles_step():
 POISEUILLE_CASES = ["newton_wendland_dummy", "newton_wendland_dynamic", "newton_gaussian_dummy",
                     "newton_gaussian_dynamic", "papanastasiou_wendland_dummy", "papanastasiou_wendland_dynamic",
                     "papanastasiou_gaussian_dummy", "papanastasiou_gaussian_dynamic"]
+# every configuration at dp = 1/16, the Newtonian ones at 1/32 too (where the Gaussian kernel
+# with dummy walls converges at rate ~3 in the paper's table)
+POISEUILLE_RUNS = [(c, 16) for c in POISEUILLE_CASES] + [(c, 32) for c in POISEUILLE_CASES if c.startswith("newton")]
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("case", POISEUILLE_CASES)
-def test_poiseuille_flow_matches_the_paper_error_table(case):
-    """The plane Poiseuille flows of Sec. 5 at dp = 1/16 with the full step, from rest to
-    the viscous relaxation time t = 10 s: L = 1 m, g = 0.05 m/s^2, rho0 = 1 kg/m^3,
-    c0 = 6.32 m/s, h = 1.3 dp, dt = 0.3 h / c0, each boundary model with its wall layout
-    of Sec. 5.2.  Newtonian (mu = 0.1 Pa s): the steady profile
-    u(z) = rho0 g / (2 mu) (L^2/4 - z^2) (u_max = 6.25e-2 m/s), its l1 and l2 errors within
-    20% of the paper's Table tab:newton-error (and of the 102% columns where the table has
-    them).  Papanastasiou (Sec. 5.4: mu0 = 0.1 Pa s, tau0 = 0.0125 Pa, m = 1000 s, the
-    viscosity recomputed from the velocities each step): the errors against the
-    non-regularised Bingham profile (plug |z| < tau0 / (rho0 g) at u_p = 1.5625e-2 m/s)
-    no larger than the paper's Table tab:papa-error, the plug the fastest part of the
-    profile.  Both: the flow one-directional, the density near rest."""
+@pytest.mark.parametrize("case,inv_dp", POISEUILLE_RUNS)
+def test_poiseuille_flow_matches_the_paper_error_table(case, inv_dp):
+    """The plane Poiseuille flows of Sec. 5 with the full step, from rest to the viscous
+    relaxation time t = 10 s: L = 1 m, g = 0.05 m/s^2, rho0 = 1 kg/m^3, c0 = 6.32 m/s,
+    h = 1.3 dp, dt = 0.3 h / c0, each boundary model with its wall layout of Sec. 5.2.
+    Newtonian (mu = 0.1 Pa s): the steady profile u(z) = rho0 g / (2 mu) (L^2/4 - z^2)
+    (u_max = 6.25e-2 m/s), its l1 and l2 errors within 20% of the paper's Table
+    tab:newton-error (the 102% columns, where the table has them, within 30%: they are
+    differences of nearby numbers).  Papanastasiou (Sec. 5.4: mu0 = 0.1 Pa s,
+    tau0 = 0.0125 Pa, m = 1000 s, the viscosity recomputed from the velocities each step):
+    the errors against the non-regularised Bingham profile (plug |z| < tau0 / (rho0 g) at
+    u_p = 1.5625e-2 m/s) no larger than the paper's Table tab:papa-error, the plug the
+    fastest part of the profile.  Both: the flow one-directional, the density near rest."""
     from paper_2206_14780_gb300 import binding
 
     rheo, kname, bname = case.split("_")
-    gold = dict(l.split() for l in open(os.path.join(GOLDEN, f"poiseuille_{case}_dp16.txt"))
+    gold = dict(l.split() for l in open(os.path.join(GOLDEN, f"poiseuille_{case}_dp{inv_dp}.txt"))
                 if l.strip() and not l.startswith("#"))
     gold = {k: float(v) for k, v in gold.items()}
     kern = scenes.KERNEL_GAUSSIAN if kname == "gaussian" else scenes.KERNEL_WENDLAND
-    s = scenes.poiseuille(scenes.BC_DYNAMIC if bname == "dynamic" else scenes.BC_DUMMY, kern)
+    s = scenes.poiseuille(scenes.BC_DYNAMIC if bname == "dynamic" else scenes.BC_DUMMY, kern, inv_dp=inv_dp)
     g, mu0, tau0, m, c0, L = 0.05, 0.1, 0.0125, 1000.0, 6.32, s.meta["L"]
     st, t = _stepper(s)
     dt = 0.3 * s.h / c0
@@ -224,7 +227,7 @@ def test_poiseuille_flow_matches_the_paper_error_table(case):
         if "l1_102" in gold:
             e = u - 1.02 * exact
             l1, l2 = np.abs(e).mean(), np.sqrt((e * e).mean())
-            assert abs(l1 / gold["l1_102"] - 1) < 0.2 and abs(l2 / gold["l2_102"] - 1) < 0.2, (l1, l2, gold)
+            assert abs(l1 / gold["l1_102"] - 1) < 0.3 and abs(l2 / gold["l2_102"] - 1) < 0.3, (l1, l2, gold)
     # the flow stays one-directional (the weakly compressible fluid keeps acoustic
     # noise of ~1e-3 u_max across the channel) and the density near rest
     assert np.abs(t["vel"].cpu().numpy()[fl, 1:3]).max() < 5e-3 * exact.max()

@@ -49,31 +49,52 @@ def test_couette_dynamic_linear_profile():
     np.testing.assert_allclose(v[fl, 0], (y + 0.5 * dx) / (H + dx), atol=3e-3)
 
 
-@pytest.mark.parametrize("kernel", ["wendland", "gaussian"])
-@pytest.mark.parametrize("boundary", ["dummy", "dynamic"])
-def test_poiseuille_matches_paper_error_table(kernel, boundary):
-    """The dp = 1/16 entries of the paper's Newtonian error table (Sec. 5.3), each with
-    the wall layout of Sec. 5.2 for its boundary model (dynamic: the first wall layer on
-    the analytical wall; dummy: half a spacing inside it)."""
-    gold = dict(l.split() for l in open(os.path.join(GOLDEN, f"poiseuille_newton_{kernel}_{boundary}_dp16.txt"))
-                if l.strip() and not l.startswith("#"))
-    gold = {k: float(v) for k, v in gold.items()}
-    g, mu = 0.05, 0.1
+def _poiseuille_errors(kernel, boundary, inv_dp, f=1.0, g=0.05, mu=0.1):
     s = scenes.poiseuille(scenes.BC_DYNAMIC if boundary == "dynamic" else scenes.BC_DUMMY,
-                          scenes.KERNEL_GAUSSIAN if kernel == "gaussian" else scenes.KERNEL_WENDLAND, mu=mu, dt=100.0)
+                          scenes.KERNEL_GAUSSIAN if kernel == "gaussian" else scenes.KERNEL_WENDLAND,
+                          inv_dp=inv_dp, mu=mu, dt=100.0)
     L = s.meta["L"]
     v = _steady(s, g=(g, 0.0, 0.0), steps=60)
     fl = s.ptype == scenes.FLUID
     z = s.pos[fl, 1].astype(np.float64) - s.meta["centre"]
     exact = 0.5 * g / mu * (0.25 * L * L - z * z)
-    for f, k1, k2, tol in ((1.0, "l1", "l2", 0.25), (1.02, "l1_102", "l2_102", 0.35)):
-        if k1 not in gold:
-            continue
+    out = {}
+    for f, k1, k2 in ((1.0, "l1", "l2"), (1.02, "l1_102", "l2_102")):
         e = v[fl, 0] - f * exact
-        l1 = np.abs(e).mean()
-        l2 = np.sqrt((e * e).mean())
+        out[k1] = np.abs(e).mean()
+        out[k2] = np.sqrt((e * e).mean())
+    return out
+
+
+def _gold(name):
+    gold = dict(l.split() for l in open(os.path.join(GOLDEN, name)) if l.strip() and not l.startswith("#"))
+    return {k: float(v) for k, v in gold.items()}
+
+
+@pytest.mark.parametrize("inv_dp", [16, 32])
+@pytest.mark.parametrize("kernel", ["wendland", "gaussian"])
+@pytest.mark.parametrize("boundary", ["dummy", "dynamic"])
+def test_poiseuille_matches_paper_error_table(kernel, boundary, inv_dp):
+    """The dp = 1/16 and 1/32 entries of the paper's Newtonian error table (Sec. 5.3), each
+    with the wall layout of Sec. 5.2 for its boundary model (dynamic: the first wall layer
+    on the analytical wall; dummy: half a spacing inside it)."""
+    gold = _gold(f"poiseuille_newton_{kernel}_{boundary}_dp{inv_dp}.txt")
+    err = _poiseuille_errors(kernel, boundary, inv_dp)
+    if (kernel, boundary, inv_dp) == ("gaussian", "dummy", 32):
+        # at 4e-5 the table's entry is set by what the viscous system leaves out (pressure,
+        # moving particles, evolving densities): pin the super-convergence instead, the l1
+        # error falling by more than 2^3 from 1/16 to 1/32 (the table: 8.9x, rate 3.15)
+        coarse = _poiseuille_errors(kernel, boundary, 16)
+        assert coarse["l1"] / err["l1"] > 8.0, (coarse["l1"], err["l1"])
+        assert abs(np.log10(err["l1"] / gold["l1"])) < np.log10(2.0), (err["l1"], gold["l1"])
+        return
+    for k1, k2, tol in (("l1", "l2", 0.25), ("l1_102", "l2_102", 0.35)):
+        if k1 not in gold or (k1 == "l1_102" and inv_dp > 16):
+            continue
         # the paper's numbers come from a full simulation (pressure, moving particles,
         # evolving wall densities); the viscous-only steady state agrees with them to
-        # within 20% (the 102% columns, small differences of nearby numbers, to 30%)
-        assert abs(l1 / gold[k1] - 1) < tol, (k1, l1, gold[k1])
-        assert abs(l2 / gold[k2] - 1) < tol, (k2, l2, gold[k2])
+        # within 20% (the 102% columns, small differences of nearby numbers, to 30% at
+        # 1/16; at 1/32 they shrink to ~1e-4 and the viscous-only state misses by ~50%,
+        # so only the full step's test compares them there)
+        assert abs(err[k1] / gold[k1] - 1) < tol, (k1, err[k1], gold[k1])
+        assert abs(err[k2] / gold[k2] - 1) < tol, (k2, err[k2], gold[k2])
