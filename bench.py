@@ -1161,7 +1161,9 @@ def run_ensemble(seed=0, dev=None, scenes_n=64):
                max_true_rel_res_sequential=max(r["true_rel_res"] for r in seq),
                max_true_rel_res_batched=max(r["true_rel_res"] for r in bat), batched_status=st,
                batched_launches=binding.launch_count() - launches0, persistent_variant=info["variant"],
-               graph=info["graph"], persistent_grid=info["grid"], autotune_ms=info["tune_ms"])
+               graph=info["graph"], persistent_grid=info["grid"], autotune_ms=info["tune_ms"],
+               tile_slices=info["tile_slices"], ntiles=info["ntiles"],
+               tile_autotune_ms=dict(zip([str(c) for c in info["tile_candidates"]], info["tile_tune_ms"])))
     batch.close()
     for nb in nbs:
         nb.close()

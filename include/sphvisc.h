@@ -420,9 +420,11 @@ sph_status sph_step(sph_state* state, const sph_step_params* params, const sph_s
  * scene (scenes at rtol drop out on the device), pass set-up, ONE persistent
  * cooperative kernel running the iterations of all active scenes, and x += d.
  * Grid barriers inside the persistent kernel wait a bounded time and report
- * SPH_ERR_TIMEOUT instead of hanging.  The persistent kernel's row-loop form
- * and block size (256 or 128 threads per 32-slice tile) are autotuned on the
- * first solve. */
+ * SPH_ERR_TIMEOUT instead of hanging.  A tile is a run of consecutive 32-row
+ * slices of one scene taken by one block (16, 32 or 64 slices; the last tile
+ * of a scene shorter).  The persistent kernel's row-loop form and block size
+ * (256 or 128 threads) are autotuned on the first solve at 32-slice tiles, then
+ * the tile length for that form. */
 typedef struct sph_batch sph_batch;
 
 /* handles: (host) [nscenes] built handles; params: (host) [nscenes] A(dt)
@@ -446,6 +448,18 @@ sph_status sph_batch_solve(sph_batch* batch, const sph_solve_opts* opts, const d
  * times (ms, [8]) and the chosen variant's grid size.  Any pointer may be NULL. */
 sph_status sph_batch_info(const sph_batch* batch, int32_t* variant, int32_t* graph, float* tune_ms,
                           int32_t* grid);
+
+/* The tile length in slices the batch uses (32 until the first solve has tuned
+ * it), the number of tiles, the three candidate lengths (host [3]) and the
+ * tuning time (ms, host [3]) of the chosen form at each (0 before tuning).  Any
+ * pointer may be NULL. */
+sph_status sph_batch_tiles(const sph_batch* batch, int32_t* tile_slices, int32_t* ntiles, int32_t* candidates,
+                           float* tune_ms);
+
+/* Fixes the tile length (one of the candidates sph_batch_tiles lists; anything
+ * else is SPH_ERR_INVALID and changes nothing): later solves use it and the
+ * tuner leaves it.  Synchronises the stream. */
+sph_status sph_batch_set_tile(sph_batch* batch, int32_t tile_slices, void* stream);
 
 sph_status sph_batch_destroy(sph_batch* batch);
 

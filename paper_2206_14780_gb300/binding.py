@@ -29,7 +29,8 @@ SPH_KERNEL_WENDLAND, SPH_KERNEL_GAUSSIAN = 0, 1
 EXPORTS = ["sph_build_neighbors", "sph_neighbors_info", "sph_neighbors_export", "sph_set_viscosity",
            "sph_neighbors_destroy", "sph_visc_setup", "sph_visc_apply", "sph_visc_apply_otf", "sph_visc_apply_noalloc", "sph_visc_residual", "sph_visc_solve",
            "sph_mu_papanastasiou", "sph_profile_enable", "sph_profile_read", "sph_last_error", "sph_version",
-           "sph_batch_create", "sph_batch_solve", "sph_batch_info", "sph_batch_destroy",
+           "sph_batch_create", "sph_batch_solve", "sph_batch_info", "sph_batch_tiles", "sph_batch_set_tile",
+           "sph_batch_destroy",
            "sph_mlp_create", "sph_mlp_set_params", "sph_mlp_get_params", "sph_mlp_destroy", "sph_mlp_features",
            "sph_mlp_targets", "sph_mlp_forward", "sph_mlp_grad", "sph_mlp_train_step", "sph_warm_start",
            "sph_mlp_residual_targets", "sph_mlp_set_mode", "sph_visc_solve_host", "sph_bicgstab_replay",
@@ -130,6 +131,9 @@ def load(path: str = LIB_PATH):
                             ctypes.POINTER(sph_solve_report), vp],
         "sph_batch_info": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
                            ctypes.POINTER(i32)],
+        "sph_batch_tiles": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                            ctypes.POINTER(ctypes.c_float)],
+        "sph_batch_set_tile": [vp, i32, vp],
         "sph_batch_destroy": [vp],
         "sph_mlp_create": [vp, ctypes.POINTER(vp)],
         "sph_mlp_set_params": [vp, vp],
@@ -484,11 +488,18 @@ class Batch:
             _check(st)
         return st, [_report(r) for r in reps]
 
+    def set_tile(self, tile_slices, stream=None):
+        _check(_lib.sph_batch_set_tile(self.handle, int(tile_slices), _stream(stream)))
+
     def info(self):
         v, g, grid = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         t = (ctypes.c_float * 8)()
         _check(_lib.sph_batch_info(self.handle, ctypes.byref(v), ctypes.byref(g), t, ctypes.byref(grid)))
-        return dict(variant=v.value, graph=bool(g.value), tune_ms=list(t), grid=grid.value)
+        ts, nt = ctypes.c_int32(), ctypes.c_int32()
+        cand, tms = (ctypes.c_int32 * 3)(), (ctypes.c_float * 3)()
+        _check(_lib.sph_batch_tiles(self.handle, ctypes.byref(ts), ctypes.byref(nt), cand, tms))
+        return dict(variant=v.value, graph=bool(g.value), tune_ms=list(t), grid=grid.value, tile_slices=ts.value,
+                    ntiles=nt.value, tile_candidates=list(cand), tile_tune_ms=list(tms))
 
     def close(self):
         if self.handle:

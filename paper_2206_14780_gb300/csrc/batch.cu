@@ -31,7 +31,13 @@
 
 namespace sph {
 
-constexpr int kTileSlices = 32;  // one 256-thread block; each warp takes every 8th slice of the tile
+// A tile is a run of consecutive SELL slices of one scene taken by one block
+// (each warp takes every 8th or 4th slice of it).  Its length is autotuned
+// among kTileCands on the first solve, after the row-loop form and block size;
+// the default is the middle one.
+constexpr int kTileCands[3] = {16, 32, 64};
+constexpr int kTileDefault = 1;
+constexpr float kTileMargin = 0.97f;
 
 struct SceneDesc {
   OpView op;
@@ -508,7 +514,12 @@ struct sph_batch {
   int variant = -1;            // autotuned form (row loop, block size) of the persistent kernel
   int grid = 0;                // grid of the auxiliary kernels
   int grids[kPassVariants] = {};   // co-resident grid of each persistent-kernel variant
+  int occ[kPassVariants] = {};     // resident blocks per SM of each variant
   float tune_ms[kPassVariants] = {};
+  int tile = kTileDefault;     // index into kTileCands
+  bool tile_fixed = false;     // set by sph_batch_set_tile: the tuner keeps it
+  float tile_ms[3] = {};       // tuning time of the chosen variant at each tile length
+  std::vector<SceneDesc> hdesc;   // host copy of the scene descriptors
   cudaGraphExec_t graph = nullptr;
   bool graph_ok = false;
   double graph_rtol = -1.0, graph_eps = -1.0;
@@ -575,6 +586,46 @@ sph_status enqueue_pass(sph_batch* Bt, const BatchView& B, int cap, cudaStream_t
   return SPH_OK;
 }
 
+// Cuts every scene into tiles of kTileCands[ti] slices (the last one of a scene
+// shorter), uploads the tile table and the descriptors' tile ranges, and sizes
+// each variant's co-resident grid.  The device arrays hold the tiles of the
+// shortest candidate.
+sph_status build_tiles(sph_batch* Bt, int ti, cudaStream_t st) {
+  const int64_t T = kTileCands[ti];
+  std::vector<int32_t> ts, t0, tn;
+  for (int s = 0; s < Bt->nscenes; ++s) {
+    const sph_neighbors* H = Bt->handles[s];
+    SceneDesc& d = Bt->hdesc[s];
+    d.tile_begin = (int32_t)ts.size();
+    for (int64_t sl = 0; sl < H->nslices; sl += T) {
+      ts.push_back(s);
+      t0.push_back((int32_t)sl);
+      tn.push_back((int32_t)((H->nslices - sl) < T ? (H->nslices - sl) : T));
+    }
+    d.tile_end = (int32_t)ts.size();
+  }
+  if ((int64_t)ts.size() > (int64_t)Bt->tile_scene.n) {
+    set_error("sph_batch: tile table larger than its allocation");
+    return SPH_ERR_INVALID;
+  }
+  Bt->ntiles = (int32_t)ts.size();
+  Bt->tile = ti;
+  SPH_TRY_CUDA(cudaMemcpyAsync(Bt->tile_scene.p, ts.data(), ts.size() * 4, cudaMemcpyHostToDevice, st));
+  SPH_TRY_CUDA(cudaMemcpyAsync(Bt->tile_slice0.p, t0.data(), t0.size() * 4, cudaMemcpyHostToDevice, st));
+  SPH_TRY_CUDA(cudaMemcpyAsync(Bt->tile_nsl.p, tn.data(), tn.size() * 4, cudaMemcpyHostToDevice, st));
+  SPH_TRY_CUDA(cudaMemcpyAsync(Bt->desc.p, Bt->hdesc.data(), Bt->nscenes * sizeof(SceneDesc), cudaMemcpyHostToDevice,
+                               st));
+  // pageable sources: the copies above complete before the host vectors go
+  SPH_TRY_CUDA(cudaStreamSynchronize(st));
+  for (int v = 0; v < kPassVariants; ++v) {
+    int g = Bt->num_sms * (Bt->occ[v] > 0 ? Bt->occ[v] : 1);
+    if (g > Bt->ntiles) g = Bt->ntiles;
+    Bt->grids[v] = g;
+  }
+  Bt->grid = Bt->grids[0];
+  return SPH_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -594,9 +645,8 @@ sph_status sph_batch_create(sph_neighbors* const* handles, const sph_visc_params
     return s;
   };
   Bt->nscenes = nscenes;
-  std::vector<SceneDesc> hd(nscenes);
-  std::vector<int32_t> ts, t0, tn;
-  int64_t rows = 0;
+  Bt->hdesc.assign(nscenes, SceneDesc{});
+  int64_t rows = 0, max_tiles = 0;
   for (int s = 0; s < nscenes; ++s) {
     sph_neighbors* H = handles[s];
     if (!H) {
@@ -610,7 +660,7 @@ sph_status sph_batch_create(sph_neighbors* const* handles, const sph_visc_params
     Bt->params.push_back(params[s]);
     Bt->row_off.push_back(rows);
     Bt->rs_version.push_back(H->rs_version);
-    SceneDesc d{};
+    SceneDesc& d = Bt->hdesc[s];
     d.op = op_view(H);
     d.op_lo = H->op_lo.p;
     d.D64 = H->D64.p;
@@ -620,18 +670,10 @@ sph_status sph_batch_create(sph_neighbors* const* handles, const sph_visc_params
     }
     d.row_off = rows;
     d.n = H->n;
-    d.tile_begin = (int32_t)ts.size();
-    for (int64_t sl = 0; sl < H->nslices; sl += kTileSlices) {
-      ts.push_back(s);
-      t0.push_back((int32_t)sl);
-      tn.push_back((int32_t)((H->nslices - sl) < kTileSlices ? (H->nslices - sl) : kTileSlices));
-    }
-    d.tile_end = (int32_t)ts.size();
-    hd[s] = d;
+    max_tiles += (H->nslices + kTileCands[0] - 1) / kTileCands[0];
     rows += H->n_pad;
   }
   Bt->nrows = rows;
-  Bt->ntiles = (int32_t)ts.size();
   if (cudaGetDevice(&Bt->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&Bt->num_sms, cudaDevAttrMultiProcessorCount, Bt->device) != cudaSuccess) {
     set_error("sph_batch_create: no CUDA device");
@@ -643,13 +685,13 @@ sph_status sph_batch_create(sph_neighbors* const* handles, const sph_visc_params
     if (s_ != SPH_OK) return fail(s_); \
   } while (0)
   BTRY(Bt->desc.alloc(nscenes));
-  BTRY(Bt->tile_scene.alloc(Bt->ntiles));
-  BTRY(Bt->tile_slice0.alloc(Bt->ntiles));
-  BTRY(Bt->tile_nsl.alloc(Bt->ntiles));
+  BTRY(Bt->tile_scene.alloc(max_tiles));
+  BTRY(Bt->tile_slice0.alloc(max_tiles));
+  BTRY(Bt->tile_nsl.alloc(max_tiles));
   BTRY(Bt->vec.alloc(9 * rows));
   BTRY(Bt->dvec.alloc(12 * rows));   // x64, b64, r64, saved x0
   BTRY(Bt->S.alloc(nscenes));
-  BTRY(Bt->partials.alloc((size_t)Bt->ntiles * kMaxDots));
+  BTRY(Bt->partials.alloc((size_t)max_tiles * kMaxDots));
   BTRY(Bt->rr64.alloc(3 * nscenes));
   BTRY(Bt->scene_cnt.alloc(nscenes));
   BTRY(Bt->iters.alloc(nscenes));
@@ -660,13 +702,8 @@ sph_status sph_batch_create(sph_neighbors* const* handles, const sph_visc_params
     set_error("sph_batch_create: pinned allocation failed");
     return fail(SPH_ERR_NOMEM);
   }
-  if (cudaMemcpyAsync(Bt->desc.p, hd.data(), nscenes * sizeof(SceneDesc), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(Bt->tile_scene.p, ts.data(), ts.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(Bt->tile_slice0.p, t0.data(), t0.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(Bt->tile_nsl.p, tn.data(), tn.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(Bt->scene_cnt.p, 0, nscenes * sizeof(unsigned int), st) != cudaSuccess ||
-      cudaMemsetAsync(Bt->ctrl.p, 0, sizeof(BatchCtrl), st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess) {
+  if (cudaMemsetAsync(Bt->scene_cnt.p, 0, nscenes * sizeof(unsigned int), st) != cudaSuccess ||
+      cudaMemsetAsync(Bt->ctrl.p, 0, sizeof(BatchCtrl), st) != cudaSuccess) {
     set_error("sph_batch_create: upload failed");
     return fail(SPH_ERR_CUDA);
   }
@@ -674,11 +711,9 @@ sph_status sph_batch_create(sph_neighbors* const* handles, const sph_visc_params
   for (int v = 0; v < kPassVariants; ++v) {
     int o = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, (const void*)pass_kernel(v), pass_block(v), 0);
-    int g = Bt->num_sms * (o > 0 ? o : 1);
-    if (g > Bt->ntiles) g = Bt->ntiles;
-    Bt->grids[v] = g;
+    Bt->occ[v] = o;
   }
-  Bt->grid = Bt->grids[0];
+  BTRY(build_tiles(Bt, kTileDefault, st));
   *out = Bt;
   return SPH_OK;
 #undef BTRY
@@ -749,62 +784,94 @@ sph_status sph_batch_solve(sph_batch* Bt, const sph_solve_opts* O, const double*
   SPH_TRY_CUDA(cudaGetLastError());
   // per-scene ||b||^2 into the descriptors, counters and reports cleared
   std::vector<double> rr(3 * S);
-  std::vector<SceneDesc> hd(S);
   SPH_TRY_CUDA(cudaMemcpyAsync(rr.data(), Bt->rr64.p, 3 * S * sizeof(double), cudaMemcpyDeviceToHost, st));
-  SPH_TRY_CUDA(cudaMemcpyAsync(hd.data(), Bt->desc.p, S * sizeof(SceneDesc), cudaMemcpyDeviceToHost, st));
   SPH_TRY_CUDA(cudaStreamSynchronize(st));
   std::vector<double> bb(S), bbc(3 * S);
   for (int s = 0; s < S; ++s) {
     for (int c = 0; c < 3; ++c) bbc[3 * s + c] = rr[3 * s + c];
     bb[s] = rr[3 * s] + rr[3 * s + 1] + rr[3 * s + 2];
-    hd[s].bb = bb[s];
-    hd[s].maxit = maxit;
+    Bt->hdesc[s].bb = bb[s];
+    Bt->hdesc[s].maxit = maxit;
   }
-  SPH_TRY_CUDA(cudaMemcpyAsync(Bt->desc.p, hd.data(), S * sizeof(SceneDesc), cudaMemcpyHostToDevice, st));
+  SPH_TRY_CUDA(cudaMemcpyAsync(Bt->desc.p, Bt->hdesc.data(), S * sizeof(SceneDesc), cudaMemcpyHostToDevice, st));
+  // pageable source: complete before the host copy can change
+  SPH_TRY_CUDA(cudaStreamSynchronize(st));
   SPH_TRY_CUDA(cudaMemsetAsync(Bt->iters.p, 0, S * sizeof(int32_t), st));
   SPH_TRY_CUDA(cudaMemsetAsync(Bt->passes.p, 0, S * sizeof(int32_t), st));
   SPH_TRY_CUDA(cudaMemsetAsync(Bt->stalled.p, 0, 3 * S * sizeof(int32_t), st));
   SPH_TRY_CUDA(cudaMemsetAsync(Bt->ctrl.p, 0, sizeof(BatchCtrl), st));
-  const BatchView B = batch_view(Bt, rtol, eps);
+  BatchView B = batch_view(Bt, rtol, eps);
   const int cap = maxit;
 
-  // autotune the persistent kernel once over its row-loop forms and block sizes:
-  // one pass per variant from the same start, timed with events, keeping the fastest
+  // autotune the persistent kernel once: first its row-loop form and block size
+  // at the default tile length, then the tile length for that variant; each
+  // candidate runs one pass of at most 16 iterations from the same start, timed
+  // with events, and the fastest is kept
   if (Bt->variant < 0) {
     cudaEvent_t e0, e1;
     SPH_TRY_CUDA(cudaEventCreate(&e0));
     SPH_TRY_CUDA(cudaEventCreate(&e1));
     double* x0save = Bt->dvec.p + 9 * N;
     SPH_TRY_CUDA(cudaMemcpyAsync(x0save, Bt->dvec.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    float best = 1e30f;
-    int bestv = 0;
-    for (int v = 0; v < kPassVariants; ++v) {
-      Bt->variant = v;
+    auto time_pass = [&](float& ms) -> sph_status {
       SPH_TRY_CUDA(cudaMemcpyAsync(Bt->dvec.p, x0save, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
       SPH_TRY_CUDA(cudaMemsetAsync(Bt->iters.p, 0, S * sizeof(int32_t), st));
       SPH_TRY_CUDA(cudaMemsetAsync(Bt->ctrl.p, 0, sizeof(BatchCtrl), st));
-      cudaEventRecord(e0, st);
+      SPH_TRY_CUDA(cudaEventRecord(e0, st));
       SPH_TRY(enqueue_pass(Bt, B, 16, st));
-      cudaEventRecord(e1, st);
+      SPH_TRY_CUDA(cudaEventRecord(e1, st));
       SPH_TRY_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      ms = 0.f;
+      SPH_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
       SPH_TRY_CUDA(cudaMemcpy(Bt->host_ctrl, Bt->ctrl.p, sizeof(BatchCtrl), cudaMemcpyDeviceToHost));
       if (Bt->host_ctrl->error) {
         set_error("sph_batch_solve: a grid barrier timed out (autotune)");
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         return SPH_ERR_TIMEOUT;
       }
+      return SPH_OK;
+    };
+    sph_status ts = SPH_OK;
+    float best = 1e30f;
+    int bestv = 0;
+    for (int v = 0; v < kPassVariants && ts == SPH_OK; ++v) {
+      Bt->variant = v;
+      float ms = 0.f;
+      ts = time_pass(ms);
       Bt->tune_ms[v] = ms;
       if (ms < best) {
         best = ms;
         bestv = v;
       }
     }
+    Bt->variant = bestv;
+    int bestt = Bt->tile;
+    for (int ti = 0; ti < 3 && ts == SPH_OK && !Bt->tile_fixed; ++ti) {
+      if (ti == kTileDefault) {
+        Bt->tile_ms[ti] = best;
+        continue;
+      }
+      ts = build_tiles(Bt, ti, st);
+      if (ts != SPH_OK) break;
+      B = batch_view(Bt, rtol, eps);
+      float ms = 0.f;
+      ts = time_pass(ms);
+      Bt->tile_ms[ti] = ms;
+      // the tuning pass has every scene active; a whole solve ends with a few
+      // large scenes alone, where long tiles leave blocks idle: leave the
+      // default only for a clear gain
+      if (ms < kTileMargin * best) {
+        best = ms;
+        bestt = ti;
+      }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    Bt->variant = bestv;
+    if (ts != SPH_OK) {
+      Bt->variant = -1;
+      return ts;
+    }
+    SPH_TRY(build_tiles(Bt, bestt, st));
+    B = batch_view(Bt, rtol, eps);
     // restore x0 and the reports
     SPH_TRY_CUDA(cudaMemcpyAsync(Bt->dvec.p, x0save, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     SPH_TRY_CUDA(cudaMemsetAsync(Bt->iters.p, 0, S * sizeof(int32_t), st));
@@ -901,6 +968,46 @@ sph_status sph_batch_info(const sph_batch* Bt, int32_t* variant, int32_t* graph,
   if (grid) *grid = Bt->grids[Bt->variant < 0 ? 0 : Bt->variant];
   if (tune_ms4)
     for (int v = 0; v < kPassVariants; ++v) tune_ms4[v] = Bt->tune_ms[v];
+  return SPH_OK;
+}
+
+sph_status sph_batch_set_tile(sph_batch* Bt, int32_t tile_slices, void* stream) {
+  clear_error();
+  if (!Bt) {
+    set_error("sph_batch_set_tile: null batch");
+    return SPH_ERR_INVALID;
+  }
+  int ti = -1;
+  for (int i = 0; i < 3; ++i)
+    if (kTileCands[i] == tile_slices) ti = i;
+  if (ti < 0) {
+    set_error("sph_batch_set_tile: tile length %d is not one of %d, %d, %d", tile_slices, kTileCands[0],
+              kTileCands[1], kTileCands[2]);
+    return SPH_ERR_INVALID;
+  }
+  SPH_TRY(build_tiles(Bt, ti, reinterpret_cast<cudaStream_t>(stream)));
+  Bt->tile_fixed = true;
+  if (Bt->graph) {   // the captured pass holds the old tile count
+    cudaGraphExecDestroy(Bt->graph);
+    Bt->graph = nullptr;
+    Bt->graph_ok = false;
+  }
+  return SPH_OK;
+}
+
+sph_status sph_batch_tiles(const sph_batch* Bt, int32_t* tile_slices, int32_t* ntiles, int32_t* candidates,
+                           float* tune_ms) {
+  clear_error();
+  if (!Bt) {
+    set_error("sph_batch_tiles: null batch");
+    return SPH_ERR_INVALID;
+  }
+  if (tile_slices) *tile_slices = kTileCands[Bt->tile];
+  if (ntiles) *ntiles = Bt->ntiles;
+  for (int i = 0; i < 3; ++i) {
+    if (candidates) candidates[i] = kTileCands[i];
+    if (tune_ms) tune_ms[i] = Bt->tile_ms[i];
+  }
   return SPH_OK;
 }
 

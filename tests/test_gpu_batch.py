@@ -31,6 +31,12 @@ def test_batch_matches_oracle_per_scene():
     assert st == 0, reps
     info = batch.info()
     assert 0 <= info["variant"] < 8 and info["grid"] > 0 and len(info["tune_ms"]) == 8
+    # the tuned tile length is one of the candidates, timed for each, and the tile
+    # table covers every scene's slices
+    assert info["tile_candidates"] == [16, 32, 64] and info["tile_slices"] in info["tile_candidates"]
+    assert all(t > 0 for t in info["tile_tune_ms"])
+    nsl = [-(-nb.info()[0] // 32) for nb in nbs]
+    assert info["ntiles"] == sum(-(-k // info["tile_slices"]) for k in nsl)
     for s, x, rep in zip(ens, xs, reps):
         off, idx, A = oracle_system(s)
         xg = x.cpu().numpy()
@@ -72,3 +78,31 @@ def test_batch_scene_already_converged_and_zero_rhs():
     assert reps[0]["iters"] == 0 and reps[1]["iters"] == 0
     np.testing.assert_array_equal(xs[1].cpu().numpy(), 0.0)
     batch.close()
+
+
+@pytest.mark.parametrize("tile", [16, 32, 64])
+def test_batch_each_tile_length_matches_oracle(tile):
+    """A tile length fixed by sph_batch_set_tile (the tuner then keeps it): every scene
+    still reaches the 1e-6 true residual the oracle computes, and the batch reports it."""
+    torch = torch_cuda()
+    from paper_2206_14780_gb300 import binding
+
+    ens = _small_ensemble()
+    nbs = [lib_build(s)[0] for s in ens]
+    batch = binding.Batch(nbs, [params_for(s) for s in ens])
+    batch.set_tile(tile)
+    bs = [torch.from_numpy(s.b).cuda() for s in ens]
+    xs = [torch.from_numpy(s.x0).cuda() for s in ens]
+    st, reps = batch.solve(binding.solve_opts(), bs, xs)
+    assert st == 0, reps
+    info = batch.info()
+    assert info["tile_slices"] == tile
+    for s, x, rep in zip(ens, xs, reps):
+        off, idx, A = oracle_system(s)
+        res, _ = oop.true_residual(A, x.cpu().numpy(), s.b)
+        assert rep["status"] == 0 and res <= 1e-6, (s.name, tile, res, rep)
+    lib = binding.load()
+    assert lib.sph_batch_set_tile(batch.handle, 24, None) == 1          # not a candidate: invalid
+    assert batch.info()["tile_slices"] == tile
+    batch.close()
+
