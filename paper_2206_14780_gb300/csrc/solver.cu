@@ -905,10 +905,20 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
   // iterations launched past a pass's convergence exit at once but still cost a
   // launch each.  Passes of one system take similar iteration counts, so the
   // first chunk of a pass runs to just short of the same pass of the last solve
-  // (or of the previous pass), then chunks of 4 follow; without a prediction the
-  // chunks double from `chunk`.
+  // with the same dt (or of the previous pass), then chunks of 4 follow; without
+  // a prediction the chunks double from `chunk`.
   int prev_pass = 0;
   int new_len[sph_neighbors::kPassHist] = {};
+  int slot = H->pass_dt[0] == P->dt ? 0 : (H->pass_dt[1] == P->dt ? 1 : -1);
+  if (slot < 0) {   // a new time step: take the slot used longest ago, empty
+    slot = H->pass_slot_next;
+    H->pass_slot_next ^= 1;
+    H->pass_dt[slot] = P->dt;
+    for (int k = 0; k < sph_neighbors::kPassHist; ++k) H->pass_len[slot][k] = 0;
+  } else {
+    H->pass_slot_next = slot ^ 1;
+  }
+  const int* hist = H->pass_len[slot];
   double rr[3] = {0, 0, 0};
   sph_status status = SPH_NOT_CONVERGED;
   // r64 after a pass comes from the update r64 -= A d (rr_full = false); the
@@ -954,8 +964,12 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
     }
     SPH_TRY_CUDA(cudaGetLastError());
     if (merged && !cg) SPH_LAUNCH(k_p_update, grid_rows, kBlock, 0, st)(np, V, S);
-    const int pred = (passes < sph_neighbors::kPassHist && H->pass_len[passes] > 0) ? H->pass_len[passes] : prev_pass;
-    int chunk = pred > chunk0 + 2 ? pred - 2 : chunk0;
+    const int pred = (passes < sph_neighbors::kPassHist && hist[passes] > 0) ? hist[passes] : prev_pass;
+    // a long pass: stop two short of the prediction (the last iterations then
+    // come in chunks of 4); a short one (a few iterations, as in the small
+    // systems of a time step): launch exactly the prediction, since a default
+    // chunk of 8 would mostly launch iterations that exit at once
+    int chunk = pred > chunk0 + 2 ? pred - 2 : (pred > 0 ? pred : chunk0);
     int iter_seen = 0;
     for (;;) {
       cudaError_t le = cudaSuccess;
@@ -991,7 +1005,7 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
         return SPH_ERR_TIMEOUT;
       }
       if (H->host_scal->done) break;
-      chunk = pred > 0 ? 4 : (chunk < 64 ? chunk * 2 : chunk);
+      chunk = pred > 0 ? (pred <= 2 ? 2 : 4) : (chunk < 64 ? chunk * 2 : chunk);
     }
     const SolverScalars& hs = *H->host_scal;
     total_iters += hs.iter;
@@ -1016,7 +1030,7 @@ sph_status solve_mixed(sph_neighbors* H, const sph_visc_params* P, const sph_sol
     rr_full = false;
   }
   if (!rr_full && status != SPH_ERR_NONFINITE) SPH_TRY(true_residual(H, st, rr));
-  for (int k = 0; k < sph_neighbors::kPassHist; ++k) H->pass_len[k] = new_len[k];
+  for (int k = 0; k < sph_neighbors::kPassHist; ++k) H->pass_len[slot][k] = new_len[k];
   SPH_LAUNCH(k_scatter_d3, grid_for(H, H->n), kBlock, 0, st)(H->x64.p, H->perm.p, H->n, x);
   SPH_TRY_CUDA(cudaGetLastError());
   SPH_TRY_CUDA(cudaStreamSynchronize(st));

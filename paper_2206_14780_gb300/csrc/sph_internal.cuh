@@ -250,9 +250,13 @@ struct sph_neighbors {
   bool tuned = false;
   int64_t tuned_n_pad = 0;
   int force_form = -1;               // sph_solve_opts.apply_form - 1 for the current solve
-  // iterations of each inner pass of the last mixed solve (sizes the launch chunks)
+  // iterations of each inner pass of the last mixed solve with each of two time
+  // steps (sizes the launch chunks; a time step alternates the predictor's dt/2
+  // and the corrector's dt on one handle)
   static constexpr int kPassHist = 16;
-  int pass_len[kPassHist] = {};
+  int pass_len[2][kPassHist] = {};
+  double pass_dt[2] = {-1.0, -1.0};
+  int pass_slot_next = 0;
   int force_grid = 0;
   sph::DBuf<sph::SolverScalars> scal_tune;
 
