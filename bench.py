@@ -51,6 +51,8 @@ def parse(argv=None):
     ap.add_argument("--no-poiseuille", action="store_true")
     ap.add_argument("--poiseuille-only", default=None,
                     help="comma-separated 1/dp list (e.g. 16,32,64): only the Poiseuille runs, one JSON line")
+    ap.add_argument("--poiseuille-cases", default=None,
+                    help="with --poiseuille-only: comma-separated configurations (default: all)")
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-shard", action="store_true")
     ap.add_argument("--ensemble-only", action="store_true")
@@ -486,7 +488,9 @@ def run_sphvisc(args):
         gaussian = run_gaussian(dev, n=args.box_side)
     poiseuille = None
     if world == 1 and not args.no_poiseuille:
-        poiseuille = run_poiseuille(dev)
+        # the default run leaves out the h = 2.5 dp Wendland runs (about 500 neighbours on
+        # a few thousand particles, 28 s); --poiseuille-only runs them too
+        poiseuille = run_poiseuille(dev, cases=[c for c in POISEUILLE_PAPER if "wendland25" not in c])
     cg = shard = None
     if world == 1 and not args.no_cg:
         cg = run_cg(dev)
@@ -893,6 +897,11 @@ POISEUILLE_PAPER = {
                                      64: _pp(7.339e-4, 7.631e-4, 27000.0)},
     "papanastasiou_wendland_dynamic": {16: _pp(3.009e-3, 3.232e-3, 74.0), 32: _pp(1.138e-3, 1.196e-3, 1000.0),
                                        64: _pp(3.715e-4, 6.833e-4, 20000.0)},
+    # Wendland at h = 2.5 dp (Sec. 5.3, Table tab:newton-error-wendland-25; no runtimes printed)
+    "newton_wendland25_dummy": {16: _pp(6.648e-4, 7.797e-4, None), 32: _pp(5.095e-5, 1.502e-4, None),
+                                64: _pp(5.941e-5, 6.696e-5, None)},
+    "newton_wendland25_dynamic": {16: _pp(5.436e-3, 5.625e-3, None), 32: _pp(2.588e-3, 2.673e-3, None),
+                                  64: _pp(1.300e-3, 1.322e-3, None)},
     "papanastasiou_gaussian_dummy": {16: _pp(7.027e-3, 7.227e-3, 180.0), 32: _pp(2.928e-3, 2.982e-3, 2600.0),
                                      64: _pp(1.336e-3, 1.360e-3, 61000.0)},
     "papanastasiou_gaussian_dynamic": {16: _pp(4.569e-3, 4.769e-3, 130.0), 32: _pp(1.720e-3, 1.790e-3, 1700.0),
@@ -905,7 +914,8 @@ def run_poiseuille_case(dev, case, inv_dp=16, t_end=10.0):
     from rest to the viscous relaxation time t = 10 s: L = 1 m, g = 0.05 m/s^2,
     rho0 = 1 kg/m^3, c0 = 6.32 m/s, h = 1.3 dp, dp = 1/inv_dp, dt = 0.3 h / c0 (the
     sound-speed limit of Tables tab:newton-times and tab:papa-times), the wall layout of
-    Sec. 5.2 for the boundary model.  Newtonian: mu = 0.1 Pa s, profile
+    Sec. 5.2 for the boundary model; "wendland25": the Wendland kernel at h = 2.5 dp
+    (Table tab:newton-error-wendland-25).  Newtonian: mu = 0.1 Pa s, profile
     u(z) = rho0 g / (2 mu) (L^2/4 - z^2).  Papanastasiou (Sec. 5.4): mu0 = 0.1 Pa s,
     tau0 = 0.0125 Pa, m = 1000 s, the viscosity recomputed from the velocities each
     step, compared with the non-regularised Bingham profile (plug |z| < tau0 / (rho0 g)).
@@ -918,9 +928,10 @@ def run_poiseuille_case(dev, case, inv_dp=16, t_end=10.0):
 
     rheo, kname, bname = case.split("_")
     kern = scenes.KERNEL_GAUSSIAN if kname == "gaussian" else scenes.KERNEL_WENDLAND
+    h_factor = 2.5 if kname == "wendland25" else 1.3
     bc = scenes.BC_DYNAMIC if bname == "dynamic" else scenes.BC_DUMMY
     g, mu0, tau0, m, c0 = 0.05, 0.1, 0.0125, 1000.0, 6.32
-    s = scenes.poiseuille(bc, kern, inv_dp=inv_dp)
+    s = scenes.poiseuille(bc, kern, inv_dp=inv_dp, h_factor=h_factor)
     L = s.meta["L"]
     dt = 0.3 * s.h / c0
     steps = int(np.ceil(t_end / dt))
@@ -928,7 +939,7 @@ def run_poiseuille_case(dev, case, inv_dp=16, t_end=10.0):
     st = binding.Stepper(t["pos"], t["vel"], t["rho"], t["mu"], t["ptype"], s.lo, s.hi, s.periodic, s.h,
                          kernel=kern)
     prm = binding.step_params(dt, 1.0, c0, 7.0, (g, 0.0, 0.0), s.boundary, s.mean,
-                              max_neighbors=512 if kern == scenes.KERNEL_GAUSSIAN else 128,
+                              max_neighbors={"wendland": 128, "gaussian": 512}.get(kname, 640),
                               rheology=(tau0, mu0, m) if rheo == "papanastasiou" else None)
     opts = binding.solve_opts(rtol=1e-8)
     stream = torch.cuda.current_stream(dev)
@@ -965,15 +976,15 @@ def run_poiseuille_case(dev, case, inv_dp=16, t_end=10.0):
     return out
 
 
-def run_poiseuille(dev, resolutions=(16,)):
-    """Every configuration of POISEUILLE_PAPER at each 1/dp in resolutions, one full run
-    each; with more than one resolution, the convergence rates log2(e_coarse / e_fine)
-    of l1 and l2 between consecutive ones (the paper prints its own rates beside its
-    errors)."""
+def run_poiseuille(dev, resolutions=(16,), cases=None):
+    """Each configuration of POISEUILLE_PAPER (all of them unless `cases` names some) at
+    each 1/dp in resolutions, one full run each; with more than one resolution, the
+    convergence rates log2(e_coarse / e_fine) of l1 and l2 between consecutive ones (the
+    paper prints its own rates beside its errors)."""
     import math
 
     out = {}
-    for case in POISEUILLE_PAPER:
+    for case in (cases or POISEUILLE_PAPER):
         runs = {r: run_poiseuille_case(dev, case, r) for r in resolutions}
         if len(resolutions) == 1:
             out[case] = runs[resolutions[0]]
@@ -1712,7 +1723,8 @@ def main():
         import torch
 
         res = tuple(int(r) for r in args.poiseuille_only.split(","))
-        print(json.dumps(run_poiseuille(torch.device("cuda", 0), res)))
+        cases = args.poiseuille_cases.split(",") if args.poiseuille_cases else None
+        print(json.dumps(run_poiseuille(torch.device("cuda", 0), res, cases)))
         return
     if args.precision_only:
         out = run_precision()

@@ -177,7 +177,7 @@ def _assemble(name, fluid_p, wall_p, wall_u, dx, rho0, mu_fluid, dt, lo, hi, per
 def couette(seed: int = 0, nx: int = 20, ny: int = 10, nz: int = 10, dx: float = 0.01,
             rho0: float = 1000.0, nu: float = 1.0, dt: float = 1e-4, U: float = 1.0,
             noise: float = 0.01, layers: int = 3, boundary: int = BC_DUMMY,
-            kernel: int = KERNEL_WENDLAND) -> Scene:
+            kernel: int = KERNEL_WENDLAND, h_factor: float = 1.3) -> Scene:
     """Plane Couette channel: fluid between two walls normal to y, periodic in x, z.
 
     Fluid at y = (j + 1/2) dx, j < ny (channel height H = ny dx); wall layers at
@@ -204,28 +204,33 @@ def couette(seed: int = 0, nx: int = 20, ny: int = 10, nz: int = 10, dx: float =
     lo = (0.0, -layers * dx, 0.0)
     hi = (nx * dx, H + layers * dx, nz * dx)
     return _assemble("couette", fluid, walls, wall_u, dx, rho0, rho0 * nu, dt, lo, hi, (1, 0, 1),
-                     v, boundary=boundary, meta=dict(seed=seed, U=U, H=H, nu=nu), kernel=kernel)
+                     v, boundary=boundary, meta=dict(seed=seed, U=U, H=H, nu=nu), kernel=kernel,
+                     h_factor=h_factor)
 
 
 def poiseuille(boundary: int = BC_DUMMY, kernel: int = KERNEL_WENDLAND, inv_dp: int = 16,
-               L: float = 1.0, mu: float = 0.1, dt: float = 1e-2) -> Scene:
+               L: float = 1.0, mu: float = 0.1, dt: float = 1e-2, h_factor: float = 1.3) -> Scene:
     """Plane Poiseuille channel of width L at rest, laid out as Sec. 5.2 does for each
-    boundary model (rho0 = 1 kg/m^3).
+    boundary model (rho0 = 1 kg/m^3, h = h_factor dp).
 
     Dummy walls: the analytical walls lie half a spacing outside the fluid, so
     1/dp fluid layers fill the channel.  Dynamic walls: the first wall layer sits on
     the analytical wall, so 1/dp - 1 fluid layers sit between the two first wall
-    layers, one of them on the centre line.  Wendland takes 3 wall layers, the
-    truncated Gaussian 4.  meta: L and "centre" (the y of the centre line; the
-    analytical profile is a function of y - centre).  The periodic x and z extent
-    (8 spacings for Wendland, 12 for the Gaussian) is twice the kernel's support.
+    layers, one of them on the centre line.  Wall layers: as many as the kernel's
+    support reaches (ceil(support / dp): 3 for Wendland at h = 1.3 dp, 4 for the
+    truncated Gaussian, 5 for Wendland at h = 2.5 dp).  meta: L and "centre" (the y
+    of the centre line; the analytical profile is a function of y - centre).  The
+    periodic x and z extent is at least three supports, rounded up to a multiple of
+    4 spacings (8, 12 and 16).
     """
     dx = L / inv_dp
     gauss = kernel == KERNEL_GAUSSIAN
+    support = (3.0 if gauss else 2.0) * h_factor        # in spacings
     ny = inv_dp if boundary == BC_DUMMY else inv_dp - 1
-    nxz = 12 if gauss else 8
+    layers = int(math.ceil(support - 1e-9))
+    nxz = 4 * int(math.ceil(3.0 * support / 4.0 - 1e-9))   # at least three neighbour-grid cells per period
     s = couette(0, nx=nxz, ny=ny, nz=nxz, dx=dx, rho0=1.0, nu=mu, dt=dt, U=0.0, noise=0.0,
-                layers=4 if gauss else 3, boundary=boundary, kernel=kernel)
+                layers=layers, boundary=boundary, kernel=kernel, h_factor=h_factor)
     s.name = "poiseuille"
     s.meta.update(L=L, centre=0.5 * ny * dx)
     return s

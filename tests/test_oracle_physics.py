@@ -50,9 +50,10 @@ def test_couette_dynamic_linear_profile():
 
 
 def _poiseuille_errors(kernel, boundary, inv_dp, f=1.0, g=0.05, mu=0.1):
+    # "wendland25": the Wendland kernel at the larger smoothing factor h = 2.5 dp
     s = scenes.poiseuille(scenes.BC_DYNAMIC if boundary == "dynamic" else scenes.BC_DUMMY,
                           scenes.KERNEL_GAUSSIAN if kernel == "gaussian" else scenes.KERNEL_WENDLAND,
-                          inv_dp=inv_dp, mu=mu, dt=100.0)
+                          inv_dp=inv_dp, mu=mu, dt=100.0, h_factor=2.5 if kernel == "wendland25" else 1.3)
     L = s.meta["L"]
     v = _steady(s, g=(g, 0.0, 0.0), steps=60)
     fl = s.ptype == scenes.FLUID
@@ -72,12 +73,14 @@ def _gold(name):
 
 
 @pytest.mark.parametrize("inv_dp", [16, 32])
-@pytest.mark.parametrize("kernel", ["wendland", "gaussian"])
+@pytest.mark.parametrize("kernel", ["wendland", "gaussian", "wendland25"])
 @pytest.mark.parametrize("boundary", ["dummy", "dynamic"])
 def test_poiseuille_matches_paper_error_table(kernel, boundary, inv_dp):
-    """The dp = 1/16 and 1/32 entries of the paper's Newtonian error table (Sec. 5.3), each
-    with the wall layout of Sec. 5.2 for its boundary model (dynamic: the first wall layer
-    on the analytical wall; dummy: half a spacing inside it)."""
+    """The dp = 1/16 and 1/32 entries of the paper's Newtonian error tables (Sec. 5.3: both
+    kernels at h = 1.3 dp, and the Wendland kernel at h = 2.5 dp of Table
+    tab:newton-error-wendland-25), each with the wall layout of Sec. 5.2 for its boundary
+    model (dynamic: the first wall layer on the analytical wall; dummy: half a spacing
+    inside it)."""
     gold = _gold(f"poiseuille_newton_{kernel}_{boundary}_dp{inv_dp}.txt")
     err = _poiseuille_errors(kernel, boundary, inv_dp)
     if (kernel, boundary, inv_dp) == ("gaussian", "dummy", 32):
