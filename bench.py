@@ -1172,7 +1172,10 @@ def run_ensemble(seed=0, dev=None, scenes_n=64):
                max_true_rel_res_sequential=max(r["true_rel_res"] for r in seq),
                max_true_rel_res_batched=max(r["true_rel_res"] for r in bat), batched_status=st,
                batched_launches=binding.launch_count() - launches0, persistent_variant=info["variant"],
-               graph=info["graph"], persistent_grid=info["grid"], autotune_ms=info["tune_ms"],
+               graph=info["graph"], graph_mode={2: "whole solve: conditional WHILE node over the passes",
+                                                1: "one pass, replayed per pass",
+                                                0: "direct launches"}[info["graph_mode"]],
+               persistent_grid=info["grid"], autotune_ms=info["tune_ms"],
                tile_slices=info["tile_slices"], ntiles=info["ntiles"],
                tile_autotune_ms=dict(zip([str(c) for c in info["tile_candidates"]], info["tile_tune_ms"])))
     batch.close()

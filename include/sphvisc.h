@@ -444,7 +444,9 @@ sph_status sph_batch_solve(sph_batch* batch, const sph_solve_opts* opts, const d
 
 /* The autotuned persistent-kernel variant (0..7: row-loop form v & 3 as in
  * sph_profile_counters, block size 256 (v < 4) or 128 threads), whether the
- * pass runs as a captured graph (1) or as direct launches (0), the tuning
+ * solve runs as one graph launch whose conditional WHILE node repeats the pass
+ * on the device (2), as a captured pass replayed per pass (1) or as direct
+ * launches (0), the tuning
  * times (ms, [8]) and the chosen variant's grid size.  Any pointer may be NULL. */
 sph_status sph_batch_info(const sph_batch* batch, int32_t* variant, int32_t* graph, float* tune_ms,
                           int32_t* grid);

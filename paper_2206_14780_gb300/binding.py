@@ -498,7 +498,8 @@ class Batch:
         ts, nt = ctypes.c_int32(), ctypes.c_int32()
         cand, tms = (ctypes.c_int32 * 3)(), (ctypes.c_float * 3)()
         _check(_lib.sph_batch_tiles(self.handle, ctypes.byref(ts), ctypes.byref(nt), cand, tms))
-        return dict(variant=v.value, graph=bool(g.value), tune_ms=list(t), grid=grid.value, tile_slices=ts.value,
+        return dict(variant=v.value, graph=bool(g.value), graph_mode=g.value, tune_ms=list(t), grid=grid.value,
+                    tile_slices=ts.value,
                     ntiles=nt.value, tile_candidates=list(cand), tile_tune_ms=list(tms))
 
     def close(self):

@@ -10,11 +10,14 @@
 // a scene to arrive (ticket on a per-scene counter) sums that scene's partials
 // in a fixed order and runs the scene's scalar update.
 //
-// One refinement pass is four launches captured once in a CUDA graph and
-// replayed per pass: float64 residual per scene (decides on the device which
-// scenes still exceed rtol), pass initialisation, one persistent cooperative
-// kernel that runs all BiCGSTAB iterations of the active scenes with grid
-// barriers between phases, and x += d.  Converged scenes are skipped tile by
+// One refinement pass is four launches: float64 residual per scene (decides on
+// the device which scenes still exceed rtol), pass initialisation, one
+// persistent cooperative kernel that runs all BiCGSTAB iterations of the active
+// scenes with grid barriers between phases, and x += d.  The whole solve is one
+// CUDA graph launch: the pass sits in the body of a conditional WHILE node whose
+// last kernel decides on the device whether another pass follows (some scene
+// still above rtol, passes left, no barrier timed out); where the driver cannot
+// build that graph, the pass alone is captured and replayed by the host.  Converged scenes are skipped tile by
 // tile, so the grid keeps working on the scenes that remain.  Every grid
 // barrier spins a bounded number of times and reports SPH_ERR_TIMEOUT instead
 // of hanging.
@@ -430,6 +433,13 @@ __global__ void __launch_bounds__(kBlock) kb_add(BatchView B, int64_t nrows) {
   }
 }
 
+// the whole solve as one graph: after each pass, keep looping while some scene was
+// above rtol at the pass's residual, no barrier timed out and passes remain
+__global__ void kb_loop_ctrl(const BatchCtrl* __restrict__ ctrl, cudaGraphConditionalHandle h, int max_passes) {
+  const bool more = ctrl->error == 0 && ctrl->need > 0 && ctrl->passes < max_passes;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 __global__ void kb_gather(const double* __restrict__ src, const int32_t* __restrict__ perm, int64_t n, int64_t n_pad,
                           double* __restrict__ dst) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
@@ -524,6 +534,10 @@ struct sph_batch {
   bool graph_ok = false;
   double graph_rtol = -1.0, graph_eps = -1.0;
   int graph_cap = 0;
+  // every pass of a solve in one graph launch: the pass inside a conditional WHILE node
+  cudaGraphExec_t solve_graph = nullptr;
+  bool solve_graph_tried = false;
+  int solve_graph_passes = 0;
 };
 
 namespace {
@@ -722,6 +736,7 @@ sph_status sph_batch_create(sph_neighbors* const* handles, const sph_visc_params
 sph_status sph_batch_destroy(sph_batch* Bt) {
   if (!Bt) return SPH_OK;
   if (Bt->graph) cudaGraphExecDestroy(Bt->graph);
+  if (Bt->solve_graph) cudaGraphExecDestroy(Bt->solve_graph);
   Bt->desc.release();
   Bt->tile_scene.release();
   Bt->tile_slice0.release();
@@ -880,8 +895,16 @@ sph_status sph_batch_solve(sph_batch* Bt, const sph_solve_opts* O, const double*
     SPH_TRY_CUDA(cudaMemsetAsync(Bt->ctrl.p, 0, sizeof(BatchCtrl), st));
   }
 
-  // capture one refinement pass in a graph (rebuilt when rtol/eps/cap change)
-  if (!Bt->graph || Bt->graph_rtol != rtol || Bt->graph_eps != eps || Bt->graph_cap != cap) {
+  // capture one refinement pass in a graph (rebuilt when rtol/eps/cap change), and the
+  // whole solve as that pass inside a conditional WHILE node
+  if (!Bt->graph || Bt->graph_rtol != rtol || Bt->graph_eps != eps || Bt->graph_cap != cap ||
+      Bt->solve_graph_passes != max_ref + 2) {
+    if (Bt->solve_graph) {
+      cudaGraphExecDestroy(Bt->solve_graph);
+      Bt->solve_graph = nullptr;
+    }
+    Bt->solve_graph_tried = false;
+    Bt->solve_graph_passes = max_ref + 2;
     if (Bt->graph) {
       cudaGraphExecDestroy(Bt->graph);
       Bt->graph = nullptr;
@@ -904,8 +927,53 @@ sph_status sph_batch_solve(sph_batch* Bt, const sph_solve_opts* O, const double*
     Bt->graph_cap = cap;
   }
 
+  if (!Bt->solve_graph_tried) {
+    Bt->solve_graph_tried = true;
+    cudaStream_t cs;
+    SPH_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h{};
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault) == cudaSuccess;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (ok) ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    if (ok) {
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+           cudaSuccess;
+      if (ok) {
+        ok = enqueue_pass(Bt, B, cap, cs) == SPH_OK;
+        kb_loop_ctrl<<<1, 1, 0, cs>>>(Bt->ctrl.p, h, max_ref + 2);
+        ok = cudaGetLastError() == cudaSuccess && ok;
+        cudaGraph_t captured = nullptr;
+        ok = cudaStreamEndCapture(cs, &captured) == cudaSuccess && ok;
+      }
+    }
+    if (ok) ok = cudaGraphInstantiate(&Bt->solve_graph, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
+    if (!ok) Bt->solve_graph = nullptr;
+  }
+
   sph_status status = SPH_NOT_CONVERGED;
-  for (int ref = 0; ref <= max_ref + 1; ++ref) {
+  if (Bt->solve_graph) {
+    SPH_TRY_CUDA(cudaGraphLaunch(Bt->solve_graph, st));
+    SPH_TRY_CUDA(cudaMemcpyAsync(Bt->host_ctrl, Bt->ctrl.p, sizeof(BatchCtrl), cudaMemcpyDeviceToHost, st));
+    SPH_TRY_CUDA(cudaStreamSynchronize(st));
+    note_launches(6 * Bt->host_ctrl->passes);   // per pass: the five pass kernels and the loop test
+    if (Bt->host_ctrl->error) {
+      set_error("sph_batch_solve: a grid barrier timed out");
+      return SPH_ERR_TIMEOUT;
+    }
+    if (Bt->host_ctrl->need == 0) status = SPH_OK;
+  }
+  for (int ref = 0; ref <= max_ref + 1 && !Bt->solve_graph; ++ref) {
     if (Bt->graph_ok) {
       SPH_TRY_CUDA(cudaGraphLaunch(Bt->graph, st));
       note_launches(5);   // kb_split, kb_residual, kb_init, kb_pass, kb_add
@@ -964,7 +1032,7 @@ sph_status sph_batch_info(const sph_batch* Bt, int32_t* variant, int32_t* graph,
     return SPH_ERR_INVALID;
   }
   if (variant) *variant = Bt->variant;
-  if (graph) *graph = Bt->graph_ok ? 1 : 0;
+  if (graph) *graph = Bt->solve_graph ? 2 : (Bt->graph_ok ? 1 : 0);
   if (grid) *grid = Bt->grids[Bt->variant < 0 ? 0 : Bt->variant];
   if (tune_ms4)
     for (int v = 0; v < kPassVariants; ++v) tune_ms4[v] = Bt->tune_ms[v];
@@ -992,6 +1060,11 @@ sph_status sph_batch_set_tile(sph_batch* Bt, int32_t tile_slices, void* stream) 
     Bt->graph = nullptr;
     Bt->graph_ok = false;
   }
+  if (Bt->solve_graph) {
+    cudaGraphExecDestroy(Bt->solve_graph);
+    Bt->solve_graph = nullptr;
+  }
+  Bt->solve_graph_tried = false;
   return SPH_OK;
 }
 

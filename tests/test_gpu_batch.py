@@ -31,6 +31,8 @@ def test_batch_matches_oracle_per_scene():
     assert st == 0, reps
     info = batch.info()
     assert 0 <= info["variant"] < 8 and info["grid"] > 0 and len(info["tune_ms"]) == 8
+    # the whole solve runs as one graph launch (its passes in a conditional WHILE node)
+    assert info["graph_mode"] == 2
     # the tuned tile length is one of the candidates, timed for each, and the tile
     # table covers every scene's slices
     assert info["tile_candidates"] == [16, 32, 64] and info["tile_slices"] in info["tile_candidates"]
